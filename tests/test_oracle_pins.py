@@ -1,0 +1,368 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+Each test checks the oracle against what the paper and the mathematics fix:
+brute-force enumeration, a library connected-components / minimum-spanning-tree
+routine, closed forms of the generators, torch autograd + torch.optim.Adam for
+the optimisation step, an independent numpy parser of the edit stream, and
+the invariants the method guarantees (Sec. 3.1-3.3 of arXiv 2604.18801).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components, minimum_spanning_tree
+
+import oracle
+from paper_2604_18801_gb300 import synth
+
+
+# ----------------------------------------------------------------- helpers
+def np_brute_pairs(P, b, xi, periodic, L=(1.0, 1.0, 1.0)):
+    """All pairs with their class, by brute force in numpy float32 (canonical order of ops)."""
+    P = np.asarray(P, np.float32)
+    n = len(P)
+    i, j = np.triu_indices(n, 1)
+    d = []
+    for a in range(3):
+        x = P[i, a] - P[j, a]
+        if periodic:
+            Lf = np.float32(L[a])
+            h = np.float32(0.5) * Lf
+            x = np.where(x > h, x - Lf, np.where(x < -h, x + Lf, x)).astype(np.float32)
+        d.append(x)
+    d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+    assert d2.dtype == np.float32
+    c = oracle.constants(P, **dict(b=b, xi=xi, periodic=int(periodic), box_hi=L))
+    cls = np.zeros(len(d2), np.uint8)
+    cls[d2 <= np.float32(c["hi2"])] = 3
+    cls[d2 <= np.float32(c["b2"])] = 2
+    cls[d2 <= np.float32(c["lo2"])] = 1
+    keep = cls > 0
+    return i[keep].astype(np.uint32), j[keep].astype(np.uint32), cls[keep], d2[keep]
+
+
+def cc_labels(n, i, j):
+    """Connected components via scipy; label = smallest member id."""
+    g = sp.coo_matrix((np.ones(len(i)), (i, j)), shape=(n, n))
+    _, comp = connected_components(g, directed=False)
+    mins = np.full(comp.max() + 1, n, np.int64)
+    np.minimum.at(mins, comp, np.arange(n))
+    return mins[comp].astype(np.int32)
+
+
+def random_points(n, seed, periodic=True, clumpy=True):
+    rng = np.random.default_rng(seed)
+    if clumpy:
+        c = rng.random((8, 3))
+        P = c[rng.integers(0, 8, n)] + 0.03 * rng.standard_normal((n, 3))
+    else:
+        P = rng.random((n, 3))
+    if periodic:
+        P = np.mod(P, 1.0)
+    P = P.astype(np.float32)
+    if periodic:
+        P = np.minimum(P, np.nextafter(np.float32(1), np.float32(0)))
+    return np.ascontiguousarray(P)
+
+
+# ----------------------------------------------------------------- link predicate
+def test_tie_at_linking_length_is_a_link():
+    # Sec. 2.4: an edge exists iff d <= b.  b = 0.5 and d = 0.5 are exact in float32.
+    P = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [np.nextafter(np.float32(0.5), np.float32(1)), 0.0, 0.0]],
+                 np.float32)
+    kw = dict(b=0.5, xi=0.01, periodic=0, box_hi=(1, 1, 1))
+    i, j, c = oracle.pairs(P, **kw)
+    cls = {(a, b_): k for a, b_, k in zip(i, j, c)}
+    assert cls[(0, 1)] == oracle.CLS_PB            # d == b: linked, potentially broken
+    assert cls[(0, 2)] == oracle.CLS_PC            # d just above b: not linked
+    lab, _, nh = oracle.fof_labels(P, **kw)
+    assert list(lab) == [0, 0, 0] and nh == 1      # 0-1 linked, 1-2 linked (tiny distance)
+
+
+def test_minimum_image_across_the_periodic_boundary():
+    P = np.array([[0.001, 0.5, 0.5], [0.999, 0.5, 0.5]], np.float32)
+    kw = dict(b=0.01, xi=0.0001, periodic=1)
+    i, j, c = oracle.pairs(P, **kw)
+    assert list(zip(i, j)) == [(0, 1)] and c[0] == oracle.CLS_SAFE
+    i, j, c = oracle.pairs(P, **dict(kw, periodic=0))
+    assert len(i) == 0
+
+
+@pytest.mark.parametrize("periodic,clumpy,xi", [(True, True, 0.1), (True, False, 0.5), (False, True, 0.3),
+                                                (False, False, 1.0), (True, True, 0.0)])
+def test_grid_search_equals_brute_force(periodic, clumpy, xi):
+    n = 1500
+    P = random_points(n, seed=11 + int(xi * 10), periodic=periodic, clumpy=clumpy)
+    b = 0.02
+    kw = dict(b=b, xi=xi * b, periodic=int(periodic))
+    gi, gj, gc = oracle.pairs(P, **kw)
+    bi, bj, bc = oracle.pairs(P, brute=True, **kw)
+    ni, nj, nc, _ = np_brute_pairs(P, b, xi * b, periodic)
+    assert len(gi) > 100
+    for a, b_ in ((gi, bi), (gj, bj), (gc, bc), (gi, ni), (gj, nj), (gc, nc)):
+        assert np.array_equal(a, b_)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_fof_labels_equal_library_components(periodic):
+    P = random_points(3000, seed=5, periodic=periodic)
+    b = 0.015
+    kw = dict(b=b, xi=0.2 * b, periodic=int(periodic))
+    lab, safe, nh = oracle.fof_labels(P, **kw)
+    i, j, c, _ = np_brute_pairs(P, b, 0.2 * b, periodic)
+    links = c <= 2
+    ref = cc_labels(len(P), i[links], j[links])
+    assert np.array_equal(lab, ref)
+    assert nh == len(np.unique(ref))
+    s = c == 1
+    assert np.array_equal(safe, cc_labels(len(P), i[s], j[s]))
+
+
+def test_md_clusters_closed_form():
+    # Step 0.8 b < b joins every cluster; gap 1.2 b > b separates clusters: components == clusters.
+    w = synth.md_box(n_clusters=300, eps_over_b=0.3, seed=21)
+    lab, _, nh = oracle.fof_labels(w.orig, **w.params())
+    cl = w.aux["cluster_of"]
+    assert nh == 300
+    mins = np.full(300, w.n)
+    np.minimum.at(mins, cl, np.arange(w.n))
+    assert np.array_equal(lab, mins[cl])
+
+
+# ----------------------------------------------------------------- selection modes
+def _modes(P, **kw):
+    out = {}
+    for mode in (0, 1, 2):
+        ai, aj, al, nv = oracle.select(P, **dict(kw, mode=mode))
+        out[mode] = (ai, aj, al, nv)
+    return out
+
+
+def test_mode_hierarchy_and_definitions():
+    w = synth.tiny_cosmo(seed=3, n=3000)
+    kw = w.params()
+    P = w.orig
+    i, j, c, d2 = np_brute_pairs(P, w.b, w.xi, True)
+    V = set(zip(i[c >= 2], j[c >= 2]))
+    m = _modes(P, **kw)
+    A = {k: set(zip(v[0], v[1])) for k, v in m.items()}
+    # VP: A = V (Sec. 3.2, Mode 1)
+    assert A[0] == V and m[0][3] == len(V)
+    # SC: V pairs joining different safe components (Mode 2)
+    safe = cc_labels(len(P), i[c == 1], j[c == 1])
+    assert A[1] == {(a, b_) for a, b_ in V if safe[a] != safe[b_]}
+    # HF: potentially created pairs across halos + spanning forest of PB links among supernodes (Mode 3)
+    halo = cc_labels(len(P), i[c <= 2], j[c <= 2])
+    pc_cross = {(a, b_) for a, b_, k in zip(i, j, c) if k == 3 and halo[a] != halo[b_]}
+    forest = A[2] - pc_cross
+    assert pc_cross <= A[2]
+    # hierarchy A_HF <= A_SC <= A_VP (Sec. 3.2)
+    assert A[2] <= A[1] <= A[0]
+    # link flags are the original link predicate
+    link_of = {(a, b_): k <= 2 for a, b_, k in zip(i, j, c)}
+    for mode in (0, 1, 2):
+        ai, aj, al, _ = m[mode]
+        assert all(bool(l) == link_of[(a, b_)] for a, b_, l in zip(ai, aj, al))
+    # forest = the minimum spanning forest of the supernode multigraph under key (d2 bits, i, j):
+    pb = [(a, b_, d) for a, b_, k, d in zip(i, j, c, d2) if k == 2 and safe[a] != safe[b_]]
+    keys = sorted((np.float32(d).view(np.uint32), a, b_) for a, b_, d in pb)
+    rank = {(a, b_): r + 1 for r, (_, a, b_) in enumerate(keys)}
+    best = {}
+    for a, b_, _ in pb:
+        u, v = sorted((safe[a], safe[b_]))
+        if (u, v) not in best or rank[(a, b_)] < rank[best[(u, v)]]:
+            best[(u, v)] = (a, b_)
+    nodes = sorted({x for e in best for x in e})
+    idx = {x: t for t, x in enumerate(nodes)}
+    rows = [idx[u] for u, v in best]
+    cols = [idx[v] for u, v in best]
+    vals = [float(rank[e]) for e in best.values()]
+    mst = minimum_spanning_tree(sp.coo_matrix((vals, (rows, cols)), shape=(len(nodes), len(nodes)))).tocoo()
+    inv = {float(rank[e]): e for e in best.values()}
+    ref_forest = {inv[float(x)] for x in mst.data}
+    assert forest == ref_forest
+    assert len(forest) > 0
+
+
+# ----------------------------------------------------------------- PGD step: torch autograd + torch Adam
+def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, steps, periodic):
+    import torch
+    o = torch.tensor(orig, dtype=torch.float64)
+    E = np.unique(np.concatenate([ai, aj]))
+    idx = {e: t for t, e in enumerate(E)}
+    a = torch.tensor([idx[x] for x in ai])
+    b = torch.tensor([idx[x] for x in aj])
+    # original separation: canonical float32 difference with minimum image
+    dp = []
+    for d in range(3):
+        x = orig[ai, d] - orig[aj, d]
+        if periodic:
+            x = np.where(x > np.float32(0.5), x - np.float32(1), np.where(x < np.float32(-0.5), x + np.float32(1), x))
+        dp.append(torch.tensor(x.astype(np.float32), dtype=torch.float64))
+    dp = torch.stack(dp, 1)
+    link = torch.tensor(alink.astype(bool))
+    delta = torch.tensor(recon[E].astype(np.float64) - orig[E].astype(np.float64), requires_grad=True)
+    opt = torch.optim.Adam([delta], lr=alpha_rel * xi, betas=(0.9, 0.999), eps=1e-8 * xi)
+    thr_l, thr_n = consts["thr_link"], consts["thr_non"]
+    for _ in range(steps):
+        opt.zero_grad()
+        r = dp + delta[a] - delta[b]
+        # |r| with d|r|/dr = r/|r|, and the original separation as direction where r == 0
+        with torch.no_grad():
+            nr = torch.sqrt((r * r).sum(1, keepdim=True))
+            u = torch.where(nr > 0, r / torch.where(nr > 0, nr, 1.0), dp / torch.sqrt((dp * dp).sum(1, keepdim=True)))
+        dh = (r * u).sum(1)
+        v = torch.where(link, dh - thr_l, thr_n - dh)
+        loss = (torch.clamp(v, min=0.0) ** 2).sum()     # Eq. 3
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            delta.clamp_(-consts["xi_box"], consts["xi_box"])
+    return E, delta.detach().numpy()
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_pgd_matches_torch_autograd_and_adam(mode):
+    w = synth.tiny_cosmo(seed=9, n=600)
+    kw = w.params(mode=mode)
+    ai, aj, al, _ = oracle.select(w.orig, **kw)
+    assert len(ai) > 50
+    c = oracle.constants(w.orig, w.recon, **kw)
+    steps = 6
+    _, delta, ed, st = oracle.pgd(w.orig, w.recon, ai, aj, al, **dict(kw, replay_iters=steps))
+    assert st["iters"] == steps
+    E, dref = _torch_pgd(w.orig, w.recon, ai, aj, al, c, w.xi, 0.5, steps, True)
+    assert np.array_equal(np.flatnonzero(ed), E)
+    assert np.abs(delta[E] - dref).max() <= 1e-9 * w.xi
+
+
+def test_adam_first_step_is_alpha():
+    # Two particles, one originally linked pair stretched beyond b by the reconstruction.
+    # At t = 1 Adam's bias-corrected ratio m/sqrt(v) is sign(g): each coordinate with a
+    # non-zero gradient moves by alpha (up to eps), the others do not move.
+    orig = np.array([[0.0, 0.0, 0.0], [0.9, 0.0, 0.0]], np.float32)
+    recon = np.array([[-0.1, 0.0, 0.0], [1.0, 0.0, 0.0]], np.float32)
+    xi = 0.1
+    kw = dict(b=1.0, xi=xi, periodic=0, alpha_rel=0.5, box_lo=(-5, -5, -5), box_hi=(5, 5, 5))
+    ai, aj, al, _ = oracle.select(orig, **kw)
+    assert list(ai) == [0] and list(aj) == [1] and list(al) == [1]
+    _, delta, _, st = oracle.pgd(orig, recon, ai, aj, al, **dict(kw, replay_iters=1))
+    alpha = 0.5 * xi
+    d0 = float(recon[0, 0]) - float(orig[0, 0])
+    d1 = float(recon[1, 0]) - float(orig[1, 0])
+    assert abs(delta[0, 0] - (d0 + alpha)) < 1e-8 * xi
+    assert abs(delta[1, 0] - (d1 - alpha)) < 1e-8 * xi
+    assert delta[0, 1] == 0 and delta[0, 2] == 0 and delta[1, 1] == 0
+
+
+def test_no_violation_means_zero_iterations_and_empty_edits():
+    # Table 2 (smallest bounds): zero violated pairs -> zero iterations, only setup.
+    # A cubic lattice of spacing 0.45 b has pair distances 0.9 b and 1.006 b near b; with
+    # xi = 0.003 b the pair at 1.006 b is vulnerable (potentially created) but a perturbation
+    # of at most 0.001 b per coordinate keeps it 0.0025 b clear of the tight threshold.
+    g = np.arange(6) * 0.45
+    orig = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    rng = np.random.default_rng(0)
+    recon = (orig + rng.uniform(-0.001, 0.001, orig.shape)).astype(np.float32)
+    kw = dict(b=1.0, xi=0.003, periodic=0, box_lo=(-1, -1, -1), box_hi=(5, 5, 5))
+    ai, aj, al, nv = oracle.select(orig, **kw)
+    assert nv > 0 and len(ai) == nv
+    corr, st = oracle.correct(orig, recon, **kw)
+    assert st["iters"] == 0 and st["loss_evals"] == 1 and st["viol0"] == 0
+    assert np.array_equal(corr, recon)
+    s = oracle.encode(recon, corr, **kw)
+    assert len(s) == 64 + (len(orig) + 7) // 8 and not any(s[64:])
+
+
+# ----------------------------------------------------------------- end-to-end invariants
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_correction_preserves_membership_and_box(mode):
+    w = synth.tiny_cosmo(seed=4, n=2500)
+    kw = w.params(mode=mode)
+    corr, st = oracle.correct(w.orig, w.recon, **kw)
+    assert st["converged"] == 1 and st["viol_final"] == 0
+    assert st["loss_evals"] == st["iters"] + 1          # Table 3: loss calls = gradient calls + 1
+    c = oracle.constants(w.orig, w.recon, **kw)
+    dev = np.abs(corr.astype(np.float64) - w.orig)
+    assert dev.max() <= w.xi
+    stream = oracle.encode(w.recon, corr, **kw)
+    dec = oracle.decode(w.recon, stream)
+    assert np.abs(dec.astype(np.float64) - w.orig).max() <= w.xi            # Eq. 2 box
+    assert np.abs(dec.astype(np.float64) - corr).max() <= c["eps_q"] + c["u"]
+    lab0, _, _ = oracle.fof_labels(w.orig, **kw)
+    lab1, _, _ = oracle.fof_labels(dec, **kw)
+    assert np.array_equal(lab0, lab1)                                         # membership preserved
+    ai, aj, al, _ = oracle.select(w.orig, **kw)
+    assert oracle.count_flips(dec, ai, aj, al, **kw) == 0                     # untightened loss 0
+    if mode == 0:
+        i0, j0, c0 = oracle.pairs(w.orig, **kw)
+        i1, j1, c1 = oracle.pairs(dec, **kw)
+        L0 = set(zip(i0[c0 <= 2], j0[c0 <= 2]))
+        L1 = set(zip(i1[c1 <= 2], j1[c1 <= 2]))
+        assert L0 == L1                                                        # VP: every link kept
+    # the base reconstruction itself breaks membership (otherwise the test is vacuous)
+    labr, _, _ = oracle.fof_labels(w.recon, **kw)
+    assert not np.array_equal(lab0, labr)
+
+
+@pytest.mark.parametrize("m_bits", [8, 16, 32])
+def test_bit_depth_introduces_no_violations(m_bits):
+    # Sec. 3.3: m in {8, 16, 32} re-introduces no violation after quantisation.
+    w = synth.md_box(n_clusters=40, eps_over_b=0.3, seed=8)
+    kw = w.params(m_bits=m_bits)
+    corr, st = oracle.correct(w.orig, w.recon, **kw)
+    assert st["converged"] == 1
+    dec = oracle.decode(w.recon, oracle.encode(w.recon, corr, **kw))
+    ai, aj, al, _ = oracle.select(w.orig, **kw)
+    assert oracle.count_flips(dec, ai, aj, al, **kw) == 0
+    lab0, _, _ = oracle.fof_labels(w.orig, **kw)
+    lab1, _, _ = oracle.fof_labels(dec, **kw)
+    assert np.array_equal(lab0, lab1)
+
+
+# ----------------------------------------------------------------- edit stream format
+def np_decode(recon, s):
+    """Independent numpy reader of the v1 edit stream."""
+    b = np.frombuffer(s, np.uint8)
+    assert bytes(b[:4]) == b"PCE1"
+    u32 = lambda o: int(np.frombuffer(b[o:o + 4].tobytes(), "<u4")[0])
+    u64 = lambda o: int(np.frombuffer(b[o:o + 8].tobytes(), "<u8")[0])
+    n, m = u64(8), u32(16)
+    xi = float(np.frombuffer(b[32:40].tobytes(), "<f8")[0])
+    nf, fb, cbytes = u64(40), u64(48), u64(56)
+    flags = np.unpackbits(b[64:64 + fb], bitorder="little")[:n].astype(bool)
+    cb = (m + 7) // 8
+    raw = b[64 + fb:64 + fb + cbytes].reshape(nf * 3, cb).astype(np.uint64)
+    q = np.zeros(nf * 3, np.uint64)
+    for k in range(cb):
+        q |= raw[:, k] << np.uint64(8 * k)
+    s_ = 4 * xi / (2.0 ** m - 1)
+    out = recon.copy()
+    ids = np.flatnonzero(flags)
+    assert len(ids) == nf
+    out[ids] = (recon[ids].astype(np.float64) + (-2 * xi + q.reshape(nf, 3).astype(np.float64) * s_)).astype(np.float32)
+    return out, ids
+
+
+def test_stream_round_trip_with_independent_reader():
+    w = synth.tiny_cosmo(seed=6, n=1500, mode="HF")
+    kw = w.params()
+    corr, _ = oracle.correct(w.orig, w.recon, **kw)
+    s = oracle.encode(w.recon, corr, **kw)
+    dec = oracle.decode(w.recon, s)
+    ref, ids = np_decode(w.recon, s)
+    assert np.array_equal(dec, ref)
+    changed = np.flatnonzero((corr != w.recon).any(axis=1))
+    assert np.array_equal(ids, changed)
+    c = oracle.constants(w.orig, w.recon, **kw)
+    assert np.abs(dec.astype(np.float64) - corr).max() <= c["eps_q"] + c["u"]
+
+
+def test_malformed_stream_is_rejected():
+    w = synth.tiny_cosmo(seed=6, n=500)
+    kw = w.params()
+    s = bytearray(oracle.encode(w.recon, w.recon, **kw))
+    s[0] = ord("X")
+    with pytest.raises(ValueError):
+        oracle.decode(w.recon, bytes(s))
+    with pytest.raises(ValueError):
+        oracle.decode(w.recon, bytes(oracle.encode(w.recon, w.recon, **kw))[:40])
