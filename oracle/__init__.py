@@ -48,7 +48,7 @@ class Consts(C.Structure):
                 ("w2", C.c_double), ("eps_q", C.c_double), ("u", C.c_double),
                 ("xi_box", C.c_double), ("dt", C.c_double), ("thr_link", C.c_double),
                 ("thr_non", C.c_double), ("alpha", C.c_double), ("eps_adam", C.c_double),
-                ("M", C.c_double)]
+                ("M", C.c_double), ("tau", C.c_double)]
 
 
 class PgdStats(C.Structure):
@@ -61,8 +61,8 @@ class PgdStats(C.Structure):
 
 
 DEFAULTS = dict(b=1.0, xi=0.1, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), periodic=0,
-                mode=0, m_bits=16, t_max=10000, alpha_rel=0.5, beta1=0.9, beta2=0.999,
-                eps_rel=1e-8, loss_tol=0.0, replay_iters=-1)
+                mode=0, m_bits=16, t_max=10000, alpha_rel=0.2, beta1=0.9, beta2=0.999,
+                eps_rel=2e-6, loss_tol=0.0, replay_iters=-1)
 
 
 def make_params(**kw) -> Params:

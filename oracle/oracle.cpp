@@ -36,8 +36,9 @@
 //  * Halo forest: the spanning forest kept is the unique minimum spanning
 //    forest under the key (float32 bits of d2, i, j) (Sec. 3.2 leaves the
 //    forest unspecified).
-//  * When a pair's current distance is exactly zero, its gradient direction
-//    is the original separation.
+//  * When a pair's current distance is at most b * 2^-30 (coincident points:
+//    the quantizer lattice makes them common, and rounding turns an exact
+//    zero into noise), its gradient direction is the original separation.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -68,7 +69,7 @@ typedef struct {
 // Derived constants (float32 link-test bounds and float64 PGD constants).
 typedef struct {
     float b2, lo2, hi2, L[3];
-    double w2, eps_q, u, xi_box, dt, thr_link, thr_non, alpha, eps_adam, M;
+    double w2, eps_q, u, xi_box, dt, thr_link, thr_non, alpha, eps_adam, M, tau;
 } or_consts;
 
 typedef struct {
@@ -119,6 +120,7 @@ or_consts make_consts(const or_params *p, const float *orig, const float *recon,
     c.dt = 2.0 * std::sqrt(3.0) * (c.eps_q + c.u) + b * std::ldexp(1.0, -20);  // Eq. 3 margin
     c.thr_link = b - c.dt;
     c.thr_non = b + c.dt;
+    c.tau = std::ldexp(b, -30);   // coincidence radius for the gradient direction
     c.alpha = p->alpha_rel * xi;
     c.eps_adam = p->eps_rel * xi;
     return c;
@@ -377,7 +379,7 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             nv += 1;
             if (!want_grad) continue;
             double u[3];
-            if (dh > 0.0) {
+            if (dh > c.tau) {
                 for (int d = 0; d < 3; ++d) u[d] = r[d] / dh;
             } else {
                 const double n0 = std::sqrt(dp[3 * k] * dp[3 * k] + dp[3 * k + 1] * dp[3 * k + 1] +

@@ -184,7 +184,7 @@ def test_mode_hierarchy_and_definitions():
 
 
 # ----------------------------------------------------------------- PGD step: torch autograd + torch Adam
-def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, steps, periodic):
+def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps, periodic):
     import torch
     o = torch.tensor(orig, dtype=torch.float64)
     E = np.unique(np.concatenate([ai, aj]))
@@ -201,7 +201,7 @@ def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, steps, periodi
     dp = torch.stack(dp, 1)
     link = torch.tensor(alink.astype(bool))
     delta = torch.tensor(recon[E].astype(np.float64) - orig[E].astype(np.float64), requires_grad=True)
-    opt = torch.optim.Adam([delta], lr=alpha_rel * xi, betas=(0.9, 0.999), eps=1e-8 * xi)
+    opt = torch.optim.Adam([delta], lr=alpha_rel * xi, betas=(0.9, 0.999), eps=eps_rel * xi)
     thr_l, thr_n = consts["thr_link"], consts["thr_non"]
     for _ in range(steps):
         opt.zero_grad()
@@ -230,7 +230,8 @@ def test_pgd_matches_torch_autograd_and_adam(mode):
     steps = 6
     _, delta, ed, st = oracle.pgd(w.orig, w.recon, ai, aj, al, **dict(kw, replay_iters=steps))
     assert st["iters"] == steps
-    E, dref = _torch_pgd(w.orig, w.recon, ai, aj, al, c, w.xi, 0.5, steps, True)
+    d = oracle.DEFAULTS
+    E, dref = _torch_pgd(w.orig, w.recon, ai, aj, al, c, w.xi, d["alpha_rel"], d["eps_rel"], steps, True)
     assert np.array_equal(np.flatnonzero(ed), E)
     assert np.abs(delta[E] - dref).max() <= 1e-9 * w.xi
 
@@ -246,11 +247,15 @@ def test_adam_first_step_is_alpha():
     ai, aj, al, _ = oracle.select(orig, **kw)
     assert list(ai) == [0] and list(aj) == [1] and list(al) == [1]
     _, delta, _, st = oracle.pgd(orig, recon, ai, aj, al, **dict(kw, replay_iters=1))
-    alpha = 0.5 * xi
+    alpha, eps = 0.5 * xi, oracle.DEFAULTS["eps_rel"] * xi
+    c = oracle.constants(orig, recon, **kw)
+    g = 2.0 * (1.1 - c["thr_link"])          # |gradient| of (d_hat - thr)^2 at d_hat = 1.1
+    step = alpha * g / (g + eps)              # m_hat / sqrt(v_hat) = sign(g) at t = 1
     d0 = float(recon[0, 0]) - float(orig[0, 0])
     d1 = float(recon[1, 0]) - float(orig[1, 0])
-    assert abs(delta[0, 0] - (d0 + alpha)) < 1e-8 * xi
-    assert abs(delta[1, 0] - (d1 - alpha)) < 1e-8 * xi
+    assert abs(step - alpha) < 1e-5 * xi
+    assert abs(delta[0, 0] - (d0 + step)) < 1e-12 * xi
+    assert abs(delta[1, 0] - (d1 - step)) < 1e-12 * xi
     assert delta[0, 1] == 0 and delta[0, 2] == 0 and delta[1, 1] == 0
 
 
