@@ -1,0 +1,180 @@
+/*
+ * pc.h -- C ABI of the GB300 cluster-preserving correction pass.
+ *
+ * Method: arXiv 2604.18801, "Preserving Clusters in Error-Bounded Lossy
+ * Compression of Scientific Particle Data".  Given original particle
+ * coordinates P, a lossy reconstruction P0 with |P0 - P| <= xi per coordinate,
+ * a linking length b and the bound xi, the pass
+ *   1. finds friends-of-friends links d <= b and the vulnerable pairs whose
+ *      distance lies in (b - 2 sqrt3 xi, b + 2 sqrt3 xi]          (Sec. 2.4, 3.1)
+ *   2. labels connected components (union-find)                 (Sec. 2.4)
+ *   3. selects active pairs in mode VP, SC or HF                  (Sec. 3.2)
+ *   4. runs projected gradient descent (Adam) on the tightened loss of Eq. 3
+ *      with every editable coordinate kept within the box         (Alg. 1, Eq. 2-3)
+ *   5. encodes the edits as flags + m-bit codes and decodes them  (Sec. 3.3)
+ *
+ * Conventions for every entry point
+ *   - Coordinates are float32, N x 3, C-contiguous (x, y, z per particle).
+ *     Pointers named *_dev are CUDA device pointers owned by the caller.
+ *   - Calls are issued on the caller's stream.  Entry points that must learn a
+ *     size on the device (pair counts, flagged counts) synchronise that stream
+ *     before returning; their outputs are complete when they return.
+ *   - Negative return codes are errors: outputs are then unspecified and no
+ *     library state leaks.  Positive codes are warnings with valid outputs.
+ *     pc_last_error() gives a thread-local message for the last failure.
+ *   - Link tests use the canonical float32 formula on the original
+ *     coordinates: dx = xi - xj in float32, minimum image (periodic boxes) by
+ *     one add or subtract of the box length when |dx| > L/2, then
+ *     d2 = (dx*dx + dy*dy) + dz*dz rounded per operation (no fused
+ *     multiply-add); linked iff d2 <= fl32(b*b).
+ *   - The library never allocates with the host heap on the data path; device
+ *     temporaries come from the stream-ordered pool of the context's device.
+ *   - Particle ids are the row indices 0..N-1; N < 2^31.
+ */
+#ifndef PC_H_
+#define PC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PC_OK = 0,
+    PC_WARN_NOT_CONVERGED = 1, /* PGD hit t_max with violations left; output valid and in the box */
+    PC_EINVAL = -1,            /* bad argument: NaN/Inf, n < 2, b <= 0, xi < 0, m outside [2,32], bad box */
+    PC_EBOUND = -2,            /* some |recon - orig| > xi: the base compressor broke its bound */
+    PC_ENOMEM = -3,            /* device or pinned-host allocation failed */
+    PC_ECUDA = -4,             /* a CUDA call failed (message in pc_last_error) */
+    PC_EFORMAT = -5,           /* malformed edit stream */
+    PC_ETIMEOUT = -6,          /* a bounded device-side wait or retry loop gave up */
+    PC_EBUSY = -7              /* server full / ticket unknown */
+} pc_status;
+
+typedef enum { PC_MODE_VP = 0, PC_MODE_SC = 1, PC_MODE_HF = 2 } pc_mode;
+
+/* Parameters: the REQUIRE line of Algorithm 1 plus the Adam moments (Sec. 4.1). */
+typedef struct {
+    double b;              /* linking length b > 0                                        */
+    double xi;             /* pointwise bound xi >= 0 (error of the base compressor)       */
+    double box_lo[3];      /* periodic boxes: [box_lo, box_hi) per axis; ignored otherwise */
+    double box_hi[3];
+    int32_t periodic;      /* 1: minimum-image distances (orig must lie inside the box)    */
+    int32_t mode;          /* pc_mode                                                     */
+    int32_t m_bits;        /* edit bit depth m in [2, 32] (default 16, Sec. 3.3)            */
+    int32_t t_max;         /* maximum number of PGD updates (default 10000)                */
+    double alpha_rel;      /* Adam step size in units of xi: alpha = alpha_rel * xi         */
+    double beta1, beta2;   /* Adam moments (0.9, 0.999)                                    */
+    double eps_rel;        /* Adam epsilon in units of xi (1e-8)                           */
+    double loss_tol;       /* eps_L: stop when the tight loss <= loss_tol (default 0)     */
+    int32_t replay_iters;  /* >= 0: run exactly this many updates, ignore the loss (-1 off) */
+    int32_t cell_cap_log2; /* tuning: at most 2^cell_cap_log2 grid cells (0 = default 27)   */
+} pc_params;
+
+/* Fills defaults: m=16, t_max=10000, alpha_rel=0.05, beta=(0.9,0.999), eps_rel=1e-8,
+ * loss_tol=0, replay_iters=-1, cell_cap_log2=0, unit box, non-periodic, mode VP. */
+void pc_params_default(pc_params *p);
+
+typedef struct pc_ctx pc_ctx;
+typedef struct pc_constraints pc_constraints;
+
+/* Context on one CUDA device (made current by every call that takes it).
+ * arena_bytes: bytes kept in the device pool between calls (0 = keep everything). */
+pc_status pc_ctx_create(int device, size_t arena_bytes, pc_ctx **out);
+void pc_ctx_destroy(pc_ctx *ctx);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *pc_last_error(void);
+
+/* Friends-of-friends labels (Sec. 2.4): labels_dev[i] = smallest id in i's
+ * component of the graph d2 <= b2 (canonical float32 test).  Only b, periodic and
+ * the box of params are used.  n_comp (host, may be NULL) receives the number of
+ * components.  Synchronises the stream. */
+pc_status pc_fof_labels(pc_ctx *ctx, const float *xyz_dev, int64_t n, const pc_params *params,
+                        int32_t *labels_dev, int64_t *n_comp, void *stream);
+
+typedef struct {
+    int64_t n_links;       /* pairs with d2 <= b2                      */
+    int64_t n_safe;        /* safe links d2 <= lo2                     */
+    int64_t n_pb;          /* potentially broken: lo2 < d2 <= b2       */
+    int64_t n_pc;          /* potentially created: b2 < d2 <= hi2      */
+    int64_t n_vulnerable;  /* |V| = n_pb + n_pc                        */
+    int64_t n_active;      /* |A| of the selected mode                  */
+    int64_t n_active_links;/* active pairs that are original links     */
+    int64_t n_halos;       /* FoF components (SC/HF modes; 0 for VP)   */
+    int64_t n_safe_comps;  /* safe components (SC/HF modes; 0 for VP)  */
+    int64_t n_forest;      /* HF: spanning-forest links kept           */
+    double ms;             /* device time of the selection             */
+} pc_select_stats;
+
+/* Constraint selection (Sec. 3.2): V, then A for params->mode.  The handle owns
+ * device memory of the context's device and is freed with pc_constraints_free.
+ * Synchronises the stream. */
+pc_status pc_select_constraints(pc_ctx *ctx, const float *orig_dev, int64_t n, const pc_params *params,
+                                pc_constraints **out, pc_select_stats *stats, void *stream);
+
+/* Copies the active pairs, canonical order (i < j, sorted by (i, j)), into caller
+ * buffers (host or device; each of length >= n_active; link_out may be NULL).
+ * link_out[k] = 1 iff the pair is an original link.  Synchronises the stream. */
+pc_status pc_constraints_copy(pc_ctx *ctx, const pc_constraints *c, uint32_t *i_out, uint32_t *j_out,
+                              uint8_t *link_out, void *stream);
+void pc_constraints_free(pc_constraints *c);
+
+typedef struct {
+    int64_t iters;         /* T: PGD updates performed                          */
+    int64_t loss_evals;    /* tight-loss evaluations (T + 1)                     */
+    int64_t viol0;         /* violated active pairs before the first update      */
+    int64_t viol_final;    /* violated active pairs at the end (0 if converged)  */
+    double loss0, loss_final;
+    int64_t n_vulnerable, n_active, n_editable;
+    int32_t converged;
+    int32_t pad_;
+    double ms_setup;       /* binning + pair search + selection + CSR build      */
+    double ms_pgd;         /* PGD loop                                          */
+} pc_correct_stats;
+
+/* The correction pass (Algorithm 1 up to Delta).  corrected_dev (N x 3) receives
+ * P_hat: the reconstruction for particles outside E, orig + delta for editable
+ * particles (every |corrected - orig| <= xi).  constraints may be NULL (selected
+ * inside) or a handle from pc_select_constraints on the same orig.  Returns PC_OK,
+ * PC_WARN_NOT_CONVERGED, or an error.  Synchronises the stream. */
+pc_status pc_correct(pc_ctx *ctx, const float *orig_dev, const float *recon_dev, int64_t n,
+                     const pc_params *params, const pc_constraints *constraints, float *corrected_dev,
+                     pc_correct_stats *stats, void *stream);
+
+/* pc_correct with extra outputs (each may be NULL):
+ *   delta_dev     N x 3 float64: P_hat - P (offset of the final iterate) for editable
+ *                 particles, 0 for the others; written in float64 from the double-float state.
+ *   hist_loss_dev, hist_viol_dev: tight loss (float64) and violated-pair count (uint64) at
+ *                 every evaluation t = 0..iters; room for t_max + 1 (or replay_iters + 1) entries.
+ * Same errors and synchronisation as pc_correct. */
+pc_status pc_correct_detail(pc_ctx *ctx, const float *orig_dev, const float *recon_dev, int64_t n,
+                            const pc_params *params, const pc_constraints *constraints, float *corrected_dev,
+                            double *delta_dev, double *hist_loss_dev, uint64_t *hist_viol_dev,
+                            pc_correct_stats *stats, void *stream);
+
+/* Edit stream v1 (Algorithm 1 last lines; Sec. 3.3).  Little endian:
+ *   0  "PCE1" | 4 u32 version=1 | 8 u64 n | 16 u32 m | 20 u32 mode | 24 u32 periodic | 28 u32 0
+ *   32 f64 xi | 40 u64 flagged | 48 u64 flag_bytes=ceil(n/8) | 56 u64 code_bytes
+ *   64 flags: particle i -> byte i>>3, bit i&7 (1 = edited)
+ *      codes: per flagged particle, ascending id, x y z codes of ceil(m/8) bytes each,
+ *      q = clamp(rint((corrected - recon + 2 xi) / s), 0, 2^m - 1), s = 4 xi / (2^m - 1),
+ *      evaluated in float64 (ties to even).
+ * Without stream_dev (NULL) only *nbytes is computed.  With it, cap must be >= the size.
+ * Synchronises the stream. */
+pc_status pc_encode_edits(pc_ctx *ctx, const float *recon_dev, const float *corrected_dev, int64_t n,
+                          const pc_params *params, uint8_t *stream_dev, size_t cap, size_t *nbytes,
+                          void *stream);
+
+/* Decoder (Sec. 3.3, "Reconstruction"): out = recon for unflagged particles and
+ * fl32(recon + (-2 xi + q s)) (float64 inside, one rounding) for flagged ones.
+ * stream_dev is a device copy of the stream.  PC_EFORMAT on a malformed stream. */
+pc_status pc_apply_edits(pc_ctx *ctx, const float *recon_dev, int64_t n, const uint8_t *stream_dev,
+                         size_t nbytes, float *out_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PC_H_ */

@@ -1,0 +1,201 @@
+"""GB300-native cluster-preserving correction of lossy particle data.
+
+Python face of the CUDA library ``libpc.so`` (C ABI in ``include/pc.h``).
+Tensors live on the GPU (torch supplies device memory and streams); every
+step of the method runs in the library's CUDA kernels:
+
+* :func:`fof_labels`            -- friends-of-friends labels (Sec. 2.4)
+* :func:`select_constraints`    -- vulnerable pairs and the active set A (Sec. 3.1-3.2)
+* :func:`correct`               -- projected Adam descent on the tight loss (Alg. 1, Eq. 3)
+* :func:`encode_edits` / :func:`apply_edits` -- edit stream and decoder (Sec. 3.3)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _native
+from ._native import PcError, make_params, struct_dict
+
+__all__ = ["Context", "fof_labels", "select_constraints", "Constraints", "correct", "correct_detail", "encode_edits",
+           "apply_edits", "PcError", "make_params", "default_context"]
+
+MODES = {"VP": 0, "SC": 1, "HF": 2}
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _xyz(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 2
+            and t.shape[1] == 3 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape (N, 3)")
+    return t
+
+
+class Context:
+    """A library context on one CUDA device (keeps pinned scratch and the device pool)."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 0):
+        self.device = int(device)
+        h = C.c_void_p()
+        _native.check(_native.lib().pc_ctx_create(self.device, arena_bytes, C.byref(h)), "pc_ctx_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            _native.lib().pc_ctx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_ctx = {}
+
+
+def default_context(device: int = 0) -> Context:
+    if device not in _ctx:
+        _ctx[device] = Context(device)
+    return _ctx[device]
+
+
+def _params(params) -> _native.Params:
+    if isinstance(params, _native.Params):
+        return params
+    d = dict(params)
+    if isinstance(d.get("mode"), str):
+        d["mode"] = MODES[d["mode"]]
+    return make_params(**d)
+
+
+def fof_labels(xyz: torch.Tensor, params, ctx: Context = None):
+    """Labels (int32, smallest id of the component) and the component count."""
+    _xyz(xyz, "xyz")
+    ctx = ctx or default_context(xyz.device.index)
+    p = _params(params)
+    lab = torch.empty(xyz.shape[0], dtype=torch.int32, device=xyz.device)
+    nc = C.c_int64(0)
+    _native.check(_native.lib().pc_fof_labels(ctx.h, xyz.data_ptr(), xyz.shape[0], C.byref(p), lab.data_ptr(),
+                                              C.byref(nc), _stream(xyz.device)), "pc_fof_labels")
+    return lab, int(nc.value)
+
+
+class Constraints:
+    """Active pairs selected on the device (owned by the library)."""
+
+    def __init__(self, ctx: Context, h: C.c_void_p, stats: dict, n: int, device):
+        self.ctx, self.h, self.stats, self.n, self.device = ctx, h, stats, n, device
+
+    def pairs(self):
+        """(i, j, link) as CUDA tensors in canonical order (i < j, sorted by (i, j))."""
+        m = self.stats["n_active"]
+        i = torch.empty(m, dtype=torch.int32, device=self.device)
+        j = torch.empty(m, dtype=torch.int32, device=self.device)
+        lk = torch.empty(m, dtype=torch.uint8, device=self.device)
+        if m:
+            _native.check(_native.lib().pc_constraints_copy(self.ctx.h, self.h, i.data_ptr(), j.data_ptr(),
+                                                            lk.data_ptr(), _stream(self.device)),
+                          "pc_constraints_copy")
+        return i, j, lk
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            _native.lib().pc_constraints_free(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def select_constraints(orig: torch.Tensor, params, ctx: Context = None) -> Constraints:
+    _xyz(orig, "orig")
+    ctx = ctx or default_context(orig.device.index)
+    p = _params(params)
+    h = C.c_void_p()
+    st = _native.SelectStats()
+    _native.check(_native.lib().pc_select_constraints(ctx.h, orig.data_ptr(), orig.shape[0], C.byref(p), C.byref(h),
+                                                      C.byref(st), _stream(orig.device)), "pc_select_constraints")
+    return Constraints(ctx, h, struct_dict(st), orig.shape[0], orig.device)
+
+
+def correct(orig: torch.Tensor, recon: torch.Tensor, params, constraints: Constraints = None,
+            out: torch.Tensor = None, ctx: Context = None):
+    """Correction pass: returns (corrected (N,3) float32 CUDA tensor, stats dict, status code)."""
+    _xyz(orig, "orig")
+    _xyz(recon, "recon")
+    if recon.shape != orig.shape:
+        raise ValueError("orig and recon differ in shape")
+    ctx = ctx or default_context(orig.device.index)
+    p = _params(params)
+    out = torch.empty_like(orig) if out is None else _xyz(out, "out")
+    st = _native.CorrectStats()
+    code = _native.lib().pc_correct(ctx.h, orig.data_ptr(), recon.data_ptr(), orig.shape[0], C.byref(p),
+                                    constraints.h if constraints is not None else None, out.data_ptr(),
+                                    C.byref(st), _stream(orig.device))
+    _native.check(code, "pc_correct", allow_warn=True)
+    return out, struct_dict(st), code
+
+
+def correct_detail(orig: torch.Tensor, recon: torch.Tensor, params, constraints: Constraints = None,
+                   ctx: Context = None):
+    """Correction pass with the float64 offsets and the loss history.
+
+    Returns (corrected, delta (N,3) float64, hist_loss float64, hist_viol int64, stats, status); the
+    histories are cut to the iterations run (iters + 1 entries)."""
+    _xyz(orig, "orig")
+    _xyz(recon, "recon")
+    ctx = ctx or default_context(orig.device.index)
+    p = _params(params)
+    cap = (p.replay_iters if p.replay_iters >= 0 else p.t_max) + 1
+    out = torch.empty_like(orig)
+    delta = torch.empty((orig.shape[0], 3), dtype=torch.float64, device=orig.device)
+    hl = torch.zeros(cap, dtype=torch.float64, device=orig.device)
+    hv = torch.zeros(cap, dtype=torch.int64, device=orig.device)
+    st = _native.CorrectStats()
+    code = _native.lib().pc_correct_detail(ctx.h, orig.data_ptr(), recon.data_ptr(), orig.shape[0], C.byref(p),
+                                           constraints.h if constraints is not None else None, out.data_ptr(),
+                                           delta.data_ptr(), hl.data_ptr(), hv.data_ptr(), C.byref(st),
+                                           _stream(orig.device))
+    _native.check(code, "pc_correct_detail", allow_warn=True)
+    d = struct_dict(st)
+    k = d["iters"] + 1
+    return out, delta, hl[:k], hv[:k], d, code
+
+
+def encode_edits(recon: torch.Tensor, corrected: torch.Tensor, params, ctx: Context = None) -> torch.Tensor:
+    """Edit stream (uint8 CUDA tensor, format v1 of include/pc.h)."""
+    _xyz(recon, "recon")
+    _xyz(corrected, "corrected")
+    ctx = ctx or default_context(recon.device.index)
+    p = _params(params)
+    nb = C.c_size_t(0)
+    s = _stream(recon.device)
+    L = _native.lib()
+    _native.check(L.pc_encode_edits(ctx.h, recon.data_ptr(), corrected.data_ptr(), recon.shape[0], C.byref(p), None,
+                                    0, C.byref(nb), s), "pc_encode_edits")
+    buf = torch.empty(nb.value, dtype=torch.uint8, device=recon.device)
+    _native.check(L.pc_encode_edits(ctx.h, recon.data_ptr(), corrected.data_ptr(), recon.shape[0], C.byref(p),
+                                    buf.data_ptr(), nb.value, C.byref(nb), s), "pc_encode_edits")
+    return buf
+
+
+def apply_edits(recon: torch.Tensor, stream: torch.Tensor, out: torch.Tensor = None, ctx: Context = None):
+    """Decoder: reconstruction + dequantized edits (float32 CUDA tensor)."""
+    _xyz(recon, "recon")
+    if not (stream.is_cuda and stream.dtype == torch.uint8 and stream.is_contiguous()):
+        raise ValueError("stream must be a contiguous uint8 CUDA tensor")
+    ctx = ctx or default_context(recon.device.index)
+    out = torch.empty_like(recon) if out is None else _xyz(out, "out")
+    _native.check(_native.lib().pc_apply_edits(ctx.h, recon.data_ptr(), recon.shape[0], stream.data_ptr(),
+                                               stream.numel(), out.data_ptr(), _stream(recon.device)),
+                  "pc_apply_edits")
+    return out

@@ -1,0 +1,472 @@
+// C ABI of libpc (include/pc.h): validation, derived constants, orchestration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pipeline.cuh"
+
+namespace pc {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+size_t encode_edits(const float *recon, const float *corr, int64_t n, const pc_params *p, uint8_t *out, size_t cap,
+                    cudaStream_t s, HostScratch &hs);
+void apply_edits(const float *recon, int64_t n, const uint8_t *in, size_t nbytes, float *out, cudaStream_t s,
+                 HostScratch &hs);
+
+namespace {
+
+double ulp32(double x) {
+    int e = 0;
+    std::frexp(std::fabs(x), &e);
+    return std::ldexp(1.0, e - 24);
+}
+
+void fail(pc_status st, const std::string &msg) {
+    set_error(msg);
+    throw Fail{st};
+}
+
+void check_params(const pc_params *p, int64_t n, bool need_pgd) {
+    if (!p) fail(PC_EINVAL, "params is NULL");
+    if (n < 2 || n >= (int64_t)0x7fffffff) fail(PC_EINVAL, "n must be in [2, 2^31-1)");
+    if (!(p->b > 0.0) || !std::isfinite(p->b)) fail(PC_EINVAL, "b must be finite and > 0");
+    if (!(p->xi >= 0.0) || !std::isfinite(p->xi)) fail(PC_EINVAL, "xi must be finite and >= 0");
+    if (p->mode < 0 || p->mode > 2) fail(PC_EINVAL, "mode must be 0 (VP), 1 (SC) or 2 (HF)");
+    if (p->periodic) {
+        for (int k = 0; k < 3; ++k) {
+            const double L = p->box_hi[k] - p->box_lo[k];
+            if (!(L > 0.0) || !std::isfinite(L)) fail(PC_EINVAL, "periodic box must have box_hi > box_lo");
+            const double reach = p->b + 2.0 * std::sqrt(3.0) * p->xi;
+            if (!(2.0 * reach * (1.0 + 1e-4) < L)) fail(PC_EINVAL, "periodic box shorter than twice the pair reach");
+        }
+    }
+    if (need_pgd) {
+        if (p->m_bits < 2 || p->m_bits > 32) fail(PC_EINVAL, "m_bits must be in [2, 32]");
+        if (p->t_max < 0) fail(PC_EINVAL, "t_max must be >= 0");
+        if (!(p->alpha_rel > 0.0) || !(p->beta1 >= 0.0 && p->beta1 < 1.0) || !(p->beta2 >= 0.0 && p->beta2 < 1.0) ||
+            !(p->eps_rel > 0.0) || !(p->loss_tol >= 0.0))
+            fail(PC_EINVAL, "bad Adam parameters");
+    }
+}
+
+void check_inspect(const Inspect &ins) {
+    if (ins.err & ERR_NONFINITE) fail(PC_EINVAL, "input holds NaN or Inf");
+    if (ins.err & ERR_OUTSIDE_BOX) fail(PC_EINVAL, "an original coordinate lies outside the periodic box");
+    if (ins.err & ERR_BOUND) fail(PC_EBOUND, "some |recon - orig| exceeds xi");
+}
+
+}  // namespace
+
+// Constants of Sec. 3.1 and Sec. 3.3 and the cell grid (see include/pc.h for the readings).
+Consts make_consts(const pc_params *p, const Inspect &ins, int64_t n, bool window) {
+    Consts c;
+    memset(&c, 0, sizeof(c));
+    const double b = p->b, xi = p->xi;
+    const double w2 = 2.0 * std::sqrt(3.0) * xi;
+    const double lo = b - w2, hi = b + w2;
+    c.b = b;
+    c.xi = xi;
+    c.b2 = (float)(b * b);
+    if (window) {
+        c.lo2 = lo > 0.0 ? (float)(lo * lo * (1.0 - std::ldexp(1.0, -20))) : -1.0f;
+        c.hi2 = (float)(hi * hi * (1.0 + std::ldexp(1.0, -20)));
+    } else {
+        c.lo2 = -1.0f;
+        c.hi2 = c.b2;
+    }
+    c.periodic = p->periodic ? 1 : 0;
+    for (int k = 0; k < 3; ++k) c.L[k] = (float)(p->box_hi[k] - p->box_lo[k]);
+    // PGD constants
+    const int m = p->m_bits >= 2 && p->m_bits <= 32 ? p->m_bits : 16;
+    c.M = (double)ins.maxabs;
+    c.eps_q = 2.0 * xi / (std::ldexp(1.0, m) - 1.0);
+    c.u = ulp32(c.M + 2.0 * xi);
+    c.xi_box_d = xi - c.eps_q - c.u;
+    c.dt = 2.0 * std::sqrt(3.0) * (c.eps_q + c.u) + b * std::ldexp(1.0, -20);
+    c.xi_box = (float)c.xi_box_d;
+    // grid: cells no smaller than the largest classified distance
+    const double reach = std::sqrt((double)c.hi2) * (1.0 + 1e-5);
+    double ext[3];
+    int nc[3];
+    for (int k = 0; k < 3; ++k) {
+        if (c.periodic) {
+            c.origin[k] = (float)p->box_lo[k];
+            ext[k] = p->box_hi[k] - p->box_lo[k];
+            int q = (int)std::min(std::floor(ext[k] / reach), 4096.0);
+            nc[k] = q < 3 ? 1 : q;
+        } else {
+            c.origin[k] = ins.lo[k];
+            ext[k] = (double)ins.hi[k] - (double)ins.lo[k];
+            nc[k] = (int)std::max(1.0, std::min(std::floor(ext[k] / reach), 4096.0));
+        }
+    }
+    int64_t cap;
+    if (p->cell_cap_log2 > 0) cap = (int64_t)1 << std::min(p->cell_cap_log2, 30);
+    else cap = std::max<int64_t>(1 << 16, std::min<int64_t>((int64_t)1 << 27, 8 * n));
+    for (int guard = 0; guard < 64 && (int64_t)nc[0] * nc[1] * nc[2] > cap; ++guard) {
+        const double f = std::cbrt((double)cap / ((double)nc[0] * nc[1] * nc[2]));
+        for (int k = 0; k < 3; ++k) {
+            int q = std::max(1, (int)std::floor(nc[k] * f));
+            if (q == nc[k] && q > 1) q -= 1;
+            if (c.periodic && q < 3) q = 1;
+            nc[k] = q;
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        c.nc[k] = nc[k];
+        c.inv_w[k] = ext[k] > 0 ? (float)(nc[k] / ext[k]) : 0.f;
+    }
+    c.ncells = (int64_t)nc[0] * nc[1] * nc[2];
+    c.key_bits = std::max(1, ceil_log2((uint64_t)c.ncells));
+    return c;
+}
+
+namespace {
+
+__global__ void k_count_roots(const uint32_t *__restrict__ lab, int64_t n, unsigned long long *out) {
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += lab[i] == (uint32_t)i;
+    c = __reduce_add_sync(0xffffffffu, (unsigned)c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+int64_t count_roots(const uint32_t *lab, int64_t n, cudaStream_t s, HostScratch &hs) {
+    DBuf<unsigned long long> d(1, s);
+    PC_CUDA(cudaMemsetAsync(d.p, 0, sizeof(unsigned long long), s));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), (int64_t)num_sms() * 8));
+    k_count_roots<<<g, 256, 0, s>>>(lab, n, d.p);
+    PC_CHECK_LAUNCH();
+    return (int64_t) * (unsigned long long *)read_back(hs, d.p, sizeof(unsigned long long), s);
+}
+
+}  // namespace
+
+}  // namespace pc
+
+using namespace pc;
+
+struct pc_ctx {
+    int device;
+    HostScratch hs;
+};
+
+struct pc_constraints {
+    int64_t n;
+    int mode;
+    Consts c;
+    Binned B;
+    DBuf<unsigned long long> A;
+    int64_t nA;
+    pc_select_stats stats;
+};
+
+namespace {
+
+template <class F>
+pc_status guarded(F &&f) {
+    try {
+        return f();
+    } catch (const Fail &e) {
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return PC_ENOMEM;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return PC_ECUDA;
+    } catch (...) {
+        set_error("unknown failure");
+        return PC_ECUDA;
+    }
+}
+
+void use_device(pc_ctx *ctx) {
+    if (!ctx) fail(PC_EINVAL, "context is NULL");
+    PC_CUDA(cudaSetDevice(ctx->device));
+}
+
+void release_to_default_stream(pc_constraints *h) {
+    // handles outlive the caller's stream: free their memory on the default stream
+    h->B.keys.s = 0;
+    h->B.order.s = 0;
+    h->B.P4.s = 0;
+    h->B.cell_start.s = 0;
+    h->B.items.s = 0;
+    h->A.s = 0;
+}
+
+// Binning, pair search, union-find and selection for params->mode (Sec. 3.2, 3.3).
+void do_select(pc_ctx *ctx, const float *orig, int64_t n, const pc_params *p, cudaStream_t s, pc_constraints *h) {
+    cudaEvent_t e0, e1;
+    PC_CUDA(cudaEventCreate(&e0));
+    PC_CUDA(cudaEventCreate(&e1));
+    PC_CUDA(cudaEventRecord(e0, s));
+    Inspect ins = inspect_inputs(orig, nullptr, n, p, s, ctx->hs);
+    check_inspect(ins);
+    h->n = n;
+    h->mode = p->mode;
+    h->c = make_consts(p, ins, n, true);
+    const Consts &c = h->c;
+    bin_particles(orig, n, c, h->B, s, ctx->hs);
+    DBuf<unsigned long long> counts(CNT_N, s);
+    DBuf<uint32_t> err(1, s);
+    PC_CUDA(cudaMemsetAsync(counts.p, 0, CNT_N * sizeof(unsigned long long), s));
+    PC_CUDA(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s));
+    DBuf<uint32_t> fof, safe;
+    if (p->mode == PC_MODE_HF) {
+        fof.alloc(n, s);
+        uf_init(fof.p, n, s);
+    }
+    if (p->mode != PC_MODE_VP) {
+        safe.alloc(n, s);
+        uf_init(safe.p, n, s);
+    }
+    pair_pass_union(h->B, c, fof.p, safe.p, counts.p, err.p, s);
+    if (fof.p) uf_flatten(fof.p, n, s);
+    if (safe.p) uf_flatten(safe.p, n, s);
+    unsigned long long cnt[CNT_N];
+    memcpy(cnt, read_back(ctx->hs, counts.p, sizeof(cnt), s), sizeof(cnt));
+    const uint32_t e1v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
+    if (e1v & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
+    memset(&h->stats, 0, sizeof(h->stats));
+    h->stats.n_links = (int64_t)cnt[CNT_LINKS];
+    h->stats.n_safe = (int64_t)cnt[CNT_SAFE];
+    h->stats.n_pb = (int64_t)cnt[CNT_PB];
+    h->stats.n_pc = (int64_t)cnt[CNT_PC];
+    h->stats.n_vulnerable = (int64_t)(cnt[CNT_PB] + cnt[CNT_PC]);
+    if (fof.p) h->stats.n_halos = count_roots(fof.p, n, s, ctx->hs);
+    if (safe.p) h->stats.n_safe_comps = count_roots(safe.p, n, s, ctx->hs);
+    const uint64_t capA = std::max<uint64_t>(1, cnt[CNT_PB] + cnt[CNT_PC]);
+    const uint64_t capC = p->mode == PC_MODE_HF ? std::max<uint64_t>(1, cnt[CNT_PB]) : 0;
+    h->A.alloc(capA, s);
+    DBuf<unsigned long long> C(capC, s);
+    pair_pass_emit(h->B, c, p->mode, fof.p, safe.p, h->A.p, capA, C.p, capC, counts.p, err.p, s);
+    memcpy(cnt, read_back(ctx->hs, counts.p, sizeof(cnt), s), sizeof(cnt));
+    const uint32_t e2v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
+    if (e2v & ERR_INDEX) fail(PC_ECUDA, "pair emission overflowed its count");
+    int64_t nA = (int64_t)cnt[CNT_A];
+    if (p->mode == PC_MODE_HF) {
+        const int64_t nf = halo_forest(h->B, c, safe.p, C.p, (int64_t)cnt[CNT_C], h->A.p, nA, err.p, s, ctx->hs);
+        h->stats.n_forest = nf;
+        nA += nf;
+        const uint32_t e3v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
+        if (e3v & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
+    }
+    h->nA = nA;
+    h->stats.n_active = nA;
+    PC_CUDA(cudaEventRecord(e1, s));
+    PC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->stats.ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+}  // namespace
+
+extern "C" {
+
+void pc_params_default(pc_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->b = 1.0;
+    p->xi = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        p->box_lo[k] = 0.0;
+        p->box_hi[k] = 1.0;
+    }
+    p->periodic = 0;
+    p->mode = PC_MODE_VP;
+    p->m_bits = 16;
+    p->t_max = 10000;
+    p->alpha_rel = 0.2;
+    p->beta1 = 0.9;
+    p->beta2 = 0.999;
+    p->eps_rel = 2e-6;
+    p->loss_tol = 0.0;
+    p->replay_iters = -1;
+    p->cell_cap_log2 = 0;
+}
+
+const char *pc_last_error(void) { return g_err.c_str(); }
+
+pc_status pc_ctx_create(int device, size_t arena_bytes, pc_ctx **out) {
+    return guarded([&]() -> pc_status {
+        if (!out) fail(PC_EINVAL, "out is NULL");
+        *out = nullptr;
+        int count = 0;
+        PC_CUDA(cudaGetDeviceCount(&count));
+        if (device < 0 || device >= count) fail(PC_EINVAL, "no such CUDA device");
+        PC_CUDA(cudaSetDevice(device));
+        cudaMemPool_t pool;
+        PC_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t thr = arena_bytes ? (uint64_t)arena_bytes : ~0ull;
+        PC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        pc_ctx *c = new pc_ctx();
+        c->device = device;
+        *out = c;
+        return PC_OK;
+    });
+}
+
+void pc_ctx_destroy(pc_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->hs.p) cudaFreeHost(ctx->hs.p);
+    delete ctx;
+}
+
+pc_status pc_fof_labels(pc_ctx *ctx, const float *xyz, int64_t n, const pc_params *p, int32_t *labels,
+                        int64_t *n_comp, void *stream) {
+    return guarded([&]() -> pc_status {
+        use_device(ctx);
+        check_params(p, n, false);
+        if (!xyz || !labels) fail(PC_EINVAL, "NULL buffer");
+        cudaStream_t s = (cudaStream_t)stream;
+        Inspect ins = inspect_inputs(xyz, nullptr, n, p, s, ctx->hs);
+        check_inspect(ins);
+        Consts c = make_consts(p, ins, n, false);
+        Binned B;
+        bin_particles(xyz, n, c, B, s, ctx->hs);
+        DBuf<unsigned long long> counts(CNT_N, s);
+        DBuf<uint32_t> err(1, s);
+        PC_CUDA(cudaMemsetAsync(counts.p, 0, CNT_N * sizeof(unsigned long long), s));
+        PC_CUDA(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s));
+        uint32_t *par = (uint32_t *)labels;
+        uf_init(par, n, s);
+        pair_pass_union(B, c, par, nullptr, counts.p, err.p, s);
+        uf_flatten(par, n, s);
+        const uint32_t ev = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
+        if (ev & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
+        if (n_comp) *n_comp = count_roots(par, n, s, ctx->hs);
+        PC_CUDA(cudaStreamSynchronize(s));
+        return PC_OK;
+    });
+}
+
+pc_status pc_select_constraints(pc_ctx *ctx, const float *orig, int64_t n, const pc_params *p, pc_constraints **out,
+                                pc_select_stats *stats, void *stream) {
+    pc_constraints *h = nullptr;
+    pc_status st = guarded([&]() -> pc_status {
+        use_device(ctx);
+        check_params(p, n, false);
+        if (!orig || !out) fail(PC_EINVAL, "NULL argument");
+        *out = nullptr;
+        h = new pc_constraints();
+        do_select(ctx, orig, n, p, (cudaStream_t)stream, h);
+        release_to_default_stream(h);
+        if (stats) *stats = h->stats;
+        *out = h;
+        return PC_OK;
+    });
+    if (st != PC_OK && h) {
+        release_to_default_stream(h);
+        delete h;
+    }
+    return st;
+}
+
+pc_status pc_constraints_copy(pc_ctx *ctx, const pc_constraints *h, uint32_t *i_out, uint32_t *j_out,
+                              uint8_t *link_out, void *stream) {
+    return guarded([&]() -> pc_status {
+        use_device(ctx);
+        if (!h || !i_out || !j_out) fail(PC_EINVAL, "NULL argument");
+        export_pairs(h->B, h->c, h->A.p, h->nA, i_out, j_out, link_out, (cudaStream_t)stream);
+        return PC_OK;
+    });
+}
+
+void pc_constraints_free(pc_constraints *h) {
+    if (!h) return;
+    release_to_default_stream(h);
+    delete h;
+}
+
+pc_status pc_correct(pc_ctx *ctx, const float *orig, const float *recon, int64_t n, const pc_params *p,
+                     const pc_constraints *given, float *corrected, pc_correct_stats *stats, void *stream) {
+    return pc_correct_detail(ctx, orig, recon, n, p, given, corrected, nullptr, nullptr, nullptr, stats, stream);
+}
+
+pc_status pc_correct_detail(pc_ctx *ctx, const float *orig, const float *recon, int64_t n, const pc_params *p,
+                            const pc_constraints *given, float *corrected, double *delta_dev, double *hist_loss,
+                            uint64_t *hist_viol, pc_correct_stats *stats, void *stream) {
+    pc_constraints *own = nullptr;
+    pc_status st = guarded([&]() -> pc_status {
+        use_device(ctx);
+        check_params(p, n, true);
+        if (!orig || !recon || !corrected) fail(PC_EINVAL, "NULL buffer");
+        cudaStream_t s = (cudaStream_t)stream;
+        const auto t0 = std::chrono::steady_clock::now();
+        Inspect ins = inspect_inputs(orig, recon, n, p, s, ctx->hs);
+        check_inspect(ins);
+        const pc_constraints *h = given;
+        if (h) {
+            if (h->n != n) fail(PC_EINVAL, "constraints were selected for another particle count");
+        } else {
+            own = new pc_constraints();
+            do_select(ctx, orig, n, p, s, own);
+            h = own;
+        }
+        Consts cp = make_consts(p, ins, n, true);
+        if (!(cp.xi_box_d > 0.0))
+            fail(PC_EINVAL, "xi too small for float32 coordinates of this magnitude (empty projection box)");
+        double ms_csr = 0;
+        PgdResult r = run_pgd(h->B, cp, p, orig, recon, h->A.p, h->nA, corrected, s, ctx->hs, &ms_csr, delta_dev,
+                              hist_loss, (unsigned long long *)hist_viol);
+        if (stats) {
+            memset(stats, 0, sizeof(*stats));
+            stats->iters = r.iters;
+            stats->loss_evals = r.loss_evals;
+            stats->viol0 = r.viol0;
+            stats->viol_final = r.viol_final;
+            stats->loss0 = r.loss0;
+            stats->loss_final = r.loss_final;
+            stats->n_vulnerable = h->stats.n_vulnerable;
+            stats->n_active = h->nA;
+            stats->n_editable = r.n_editable;
+            stats->converged = r.converged ? 1 : 0;
+            stats->ms_setup = (given ? 0.0 : h->stats.ms) + ms_csr;
+            stats->ms_pgd = r.ms;
+        }
+        (void)t0;
+        return r.converged ? PC_OK : PC_WARN_NOT_CONVERGED;
+    });
+    if (own) {
+        release_to_default_stream(own);
+        delete own;
+    }
+    return st;
+}
+
+pc_status pc_encode_edits(pc_ctx *ctx, const float *recon, const float *corrected, int64_t n, const pc_params *p,
+                          uint8_t *stream_dev, size_t cap, size_t *nbytes, void *stream) {
+    return guarded([&]() -> pc_status {
+        use_device(ctx);
+        if (!p || !recon || !corrected || !nbytes) fail(PC_EINVAL, "NULL argument");
+        if (n < 1) fail(PC_EINVAL, "n must be >= 1");
+        if (p->m_bits < 2 || p->m_bits > 32) fail(PC_EINVAL, "m_bits must be in [2, 32]");
+        if (!(p->xi > 0.0) || !std::isfinite(p->xi)) fail(PC_EINVAL, "xi must be finite and > 0 to encode edits");
+        *nbytes = encode_edits(recon, corrected, n, p, stream_dev, cap, (cudaStream_t)stream, ctx->hs);
+        return PC_OK;
+    });
+}
+
+pc_status pc_apply_edits(pc_ctx *ctx, const float *recon, int64_t n, const uint8_t *stream_dev, size_t nbytes,
+                         float *out, void *stream) {
+    return guarded([&]() -> pc_status {
+        use_device(ctx);
+        if (!recon || !stream_dev || !out) fail(PC_EINVAL, "NULL buffer");
+        if (n < 1) fail(PC_EINVAL, "n must be >= 1");
+        apply_edits(recon, n, stream_dev, nbytes, out, (cudaStream_t)stream, ctx->hs);
+        return PC_OK;
+    });
+}
+
+}  // extern "C"
