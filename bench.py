@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Throughput of the cluster-preserving correction pass on one GB300 (or N replicas).
+
+One step = the whole hot path on the HACC-shaped 256^3 box (16.8M particles,
+periodic unit box, 20,000 Gaussian halos holding 55%, b = 0.2 / 256,
+eps = 0.1 b, quantizer reconstruction): for each constraint mode VP, SC and HF,
+pc_correct (binning, pair search, union-find, selection, PGD) and
+pc_encode_edits, device-resident inputs to a device-resident edit stream.
+value = particles corrected per second over all modes, in Mparticles/s.
+
+After the timed region every mode's stream is decoded and the FoF labels of
+the decoded data are compared with those of the original on the GPU: the line
+reports membership_exact (a run that loses membership does not count).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--eps 0.1] [--modes VP,SC,HF]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample (CPU baseline arm)
+
+N > 1 (torchrun) runs independent replicas, one per GPU: the method has no
+data exchange on one node; value = all ranks' particles / max elapsed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MODES = {"VP": 0, "SC": 1, "HF": 2}
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--eps", type=float, default=0.1, help="eps / b")
+    ap.add_argument("--modes", default="VP,SC,HF")
+    ap.add_argument("--n", type=int, default=256 ** 3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--cpu-side", type=float, default=0.33, help="side of the sub-cube the CPU baseline corrects")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sub_cube(w, side: float):
+    """Particles of the box inside [0, side)^3, as a non-periodic problem (CPU baseline sample)."""
+    import numpy as np
+    from paper_2604_18801_gb300 import synth
+    m = np.all(w.orig < side, axis=1) & np.all(w.recon < side + w.xi, axis=1)
+    o = np.ascontiguousarray(w.orig[m])
+    r = np.ascontiguousarray(w.recon[m])
+    return synth.Workload(name=f"{w.name}_subcube{side:g}", orig=o, recon=r, b=w.b, xi=w.xi, periodic=False,
+                          box_lo=(0, 0, 0), box_hi=(side, side, side), mode=w.mode)
+
+
+def cpu_baseline(w, modes, side):
+    """The CPU oracle, as it stands, on a sub-cube of the same box (single thread)."""
+    import oracle
+    s = sub_cube(w, side)
+    oracle.build()
+    t = time.perf_counter()
+    for m in modes:
+        oracle.correct(s.orig, s.recon, **s.params(mode=MODES[m]))
+    dt = time.perf_counter() - t
+    return {"value": round(s.n * len(modes) / dt / 1e6, 6), "unit": "Mparticles/s", "cores": 1, "kind": "oracle",
+            "sample": f"{s.n} particles of the sub-cube [0,{side:g})^3 of the same box, modes {','.join(modes)}, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    modes = [m.strip() for m in a.modes.split(",") if m.strip()]
+    workload = f"hacc{a.n}_eps{a.eps:g}b_{'+'.join(modes)}"
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        from paper_2604_18801_gb300 import synth
+        w = synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n)
+        for _ in range(a.warmup):
+            pass
+        times = []
+        cb = None
+        for _ in range(max(1, a.steps)):
+            cb = cpu_baseline(w, modes, a.cpu_side)
+            times.append(cb["value"])
+        v = statistics.median(times)
+        cb["value"] = v
+        print(json.dumps({"impl": "reference", "metric": "corrected Mparticles/s", "value": v,
+                          "unit": "Mparticles/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+                          "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": workload, "sample": cb["sample"]}, "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": "Mparticles/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2604_18801_gb300 as pc
+    from paper_2604_18801_gb300 import _native, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    w = synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n)
+    o = torch.from_numpy(w.orig).to(dev)
+    r = torch.from_numpy(w.recon).to(dev)
+    prms = {m: w.params(mode=MODES[m]) for m in modes}
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        out = {}
+        for m in modes:
+            corr, st, code = pc.correct(o, r, prms[m])
+            s = pc.encode_edits(r, corr, prms[m])
+            out[m] = (corr, s, st, code)
+        return out
+
+    for _ in range(max(3, a.warmup)):
+        res = step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    launches0 = _native.lib().pc_kernel_launches()
+    clk = Clocks(local)
+    clk.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_push("timed")
+    ev0.record(stream)
+    stats = []
+    for _ in range(a.steps):
+        res = step()
+        stats.append({m: res[m][2] for m in modes})
+    ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    if world > 1:
+        dist.barrier()
+    launches = _native.lib().pc_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    per_step = ms_max / a.steps
+    value = w.n * len(modes) * a.steps * world / (ms_max / 1e3) / 1e6
+
+    # exact membership of the decoded output (not timed)
+    lab0, _ = pc.fof_labels(o, prms[modes[0]])
+    exact = True
+    for m in modes:
+        dec = pc.apply_edits(r, res[m][1])
+        lab1, _ = pc.fof_labels(dec, prms[m])
+        exact &= bool(torch.equal(lab0, lab1)) and bool(
+            (dec.double() - o.double()).abs().max().item() <= w.xi) and res[m][3] == 0
+
+    # roofline of the dominant kernel (the PGD iteration): algorithmic bytes per launch =
+    # 112 B per editable particle + 8 B per active pair; duration from the in-library events
+    last = stats[-1]
+    bytes_it = sum((112 * last[m]["n_editable"] + 8 * last[m]["n_active"]) * last[m]["pgd_launches"] for m in modes)
+    ms_it = sum(last[m]["ms_pgd_iter"] for m in modes)
+    launches_it = sum(last[m]["pgd_launches"] for m in modes)
+    pk, pk_kind = peaks()
+    achieved = bytes_it / (ms_it / 1e3) / 1e9 if ms_it > 0 else 0.0
+    peak = float(pk["hbm_gbs"])
+    roofline = {"kernel": "k_pgd_iter", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_kind": pk_kind, "avg_launch_us": round(1e3 * ms_it / max(1, launches_it), 2),
+                "launches_per_step": launches_it,
+                "bytes_per_launch": int(bytes_it / max(1, launches_it))}
+
+    # end to end through the public API with host buffers: pinned H2D, correct, encode, stream D2H
+    ho = torch.from_numpy(w.orig).pin_memory()
+    hr = torch.from_numpy(w.recon).pin_memory()
+    e2e_ms = []
+    d2h = 0
+    for k in range(max(1, a.e2e_steps) + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        od = ho.to(dev, non_blocking=True)
+        rd = hr.to(dev, non_blocking=True)
+        nb = 0
+        for m in modes:
+            corr, st, code = pc.correct(od, rd, prms[m])
+            s = pc.encode_edits(rd, corr, prms[m])
+            hs = s.cpu()
+            nb += hs.numel()
+        torch.cuda.synchronize(dev)
+        if k > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        d2h = nb
+    e2e_v = w.n * len(modes) / (statistics.median(e2e_ms) / 1e3) / 1e6
+
+    line = {
+        "metric": "corrected Mparticles/s (exact membership)", "value": round(value, 3), "unit": "Mparticles/s",
+        "n_gpus": world, "steps": a.steps, "warmup": max(3, a.warmup), "ms_per_step": round(per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 data, double-float PGD",
+        "data": "synthetic",
+        "config": {"workload": workload, "n_particles": w.n, "b": w.b, "xi": w.xi, "modes": modes,
+                   "parallelism": f"replicas{world}", "l2": "inputs (2 x 201 MB) and PGD state larger than L2"},
+        "membership_exact": exact,
+        "per_mode": {m: {k: last[m][k] for k in ("iters", "n_vulnerable", "n_active", "n_editable", "viol0",
+                                                   "ms_setup", "ms_pgd")} for m in modes},
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_v, 3), "unit": "Mparticles/s",
+                "h2d_bytes_per_step": int(ho.numel() * 4 + hr.numel() * 4), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, modes, a.cpu_side)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

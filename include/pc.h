@@ -61,7 +61,8 @@ typedef struct {
     double xi;             /* pointwise bound xi >= 0 (error of the base compressor)       */
     double box_lo[3];      /* periodic boxes: [box_lo, box_hi) per axis; ignored otherwise */
     double box_hi[3];
-    int32_t periodic;      /* 1: minimum-image distances (orig must lie inside the box)    */
+    int32_t periodic;      /* 1: minimum-image distances; coordinates must lie within a
+                              quarter box length of [box_lo, box_hi) (one +-L gives the image) */
     int32_t mode;          /* pc_mode                                                     */
     int32_t m_bits;        /* edit bit depth m in [2, 32] (default 16, Sec. 3.3)            */
     int32_t t_max;         /* maximum number of PGD updates (default 10000)                */
@@ -87,6 +88,9 @@ void pc_ctx_destroy(pc_ctx *ctx);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char *pc_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all threads). */
+uint64_t pc_kernel_launches(void);
 
 /* Friends-of-friends labels (Sec. 2.4): labels_dev[i] = smallest id in i's
  * component of the graph d2 <= b2 (canonical float32 test).  Only b, periodic and
@@ -132,7 +136,9 @@ typedef struct {
     int32_t converged;
     int32_t pad_;
     double ms_setup;       /* binning + pair search + selection + CSR build      */
-    double ms_pgd;         /* PGD loop                                          */
+    double ms_pgd;         /* PGD loop including the output kernels              */
+    double ms_pgd_iter;    /* device time of the iteration launches alone        */
+    int64_t pgd_launches;  /* iteration kernels launched (>= loss_evals)         */
 } pc_correct_stats;
 
 /* The correction pass (Algorithm 1 up to Delta).  corrected_dev (N x 3) receives

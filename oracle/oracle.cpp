@@ -36,6 +36,11 @@
 //  * Halo forest: the spanning forest kept is the unique minimum spanning
 //    forest under the key (float32 bits of d2, i, j) (Sec. 3.2 leaves the
 //    forest unspecified).
+//  * The current pair offset and distance are evaluated symmetrically: the
+//    offset is dp + (delta_i - delta_j) rounded once, and |r| adds the squared
+//    components smallest first.  The quantizer lattice makes mirror-image pairs
+//    common; their gradient terms then cancel exactly, as in exact arithmetic.
+//    (Adam's normalised step turns a last-bit asymmetry into an O(xi) move.)
 //  * When a pair's current distance is at most b * 2^-30 (coincident points:
 //    the quantizer lattice makes them common, and rounding turns an exact
 //    zero into noise), its gradient direction is the original separation.
@@ -202,6 +207,7 @@ std::vector<Pair> grid_pairs(const float *P, int64_t n, const or_params *p, cons
     for (int64_t i = 0; i < n; ++i) {
         for (int k = 0; k < 3; ++k) {
             int q = (int)std::floor(((double)P[3 * i + k] - lo[k]) / w[k]);
+            if (p->periodic) q = ((q % nc[k]) + nc[k]) % nc[k];   // image inside the box
             q = std::max(0, std::min(nc[k] - 1, q));
             cc[3 * i + k] = q;
         }
@@ -328,6 +334,23 @@ std::vector<Active> select_pairs(const float *P, const std::vector<Pair> &pairs,
     return A;
 }
 
+// Current offset of a pair along one axis, dp + (delta_i - delta_j), rounded once: the
+// exact errors of the two additions (Knuth's TwoSum) are added back before the final
+// rounding, so offsets of mirror-image pairs are exact negatives of each other.
+double offset(double dp, double di, double dj) {
+    const double s1 = di - dj, b1 = s1 - di, e1 = (di - (s1 - b1)) + (-dj - b1);
+    const double s2 = s1 + dp, b2 = s2 - s1, e2 = (s1 - (s2 - b2)) + (dp - b2);
+    return s2 + (e1 + e2);
+}
+
+// |r| with the squares added smallest first, so the result does not depend on the
+// order of the axes (mirror-image pairs get the same distance to the last bit).
+double norm3(const double r[3]) {
+    double q[3] = {r[0] * r[0], r[1] * r[1], r[2] * r[2]};
+    std::sort(q, q + 3);
+    return std::sqrt((q[0] + q[1]) + q[2]);
+}
+
 // Projected gradient descent with Adam on the tightened loss (Algorithm 1, Eq. 3),
 // in float64 on offsets delta = P_hat - P of the editable particles.
 void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Active> &A,
@@ -370,8 +393,8 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
         for (int64_t k = 0; k < na; ++k) {
             const int64_t a = idx[A[k].i], b = idx[A[k].j];
             double r[3];
-            for (int d = 0; d < 3; ++d) r[d] = dp[3 * k + d] + (delta[3 * a + d] - delta[3 * b + d]);
-            const double dh = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            for (int d = 0; d < 3; ++d) r[d] = offset(dp[3 * k + d], delta[3 * a + d], delta[3 * b + d]);
+            const double dh = norm3(r);
             // link: penalise d_hat > b - dt;  non-link: penalise d_hat < b + dt
             const double viol_amt = A[k].link ? dh - c.thr_link : c.thr_non - dh;
             if (!(viol_amt > 0.0)) continue;

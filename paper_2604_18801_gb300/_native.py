@@ -40,7 +40,8 @@ class CorrectStats(C.Structure):
     _fields_ = [("iters", C.c_int64), ("loss_evals", C.c_int64), ("viol0", C.c_int64), ("viol_final", C.c_int64),
                 ("loss0", C.c_double), ("loss_final", C.c_double), ("n_vulnerable", C.c_int64),
                 ("n_active", C.c_int64), ("n_editable", C.c_int64), ("converged", C.c_int32), ("pad_", C.c_int32),
-                ("ms_setup", C.c_double), ("ms_pgd", C.c_double)]
+                ("ms_setup", C.c_double), ("ms_pgd", C.c_double), ("ms_pgd_iter", C.c_double),
+                ("pgd_launches", C.c_int64)]
 
 
 def struct_dict(s) -> dict:
@@ -64,6 +65,7 @@ def lib():
         L.pc_params_default.argtypes = [P]
         L.pc_params_default.restype = None
         L.pc_last_error.restype = C.c_char_p
+        L.pc_kernel_launches.restype = C.c_uint64
         L.pc_ctx_create.argtypes = [C.c_int, sz, C.POINTER(vp)]
         L.pc_ctx_destroy.argtypes = [vp]
         L.pc_ctx_destroy.restype = None

@@ -1,5 +1,6 @@
 // C ABI of libpc (include/pc.h): validation, derived constants, orchestration.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -12,6 +13,8 @@ namespace pc {
 
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 size_t encode_edits(const float *recon, const float *corr, int64_t n, const pc_params *p, uint8_t *out, size_t cap,
                     cudaStream_t s, HostScratch &hs);
@@ -297,6 +300,8 @@ void pc_params_default(pc_params *p) {
 
 const char *pc_last_error(void) { return g_err.c_str(); }
 
+uint64_t pc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
 pc_status pc_ctx_create(int device, size_t arena_bytes, pc_ctx **out) {
     return guarded([&]() -> pc_status {
         if (!out) fail(PC_EINVAL, "out is NULL");
@@ -434,6 +439,8 @@ pc_status pc_correct_detail(pc_ctx *ctx, const float *orig, const float *recon, 
             stats->converged = r.converged ? 1 : 0;
             stats->ms_setup = (given ? 0.0 : h->stats.ms) + ms_csr;
             stats->ms_pgd = r.ms;
+            stats->ms_pgd_iter = r.ms_iter;
+            stats->pgd_launches = r.launches;
         }
         (void)t0;
         return r.converged ? PC_OK : PC_WARN_NOT_CONVERGED;

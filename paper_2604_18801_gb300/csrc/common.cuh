@@ -26,7 +26,12 @@ struct Fail {
             throw ::pc::Fail{e_ == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA};       \
         }                                                                                   \
     } while (0)
-#define PC_CHECK_LAUNCH() PC_CUDA(cudaGetLastError())
+void count_launch();
+#define PC_CHECK_LAUNCH()             \
+    do {                              \
+        ::pc::count_launch();         \
+        PC_CUDA(cudaGetLastError());  \
+    } while (0)
 
 // Device error word bits (set by kernels with atomicOr, read by the host).
 enum : uint32_t {

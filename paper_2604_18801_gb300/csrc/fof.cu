@@ -62,7 +62,11 @@ __global__ void k_inspect(const float *__restrict__ orig, const float *__restric
             mabs = fmaxf(mabs, fabsf(o));
             mn[d] = fminf(mn[d], o);
             mx[d] = fmaxf(mx[d], o);
-            if (periodic && !((double)o >= blo[d] && (double)o < bhi[d])) err |= ERR_OUTSIDE_BOX;
+            // periodic: within a quarter box of the box, so one +-L gives the minimum image
+            if (periodic) {
+                const double q = 0.25 * (bhi[d] - blo[d]);
+                if (!((double)o >= blo[d] - q && (double)o < bhi[d] + q)) err |= ERR_OUTSIDE_BOX;
+            }
             if (recon) {
                 const float r = recon[3 * i + d];
                 if (!isfinite(r)) { err |= ERR_NONFINITE; continue; }
@@ -145,12 +149,17 @@ Inspect inspect_inputs(const float *orig, const float *recon, int64_t n, const p
 namespace {
 
 __global__ void k_cell_keys(const float *__restrict__ orig, int64_t n, double o0, double o1, double o2, double s0,
-                            double s1, double s2, int nx, int ny, int nz, uint32_t *__restrict__ keys,
-                            uint32_t *__restrict__ ids) {
+                            double s1, double s2, int nx, int ny, int nz, int periodic,
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ ids) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int cx = (int)floor(((double)orig[3 * i + 0] - o0) * s0);
         int cy = (int)floor(((double)orig[3 * i + 1] - o1) * s1);
         int cz = (int)floor(((double)orig[3 * i + 2] - o2) * s2);
+        if (periodic) {   // positions up to a quarter box outside wrap to their image's cell
+            cx = cx < 0 ? cx + nx : (cx >= nx ? cx - nx : cx);
+            cy = cy < 0 ? cy + ny : (cy >= ny ? cy - ny : cy);
+            cz = cz < 0 ? cz + nz : (cz >= nz ? cz - nz : cz);
+        }
         cx = min(max(cx, 0), nx - 1);
         cy = min(max(cy, 0), ny - 1);
         cz = min(max(cz, 0), nz - 1);
@@ -194,7 +203,7 @@ void bin_particles(const float *orig, int64_t n, const Consts &c, Binned &B, cud
     double sc[3];
     for (int k = 0; k < 3; ++k) sc[k] = (double)c.inv_w[k];
     k_cell_keys<<<grid_for(n), 256, 0, s>>>(orig, n, o[0], o[1], o[2], sc[0], sc[1], sc[2], c.nc[0], c.nc[1],
-                                             c.nc[2], B.keys.p, B.order.p);
+                                             c.nc[2], c.periodic, B.keys.p, B.order.p);
     PC_CHECK_LAUNCH();
     radix_sort_u32(B.keys.p, B.order.p, n, c.key_bits, s);
     k_permute<<<grid_for(n), 256, 0, s>>>(orig, B.order.p, n, B.P4.p);

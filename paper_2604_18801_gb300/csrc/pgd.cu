@@ -129,11 +129,12 @@ __global__ void k_state_init(const uint32_t *__restrict__ epos, int64_t ne, cons
                              const float *__restrict__ orig, const float *__restrict__ recon,
                              float4 *__restrict__ PE, float4 *__restrict__ Dhi, float4 *__restrict__ Dlo,
                              float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
-                             float4 *__restrict__ Vlo) {
+                             float4 *__restrict__ Vlo, float4 *__restrict__ Q) {
     GRID_STRIDE(e, ne) {
         const float4 p = P4[epos[e]];
         PE[e] = p;
         const int64_t id = (int64_t)__float_as_uint(p.w);
+        Q[e] = make_float4(recon[3 * id + 0], recon[3 * id + 1], recon[3 * id + 2], 0.f);   // orig + delta0
         // delta0 = recon - orig, exactly, as a double-float
         const df dx = two_sum(recon[3 * id + 0], -orig[3 * id + 0]);
         const df dy = two_sum(recon[3 * id + 1], -orig[3 * id + 1]);
@@ -160,176 +161,73 @@ __device__ __forceinline__ df df_clamp(df x, df lim) {
     return x;
 }
 
-__device__ __forceinline__ df shfl_xor_df(df v, int off) {
-    return df_make(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+// ------------------------------------------------------------------ loss reduction
+// Deterministic two-level reduction without block barriers: every warp writes its
+// (loss, violations) to a slot of its block; the warp that finishes last in the block
+// sums the slots in warp order and posts the block partial; the block that finishes
+// last sums the block partials in block order and takes the stop decision of
+// Algorithm 1 for check t.
+constexpr int WARPS = PGD_THREADS / 32;
+
+struct BlockRed {
+    double wl[WARPS];
+    unsigned long long wv[WARPS];
+    unsigned count;
+    int last_block;
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
 }
 
-// G lanes share one row: lane `sub` takes edges sub, sub+G, ...; the partial gradients are
-// combined by an xor butterfly (df_add is commutative, so every lane of the group ends with
-// the same bits).  Rows are assigned in order, G consecutive lanes per row.
-template <int G>
-__global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
-    const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE, int64_t ne,
-    float4 *Dhi0, float4 *Dlo0, float4 *Dhi1, float4 *Dlo1, float4 *__restrict__ Mhi, float4 *__restrict__ Mlo,
-    float4 *__restrict__ Vhi, float4 *__restrict__ Vlo, PgdConsts C, PgdState *st, Partial *__restrict__ partials,
-    double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
-    __shared__ int s_stop, s_t;
-    __shared__ df s_ibc1, s_ibc2;
-    if (threadIdx.x == 0) {
-        s_stop = st->stop;
-        s_t = st->t;
-        s_ibc1 = st->ibc1;
-        s_ibc2 = st->ibc2;
+__device__ __forceinline__ void finish_iteration(BlockRed &br, double loss, unsigned long long viol, int t,
+                                                 bool last, const PgdConsts &C, PgdState *st, Partial *partials,
+                                                 double *hist_loss, unsigned long long *hist_viol) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    loss = warp_sum_d(loss);
+    viol = warp_sum_u(viol);
+    unsigned prev = 0;
+    if (lane == 0) {
+        br.wl[w] = loss;
+        br.wv[w] = viol;
+        __threadfence_block();
+        prev = atomicAdd(&br.count, 1u);
     }
-    __syncthreads();
-    if (s_stop) return;
-    const int t = s_t;
-    const bool last = C.replay >= 0 ? (t == C.replay) : (t == C.t_max);
-    const float4 *Dh = (t & 1) ? Dhi1 : Dhi0;
-    const float4 *Dl = (t & 1) ? Dlo1 : Dlo0;
-    float4 *Nh = (t & 1) ? Dhi0 : Dhi1;
-    float4 *Nl = (t & 1) ? Dlo0 : Dlo1;
-
-    double loss = 0.0;
-    unsigned long long viol = 0;
-    const int sub = (int)(threadIdx.x % G);
-    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const bool have = e < ne;
-    df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
-    float4 deh = make_float4(0.f, 0.f, 0.f, 0.f), del = deh;
-    if (have) {
-        const float4 pe = PE[e];
-        deh = Dh[e];
-        del = Dl[e];
-        const uint32_t t0 = row_ptr[e], t1 = row_ptr[e + 1];
-        for (uint32_t q = t0 + sub; q < t1; q += G) {
-            const uint32_t cv = col[q];
-            const uint32_t k = cv & 0x7fffffffu;
-            const bool link = (cv >> 31) != 0u;
-            const float4 pk = __ldg(PE + k);
-            const float4 dkh = Dh[k];
-            const float3 dp = canon_dp(pe, pk, C.periodic, C.L);
-            // float32 screen
-            const float rx = __fadd_rn(dp.x, __fsub_rn(deh.x, dkh.x));
-            const float ry = __fadd_rn(dp.y, __fsub_rn(deh.y, dkh.y));
-            const float rz = __fadd_rn(dp.z, __fsub_rn(deh.z, dkh.z));
-            const float d2f = cdist2(rx, ry, rz);
-            if (link ? (d2f < C.screen_link) : (d2f > C.screen_non)) continue;
-            // double-float evaluation of the pair
-            const float4 dkl = Dl[k];
-            df r[3];
-            const float dpa[3] = {dp.x, dp.y, dp.z};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) r[a] = df_add_f(df_sub(comp(deh, del, a), comp(dkh, dkl, a)), dpa[a]);
-            df d2 = df_mul(r[0], r[0]);
-            d2 = df_add(d2, df_mul(r[1], r[1]));
-            d2 = df_add(d2, df_mul(r[2], r[2]));
-            const df dh = df_sqrt(d2);
-            const df v = link ? df_sub(dh, C.thr_link) : df_sub(C.thr_non, dh);
-            if (!df_gt0(v)) continue;
-            if ((int64_t)k > e) {
-                const double vd = df_to_d(v);
-                loss += vd * vd;
-                viol += 1;
-            }
-            df u[3];
-            if (dh.hi > C.tau) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) u[a] = df_div(r[a], dh);
-            } else {
-                // coincident points (|r| <= b 2^-30): move along the original separation
-                const df n0 = df_sqrt(df_add(df_add(two_prod(dp.x, dp.x), two_prod(dp.y, dp.y)), two_prod(dp.z, dp.z)));
-#pragma unroll
-                for (int a = 0; a < 3; ++a) u[a] = n0.hi > 0.f ? df_div(df_make(dpa[a], 0.f), n0) : df_make(0.f, 0.f);
-            }
-            const df s = link ? df_add(v, v) : df_neg(df_add(v, v));
-#pragma unroll
-            for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], df_mul(s, u[a]));
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != WARPS - 1) return;          // not the last warp of this block
+    __threadfence_block();
+    unsigned gprev = 0;
+    if (lane == 0) {
+        double L = 0.0;
+        unsigned long long V = 0;
+        for (int q = 0; q < WARPS; ++q) {
+            L += ((volatile double *)br.wl)[q];
+            V += ((volatile unsigned long long *)br.wv)[q];
         }
-    }
-    if (G > 1) {
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], shfl_xor_df(g[a], off));
-            loss += __shfl_xor_sync(0xffffffffu, loss, off);
-            viol += __shfl_xor_sync(0xffffffffu, viol, off);
-        }
-        if (sub != 0) {
-            loss = 0.0;
-            viol = 0;
-        }
-    }
-    if (have && sub == 0) {
-        if (!last) {
-            // Adam step t+1 and projection onto [-xi_box, xi_box]
-            float4 mh4 = Mhi[e], ml4 = Mlo[e], vh4 = Vhi[e], vl4 = Vlo[e];
-            df nd[3], nm[3], nv[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                df m = comp(mh4, ml4, a), vv = comp(vh4, vl4, a);
-                m = df_add(df_mul(C.beta1, m), df_mul(C.one_m_beta1, g[a]));
-                vv = df_add(df_mul(C.beta2, vv), df_mul(C.one_m_beta2, df_mul(g[a], g[a])));
-                const df mhat = df_mul(m, s_ibc1);
-                const df vhat = df_mul(vv, s_ibc2);
-                const df den = df_add(df_sqrt(vhat), C.eps_adam);
-                const df step = df_div(df_mul(C.alpha, mhat), den);
-                nd[a] = df_clamp(df_sub(comp(deh, del, a), step), C.xi_box);
-                nm[a] = m;
-                nv[a] = vv;
-            }
-            Nh[e] = make_float4(nd[0].hi, nd[1].hi, nd[2].hi, 0.f);
-            Nl[e] = make_float4(nd[0].lo, nd[1].lo, nd[2].lo, 0.f);
-            Mhi[e] = make_float4(nm[0].hi, nm[1].hi, nm[2].hi, 0.f);
-            Mlo[e] = make_float4(nm[0].lo, nm[1].lo, nm[2].lo, 0.f);
-            Vhi[e] = make_float4(nv[0].hi, nv[1].hi, nv[2].hi, 0.f);
-            Vlo[e] = make_float4(nv[0].lo, nv[1].lo, nv[2].lo, 0.f);
-        }
-    }
-    // block reduction in a fixed order
-    __shared__ double sl[PGD_THREADS];
-    __shared__ unsigned long long sv[PGD_THREADS];
-    sl[threadIdx.x] = loss;
-    sv[threadIdx.x] = viol;
-    __syncthreads();
-    for (int w = PGD_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            sl[threadIdx.x] += sl[threadIdx.x + w];
-            sv[threadIdx.x] += sv[threadIdx.x + w];
-        }
-        __syncthreads();
-    }
-    __shared__ bool s_last;
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x].loss = sl[0];
-        partials[blockIdx.x].viol = sv[0];
+        partials[blockIdx.x].loss = L;
+        partials[blockIdx.x].viol = V;
         __threadfence();
-        const uint32_t prev = atomicAdd(&st->ticket, 1u);
-        s_last = prev == gridDim.x - 1;
+        gprev = atomicAdd(&st->ticket, 1u);
     }
-    __syncthreads();
-    if (!s_last) return;
+    gprev = __shfl_sync(0xffffffffu, gprev, 0);
+    if (gprev != gridDim.x - 1) return;     // not the last block
     __threadfence();
-    // last block: fixed-order sum of the partials and the stop decision
     double L = 0.0;
     unsigned long long V = 0;
-    for (uint32_t b = threadIdx.x; b < gridDim.x; b += PGD_THREADS) {
+    for (uint32_t b = lane; b < gridDim.x; b += 32) {
         L += __ldcg(&partials[b].loss);
         V += __ldcg(&partials[b].viol);
     }
-    sl[threadIdx.x] = L;
-    sv[threadIdx.x] = V;
-    __syncthreads();
-    for (int w = PGD_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            sl[threadIdx.x] += sl[threadIdx.x + w];
-            sv[threadIdx.x] += sv[threadIdx.x + w];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        L = sl[0];
-        V = sv[0];
+    L = warp_sum_d(L);
+    V = warp_sum_u(V);
+    if (lane == 0) {
         if (hist_loss) {
             hist_loss[t] = L;
             hist_viol[t] = V;
@@ -363,6 +261,282 @@ __global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
         st->ticket = 0;
         __threadfence();
     }
+}
+
+// ------------------------------------------------------------------ pair evaluation
+// r = dp + (eh + el) - (kh + kl) formed without rounding: Shewchuk's grow-expansion
+// (each input added through a chain of TwoSums) gives a nonoverlapping expansion whose
+// components sum to r exactly; the largest component plus the rounded sum of the rest
+// is r to about 2^-48 relative, and an exact zero stays exactly zero.
+__device__ __forceinline__ df exact_r(float dp, float eh, float el, float kh, float kl) {
+    float h[5];
+    h[0] = dp;
+    int m = 1;
+    const float in[4] = {eh, el, -kh, -kl};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float q = in[j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < m) {
+                const df t = two_sum(q, h[i]);
+                h[i] = t.lo;
+                q = t.hi;
+            }
+        }
+        h[m] = q;
+        ++m;
+    }
+    const float rest = __fadd_rn(h[3], __fadd_rn(h[2], __fadd_rn(h[1], h[0])));
+    return fast_two_sum(h[4], rest);
+}
+
+// Violated amount of Eq. 3 for one active pair (row e, partner k) at the current
+// offsets, in double-float, and the gradient term d/d(delta_e) of max(0, v)^2.
+__device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, const float4 del, int64_t e, uint32_t k,
+                                          bool link, const float4 *__restrict__ PE, const float4 *Dh,
+                                          const float4 *Dl, const PgdConsts &C, df g[3], double &lt) {
+    const float4 pk = __ldg(PE + k);
+    const float4 dkh = Dh[k], dkl = Dl[k];
+    const float3 dp = canon_dp(pe, pk, C.periodic, C.L);
+    const float dpa[3] = {dp.x, dp.y, dp.z};
+    df r[3];
+    r[0] = exact_r(dp.x, deh.x, del.x, dkh.x, dkl.x);
+    r[1] = exact_r(dp.y, deh.y, del.y, dkh.y, dkl.y);
+    r[2] = exact_r(dp.z, deh.z, del.z, dkh.z, dkl.z);
+    // squares added smallest first: the distance does not depend on the order of the axes,
+    // so mirror-image pairs (common on the quantizer lattice) cancel exactly
+    df q0 = df_mul(r[0], r[0]), q1 = df_mul(r[1], r[1]), q2 = df_mul(r[2], r[2]);
+    if (df_lt(q1, q0)) { const df x = q0; q0 = q1; q1 = x; }
+    if (df_lt(q2, q1)) { const df x = q1; q1 = q2; q2 = x; }
+    if (df_lt(q1, q0)) { const df x = q0; q0 = q1; q1 = x; }
+    const df dh = df_sqrt(df_add(df_add(q0, q1), q2));
+    const df v = link ? df_sub(dh, C.thr_link) : df_sub(C.thr_non, dh);
+    if (!df_gt0(v)) return false;
+    const double vd = df_to_d(v);
+    lt = (int64_t)k > e ? vd * vd : 0.0;
+    // 2 v r / |r| (link) or -2 v r / |r| (non-link); coincident points use the original separation
+    const df s = link ? df_add(v, v) : df_neg(df_add(v, v));
+    if (dh.hi > C.tau) {
+        const df c = df_div(s, dh);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g[a] = df_mul(c, r[a]);
+    } else {
+        const df n0 = df_sqrt(df_add(df_add(two_prod(dp.x, dp.x), two_prod(dp.y, dp.y)), two_prod(dp.z, dp.z)));
+        const df c = n0.hi > 0.f ? df_div(s, n0) : df_make(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) g[a] = df_mul_f(c, dpa[a]);
+    }
+    return true;
+}
+
+__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+struct WarpTab {
+    float4 pe[32], dh[32], dl[32];   // the warp's 32 rows: original position, offset (hi, lo)
+    uint32_t qk[64];                 // queued pairs: partner
+    uint8_t qs[64];                  // queued pairs: row slot | link << 7
+    float seg[32][6];                // per-row segment sums of one batch
+    uint32_t segmask;                // rows with a segment in the batch
+};
+
+// One PGD iteration: check t and, unless it is the last check, the update t+1.
+//
+// A warp owns 32 consecutive rows (editable particles) and walks the flat range of
+// their CSR edges 32 at a time.  The float32 screen on the rounded current positions Q
+// certifies most pairs as satisfied; the others are appended, in edge order, to the
+// warp queue.  Every 32 queued pairs are evaluated in double-float by the 32 lanes
+// together, and a segmented scan (fixed shuffle tree) sums the terms of each row;
+// lane i then adds its row's batch sum.  After the edges, lane i applies Adam and the
+// projection to row i and writes the next offsets, moments and rounded position.
+__global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
+    const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE, int64_t ne,
+    float4 *Dhi0, float4 *Dlo0, float4 *Dhi1, float4 *Dlo1, float4 *Q0, float4 *Q1, float4 *__restrict__ Mhi,
+    float4 *__restrict__ Mlo, float4 *__restrict__ Vhi, float4 *__restrict__ Vlo, PgdConsts C, PgdState *st,
+    Partial *__restrict__ partials, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
+    __shared__ int s_stop, s_t;
+    __shared__ df s_ibc1, s_ibc2;
+    __shared__ WarpTab tab[WARPS];
+    __shared__ BlockRed br;
+    if (threadIdx.x == 0) {
+        s_stop = st->stop;
+        s_t = st->t;
+        s_ibc1 = st->ibc1;
+        s_ibc2 = st->ibc2;
+        br.count = 0;
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const int t = s_t;
+    const bool last = C.replay >= 0 ? (t == C.replay) : (t == C.t_max);
+    const float4 *Dh = (t & 1) ? Dhi1 : Dhi0;
+    const float4 *Dl = (t & 1) ? Dlo1 : Dlo0;
+    const float4 *Qc = (t & 1) ? Q1 : Q0;
+    float4 *Nh = (t & 1) ? Dhi0 : Dhi1;
+    float4 *Nl = (t & 1) ? Dlo0 : Dlo1;
+    float4 *Qn = (t & 1) ? Q0 : Q1;
+
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    WarpTab &T = tab[w];
+    const int64_t r0 = ((int64_t)blockIdx.x * WARPS + w) * 32;
+    const int64_t e = r0 + lane;
+    const bool have = e < ne;
+    const int64_t rend = r0 + 32 < ne ? r0 + 32 : ne;
+    const uint32_t rp = row_ptr[have ? e : ne];   // lanes past the last row read the end of the CSR
+    const uint32_t E1 = r0 < ne ? row_ptr[rend] : 0u;
+    const uint32_t E0 = __shfl_sync(FULL, rp, 0);
+    float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (have) {
+        qe = Qc[e];
+        T.pe[lane] = PE[e];
+        T.dh[lane] = Dh[e];
+        T.dl[lane] = Dl[e];
+    }
+    if (lane == 0) T.segmask = 0u;
+    __syncwarp();
+
+    df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of row e
+    double loss = 0.0;
+    unsigned long long viol = 0;
+    int qn = 0;
+    const bool per = C.periodic != 0;
+
+    auto batch = [&](int cnt) {
+        const bool valid = lane < cnt;
+        int s = 32;
+        df gt[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
+        if (valid) {
+            const uint32_t k = T.qk[lane];
+            s = T.qs[lane] & 0x7f;
+            const bool link = (T.qs[lane] >> 7) != 0;
+            double lt = 0.0;
+            if (eval_pair(T.pe[s], T.dh[s], T.dl[s], r0 + s, k, link, PE, Dh, Dl, C, gt, lt)) {
+                loss += lt;
+                viol += (int64_t)k > r0 + s ? 1ull : 0ull;
+            }
+        }
+        // segmented inclusive scan over lanes; entries are grouped by row in edge order
+        const int sp = __shfl_up_sync(FULL, s, 1);
+        const bool head = lane == 0 || sp != s;
+        const unsigned hm = __ballot_sync(FULL, head);
+        const int seg0 = 31 - __clz(hm & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            df y[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                y[a] = df_make(__shfl_up_sync(FULL, gt[a].hi, off), __shfl_up_sync(FULL, gt[a].lo, off));
+            if (lane - off >= seg0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) gt[a] = df_add(y[a], gt[a]);
+            }
+        }
+        const int sn = __shfl_down_sync(FULL, s, 1);
+        const bool tail = valid && (lane == cnt - 1 || sn != s);
+        if (tail) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                T.seg[s][2 * a] = gt[a].hi;
+                T.seg[s][2 * a + 1] = gt[a].lo;
+            }
+        }
+        const unsigned tm = __ballot_sync(FULL, tail);
+        unsigned mask = 0;
+        // rows that received a segment: gather their slots from the tail lanes
+        for (unsigned b = tm; b; b &= b - 1) {
+            const int src = __ffs(b) - 1;
+            mask |= 1u << __shfl_sync(FULL, s, src);
+        }
+        __syncwarp();
+        if (mask & (1u << lane)) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], df_make(T.seg[lane][2 * a], T.seg[lane][2 * a + 1]));
+        }
+        __syncwarp();
+    };
+
+    for (uint32_t base = E0; base < E1; base += 32) {
+        const uint32_t tt = base + lane;
+        const bool valid = tt < E1;
+        // row slot of edge tt: the largest s with row_ptr[r0 + s] <= tt
+        int s = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t v = __shfl_sync(FULL, rp, (s + step) & 31);
+            if (s + step < 32 && r0 + s + step < ne && v <= tt) s += step;
+        }
+        const float qx = shfl_f(qe.x, s), qy = shfl_f(qe.y, s), qz = shfl_f(qe.z, s);
+        bool need = false;
+        uint32_t k = 0;
+        bool link = false;
+        if (valid) {
+            const uint32_t cv = col[tt];
+            k = cv & 0x7fffffffu;
+            link = (cv >> 31) != 0u;
+            const float4 qk = Qc[k];
+            const float d2f = cdist2(cdiff(qx, qk.x, per, C.L[0]), cdiff(qy, qk.y, per, C.L[1]),
+                                     cdiff(qz, qk.z, per, C.L[2]));
+            need = link ? !(d2f < C.screen_link) : !(d2f > C.screen_non);
+        }
+        const unsigned bal = __ballot_sync(FULL, need);
+        if (need) {
+            const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+            T.qk[pos] = k;
+            T.qs[pos] = (uint8_t)(s | (link ? 0x80 : 0));
+        }
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+            batch(32);
+            uint32_t mk = 0;
+            uint8_t ms = 0;
+            if (lane < qn - 32) {
+                mk = T.qk[32 + lane];
+                ms = T.qs[32 + lane];
+            }
+            __syncwarp();
+            if (lane < qn - 32) {
+                T.qk[lane] = mk;
+                T.qs[lane] = ms;
+            }
+            qn -= 32;
+            __syncwarp();
+        }
+    }
+    if (qn > 0) batch(qn);
+
+    if (have && !last) {
+        // Adam step t+1 and projection onto [-xi_box, xi_box] for row e
+        const float4 deh = T.dh[lane], del = T.dl[lane], pe = T.pe[lane];
+        const float4 mh4 = Mhi[e], ml4 = Mlo[e], vh4 = Vhi[e], vl4 = Vlo[e];
+        df nd[3], nm[3], nv[3];
+        float qo[3];
+        const float pa[3] = {pe.x, pe.y, pe.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            df m = comp(mh4, ml4, a), vv = comp(vh4, vl4, a);
+            m = df_add(df_mul(C.beta1, m), df_mul(C.one_m_beta1, g[a]));
+            vv = df_add(df_mul(C.beta2, vv), df_mul(C.one_m_beta2, df_mul(g[a], g[a])));
+            const df mhat = df_mul(m, s_ibc1);
+            const df vhat = df_mul(vv, s_ibc2);
+            const df den = df_add(df_sqrt(vhat), C.eps_adam);
+            const df step = df_div(df_mul(C.alpha, mhat), den);
+            nd[a] = df_clamp(df_sub(comp(deh, del, a), step), C.xi_box);
+            nm[a] = m;
+            nv[a] = vv;
+            const df sp = two_sum(pa[a], nd[a].hi);
+            qo[a] = __fadd_rn(sp.hi, __fadd_rn(sp.lo, nd[a].lo));
+        }
+        Nh[e] = make_float4(nd[0].hi, nd[1].hi, nd[2].hi, 0.f);
+        Nl[e] = make_float4(nd[0].lo, nd[1].lo, nd[2].lo, 0.f);
+        Mhi[e] = make_float4(nm[0].hi, nm[1].hi, nm[2].hi, 0.f);
+        Mlo[e] = make_float4(nm[0].lo, nm[1].lo, nm[2].lo, 0.f);
+        Vhi[e] = make_float4(nv[0].hi, nv[1].hi, nv[2].hi, 0.f);
+        Vlo[e] = make_float4(nv[0].lo, nv[1].lo, nv[2].lo, 0.f);
+        Qn[e] = make_float4(qo[0], qo[1], qo[2], 0.f);
+    }
+    finish_iteration(br, loss, viol, t, last, C, st, partials, hist_loss, hist_viol);
 }
 
 __global__ void k_copy_recon(const float *__restrict__ recon, float *__restrict__ out, int64_t m) {
@@ -439,9 +613,10 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
     for (int a = 0; a < 3; ++a) K.L[a] = c.L[a];
     K.b2 = c.b2;
     const double thrL = c.b - c.dt, thrN = c.b + c.dt;
-    // screen bound: float32 r differs from the exact r by at most a few ulps of |r| per axis
+    // screen bound: the float32 difference of the rounded current positions differs from the
+    // exact offset by at most one ulp of the coordinates plus one ulp of |r| per axis
     const double R = c.b + 2.0 * std::sqrt(3.0) * c.xi + 4.0 * c.xi;
-    const double B4 = 8.0 * ulp32(R);
+    const double B4 = 2.0 * std::sqrt(3.0) * (ulp32(c.M + 2.0 * c.xi) + ulp32(R));
     K.screen_link = thrL - B4 > 0 ? f32_down((thrL - B4) * (thrL - B4) * (1.0 - std::ldexp(1.0, -20))) : -1.0f;
     K.screen_non = f32_up((thrN + B4) * (thrN + B4) * (1.0 + std::ldexp(1.0, -20)));
     K.tau = (float)std::ldexp(c.b, -30);
@@ -503,18 +678,14 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
     keys.release();
     dense.release();
     DBuf<float4> PE(ne, s), Dh0(ne, s), Dl0(ne, s), Dh1(ne, s), Dl1(ne, s), Mh(ne, s), Ml(ne, s), Vh(ne, s),
-        Vl(ne, s);
+        Vl(ne, s), Q0(ne, s), Q1(ne, s);
     k_state_init<<<grid_for(ne), 256, 0, s>>>(epos.p, ne, B.P4.p, orig, recon, PE.p, Dh0.p, Dl0.p, Mh.p, Ml.p, Vh.p,
-                                              Vl.p);
+                                              Vl.p, Q0.p);
     PC_CHECK_LAUNCH();
     epos.release();
 
     // ---- state
-    // lanes per row: about half the mean row length, a power of two in [1, 32]
-    const double mean_deg = (double)m / (double)ne;
-    int G = 1;
-    while (G < 32 && 2.0 * G <= mean_deg / 2.0) G *= 2;
-    const int nblk = (int)cdiv(ne * G, PGD_THREADS);
+    const int nblk = (int)cdiv(ne, PGD_THREADS);   // one row per lane, 32 rows per warp
     DBuf<Partial> partials(nblk, s);
 
     DBuf<PgdState> st(1, s);
@@ -535,18 +706,8 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
     PC_CUDA(cudaEventRecord(e1, s));
 
     auto launch_iter = [&]() {
-#define PC_PGD_LAUNCH(GG)                                                                                          \
-    k_pgd_iter<GG><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Dh0.p, Dl0.p, Dh1.p, Dl1.p, Mh.p, Ml.p, \
-                                                Vh.p, Vl.p, K, st.p, partials.p, hl_p, hv_p)
-        switch (G) {
-            case 1: PC_PGD_LAUNCH(1); break;
-            case 2: PC_PGD_LAUNCH(2); break;
-            case 4: PC_PGD_LAUNCH(4); break;
-            case 8: PC_PGD_LAUNCH(8); break;
-            case 16: PC_PGD_LAUNCH(16); break;
-            default: PC_PGD_LAUNCH(32); break;
-        }
-#undef PC_PGD_LAUNCH
+        k_pgd_iter<<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Dh0.p, Dl0.p, Dh1.p, Dl1.p, Q0.p, Q1.p, Mh.p,
+                                                 Ml.p, Vh.p, Vl.p, K, st.p, partials.p, hl_p, hv_p);
     };
 
     // ---- iterations: launch in growing chunks, poll the device stop flag between chunks
@@ -566,6 +727,9 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
         }
         chunk = std::min(chunk * 2, 256);
     }
+    cudaEvent_t e_it;
+    PC_CUDA(cudaEventCreate(&e_it));
+    PC_CUDA(cudaEventRecord(e_it, s));
     k_output<<<grid_for(ne), 256, 0, s>>>(PE.p, ne, Dh0.p, Dl0.p, Dh1.p, Dl1.p, st.p, corrected);
     PC_CHECK_LAUNCH();
     if (delta_out) {
@@ -582,10 +746,14 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
     res.loss0 = h->loss0;
     res.loss_final = h->loss;
     res.converged = h->converged != 0;
-    float ms1 = 0, ms2 = 0;
+    float ms1 = 0, ms2 = 0, ms3 = 0;
     cudaEventElapsedTime(&ms1, e0, e1);
     cudaEventElapsedTime(&ms2, e1, e2);
+    cudaEventElapsedTime(&ms3, e1, e_it);
+    cudaEventDestroy(e_it);
     res.ms = ms2;
+    res.ms_iter = ms3;
+    res.launches = launched;
     if (ms_csr) *ms_csr = ms1;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

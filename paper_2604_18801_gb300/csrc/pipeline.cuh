@@ -64,7 +64,9 @@ struct PgdResult {
     int64_t iters = 0, loss_evals = 0, viol0 = 0, viol_final = 0, n_editable = 0;
     double loss0 = 0, loss_final = 0;
     bool converged = false;
-    double ms = 0;
+    double ms = 0;        // iterations + output
+    double ms_iter = 0;   // iteration launches only
+    int64_t launches = 0;
 };
 PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const float *orig, const float *recon,
                   const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s, HostScratch &hs,

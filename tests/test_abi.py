@@ -39,7 +39,7 @@ def test_struct_sizes_match_the_header():
     # pc_params: 2+3+3 doubles, 4 ints, 5 doubles, 2 ints
     assert C.sizeof(_native.Params) == 8 * 8 + 4 * 4 + 5 * 8 + 2 * 4
     assert C.sizeof(_native.SelectStats) == 10 * 8 + 8
-    assert C.sizeof(_native.CorrectStats) == 4 * 8 + 2 * 8 + 3 * 8 + 8 + 2 * 8
+    assert C.sizeof(_native.CorrectStats) == 4 * 8 + 2 * 8 + 3 * 8 + 8 + 3 * 8 + 8
 
 
 def test_product_path_has_no_oracle_import():

@@ -5,14 +5,17 @@ bytes) must be bit-exact.  Corrected coordinates must equal a float32
 rounding of a value within 1e-6 * xi of the oracle's float64 result:
 |gpu - (orig + delta_oracle)| <= ulp(gpu)/2 + 1e-6 xi.
 
-The projected Adam iteration on dense vulnerable-pair problems is chaotic:
-reordering the float64 sum alone moves the oracle's own coordinates from
-4e-15 xi (10 iterations) to 3e-12 xi (50 iterations), growing ~1.18x per
-iteration.  Coordinate parity is therefore checked at the converged answer
-where the dynamics are stable (halo-forest mode, short runs) and after a
-fixed number of replayed iterations otherwise; converged runs in every
-mode are checked through the invariants the method guarantees (membership,
-box, zero untightened loss after decoding).
+The projected Adam iteration can be ill-conditioned: Adam's normalised step
+turns a last-bit difference in a gradient near its epsilon into a visible
+move, and dense lattice-quantized problems amplify it further.  Two float64
+builds of the oracle that differ only in rounding choices agree to 1e-8 xi
+at convergence on md300 (HF) and cosmo4096 (HF), but only to 4e-5 xi on the
+32^3 HACC-shaped box at eps = 0.5 b (HF; they agree to 8e-10 xi after 60
+iterations).  Converged coordinates are therefore compared where the answer
+is well conditioned, and after a fixed number of replayed iterations
+elsewhere; every converged run, in every mode, is also checked through the
+invariants the method guarantees (membership, box, zero untightened loss
+after decoding).
 """
 import numpy as np
 import pytest
@@ -120,7 +123,7 @@ def _check_coords(gpu, w, delta, editable, iters):
     assert err.max() <= TOL * w.xi, f"max excess {err.max() / w.xi:.3e} xi"
 
 
-@pytest.mark.parametrize("name", ["cosmo4096", "md300", "hacc32k"])
+@pytest.mark.parametrize("name", ["cosmo4096", "md300"])
 def test_correct_halo_forest_converged_parity(cuda, name):
     import paper_2604_18801_gb300 as pc
     w = W_(name)
@@ -133,10 +136,12 @@ def test_correct_halo_forest_converged_parity(cuda, name):
     _check_coords(corr.cpu().numpy(), w, delta, ed, st["iters"])
 
 
-@pytest.mark.parametrize("mode,R", [(0, 10), (1, 10), (0, 3), (2, 5)])
-def test_correct_replayed_iterations_parity(cuda, mode, R):
+@pytest.mark.parametrize("name,mode,R", [("cosmo4096", 0, 10), ("cosmo4096", 1, 10), ("cosmo4096", 0, 30),
+                                         ("cosmo4096", 2, 5), ("md300", 0, 20), ("hacc32k", 2, 3),
+                                         ("hacc32k", 0, 3), ("fluid20k", 1, 10)])
+def test_correct_replayed_iterations_parity(cuda, name, mode, R):
     import paper_2604_18801_gb300 as pc
-    w = W_("cosmo4096")
+    w = W_(name)
     prm = w.params(mode=mode, replay_iters=R)
     corr, st, code = pc.correct(dev(w.orig, cuda), dev(w.recon, cuda), prm)
     assert st["iters"] == R
@@ -147,7 +152,7 @@ def test_correct_replayed_iterations_parity(cuda, mode, R):
 
 
 @pytest.mark.parametrize("name,mode", [("cosmo4096", 0), ("cosmo4096", 1), ("fluid20k", 0), ("md300", 1),
-                                       ("hacc32k", 0)])
+                                       ("hacc32k", 0), ("hacc32k", 2), ("fluid20k", 2)])
 def test_correct_converged_invariants(cuda, name, mode):
     import paper_2604_18801_gb300 as pc
     w = W_(name)
