@@ -180,6 +180,25 @@ pc_status pc_encode_edits(pc_ctx *ctx, const float *recon_dev, const float *corr
 pc_status pc_apply_edits(pc_ctx *ctx, const float *recon_dev, int64_t n, const uint8_t *stream_dev,
                          size_t nbytes, float *out_dev, void *stream);
 
+/* Allocation-free decoder.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory while decoding, for instance a simulation
+ * or analysis code that reserves nearly all of the GPU's memory for its own arena at
+ * start-up, or a caller working where device allocation is not allowed.  It computes
+ * exactly what pc_apply_edits computes, takes no context, and calls no cudaMalloc,
+ * cudaFree, pinned-host or pool allocation: its scratch (per-block flag counts and
+ * their prefix sums) is one file-scope device array of 512 KB that every GPU which
+ * loads the library holds until the process exits.
+ *   - n must be in [1, 16,777,216]; larger n returns PC_EINVAL.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before
+ *     any stream capture.
+ *   - All calls share the array and it keeps the last call's contents (each call
+ *     rewrites every entry it reads): calls that overlap on the GPU race, so issue
+ *     them on one stream or one after another.
+ *   - Synchronises the stream; PC_EFORMAT on a malformed stream. */
+pc_status pc_apply_edits_static(const float *recon_dev, int64_t n, const uint8_t *stream_dev, size_t nbytes,
+                                float *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
