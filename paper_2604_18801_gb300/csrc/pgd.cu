@@ -5,20 +5,23 @@
 // index e), so neighbouring particles sit close in memory.  A is stored as a
 // CSR by endpoint: row e lists every active partner k of e (col = k | link
 // bit << 31), rows sorted by the partner's position.  State per editable
-// particle, float4 each (w unused): original position PE (w = id bits),
-// offset delta = P_hat - P as a double-float (hi, lo) in two ping-pong
-// buffers, and the Adam moments m, v as double-floats.
+// particle, float4 each (w unused): original position PE (w = id bits); the
+// offset delta = P_hat - P as a double-float (hi, lo) and its float32 rounding
+// Q = fl(P + delta), both in two ping-pong buffers; the Adam moments m, v as
+// double-floats; one activity byte.
 //
-// One launch per iteration.  Thread e evaluates all active pairs of row e at
-// the current offsets: the gradient of row e is a fixed-order segment sum, so
-// no float atomics are used and the result is deterministic.  A float32
-// screen first discards pairs that are certainly not violated; the others are
-// evaluated in double-float.  The loss (each pair counted once, in the row of
-// its smaller dense index) and the violation count are reduced per block and
-// the last block sums the block partials in a fixed order and takes the stop
-// decision of Algorithm 1.  The Adam step of the same launch is written to the
-// other offset buffer, so when the check says "stop" the current buffer is
-// the answer and nothing has to be undone.
+// One iteration = k_pgd_iter (+ k_pgd_heavy when some rows have more than
+// HEAVY partners).  Warps take work items (groups of 32 light rows, or one
+// HEAVY-edge chunk of a heavy row) from a counter.  A float32 screen on Q
+// certifies most pairs as satisfied; the others are evaluated in
+// double-float, 32 at a time, and each row's gradient is a fixed-order sum
+// (segmented shuffle scan within a batch, batches in edge order, chunks in
+// chunk order), so no float atomics are used and the offsets are
+// deterministic.  The loss (each pair counted once, in the row of its smaller
+// dense index) is accumulated in fixed point and the violations are counted;
+// the last block takes the stop decision of Algorithm 1.  The Adam step of
+// the same launch is written to the other buffers, so when the check says
+// "stop" the current buffer is the answer and nothing has to be undone.
 #include <algorithm>
 #include <cmath>
 
@@ -51,6 +54,8 @@ struct PgdConsts {
     int replay;
     double loss_tol;
     double beta1_d, beta2_d;
+    double loss_unit;    // xi^2 2^-24: fixed-point unit of the loss
+    double inv_loss_unit;
 };
 
 struct PgdState {
@@ -64,6 +69,11 @@ struct PgdState {
     double loss, loss0;
     double b1p, b2p;    // beta^(t+1) for the update of this launch
     df ibc1, ibc2;      // 1 / (1 - beta^(t+1))
+    int32_t upd_t;      // check index of the last iteration launch
+    int32_t upd_on;     // 1 if that launch's update stands (no stop decided)
+    df upd_ibc1, upd_ibc2;
+    unsigned long long lfx, vacc;   // launch accumulators: loss (fixed point), violations
+    unsigned long long work;        // next work item of the launch
 };
 
 struct Partial {
@@ -129,18 +139,29 @@ __global__ void k_state_init(const uint32_t *__restrict__ epos, int64_t ne, cons
                              const float *__restrict__ orig, const float *__restrict__ recon,
                              float4 *__restrict__ PE, float4 *__restrict__ Dhi, float4 *__restrict__ Dlo,
                              float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
-                             float4 *__restrict__ Vlo, float4 *__restrict__ Q) {
+                             float4 *__restrict__ Vlo, float4 *__restrict__ Q, float4 *__restrict__ Dhi1,
+                             float4 *__restrict__ Dlo1, float4 *__restrict__ Q1, uint8_t *__restrict__ act,
+                             df xi_box) {
     GRID_STRIDE(e, ne) {
         const float4 p = P4[epos[e]];
         PE[e] = p;
         const int64_t id = (int64_t)__float_as_uint(p.w);
-        Q[e] = make_float4(recon[3 * id + 0], recon[3 * id + 1], recon[3 * id + 2], 0.f);   // orig + delta0
+        const float4 q = make_float4(recon[3 * id + 0], recon[3 * id + 1], recon[3 * id + 2], 0.f);   // orig + delta0
+        Q[e] = q;
+        Q1[e] = q;
         // delta0 = recon - orig, exactly, as a double-float
         const df dx = two_sum(recon[3 * id + 0], -orig[3 * id + 0]);
         const df dy = two_sum(recon[3 * id + 1], -orig[3 * id + 1]);
         const df dz = two_sum(recon[3 * id + 2], -orig[3 * id + 2]);
         Dhi[e] = make_float4(dx.hi, dy.hi, dz.hi, 0.f);
         Dlo[e] = make_float4(dx.lo, dy.lo, dz.lo, 0.f);
+        Dhi1[e] = make_float4(dx.hi, dy.hi, dz.hi, 0.f);
+        Dlo1[e] = make_float4(dx.lo, dy.lo, dz.lo, 0.f);
+        // a row must be updated from the first update on if the projection moves it
+        const df nl = df_neg(xi_box);
+        const bool out = df_lt(xi_box, dx) || df_lt(dx, nl) || df_lt(xi_box, dy) || df_lt(dy, nl) ||
+                         df_lt(xi_box, dz) || df_lt(dz, nl);
+        act[e] = out ? 1 : 0;
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         Mhi[e] = z;
         Mlo[e] = z;
@@ -162,105 +183,93 @@ __device__ __forceinline__ df df_clamp(df x, df lim) {
 }
 
 // ------------------------------------------------------------------ loss reduction
-// Deterministic two-level reduction without block barriers: every warp writes its
-// (loss, violations) to a slot of its block; the warp that finishes last in the block
-// sums the slots in warp order and posts the block partial; the block that finishes
-// last sums the block partials in block order and takes the stop decision of
-// Algorithm 1 for check t.
+// The tight loss is accumulated in fixed point: each violated pair adds
+// llrint(v^2 / unit) with unit = xi^2 2^-24 (v <= 2 sqrt3 xi + delta_t, so a term is
+// below 2^28 units and 2^35 terms fit in 63 bits), and the violated pairs are counted.
+// Integer sums do not depend on the order in which warps finish, so the result is
+// deterministic although work items are handed out dynamically.  Warps add into
+// their block's counters, the last warp of a block into the launch counters, and the
+// last block takes the stop decision of Algorithm 1 for check t (at eps_L = 0 the
+// count decides: the loss is zero exactly when no active pair is violated).
 constexpr int WARPS = PGD_THREADS / 32;
 
 struct BlockRed {
-    double wl[WARPS];
-    unsigned long long wv[WARPS];
+    unsigned long long lfx, viol;
     unsigned count;
-    int last_block;
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
-}
 __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
 }
 
-__device__ __forceinline__ void finish_iteration(BlockRed &br, double loss, unsigned long long viol, int t,
-                                                 bool last, const PgdConsts &C, PgdState *st, Partial *partials,
+__device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long long lfx, unsigned long long viol, int t,
+                                                 bool last, const PgdConsts &C, PgdState *st,
                                                  double *hist_loss, unsigned long long *hist_viol) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    loss = warp_sum_d(loss);
+    const int lane = threadIdx.x & 31;
+    lfx = warp_sum_u(lfx);
     viol = warp_sum_u(viol);
     unsigned prev = 0;
     if (lane == 0) {
-        br.wl[w] = loss;
-        br.wv[w] = viol;
+        if (lfx) atomicAdd(&br.lfx, lfx);
+        if (viol) atomicAdd(&br.viol, viol);
         __threadfence_block();
         prev = atomicAdd(&br.count, 1u);
     }
     prev = __shfl_sync(0xffffffffu, prev, 0);
     if (prev != WARPS - 1) return;          // not the last warp of this block
+    if (lane != 0) return;
     __threadfence_block();
-    unsigned gprev = 0;
-    if (lane == 0) {
-        double L = 0.0;
-        unsigned long long V = 0;
-        for (int q = 0; q < WARPS; ++q) {
-            L += ((volatile double *)br.wl)[q];
-            V += ((volatile unsigned long long *)br.wv)[q];
-        }
-        partials[blockIdx.x].loss = L;
-        partials[blockIdx.x].viol = V;
-        __threadfence();
-        gprev = atomicAdd(&st->ticket, 1u);
-    }
-    gprev = __shfl_sync(0xffffffffu, gprev, 0);
+    const unsigned long long bl = atomicAdd(&br.lfx, 0ull), bv = atomicAdd(&br.viol, 0ull);
+    if (bl) atomicAdd(&st->lfx, bl);
+    if (bv) atomicAdd(&st->vacc, bv);
+    __threadfence();
+    const unsigned gprev = atomicAdd(&st->ticket, 1u);
     if (gprev != gridDim.x - 1) return;     // not the last block
     __threadfence();
-    double L = 0.0;
-    unsigned long long V = 0;
-    for (uint32_t b = lane; b < gridDim.x; b += 32) {
-        L += __ldcg(&partials[b].loss);
-        V += __ldcg(&partials[b].viol);
+    const unsigned long long LF = atomicAdd(&st->lfx, 0ull), V = atomicAdd(&st->vacc, 0ull);
+    const double L = (double)LF * C.loss_unit;
+    if (hist_loss) {
+        hist_loss[t] = L;
+        hist_viol[t] = V;
     }
-    L = warp_sum_d(L);
-    V = warp_sum_u(V);
-    if (lane == 0) {
-        if (hist_loss) {
-            hist_loss[t] = L;
-            hist_viol[t] = V;
-        }
-        if (t == 0) {
-            st->loss0 = L;
-            st->viol0 = V;
-        }
-        st->loss = L;
-        st->viol = V;
-        const bool replay = C.replay >= 0;
-        const bool conv = L <= C.loss_tol;
-        if ((!replay && conv) || last) {
-            st->stop = 1;
-            st->final_buf = t & 1;
-            st->converged = conv ? 1 : 0;
-        } else {
-            st->t = t + 1;
-            const double b1 = st->b1p * C.beta1_d, b2 = st->b2p * C.beta2_d;
-            st->b1p = b1;
-            st->b2p = b2;
-            const double i1 = 1.0 / (1.0 - b1), i2 = 1.0 / (1.0 - b2);
-            df x, y;
-            x.hi = (float)i1;
-            x.lo = (float)(i1 - (double)x.hi);
-            y.hi = (float)i2;
-            y.lo = (float)(i2 - (double)y.hi);
-            st->ibc1 = x;
-            st->ibc2 = y;
-        }
-        st->ticket = 0;
-        __threadfence();
+    if (t == 0) {
+        st->loss0 = L;
+        st->viol0 = V;
     }
+    st->loss = L;
+    st->viol = V;
+    const bool replay = C.replay >= 0;
+    const bool conv = C.loss_tol > 0.0 ? (L <= C.loss_tol) : (V == 0);
+    st->upd_t = t;
+    st->upd_ibc1 = st->ibc1;
+    st->upd_ibc2 = st->ibc2;
+    if ((!replay && conv) || last) {
+        st->stop = 1;
+        st->final_buf = t & 1;
+        st->converged = conv ? 1 : 0;
+        st->upd_on = 0;
+    } else {
+        st->upd_on = 1;
+        st->t = t + 1;
+        const double b1 = st->b1p * C.beta1_d, b2 = st->b2p * C.beta2_d;
+        st->b1p = b1;
+        st->b2p = b2;
+        const double i1 = 1.0 / (1.0 - b1), i2 = 1.0 / (1.0 - b2);
+        df x, y;
+        x.hi = (float)i1;
+        x.lo = (float)(i1 - (double)x.hi);
+        y.hi = (float)i2;
+        y.lo = (float)(i2 - (double)y.hi);
+        st->ibc1 = x;
+        st->ibc2 = y;
+    }
+    st->lfx = 0;
+    st->vacc = 0;
+    st->work = 0;
+    st->ticket = 0;
+    __threadfence();
 }
 
 // ------------------------------------------------------------------ pair evaluation
@@ -314,7 +323,7 @@ __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, con
     const df v = link ? df_sub(dh, C.thr_link) : df_sub(C.thr_non, dh);
     if (!df_gt0(v)) return false;
     const double vd = df_to_d(v);
-    lt = (int64_t)k > e ? vd * vd : 0.0;
+    lt = (int64_t)k > e ? vd * vd * C.inv_loss_unit : 0.0;   // in loss units
     // 2 v r / |r| (link) or -2 v r / |r| (non-link); coincident points use the original separation
     const df s = link ? df_add(v, v) : df_neg(df_add(v, v));
     if (dh.hi > C.tau) {
@@ -333,27 +342,85 @@ __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, con
 __device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 struct WarpTab {
-    float4 pe[32], dh[32], dl[32];   // the warp's 32 rows: original position, offset (hi, lo)
-    uint32_t qk[64];                 // queued pairs: partner
-    uint8_t qs[64];                  // queued pairs: row slot | link << 7
+    int64_t row[32];                 // the warp's rows: dense index
+    uint32_t qk[96];                 // queued pairs: partner
+    uint8_t qs[96];                  // queued pairs: row slot | link << 7
     float seg[32][6];                // per-row segment sums of one batch
     uint32_t segmask;                // rows with a segment in the batch
 };
 
+// Adam step t+1 and projection onto [-xi_box, xi_box] for one row; writes the next
+// offsets, the moments and the next rounded position.
+// A row that has never had a gradient (and needs no projection) has zero moments and an
+// unchanged offset: Adam leaves it where it is, and both offset buffers already hold
+// that value, so nothing is read or written for it.
+__device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 *Dh, const float4 *Dl,
+                                         const float4 *__restrict__ PE, uint8_t *__restrict__ act, const df ibc1,
+                                         const df ibc2, const PgdConsts &C, float4 *Nh, float4 *Nl,
+                                         float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
+                                         float4 *__restrict__ Vlo, float4 *Qn) {
+    const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
+    const bool was = act[e] != 0;
+    if (!was && gz) return;
+    if (!was) act[e] = 1;
+    const float4 deh = Dh[e], del = Dl[e], pe = PE[e];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 mh4 = was ? Mhi[e] : z4, ml4 = was ? Mlo[e] : z4, vh4 = was ? Vhi[e] : z4, vl4 = was ? Vlo[e] : z4;
+    df nd[3], nm[3], nv[3];
+    float qo[3];
+    const float pa[3] = {pe.x, pe.y, pe.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        df m = comp(mh4, ml4, a), vv = comp(vh4, vl4, a);
+        m = df_add(df_mul(C.beta1, m), df_mul(C.one_m_beta1, g[a]));
+        vv = df_add(df_mul(C.beta2, vv), df_mul(C.one_m_beta2, df_mul(g[a], g[a])));
+        const df mhat = df_mul(m, ibc1);
+        const df vhat = df_mul(vv, ibc2);
+        const df den = df_add(df_sqrt(vhat), C.eps_adam);
+        const df step = df_div(df_mul(C.alpha, mhat), den);
+        nd[a] = df_clamp(df_sub(comp(deh, del, a), step), C.xi_box);
+        nm[a] = m;
+        nv[a] = vv;
+        const df sp = two_sum(pa[a], nd[a].hi);
+        qo[a] = __fadd_rn(sp.hi, __fadd_rn(sp.lo, nd[a].lo));
+    }
+    Nh[e] = make_float4(nd[0].hi, nd[1].hi, nd[2].hi, 0.f);
+    Nl[e] = make_float4(nd[0].lo, nd[1].lo, nd[2].lo, 0.f);
+    Mhi[e] = make_float4(nm[0].hi, nm[1].hi, nm[2].hi, 0.f);
+    Mlo[e] = make_float4(nm[0].lo, nm[1].lo, nm[2].lo, 0.f);
+    Vhi[e] = make_float4(nv[0].hi, nv[1].hi, nv[2].hi, 0.f);
+    Vlo[e] = make_float4(nv[0].lo, nv[1].lo, nv[2].lo, 0.f);
+    Qn[e] = make_float4(qo[0], qo[1], qo[2], 0.f);
+}
+
+// Rows with more than HEAVY partners are split into chunks of HEAVY edges.
+constexpr uint32_t HEAVY = 256;
+
+struct HeavyPlan {
+    int64_t n_light_blocks;          // blocks of 8 warps x 32 light rows
+    int64_t n_chunks;                // heavy chunks (one warp each)
+    const uint32_t *chunk_row;       // row of each chunk
+    const uint32_t *chunk_start;     // first edge of each chunk
+    float4 *chunk_g;                 // per chunk: gradient partial (hi at 2c, lo at 2c+1)
+};
+
 // One PGD iteration: check t and, unless it is the last check, the update t+1.
 //
-// A warp owns 32 consecutive rows (editable particles) and walks the flat range of
-// their CSR edges 32 at a time.  The float32 screen on the rounded current positions Q
-// certifies most pairs as satisfied; the others are appended, in edge order, to the
-// warp queue.  Every 32 queued pairs are evaluated in double-float by the 32 lanes
-// together, and a segmented scan (fixed shuffle tree) sums the terms of each row;
-// lane i then adds its row's batch sum.  After the edges, lane i applies Adam and the
-// projection to row i and writes the next offsets, moments and rounded position.
-__global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
+// Light warps own 32 consecutive rows (editable particles) and walk the flat range of
+// the light rows' CSR edges 32 at a time; heavy warps take one chunk of HEAVY edges of
+// a heavy row.  The float32 screen on the rounded current positions Q certifies most
+// pairs as satisfied; the others are appended, in edge order, to the warp queue.  Every
+// 32 queued pairs are evaluated in double-float by the 32 lanes together, and a
+// segmented scan (fixed shuffle tree) sums the terms of each row; the row's lane adds
+// its batch sum.  Light lane i then applies Adam to its row; a heavy warp writes its
+// chunk partial, and k_pgd_heavy adds the partials of a heavy row in chunk order.
+__global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
     const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE, int64_t ne,
     float4 *Dhi0, float4 *Dlo0, float4 *Dhi1, float4 *Dlo1, float4 *Q0, float4 *Q1, float4 *__restrict__ Mhi,
-    float4 *__restrict__ Mlo, float4 *__restrict__ Vhi, float4 *__restrict__ Vlo, PgdConsts C, PgdState *st,
-    Partial *__restrict__ partials, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
+    float4 *__restrict__ Mlo, float4 *__restrict__ Vhi, float4 *__restrict__ Vlo, uint8_t *__restrict__ act,
+    HeavyPlan H, PgdConsts C,
+    PgdState *st, double *__restrict__ hist_loss,
+    unsigned long long *__restrict__ hist_viol) {
     __shared__ int s_stop, s_t;
     __shared__ df s_ibc1, s_ibc2;
     __shared__ WarpTab tab[WARPS];
@@ -364,6 +431,8 @@ __global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
         s_ibc1 = st->ibc1;
         s_ibc2 = st->ibc2;
         br.count = 0;
+        br.lfx = 0;
+        br.viol = 0;
     }
     __syncthreads();
     if (s_stop) return;
@@ -379,26 +448,63 @@ __global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpTab &T = tab[w];
-    const int64_t r0 = ((int64_t)blockIdx.x * WARPS + w) * 32;
-    const int64_t e = r0 + lane;
-    const bool have = e < ne;
-    const int64_t rend = r0 + 32 < ne ? r0 + 32 : ne;
-    const uint32_t rp = row_ptr[have ? e : ne];   // lanes past the last row read the end of the CSR
-    const uint32_t E1 = r0 < ne ? row_ptr[rend] : 0u;
-    const uint32_t E0 = __shfl_sync(FULL, rp, 0);
+    unsigned long long lfx = 0;     // this lane's share of the tight loss, fixed point
+    unsigned long long viol = 0;
+    // work items: 32-row groups of light rows, then chunks of heavy rows; the grid is
+    // persistent (a few blocks per SM) and warps take items round-robin
+    const int64_t n_light_warps = (ne + 31) / 32;
+    const int64_t n_items = n_light_warps + H.n_chunks;
+    for (;;) {
+    unsigned long long itm = 0;
+    if (lane == 0) itm = atomicAdd(&st->work, 1ull);
+    const int64_t item = (int64_t)__shfl_sync(FULL, itm, 0);
+    if (item >= n_items) break;
+    const bool heavy_warp = item >= n_light_warps;
+
+    // Virtual edge range [0, VT): light warps map v to (row slot, edge) through the
+    // prefix vp of the light rows' degrees; a heavy warp maps v to edge start + v of slot 0.
+    int64_t e = -1;              // row of this lane (light warps) / of slot 0 (heavy warps, lane 0)
+    bool own = false;            // this lane applies Adam to row e
+    uint32_t rp = 0, vp = 0, VT = 0, hstart = 0;
+    int64_t chunk = -1;
     float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (have) {
-        qe = Qc[e];
-        T.pe[lane] = PE[e];
-        T.dh[lane] = Dh[e];
-        T.dl[lane] = Dl[e];
+    if (!heavy_warp) {
+        const int64_t r0 = item * 32;
+        e = r0 + lane;
+        const bool have = e < ne;
+        uint32_t deg = 0;
+        if (have) {
+            rp = row_ptr[e];
+            deg = row_ptr[e + 1] - rp;
+            qe = Qc[e];
+            T.row[lane] = e;
+        }
+        const uint32_t ld = deg <= HEAVY ? deg : 0u;
+        own = have && deg <= HEAVY;
+        // exclusive warp scan of the light degrees
+        uint32_t inc = ld;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, off);
+            if (lane >= off) inc += y;
+        }
+        vp = inc - ld;
+        VT = __shfl_sync(FULL, inc, 31);
+    } else {
+        chunk = item - n_light_warps;
+        if (chunk < H.n_chunks) {
+            const uint32_t row = H.chunk_row[chunk];
+            hstart = H.chunk_start[chunk];
+            const uint32_t rend = row_ptr[row + 1];
+            VT = min(HEAVY, rend - hstart);
+            e = row;
+            if (lane == 0) T.row[0] = row;
+            qe = Qc[row];
+        }
     }
-    if (lane == 0) T.segmask = 0u;
     __syncwarp();
 
-    df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of row e
-    double loss = 0.0;
-    unsigned long long viol = 0;
+    df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of the lane's row
     int qn = 0;
     const bool per = C.periodic != 0;
 
@@ -410,10 +516,11 @@ __global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
             const uint32_t k = T.qk[lane];
             s = T.qs[lane] & 0x7f;
             const bool link = (T.qs[lane] >> 7) != 0;
+            const int64_t er = T.row[s];
             double lt = 0.0;
-            if (eval_pair(T.pe[s], T.dh[s], T.dl[s], r0 + s, k, link, PE, Dh, Dl, C, gt, lt)) {
-                loss += lt;
-                viol += (int64_t)k > r0 + s ? 1ull : 0ull;
+            if (eval_pair(PE[er], Dh[er], Dl[er], er, k, link, PE, Dh, Dl, C, gt, lt)) {
+                lfx += (unsigned long long)llrint(lt);
+                viol += (int64_t)k > er ? 1ull : 0ull;
             }
         }
         // segmented inclusive scan over lanes; entries are grouped by row in edge order
@@ -443,7 +550,6 @@ __global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
         }
         const unsigned tm = __ballot_sync(FULL, tail);
         unsigned mask = 0;
-        // rows that received a segment: gather their slots from the tail lanes
         for (unsigned b = tm; b; b &= b - 1) {
             const int src = __ffs(b) - 1;
             mask |= 1u << __shfl_sync(FULL, s, src);
@@ -456,29 +562,20 @@ __global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
         __syncwarp();
     };
 
-    for (uint32_t base = E0; base < E1; base += 32) {
-        const uint32_t tt = base + lane;
-        const bool valid = tt < E1;
-        // row slot of edge tt: the largest s with row_ptr[r0 + s] <= tt
-        int s = 0;
+    // row slot and edge of virtual edge v (light: largest s with vp[s] <= v)
+    auto locate = [&](uint32_t v, int &s, uint32_t &tt) {
+        s = 0;
+        tt = hstart + v;
+        if (!heavy_warp) {
 #pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t v = __shfl_sync(FULL, rp, (s + step) & 31);
-            if (s + step < 32 && r0 + s + step < ne && v <= tt) s += step;
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t y = __shfl_sync(FULL, vp, (s + step) & 31);
+                if (s + step < 32 && y <= v) s += step;
+            }
+            tt = __shfl_sync(FULL, rp, s) + (v - __shfl_sync(FULL, vp, s));
         }
-        const float qx = shfl_f(qe.x, s), qy = shfl_f(qe.y, s), qz = shfl_f(qe.z, s);
-        bool need = false;
-        uint32_t k = 0;
-        bool link = false;
-        if (valid) {
-            const uint32_t cv = col[tt];
-            k = cv & 0x7fffffffu;
-            link = (cv >> 31) != 0u;
-            const float4 qk = Qc[k];
-            const float d2f = cdist2(cdiff(qx, qk.x, per, C.L[0]), cdiff(qy, qk.y, per, C.L[1]),
-                                     cdiff(qz, qk.z, per, C.L[2]));
-            need = link ? !(d2f < C.screen_link) : !(d2f > C.screen_non);
-        }
+    };
+    auto enqueue = [&](bool need, uint32_t k, int s, bool link) {
         const unsigned bal = __ballot_sync(FULL, need);
         if (need) {
             const int pos = qn + __popc(bal & ((1u << lane) - 1u));
@@ -486,57 +583,119 @@ __global__ void __launch_bounds__(PGD_THREADS) k_pgd_iter(
             T.qs[pos] = (uint8_t)(s | (link ? 0x80 : 0));
         }
         qn += __popc(bal);
+    };
+    // two edges per lane per trip: both partner loads are in flight before either is used
+    for (uint32_t base = 0; base < VT; base += 64) {
+        const uint32_t v0 = base + lane, v1 = base + 32 + lane;
+        int s0, s1;
+        uint32_t t0, t1;
+        locate(v0, s0, t0);
+        locate(v1, s1, t1);
+        const bool ok0 = v0 < VT, ok1 = v1 < VT;
+        const uint32_t c0v = ok0 ? col[t0] : 0u, c1v = ok1 ? col[t1] : 0u;
+        const uint32_t k0 = c0v & 0x7fffffffu, k1 = c1v & 0x7fffffffu;
+        const float4 q0 = ok0 ? Qc[k0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q1 = ok1 ? Qc[k1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float ax = shfl_f(qe.x, s0), ay = shfl_f(qe.y, s0), az = shfl_f(qe.z, s0);
+        const float bx = shfl_f(qe.x, s1), by = shfl_f(qe.y, s1), bz = shfl_f(qe.z, s1);
+        const bool l0 = (c0v >> 31) != 0u, l1 = (c1v >> 31) != 0u;
+        const float d0 = cdist2(cdiff(ax, q0.x, per, C.L[0]), cdiff(ay, q0.y, per, C.L[1]), cdiff(az, q0.z, per, C.L[2]));
+        const float d1 = cdist2(cdiff(bx, q1.x, per, C.L[0]), cdiff(by, q1.y, per, C.L[1]), cdiff(bz, q1.z, per, C.L[2]));
+        const bool n0 = ok0 && (l0 ? !(d0 < C.screen_link) : !(d0 > C.screen_non));
+        const bool n1 = ok1 && (l1 ? !(d1 < C.screen_link) : !(d1 > C.screen_non));
+        enqueue(n0, k0, s0, l0);
+        enqueue(n1, k1, s1, l1);
         __syncwarp();
-        if (qn >= 32) {
+        while (qn >= 32) {
             batch(32);
-            uint32_t mk = 0;
-            uint8_t ms = 0;
-            if (lane < qn - 32) {
-                mk = T.qk[32 + lane];
-                ms = T.qs[32 + lane];
-            }
+            uint32_t mk[2] = {0u, 0u};
+            uint8_t ms[2] = {0, 0};
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (lane + 32 * h < qn - 32) {
+                    mk[h] = T.qk[32 + lane + 32 * h];
+                    ms[h] = T.qs[32 + lane + 32 * h];
+                }
             __syncwarp();
-            if (lane < qn - 32) {
-                T.qk[lane] = mk;
-                T.qs[lane] = ms;
-            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (lane + 32 * h < qn - 32) {
+                    T.qk[lane + 32 * h] = mk[h];
+                    T.qs[lane + 32 * h] = ms[h];
+                }
             qn -= 32;
             __syncwarp();
         }
     }
     if (qn > 0) batch(qn);
 
-    if (have && !last) {
-        // Adam step t+1 and projection onto [-xi_box, xi_box] for row e
-        const float4 deh = T.dh[lane], del = T.dl[lane], pe = T.pe[lane];
-        const float4 mh4 = Mhi[e], ml4 = Mlo[e], vh4 = Vhi[e], vl4 = Vlo[e];
-        df nd[3], nm[3], nv[3];
-        float qo[3];
-        const float pa[3] = {pe.x, pe.y, pe.z};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            df m = comp(mh4, ml4, a), vv = comp(vh4, vl4, a);
-            m = df_add(df_mul(C.beta1, m), df_mul(C.one_m_beta1, g[a]));
-            vv = df_add(df_mul(C.beta2, vv), df_mul(C.one_m_beta2, df_mul(g[a], g[a])));
-            const df mhat = df_mul(m, s_ibc1);
-            const df vhat = df_mul(vv, s_ibc2);
-            const df den = df_add(df_sqrt(vhat), C.eps_adam);
-            const df step = df_div(df_mul(C.alpha, mhat), den);
-            nd[a] = df_clamp(df_sub(comp(deh, del, a), step), C.xi_box);
-            nm[a] = m;
-            nv[a] = vv;
-            const df sp = two_sum(pa[a], nd[a].hi);
-            qo[a] = __fadd_rn(sp.hi, __fadd_rn(sp.lo, nd[a].lo));
-        }
-        Nh[e] = make_float4(nd[0].hi, nd[1].hi, nd[2].hi, 0.f);
-        Nl[e] = make_float4(nd[0].lo, nd[1].lo, nd[2].lo, 0.f);
-        Mhi[e] = make_float4(nm[0].hi, nm[1].hi, nm[2].hi, 0.f);
-        Mlo[e] = make_float4(nm[0].lo, nm[1].lo, nm[2].lo, 0.f);
-        Vhi[e] = make_float4(nv[0].hi, nv[1].hi, nv[2].hi, 0.f);
-        Vlo[e] = make_float4(nv[0].lo, nv[1].lo, nv[2].lo, 0.f);
-        Qn[e] = make_float4(qo[0], qo[1], qo[2], 0.f);
+    if (!heavy_warp) {
+        if (own && !last) adam_row(e, g, Dh, Dl, PE, act, s_ibc1, s_ibc2, C, Nh, Nl, Mhi, Mlo, Vhi, Vlo, Qn);
+    } else if (chunk >= 0 && chunk < H.n_chunks && lane == 0) {
+        H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, 0.f);
+        H.chunk_g[2 * chunk + 1] = make_float4(g[0].lo, g[1].lo, g[2].lo, 0.f);
     }
-    finish_iteration(br, loss, viol, t, last, C, st, partials, hist_loss, hist_viol);
+    __syncwarp();
+    }   // work items
+    finish_iteration(br, lfx, viol, t, last, C, st, hist_loss, hist_viol);
+}
+
+// Heavy rows: sum the chunk partials in chunk order and apply Adam (same update as
+// light rows).  Runs after k_pgd_iter of the same iteration, with the step and buffers
+// that launch used (recorded in the state by its last block).
+__global__ void k_pgd_heavy(const uint32_t *__restrict__ hrow, const uint32_t *__restrict__ hc0, int64_t nh,
+                            const float4 *__restrict__ chunk_g, const float4 *__restrict__ PE, float4 *Dhi0,
+                            float4 *Dlo0, float4 *Dhi1, float4 *Dlo1, float4 *Q0, float4 *Q1,
+                            float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
+                            float4 *__restrict__ Vlo, uint8_t *__restrict__ act, PgdConsts C,
+                            const PgdState *st) {
+    if (!st->upd_on) return;
+    const int t = st->upd_t;
+    const df ibc1 = st->upd_ibc1, ibc2 = st->upd_ibc2;
+    const float4 *Dh = (t & 1) ? Dhi1 : Dhi0;
+    const float4 *Dl = (t & 1) ? Dlo1 : Dlo0;
+    float4 *Nh = (t & 1) ? Dhi0 : Dhi1;
+    float4 *Nl = (t & 1) ? Dlo0 : Dlo1;
+    float4 *Qn = (t & 1) ? Q0 : Q1;
+    GRID_STRIDE(i, nh) {
+        const uint32_t e = hrow[i];
+        df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
+        for (uint32_t c = hc0[i]; c < hc0[i + 1]; ++c) {
+            const float4 h = chunk_g[2 * c], l = chunk_g[2 * c + 1];
+            g[0] = df_add(g[0], df_make(h.x, l.x));
+            g[1] = df_add(g[1], df_make(h.y, l.y));
+            g[2] = df_add(g[2], df_make(h.z, l.z));
+        }
+        adam_row(e, g, Dh, Dl, PE, act, ibc1, ibc2, C, Nh, Nl, Mhi, Mlo, Vhi, Vlo, Qn);
+    }
+}
+
+// CSR-side plan of the heavy rows: chunk counts, row list, chunk list.
+__global__ void k_heavy_count(const uint32_t *__restrict__ row_ptr, int64_t ne, uint32_t *__restrict__ nchunk,
+                              uint32_t *__restrict__ isheavy) {
+    GRID_STRIDE(e, ne) {
+        const uint32_t d = row_ptr[e + 1] - row_ptr[e];
+        const bool h = d > HEAVY;
+        nchunk[e] = h ? (d + HEAVY - 1) / HEAVY : 0u;
+        isheavy[e] = h ? 1u : 0u;
+    }
+}
+
+__global__ void k_heavy_fill(const uint32_t *__restrict__ row_ptr, int64_t ne, const uint32_t *__restrict__ nchunk,
+                             const uint32_t *__restrict__ c0, const uint32_t *__restrict__ isheavy,
+                             const uint32_t *__restrict__ hpos, uint32_t *__restrict__ chunk_row,
+                             uint32_t *__restrict__ chunk_start, uint32_t *__restrict__ hrow,
+                             uint32_t *__restrict__ hc0) {
+    GRID_STRIDE(e, ne) {
+        if (!isheavy[e]) continue;
+        const uint32_t c = c0[e];
+        for (uint32_t j = 0; j < nchunk[e]; ++j) {
+            chunk_row[c + j] = (uint32_t)e;
+            chunk_start[c + j] = row_ptr[e] + j * HEAVY;
+        }
+        hrow[hpos[e]] = (uint32_t)e;
+        hc0[hpos[e]] = c;
+    }
 }
 
 __global__ void k_copy_recon(const float *__restrict__ recon, float *__restrict__ out, int64_t m) {
@@ -634,6 +793,8 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
     K.loss_tol = p->loss_tol;
     K.beta1_d = p->beta1;
     K.beta2_d = p->beta2;
+    K.loss_unit = c.xi * c.xi * std::ldexp(1.0, -24);
+    K.inv_loss_unit = 1.0 / K.loss_unit;
 
     if (nA == 0) {
         // nothing to enforce: the reconstruction stands, zero iterations
@@ -679,14 +840,42 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
     dense.release();
     DBuf<float4> PE(ne, s), Dh0(ne, s), Dl0(ne, s), Dh1(ne, s), Dl1(ne, s), Mh(ne, s), Ml(ne, s), Vh(ne, s),
         Vl(ne, s), Q0(ne, s), Q1(ne, s);
+    DBuf<uint8_t> act(ne, s);
     k_state_init<<<grid_for(ne), 256, 0, s>>>(epos.p, ne, B.P4.p, orig, recon, PE.p, Dh0.p, Dl0.p, Mh.p, Ml.p, Vh.p,
-                                              Vl.p, Q0.p);
+                                              Vl.p, Q0.p, Dh1.p, Dl1.p, Q1.p, act.p, K.xi_box);
     PC_CHECK_LAUNCH();
     epos.release();
 
     // ---- state
-    const int nblk = (int)cdiv(ne, PGD_THREADS);   // one row per lane, 32 rows per warp
-    DBuf<Partial> partials(nblk, s);
+    // heavy rows (more than HEAVY partners) are split into chunks of HEAVY edges
+    DBuf<uint32_t> nchunk(ne, s), isheavy(ne, s), c0(ne, s), hpos(ne, s), tot2(2, s);
+    k_heavy_count<<<grid_for(ne), 256, 0, s>>>(row_ptr.p, ne, nchunk.p, isheavy.p);
+    PC_CHECK_LAUNCH();
+    scan_exclusive_u32(nchunk.p, c0.p, ne, tot2.p, s);
+    scan_exclusive_u32(isheavy.p, hpos.p, ne, tot2.p + 1, s);
+    uint32_t tots[2];
+    memcpy(tots, read_back(hs, tot2.p, 2 * sizeof(uint32_t), s), sizeof(tots));
+    const int64_t n_chunks = tots[0], n_heavy = tots[1];
+    DBuf<uint32_t> chunk_row(n_chunks, s), chunk_start(n_chunks, s), hrow(n_heavy, s), hc0(n_heavy + 1, s);
+    DBuf<float4> chunk_g(2 * n_chunks, s);
+    if (n_heavy > 0) {
+        k_heavy_fill<<<grid_for(ne), 256, 0, s>>>(row_ptr.p, ne, nchunk.p, c0.p, isheavy.p, hpos.p, chunk_row.p,
+                                                  chunk_start.p, hrow.p, hc0.p);
+        PC_CHECK_LAUNCH();
+        PC_CUDA(cudaMemcpyAsync(hc0.p + n_heavy, tot2.p, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    nchunk.release();
+    isheavy.release();
+    c0.release();
+    hpos.release();
+    HeavyPlan HP;
+    HP.n_light_blocks = cdiv(ne, PGD_THREADS);      // one row per lane, 32 rows per warp
+    HP.n_chunks = n_chunks;
+    HP.chunk_row = chunk_row.p;
+    HP.chunk_start = chunk_start.p;
+    HP.chunk_g = chunk_g.p;
+    const int64_t n_items = cdiv(ne, 32) + n_chunks;
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS), (int64_t)num_sms() * 4));
 
     DBuf<PgdState> st(1, s);
     const int64_t hist_n = (p->replay_iters >= 0 ? p->replay_iters : p->t_max) + 1;
@@ -707,7 +896,12 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
 
     auto launch_iter = [&]() {
         k_pgd_iter<<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Dh0.p, Dl0.p, Dh1.p, Dl1.p, Q0.p, Q1.p, Mh.p,
-                                                 Ml.p, Vh.p, Vl.p, K, st.p, partials.p, hl_p, hv_p);
+                                                 Ml.p, Vh.p, Vl.p, act.p, HP, K, st.p, hl_p, hv_p);
+        if (n_heavy > 0) {
+            PC_CHECK_LAUNCH();
+            k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, Dh0.p, Dl0.p, Dh1.p,
+                                                          Dl1.p, Q0.p, Q1.p, Mh.p, Ml.p, Vh.p, Vl.p, act.p, K, st.p);
+        }
     };
 
     // ---- iterations: launch in growing chunks, poll the device stop flag between chunks
