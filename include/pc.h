@@ -161,6 +161,24 @@ pc_status pc_correct_detail(pc_ctx *ctx, const float *orig_dev, const float *rec
                             double *delta_dev, double *hist_loss_dev, uint64_t *hist_viol_dev,
                             pc_correct_stats *stats, void *stream);
 
+/* Batched form: independent blocks of particles, concatenated in orig/recon/corrected
+ * (block k owns rows [offset_k, offset_k + n_k); the blocks must tile the arrays in
+ * order: offset_0 = 0, offset_{k+1} = offset_k + n_k).  Each block has its own
+ * parameters (b, xi, mode, box, Adam settings).  Every stage runs once over all
+ * blocks -- one sort, one pair search, one selection, and PGD iterations in which all
+ * blocks that have not stopped advance together -- and blocks never interact: each
+ * block's corrected coordinates are bit-identical to pc_correct on that block alone.
+ * stats (host, may be NULL) receives nblocks entries.  Returns PC_OK when every block
+ * converged, PC_WARN_NOT_CONVERGED otherwise; errors name the offending block.  This
+ * is a batching layer around the method, not part of the paper. */
+typedef struct {
+    int64_t offset;
+    int64_t n;
+    pc_params params;
+} pc_block;
+pc_status pc_correct_batch(pc_ctx *ctx, const float *orig_dev, const float *recon_dev, const pc_block *blocks,
+                           int32_t nblocks, float *corrected_dev, pc_correct_stats *stats, void *stream);
+
 /* Edit stream v1 (Algorithm 1 last lines; Sec. 3.3).  Little endian:
  *   0  "PCE1" | 4 u32 version=1 | 8 u64 n | 16 u32 m | 20 u32 mode | 24 u32 periodic | 28 u32 0
  *   32 f64 xi | 40 u64 flagged | 48 u64 flag_bytes=ceil(n/8) | 56 u64 code_bytes

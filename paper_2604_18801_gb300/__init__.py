@@ -18,7 +18,8 @@ import torch
 from . import _native
 from ._native import PcError, make_params, struct_dict
 
-__all__ = ["Context", "fof_labels", "select_constraints", "Constraints", "correct", "correct_detail", "encode_edits",
+__all__ = ["Context", "fof_labels", "select_constraints", "Constraints", "correct", "correct_detail", "correct_batch",
+           "encode_edits",
            "apply_edits", "PcError", "make_params", "default_context"]
 
 MODES = {"VP": 0, "SC": 1, "HF": 2}
@@ -169,6 +170,33 @@ def correct_detail(orig: torch.Tensor, recon: torch.Tensor, params, constraints:
     d = struct_dict(st)
     k = d["iters"] + 1
     return out, delta, hl[:k], hv[:k], d, code
+
+
+def correct_batch(orig: torch.Tensor, recon: torch.Tensor, sizes, params_list, out: torch.Tensor = None,
+                  ctx: Context = None):
+    """Batched correction of independent blocks concatenated along the rows of orig/recon.
+
+    sizes[k] rows belong to block k (in order); params_list[k] are its parameters.
+    Returns (corrected, [stats per block], status)."""
+    _xyz(orig, "orig")
+    _xyz(recon, "recon")
+    if len(sizes) != len(params_list) or sum(int(n) for n in sizes) != orig.shape[0]:
+        raise ValueError("sizes must match params_list and sum to the number of rows")
+    ctx = ctx or default_context(orig.device.index)
+    nb = len(sizes)
+    blocks = (_native.Block * nb)()
+    at = 0
+    for k, (n, prm) in enumerate(zip(sizes, params_list)):
+        blocks[k].offset = at
+        blocks[k].n = int(n)
+        blocks[k].params = _params(prm)
+        at += int(n)
+    out = torch.empty_like(orig) if out is None else _xyz(out, "out")
+    stats = (_native.CorrectStats * nb)()
+    code = _native.lib().pc_correct_batch(ctx.h, orig.data_ptr(), recon.data_ptr(), blocks, nb, out.data_ptr(), stats,
+                                          _stream(orig.device))
+    _native.check(code, "pc_correct_batch", allow_warn=True)
+    return out, [struct_dict(st) for st in stats], code
 
 
 def encode_edits(recon: torch.Tensor, corrected: torch.Tensor, params, ctx: Context = None) -> torch.Tensor:

@@ -44,6 +44,10 @@ class CorrectStats(C.Structure):
                 ("pgd_launches", C.c_int64)]
 
 
+class Block(C.Structure):
+    _fields_ = [("offset", C.c_int64), ("n", C.c_int64), ("params", Params)]
+
+
 def struct_dict(s) -> dict:
     return {k: getattr(s, k) for k, _ in s._fields_ if not k.endswith("_")}
 
@@ -76,10 +80,11 @@ def lib():
         L.pc_constraints_free.restype = None
         L.pc_correct.argtypes = [vp, vp, vp, i64, P, vp, vp, C.POINTER(CorrectStats), vp]
         L.pc_correct_detail.argtypes = [vp, vp, vp, i64, P, vp, vp, vp, vp, vp, C.POINTER(CorrectStats), vp]
+        L.pc_correct_batch.argtypes = [vp, vp, vp, C.POINTER(Block), C.c_int32, vp, C.POINTER(CorrectStats), vp]
         L.pc_encode_edits.argtypes = [vp, vp, vp, i64, P, vp, sz, C.POINTER(sz), vp]
         L.pc_apply_edits.argtypes = [vp, vp, i64, vp, sz, vp, vp]
         for f in ("pc_ctx_create", "pc_fof_labels", "pc_select_constraints", "pc_constraints_copy", "pc_correct",
-                  "pc_correct_detail",
+                  "pc_correct_detail", "pc_correct_batch",
                   "pc_encode_edits", "pc_apply_edits"):
             getattr(L, f).restype = C.c_int
         _lib = L

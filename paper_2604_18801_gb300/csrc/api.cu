@@ -139,6 +139,12 @@ __global__ void k_count_roots(const uint32_t *__restrict__ lab, int64_t n, unsig
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+__global__ void k_pairs_per_block(const unsigned long long *__restrict__ A, int64_t m, const int64_t *__restrict__ off,
+                                  int nb, unsigned long long *__restrict__ cnt) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + find_block(off, nb, (int64_t)(A[r] >> 32)), 1ull);
+}
+
 int64_t count_roots(const uint32_t *lab, int64_t n, cudaStream_t s, HostScratch &hs) {
     DBuf<unsigned long long> d(1, s);
     PC_CUDA(cudaMemsetAsync(d.p, 0, sizeof(unsigned long long), s));
@@ -160,13 +166,11 @@ struct pc_ctx {
 };
 
 struct pc_constraints {
-    int64_t n;
-    int mode;
-    Consts c;
+    BlockSet S;
     Binned B;
-    DBuf<unsigned long long> A;
-    int64_t nA;
-    pc_select_stats stats;
+    DBuf<unsigned long long> A;     // active pairs (min_pos << 32 | max_pos)
+    int64_t nA = 0;
+    std::vector<pc_select_stats> stats;   // per block
 };
 
 namespace {
@@ -196,80 +200,192 @@ void use_device(pc_ctx *ctx) {
 
 void release_to_default_stream(pc_constraints *h) {
     // handles outlive the caller's stream: free their memory on the default stream
-    h->B.keys.s = 0;
-    h->B.order.s = 0;
-    h->B.P4.s = 0;
-    h->B.cell_start.s = 0;
-    h->B.items.s = 0;
+    h->S.release_to_default_stream();
+    h->B.release_to_default_stream();
     h->A.s = 0;
 }
 
-// Binning, pair search, union-find and selection for params->mode (Sec. 3.2, 3.3).
-void do_select(pc_ctx *ctx, const float *orig, int64_t n, const pc_params *p, cudaStream_t s, pc_constraints *h) {
+void check_block_inputs(const BlockSet &S) {
+    for (int b = 0; b < S.nb; ++b) {
+        try {
+            check_inspect(S.ins[b]);
+        } catch (const Fail &f) {
+            if (S.nb > 1) set_error("block " + std::to_string(b) + ": " + pc_last_error());
+            throw;
+        }
+    }
+}
+
+// Binning, pair search, union-find and selection for every block of S (Sec. 3.2, 3.3).
+// S.prm and S.off must be set; fills S and the handle.
+void do_select(pc_ctx *ctx, const float *orig, cudaStream_t s, pc_constraints *h) {
+    BlockSet &S = h->S;
+    const int nb = S.nb;
+    const int64_t n = S.n;
     cudaEvent_t e0, e1;
     PC_CUDA(cudaEventCreate(&e0));
     PC_CUDA(cudaEventCreate(&e1));
     PC_CUDA(cudaEventRecord(e0, s));
-    Inspect ins = inspect_inputs(orig, nullptr, n, p, s, ctx->hs);
-    check_inspect(ins);
-    h->n = n;
-    h->mode = p->mode;
-    h->c = make_consts(p, ins, n, true);
-    const Consts &c = h->c;
-    bin_particles(orig, n, c, h->B, s, ctx->hs);
-    DBuf<unsigned long long> counts(CNT_N, s);
+    inspect_blocks(orig, nullptr, S, s, ctx->hs);
+    check_block_inputs(S);
+    setup_blocks(S, true, s);
+    bin_particles(orig, S, h->B, s, ctx->hs);
+    bool any_fof = false, any_safe = false;
+    for (int b = 0; b < nb; ++b) {
+        any_fof |= S.prm[b].mode == PC_MODE_HF;
+        any_safe |= S.prm[b].mode != PC_MODE_VP;
+    }
+    DBuf<unsigned long long> counts(CNT_N, s), bc(4 * nb + nb, s);
     DBuf<uint32_t> err(1, s);
     PC_CUDA(cudaMemsetAsync(counts.p, 0, CNT_N * sizeof(unsigned long long), s));
+    PC_CUDA(cudaMemsetAsync(bc.p, 0, 5 * nb * sizeof(unsigned long long), s));
     PC_CUDA(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s));
     DBuf<uint32_t> fof, safe;
-    if (p->mode == PC_MODE_HF) {
+    if (any_fof) {
         fof.alloc(n, s);
         uf_init(fof.p, n, s);
     }
-    if (p->mode != PC_MODE_VP) {
+    if (any_safe) {
         safe.alloc(n, s);
         uf_init(safe.p, n, s);
     }
-    pair_pass_union(h->B, c, fof.p, safe.p, counts.p, err.p, s);
+    pair_pass_union(h->B, S, fof.p, safe.p, counts.p, err.p, s, nb > 1 ? bc.p : nullptr);
     if (fof.p) uf_flatten(fof.p, n, s);
     if (safe.p) uf_flatten(safe.p, n, s);
     unsigned long long cnt[CNT_N];
     memcpy(cnt, read_back(ctx->hs, counts.p, sizeof(cnt), s), sizeof(cnt));
     const uint32_t e1v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
     if (e1v & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
-    memset(&h->stats, 0, sizeof(h->stats));
-    h->stats.n_links = (int64_t)cnt[CNT_LINKS];
-    h->stats.n_safe = (int64_t)cnt[CNT_SAFE];
-    h->stats.n_pb = (int64_t)cnt[CNT_PB];
-    h->stats.n_pc = (int64_t)cnt[CNT_PC];
-    h->stats.n_vulnerable = (int64_t)(cnt[CNT_PB] + cnt[CNT_PC]);
-    if (fof.p) h->stats.n_halos = count_roots(fof.p, n, s, ctx->hs);
-    if (safe.p) h->stats.n_safe_comps = count_roots(safe.p, n, s, ctx->hs);
     const uint64_t capA = std::max<uint64_t>(1, cnt[CNT_PB] + cnt[CNT_PC]);
-    const uint64_t capC = p->mode == PC_MODE_HF ? std::max<uint64_t>(1, cnt[CNT_PB]) : 0;
+    const uint64_t capC = any_fof ? std::max<uint64_t>(1, cnt[CNT_PB]) : 0;
     h->A.alloc(capA, s);
     DBuf<unsigned long long> C(capC, s);
-    pair_pass_emit(h->B, c, p->mode, fof.p, safe.p, h->A.p, capA, C.p, capC, counts.p, err.p, s);
-    memcpy(cnt, read_back(ctx->hs, counts.p, sizeof(cnt), s), sizeof(cnt));
+    pair_pass_emit(h->B, S, fof.p, safe.p, h->A.p, capA, C.p, capC, counts.p, err.p, s);
+    unsigned long long cnt2[CNT_N];
+    memcpy(cnt2, read_back(ctx->hs, counts.p, sizeof(cnt2), s), sizeof(cnt2));
     const uint32_t e2v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
     if (e2v & ERR_INDEX) fail(PC_ECUDA, "pair emission overflowed its count");
-    int64_t nA = (int64_t)cnt[CNT_A];
-    if (p->mode == PC_MODE_HF) {
-        const int64_t nf = halo_forest(h->B, c, safe.p, C.p, (int64_t)cnt[CNT_C], h->A.p, nA, err.p, s, ctx->hs);
-        h->stats.n_forest = nf;
-        nA += nf;
+    int64_t nA = (int64_t)cnt2[CNT_A];
+    int64_t n_forest = 0;
+    if (any_fof) {
+        n_forest = halo_forest(h->B, S, safe.p, C.p, (int64_t)cnt2[CNT_C], h->A.p, nA, err.p, s, ctx->hs);
+        nA += n_forest;
         const uint32_t e3v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
         if (e3v & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
     }
     h->nA = nA;
-    h->stats.n_active = nA;
+    // statistics per block
+    h->stats.assign(nb, pc_select_stats());
+    for (auto &st : h->stats) memset(&st, 0, sizeof(st));
+    if (nb == 1) {
+        pc_select_stats &st = h->stats[0];
+        st.n_links = (int64_t)cnt[CNT_LINKS];
+        st.n_safe = (int64_t)cnt[CNT_SAFE];
+        st.n_pb = (int64_t)cnt[CNT_PB];
+        st.n_pc = (int64_t)cnt[CNT_PC];
+        st.n_vulnerable = (int64_t)(cnt[CNT_PB] + cnt[CNT_PC]);
+        st.n_active = nA;
+        st.n_forest = n_forest;
+        if (fof.p) st.n_halos = count_roots(fof.p, n, s, ctx->hs);
+        if (safe.p) st.n_safe_comps = count_roots(safe.p, n, s, ctx->hs);
+    } else {
+        if (nA > 0) {
+            const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nA, 256), (int64_t)num_sms() * 8));
+            k_pairs_per_block<<<g, 256, 0, s>>>(h->A.p, nA, S.doff.p, nb, bc.p + 4 * nb);
+            PC_CHECK_LAUNCH();
+        }
+        const unsigned long long *hc =
+            (const unsigned long long *)read_back(ctx->hs, bc.p, 5 * nb * sizeof(unsigned long long), s);
+        for (int b = 0; b < nb; ++b) {
+            pc_select_stats &st = h->stats[b];
+            st.n_links = (int64_t)hc[4 * b + 0];
+            st.n_safe = (int64_t)hc[4 * b + 1];
+            st.n_pb = (int64_t)hc[4 * b + 2];
+            st.n_pc = (int64_t)hc[4 * b + 3];
+            st.n_vulnerable = st.n_pb + st.n_pc;
+            st.n_active = (int64_t)hc[4 * nb + b];
+        }
+    }
     PC_CUDA(cudaEventRecord(e1, s));
     PC_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    h->stats.ms = ms;
+    for (auto &st : h->stats) st.ms = ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+}
+
+void single_block(BlockSet &S, int64_t n, const pc_params *p) {
+    S.nb = 1;
+    S.n = n;
+    S.prm.assign(1, *p);
+    S.off = {0, n};
+}
+
+// The correction pass over a block set (Algorithm 1 up to Delta for every block).
+void correct_blocks(pc_ctx *ctx, const float *orig, const float *recon, BlockSet &&S, const pc_constraints *given,
+                    float *corrected, double *delta_dev, double *hist_loss, uint64_t *hist_viol,
+                    pc_correct_stats *stats, bool &all_converged, cudaStream_t s) {
+    pc_constraints *own = nullptr;
+    try {
+        const pc_constraints *h = given;
+        // validate against the reconstruction (bound, finiteness, box) and get per-block M
+        BlockSet &V = S;
+        inspect_blocks(orig, recon, V, s, ctx->hs);
+        check_block_inputs(V);
+        if (h) {
+            if (h->S.n != V.n || h->S.nb != V.nb) fail(PC_EINVAL, "constraints were selected for another problem");
+        } else {
+            own = new pc_constraints();
+            own->S.nb = V.nb;
+            own->S.n = V.n;
+            own->S.prm = V.prm;
+            own->S.off = V.off;
+            do_select(ctx, orig, s, own);
+            h = own;
+        }
+        std::vector<Consts> cp(V.nb);
+        for (int b = 0; b < V.nb; ++b) {
+            cp[b] = make_consts(&V.prm[b], V.ins[b], V.off[b + 1] - V.off[b], true);
+            if (!(cp[b].xi_box_d > 0.0))
+                fail(PC_EINVAL, (V.nb > 1 ? "block " + std::to_string(b) + ": " : std::string()) +
+                                    "xi too small for float32 coordinates of this magnitude (empty projection box)");
+        }
+        PgdRun r = run_pgd(h->B, h->S, cp, orig, recon, h->A.p, h->nA, corrected, s, ctx->hs, delta_dev, hist_loss,
+                           (unsigned long long *)hist_viol);
+        all_converged = true;
+        for (int b = 0; b < V.nb; ++b) {
+            const PgdResult &pr = r.blocks[b];
+            all_converged &= pr.converged;
+            if (!stats) continue;
+            pc_correct_stats &st = stats[b];
+            memset(&st, 0, sizeof(st));
+            st.iters = pr.iters;
+            st.loss_evals = pr.loss_evals;
+            st.viol0 = pr.viol0;
+            st.viol_final = pr.viol_final;
+            st.loss0 = pr.loss0;
+            st.loss_final = pr.loss_final;
+            st.n_vulnerable = h->stats[b].n_vulnerable;
+            st.n_active = h->stats[b].n_active;
+            st.n_editable = pr.n_editable;
+            st.converged = pr.converged ? 1 : 0;
+            st.ms_setup = (given ? 0.0 : h->stats[b].ms) + r.ms_csr;
+            st.ms_pgd = r.ms;
+            st.ms_pgd_iter = r.ms_iter;
+            st.pgd_launches = r.launches;
+        }
+    } catch (...) {
+        if (own) {
+            release_to_default_stream(own);
+            delete own;
+        }
+        throw;
+    }
+    if (own) {
+        release_to_default_stream(own);
+        delete own;
+    }
 }
 
 }  // namespace
@@ -335,18 +451,20 @@ pc_status pc_fof_labels(pc_ctx *ctx, const float *xyz, int64_t n, const pc_param
         check_params(p, n, false);
         if (!xyz || !labels) fail(PC_EINVAL, "NULL buffer");
         cudaStream_t s = (cudaStream_t)stream;
-        Inspect ins = inspect_inputs(xyz, nullptr, n, p, s, ctx->hs);
-        check_inspect(ins);
-        Consts c = make_consts(p, ins, n, false);
+        BlockSet S;
+        single_block(S, n, p);
+        inspect_blocks(xyz, nullptr, S, s, ctx->hs);
+        check_block_inputs(S);
+        setup_blocks(S, false, s);
         Binned B;
-        bin_particles(xyz, n, c, B, s, ctx->hs);
+        bin_particles(xyz, S, B, s, ctx->hs);
         DBuf<unsigned long long> counts(CNT_N, s);
         DBuf<uint32_t> err(1, s);
         PC_CUDA(cudaMemsetAsync(counts.p, 0, CNT_N * sizeof(unsigned long long), s));
         PC_CUDA(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s));
         uint32_t *par = (uint32_t *)labels;
         uf_init(par, n, s);
-        pair_pass_union(B, c, par, nullptr, counts.p, err.p, s);
+        pair_pass_union(B, S, par, nullptr, counts.p, err.p, s);
         uf_flatten(par, n, s);
         const uint32_t ev = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
         if (ev & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
@@ -365,9 +483,10 @@ pc_status pc_select_constraints(pc_ctx *ctx, const float *orig, int64_t n, const
         if (!orig || !out) fail(PC_EINVAL, "NULL argument");
         *out = nullptr;
         h = new pc_constraints();
-        do_select(ctx, orig, n, p, (cudaStream_t)stream, h);
+        single_block(h->S, n, p);
+        do_select(ctx, orig, (cudaStream_t)stream, h);
         release_to_default_stream(h);
-        if (stats) *stats = h->stats;
+        if (stats) *stats = h->stats[0];
         *out = h;
         return PC_OK;
     });
@@ -383,7 +502,7 @@ pc_status pc_constraints_copy(pc_ctx *ctx, const pc_constraints *h, uint32_t *i_
     return guarded([&]() -> pc_status {
         use_device(ctx);
         if (!h || !i_out || !j_out) fail(PC_EINVAL, "NULL argument");
-        export_pairs(h->B, h->c, h->A.p, h->nA, i_out, j_out, link_out, (cudaStream_t)stream);
+        export_pairs(h->B, h->S, h->A.p, h->nA, i_out, j_out, link_out, (cudaStream_t)stream);
         return PC_OK;
     });
 }
@@ -402,54 +521,52 @@ pc_status pc_correct(pc_ctx *ctx, const float *orig, const float *recon, int64_t
 pc_status pc_correct_detail(pc_ctx *ctx, const float *orig, const float *recon, int64_t n, const pc_params *p,
                             const pc_constraints *given, float *corrected, double *delta_dev, double *hist_loss,
                             uint64_t *hist_viol, pc_correct_stats *stats, void *stream) {
-    pc_constraints *own = nullptr;
-    pc_status st = guarded([&]() -> pc_status {
+    return guarded([&]() -> pc_status {
         use_device(ctx);
         check_params(p, n, true);
         if (!orig || !recon || !corrected) fail(PC_EINVAL, "NULL buffer");
-        cudaStream_t s = (cudaStream_t)stream;
-        const auto t0 = std::chrono::steady_clock::now();
-        Inspect ins = inspect_inputs(orig, recon, n, p, s, ctx->hs);
-        check_inspect(ins);
-        const pc_constraints *h = given;
-        if (h) {
-            if (h->n != n) fail(PC_EINVAL, "constraints were selected for another particle count");
-        } else {
-            own = new pc_constraints();
-            do_select(ctx, orig, n, p, s, own);
-            h = own;
-        }
-        Consts cp = make_consts(p, ins, n, true);
-        if (!(cp.xi_box_d > 0.0))
-            fail(PC_EINVAL, "xi too small for float32 coordinates of this magnitude (empty projection box)");
-        double ms_csr = 0;
-        PgdResult r = run_pgd(h->B, cp, p, orig, recon, h->A.p, h->nA, corrected, s, ctx->hs, &ms_csr, delta_dev,
-                              hist_loss, (unsigned long long *)hist_viol);
-        if (stats) {
-            memset(stats, 0, sizeof(*stats));
-            stats->iters = r.iters;
-            stats->loss_evals = r.loss_evals;
-            stats->viol0 = r.viol0;
-            stats->viol_final = r.viol_final;
-            stats->loss0 = r.loss0;
-            stats->loss_final = r.loss_final;
-            stats->n_vulnerable = h->stats.n_vulnerable;
-            stats->n_active = h->nA;
-            stats->n_editable = r.n_editable;
-            stats->converged = r.converged ? 1 : 0;
-            stats->ms_setup = (given ? 0.0 : h->stats.ms) + ms_csr;
-            stats->ms_pgd = r.ms;
-            stats->ms_pgd_iter = r.ms_iter;
-            stats->pgd_launches = r.launches;
-        }
-        (void)t0;
-        return r.converged ? PC_OK : PC_WARN_NOT_CONVERGED;
+        BlockSet S;
+        single_block(S, n, p);
+        bool conv = false;
+        correct_blocks(ctx, orig, recon, std::move(S), given, corrected, delta_dev, hist_loss, hist_viol, stats, conv,
+                       (cudaStream_t)stream);
+        return conv ? PC_OK : PC_WARN_NOT_CONVERGED;
     });
-    if (own) {
-        release_to_default_stream(own);
-        delete own;
-    }
-    return st;
+}
+
+pc_status pc_correct_batch(pc_ctx *ctx, const float *orig, const float *recon, const pc_block *blocks,
+                           int32_t nblocks, float *corrected, pc_correct_stats *stats, void *stream) {
+    return guarded([&]() -> pc_status {
+        use_device(ctx);
+        if (!orig || !recon || !corrected || !blocks) fail(PC_EINVAL, "NULL argument");
+        if (nblocks < 1 || nblocks > (1 << 20)) fail(PC_EINVAL, "nblocks must be in [1, 2^20]");
+        BlockSet S;
+        S.nb = nblocks;
+        S.prm.resize(nblocks);
+        S.off.resize(nblocks + 1);
+        int64_t at = 0;
+        for (int b = 0; b < nblocks; ++b) {
+            if (blocks[b].offset != at)
+                fail(PC_EINVAL, "blocks must tile the arrays in order: block " + std::to_string(b) +
+                                    " does not start where the previous one ends");
+            try {
+                check_params(&blocks[b].params, blocks[b].n, true);
+            } catch (const Fail &) {
+                set_error("block " + std::to_string(b) + ": " + pc_last_error());
+                throw;
+            }
+            S.prm[b] = blocks[b].params;
+            S.off[b] = at;
+            at += blocks[b].n;
+        }
+        S.off[nblocks] = at;
+        S.n = at;
+        if (at >= (int64_t)0x7fffffff) fail(PC_EINVAL, "more than 2^31-1 particles in one batch");
+        bool conv = false;
+        correct_blocks(ctx, orig, recon, std::move(S), nullptr, corrected, nullptr, nullptr, nullptr, stats, conv,
+                       (cudaStream_t)stream);
+        return conv ? PC_OK : PC_WARN_NOT_CONVERGED;
+    });
 }
 
 pc_status pc_encode_edits(pc_ctx *ctx, const float *recon, const float *corrected, int64_t n, const pc_params *p,

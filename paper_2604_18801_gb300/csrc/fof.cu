@@ -47,14 +47,25 @@ struct InspectDev {
     uint32_t hi[3];
 };
 
-__global__ void k_inspect(const float *__restrict__ orig, const float *__restrict__ recon, int64_t n, double xi,
-                          int periodic, double lo0, double lo1, double lo2, double hi0, double hi1, double hi2,
-                          InspectDev *out) {
-    const double blo[3] = {lo0, lo1, lo2}, bhi[3] = {hi0, hi1, hi2};
+struct InspectIn {      // per block: what the check needs
+    double xi;
+    double lo[3], hi[3];
+    int periodic;
+};
+
+constexpr int TILE = 4096;   // particles per CTA of the inspection (tiles never straddle blocks)
+
+__global__ void k_inspect(const float *__restrict__ orig, const float *__restrict__ recon,
+                          const int2 *__restrict__ tiles, const int64_t *__restrict__ off,
+                          const InspectIn *__restrict__ bin, InspectDev *out) {
+    const int b = tiles[blockIdx.x].x;
+    const int64_t start = off[b] + (int64_t)tiles[blockIdx.x].y * TILE;
+    const int64_t end = min(off[b + 1], start + TILE);
+    const InspectIn B = bin[b];
     uint32_t err = 0;
     float mabs = 0.f;
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = start + threadIdx.x; i < end; i += blockDim.x) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float o = orig[3 * i + d];
@@ -63,19 +74,19 @@ __global__ void k_inspect(const float *__restrict__ orig, const float *__restric
             mn[d] = fminf(mn[d], o);
             mx[d] = fmaxf(mx[d], o);
             // periodic: within a quarter box of the box, so one +-L gives the minimum image
-            if (periodic) {
-                const double q = 0.25 * (bhi[d] - blo[d]);
-                if (!((double)o >= blo[d] - q && (double)o < bhi[d] + q)) err |= ERR_OUTSIDE_BOX;
+            if (B.periodic) {
+                const double q = 0.25 * (B.hi[d] - B.lo[d]);
+                if (!((double)o >= B.lo[d] - q && (double)o < B.hi[d] + q)) err |= ERR_OUTSIDE_BOX;
             }
             if (recon) {
                 const float r = recon[3 * i + d];
                 if (!isfinite(r)) { err |= ERR_NONFINITE; continue; }
                 mabs = fmaxf(mabs, fabsf(r));
-                if (fabs((double)r - (double)o) > xi) err |= ERR_BOUND;
+                if (fabs((double)r - (double)o) > B.xi) err |= ERR_BOUND;
             }
         }
     }
-    // warp reductions then one atomic per warp
+    // warp reductions then one atomic per warp into the block's record
     const unsigned FULL = 0xffffffffu;
     err = __reduce_or_sync(FULL, err);
     uint32_t ma = __reduce_max_sync(FULL, __float_as_uint(mabs));
@@ -86,12 +97,13 @@ __global__ void k_inspect(const float *__restrict__ orig, const float *__restric
         h[d] = __reduce_max_sync(FULL, ord_f32(mx[d]));
     }
     if ((threadIdx.x & 31) == 0) {
-        if (err) atomicOr(&out->err, err);
-        atomicMax(&out->maxabs, ma);
+        InspectDev *o = out + b;
+        if (err) atomicOr(&o->err, err);
+        atomicMax(&o->maxabs, ma);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            atomicMin(&out->lo[d], l[d]);
-            atomicMax(&out->hi[d], h[d]);
+            atomicMin(&o->lo[d], l[d]);
+            atomicMax(&o->hi[d], h[d]);
         }
     }
 }
@@ -116,46 +128,112 @@ void *read_back(HostScratch &hs, const void *dev, size_t bytes, cudaStream_t s) 
     return h;
 }
 
-Inspect inspect_inputs(const float *orig, const float *recon, int64_t n, const pc_params *p, cudaStream_t s,
-                       HostScratch &hs) {
-    DBuf<InspectDev> d(1, s);
-    InspectDev init;
-    init.err = 0;
-    init.maxabs = 0;
-    for (int k = 0; k < 3; ++k) {
-        init.lo[k] = 0xffffffffu;
-        init.hi[k] = 0u;
+void inspect_blocks(const float *orig, const float *recon, BlockSet &S, cudaStream_t s, HostScratch &hs) {
+    const int nb = S.nb;
+    std::vector<InspectIn> bin(nb);
+    std::vector<int2> tiles;
+    for (int b = 0; b < nb; ++b) {
+        const pc_params *p = &S.prm[b];
+        bin[b].xi = p->xi;
+        bin[b].periodic = p->periodic;
+        for (int d = 0; d < 3; ++d) {
+            bin[b].lo[d] = p->box_lo[d];
+            bin[b].hi[d] = p->box_hi[d];
+        }
+        const int64_t nt = cdiv(S.off[b + 1] - S.off[b], TILE);
+        for (int64_t t = 0; t < nt; ++t) tiles.push_back(make_int2(b, (int)t));
     }
-    InspectDev *h0 = (InspectDev *)host_scratch(hs, sizeof(InspectDev));
-    *h0 = init;
-    PC_CUDA(cudaMemcpyAsync(d.p, h0, sizeof(InspectDev), cudaMemcpyHostToDevice, s));
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), (int64_t)num_sms() * 8));
-    k_inspect<<<grid, 256, 0, s>>>(orig, recon, n, p->xi, p->periodic, p->box_lo[0], p->box_lo[1], p->box_lo[2],
-                                   p->box_hi[0], p->box_hi[1], p->box_hi[2], d.p);
-    PC_CHECK_LAUNCH();
-    InspectDev *h = (InspectDev *)read_back(hs, d.p, sizeof(InspectDev), s);
-    Inspect r;
-    r.err = h->err;
-    uint32_t ma = h->maxabs;
-    memcpy(&r.maxabs, &ma, 4);
-    for (int k = 0; k < 3; ++k) {
-        r.lo[k] = unord_f32(h->lo[k]);
-        r.hi[k] = unord_f32(h->hi[k]);
+    // one staging area: offsets | per-block inputs | tiles | results
+    const size_t b_off = (nb + 1) * sizeof(int64_t), b_in = nb * sizeof(InspectIn), b_t = tiles.size() * sizeof(int2),
+                 b_out = nb * sizeof(InspectDev);
+    uint8_t *h = (uint8_t *)host_scratch(hs, b_off + b_in + b_t + b_out);
+    memcpy(h, S.off.data(), b_off);
+    memcpy(h + b_off, bin.data(), b_in);
+    memcpy(h + b_off + b_in, tiles.data(), b_t);
+    InspectDev *init = (InspectDev *)(h + b_off + b_in + b_t);
+    for (int b = 0; b < nb; ++b) {
+        init[b].err = 0;
+        init[b].maxabs = 0;
+        for (int k = 0; k < 3; ++k) {
+            init[b].lo[k] = 0xffffffffu;
+            init[b].hi[k] = 0u;
+        }
     }
-    return r;
+    S.doff.alloc(nb + 1, s);
+    DBuf<uint8_t> d(b_in + b_t + b_out, s);
+    PC_CUDA(cudaMemcpyAsync(S.doff.p, h, b_off, cudaMemcpyHostToDevice, s));
+    PC_CUDA(cudaMemcpyAsync(d.p, h + b_off, b_in + b_t + b_out, cudaMemcpyHostToDevice, s));
+    InspectIn *din = (InspectIn *)d.p;
+    int2 *dt = (int2 *)(d.p + b_in);
+    InspectDev *dout = (InspectDev *)(d.p + b_in + b_t);
+    if (!tiles.empty()) {
+        k_inspect<<<(unsigned)tiles.size(), 256, 0, s>>>(orig, recon, dt, S.doff.p, din, dout);
+        PC_CHECK_LAUNCH();
+    }
+    InspectDev *r = (InspectDev *)read_back(hs, dout, b_out, s);
+    S.ins.assign(nb, Inspect());
+    for (int b = 0; b < nb; ++b) {
+        S.ins[b].err = r[b].err;
+        uint32_t ma = r[b].maxabs;
+        memcpy(&S.ins[b].maxabs, &ma, 4);
+        for (int k = 0; k < 3; ++k) {
+            S.ins[b].lo[k] = unord_f32(r[b].lo[k]);
+            S.ins[b].hi[k] = unord_f32(r[b].hi[k]);
+        }
+    }
+}
+
+void setup_blocks(BlockSet &S, bool window, cudaStream_t s) {
+    const int nb = S.nb;
+    S.c.resize(nb);
+    std::vector<BlockDev> h(nb);
+    int64_t base = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t n = S.off[b + 1] - S.off[b];
+        S.c[b] = make_consts(&S.prm[b], S.ins[b], n, window);
+        const Consts &c = S.c[b];
+        BlockDev &d = h[b];
+        memset(&d, 0, sizeof(d));
+        d.off = S.off[b];
+        d.n = n;
+        d.cell_base = base;
+        for (int k = 0; k < 3; ++k) {
+            d.origin[k] = (double)c.origin[k];
+            d.inv_w[k] = (double)c.inv_w[k];
+            d.L[k] = c.L[k];
+            d.nc[k] = c.nc[k];
+        }
+        d.b2 = c.b2;
+        d.lo2 = c.lo2;
+        d.hi2 = c.hi2;
+        d.periodic = c.periodic;
+        d.mode = S.prm[b].mode;
+        base += c.ncells;
+    }
+    if (base >= (int64_t)0xffffffffll) {
+        set_error("too many grid cells for 32-bit cell keys (lower cell_cap_log2)");
+        throw Fail{PC_EINVAL};
+    }
+    S.ncells = base;
+    S.key_bits = std::max(1, ceil_log2((uint64_t)base));
+    S.dev.alloc(nb, s);
+    PC_CUDA(cudaMemcpyAsync(S.dev.p, h.data(), nb * sizeof(BlockDev), cudaMemcpyHostToDevice, s));
+    PC_CUDA(cudaStreamSynchronize(s));   // h lives on this stack frame
 }
 
 // ======================================================================= binning
 namespace {
 
-__global__ void k_cell_keys(const float *__restrict__ orig, int64_t n, double o0, double o1, double o2, double s0,
-                            double s1, double s2, int nx, int ny, int nz, int periodic,
-                            uint32_t *__restrict__ keys, uint32_t *__restrict__ ids) {
+__global__ void k_cell_keys(const float *__restrict__ orig, int64_t n, const BlockDev *__restrict__ bt,
+                            const int64_t *__restrict__ off, int nb, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ ids) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int cx = (int)floor(((double)orig[3 * i + 0] - o0) * s0);
-        int cy = (int)floor(((double)orig[3 * i + 1] - o1) * s1);
-        int cz = (int)floor(((double)orig[3 * i + 2] - o2) * s2);
-        if (periodic) {   // positions up to a quarter box outside wrap to their image's cell
+        const BlockDev &B = bt[find_block(off, nb, i)];
+        const int nx = B.nc[0], ny = B.nc[1], nz = B.nc[2];
+        int cx = (int)floor(((double)orig[3 * i + 0] - B.origin[0]) * B.inv_w[0]);
+        int cy = (int)floor(((double)orig[3 * i + 1] - B.origin[1]) * B.inv_w[1]);
+        int cz = (int)floor(((double)orig[3 * i + 2] - B.origin[2]) * B.inv_w[2]);
+        if (B.periodic) {   // positions up to a quarter box outside wrap to their image's cell
             cx = cx < 0 ? cx + nx : (cx >= nx ? cx - nx : cx);
             cy = cy < 0 ? cy + ny : (cy >= ny ? cy - ny : cy);
             cz = cz < 0 ? cz + nz : (cz >= nz ? cz - nz : cz);
@@ -163,7 +241,7 @@ __global__ void k_cell_keys(const float *__restrict__ orig, int64_t n, double o0
         cx = min(max(cx, 0), nx - 1);
         cy = min(max(cy, 0), ny - 1);
         cz = min(max(cz, 0), nz - 1);
-        keys[i] = ((uint32_t)cz * (uint32_t)ny + (uint32_t)cy) * (uint32_t)nx + (uint32_t)cx;
+        keys[i] = (uint32_t)B.cell_base + ((uint32_t)cz * (uint32_t)ny + (uint32_t)cy) * (uint32_t)nx + (uint32_t)cx;
         ids[i] = (uint32_t)i;
     }
 }
@@ -193,22 +271,21 @@ inline int grid_for(int64_t n, int threads = 256) {
 
 }  // namespace
 
-void bin_particles(const float *orig, int64_t n, const Consts &c, Binned &B, cudaStream_t s, HostScratch &hs) {
+// Keys are ordered by block (cell bases increase with the block index), so after the
+// stable sort the particles of block b occupy sorted positions [off_b, off_b + n_b).
+void bin_particles(const float *orig, const BlockSet &S, Binned &B, cudaStream_t s, HostScratch &hs) {
+    const int64_t n = S.n;
     B.n = n;
     B.keys.alloc(n, s);
     B.order.alloc(n, s);
     B.P4.alloc(n, s);
-    B.cell_start.alloc(c.ncells + 1, s);
-    const double o[3] = {c.origin[0], c.origin[1], c.origin[2]};
-    double sc[3];
-    for (int k = 0; k < 3; ++k) sc[k] = (double)c.inv_w[k];
-    k_cell_keys<<<grid_for(n), 256, 0, s>>>(orig, n, o[0], o[1], o[2], sc[0], sc[1], sc[2], c.nc[0], c.nc[1],
-                                             c.nc[2], c.periodic, B.keys.p, B.order.p);
+    B.cell_start.alloc(S.ncells + 1, s);
+    k_cell_keys<<<grid_for(n), 256, 0, s>>>(orig, n, S.dev.p, S.doff.p, S.nb, B.keys.p, B.order.p);
     PC_CHECK_LAUNCH();
-    radix_sort_u32(B.keys.p, B.order.p, n, c.key_bits, s);
+    radix_sort_u32(B.keys.p, B.order.p, n, S.key_bits, s);
     k_permute<<<grid_for(n), 256, 0, s>>>(orig, B.order.p, n, B.P4.p);
     PC_CHECK_LAUNCH();
-    k_cell_bounds<<<grid_for(n + 1), 256, 0, s>>>(B.keys.p, n, c.ncells, B.cell_start.p);
+    k_cell_bounds<<<grid_for(n + 1), 256, 0, s>>>(B.keys.p, n, S.ncells, B.cell_start.p);
     PC_CHECK_LAUNCH();
     (void)hs;
 }
@@ -271,14 +348,8 @@ void uf_flatten(uint32_t *par, int64_t n, cudaStream_t s) {
 // ======================================================================= pair search
 namespace {
 
-struct Stencil {
-    int n_off;
-    int off[14][3];
-};
-
-__constant__ Stencil c_stencil;
-
 struct PairArgs {
+    unsigned long long *blk_counts;   // pass 1: per block links, safe, pb, pc (may be null)
     uint32_t *fof_par, *safe_par;
     const uint32_t *fof_lab, *safe_lab;
     unsigned long long *A, *C;
@@ -299,29 +370,42 @@ __device__ __forceinline__ void emit_pair(unsigned long long key, unsigned long 
     else atomicOr(err, ERR_INDEX);
 }
 
-// PASS 1: union-find + counts.  PASS 2: emission for MODE (0 VP, 1 SC, 2 HF).
-template <int PASS, int MODE>
+// Home cell first, then the 13 forward neighbours (lexicographically positive (dz, dy, dx)).
+__constant__ int c_off[14][3] = {{0, 0, 0},  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}, {-1, 0, 1},
+                                 {0, 0, 1},  {1, 0, 1},   {-1, 1, 1}, {0, 1, 1},  {1, 1, 1},
+                                 {-1, 1, 0}, {0, 1, 0},   {1, 1, 0},  {1, 0, 0}};
+
+// PASS 1: union-find + counts.  PASS 2: emission by the block's mode (0 VP, 1 SC, 2 HF).
+template <int PASS>
 __global__ void __launch_bounds__(256) k_pairs(const float4 *__restrict__ P4, const uint32_t *__restrict__ keys,
-                                               const uint32_t *__restrict__ cell_start, int64_t n, Consts c,
-                                               PairArgs a) {
+                                               const uint32_t *__restrict__ cell_start, int64_t n,
+                                               const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
+                                               int nb, PairArgs a) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t n_links = 0, n_safe = 0, n_pb = 0, n_pc = 0;
+    const int bk = k < n ? find_block(off, nb, k) : -1;
     if (k < n) {
+        const BlockDev &B = bt[bk];
         const float4 p = P4[k];
         const uint32_t id = __float_as_uint(p.w);
-        const uint32_t key = keys[k];
-        const int nx = c.nc[0], ny = c.nc[1], nz = c.nc[2];
+        const uint32_t key = keys[k] - (uint32_t)B.cell_base;
+        const int nx = B.nc[0], ny = B.nc[1], nz = B.nc[2];
         const int cx = (int)(key % (uint32_t)nx);
         const int cy = (int)((key / (uint32_t)nx) % (uint32_t)ny);
         const int cz = (int)(key / ((uint32_t)nx * (uint32_t)ny));
-        const bool per = c.periodic != 0;
+        const bool per = B.periodic != 0;
+        const float lo2 = B.lo2, b2 = B.b2, hi2 = B.hi2;
+        const int mode = B.mode;
         uint32_t my_safe = 0, my_fof = 0;
         if (PASS == 2) {
-            if (MODE >= 1) my_safe = a.safe_lab[id];
-            if (MODE == 2) my_fof = a.fof_lab[id];
+            if (mode >= 1) my_safe = a.safe_lab[id];
+            if (mode == 2) my_fof = a.fof_lab[id];
         }
-        for (int o = 0; o < c_stencil.n_off; ++o) {
-            int qx = cx + c_stencil.off[o][0], qy = cy + c_stencil.off[o][1], qz = cz + c_stencil.off[o][2];
+        for (int o = 0; o < 14; ++o) {
+            const int ox = c_off[o][0], oy = c_off[o][1], oz = c_off[o][2];
+            // a periodic axis with a single cell has no distinct neighbour along it
+            if (per && ((nx == 1 && ox) || (ny == 1 && oy) || (nz == 1 && oz))) continue;
+            int qx = cx + ox, qy = cy + oy, qz = cz + oz;
             if (per) {
                 qx = qx < 0 ? qx + nx : (qx >= nx ? qx - nx : qx);
                 qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
@@ -329,25 +413,26 @@ __global__ void __launch_bounds__(256) k_pairs(const float4 *__restrict__ P4, co
             } else if (qx < 0 || qx >= nx || qy < 0 || qy >= ny || qz < 0 || qz >= nz) {
                 continue;
             }
-            const uint32_t cell = ((uint32_t)qz * (uint32_t)ny + (uint32_t)qy) * (uint32_t)nx + (uint32_t)qx;
+            const uint32_t cell = (uint32_t)B.cell_base +
+                                  ((uint32_t)qz * (uint32_t)ny + (uint32_t)qy) * (uint32_t)nx + (uint32_t)qx;
             int64_t js = min((int64_t)cell_start[cell], n);
             const int64_t je = min((int64_t)cell_start[cell + 1], n);
             if (o == 0) js = k + 1;
             for (int64_t kj = js; kj < je; ++kj) {
                 const float4 q = __ldg(P4 + kj);
-                const float dx = cdiff(p.x, q.x, per, c.L[0]);
-                const float dy = cdiff(p.y, q.y, per, c.L[1]);
-                const float dz = cdiff(p.z, q.z, per, c.L[2]);
+                const float dx = cdiff(p.x, q.x, per, B.L[0]);
+                const float dy = cdiff(p.y, q.y, per, B.L[1]);
+                const float dz = cdiff(p.z, q.z, per, B.L[2]);
                 const float d2 = cdist2(dx, dy, dz);
-                if (d2 > c.hi2) continue;
+                if (d2 > hi2) continue;
                 const uint32_t jd = __float_as_uint(q.w);
                 if (PASS == 1) {
-                    if (d2 <= c.lo2) {
+                    if (d2 <= lo2) {
                         ++n_safe;
                         ++n_links;
                         if (a.safe_par) uf_union(a.safe_par, id, jd, a.err);
                         if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
-                    } else if (d2 <= c.b2) {
+                    } else if (d2 <= b2) {
                         ++n_pb;
                         ++n_links;
                         if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
@@ -355,15 +440,15 @@ __global__ void __launch_bounds__(256) k_pairs(const float4 *__restrict__ P4, co
                         ++n_pc;
                     }
                 } else {
-                    if (d2 <= c.lo2) continue;   // safe link: never vulnerable
+                    if (d2 <= lo2) continue;   // safe link: never vulnerable
                     const unsigned long long pk = k < kj ? (((unsigned long long)k << 32) | (unsigned long long)kj)
                                                          : (((unsigned long long)kj << 32) | (unsigned long long)k);
-                    if (MODE == 0) {
+                    if (mode == 0) {
                         emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
-                    } else if (MODE == 1) {
+                    } else if (mode == 1) {
                         if (a.safe_lab[jd] != my_safe) emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
                     } else {
-                        if (d2 > c.b2) {
+                        if (d2 > b2) {
                             if (a.fof_lab[jd] != my_fof) emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
                         } else {
                             if (a.safe_lab[jd] != my_safe) emit_pair(pk, a.C, a.capC, a.counts + CNT_C, a.err);
@@ -376,6 +461,29 @@ __global__ void __launch_bounds__(256) k_pairs(const float4 *__restrict__ P4, co
     if (PASS == 1) {
         __syncwarp();
         const unsigned FULL = 0xffffffffu;
+        if (a.blk_counts) {
+            // per-block counts: one atomic per warp when the warp lies in one block
+            int same = 0;
+            __match_all_sync(FULL, bk, &same);
+            if (!same) {
+                if (bk >= 0) {
+                    unsigned long long *c = a.blk_counts + 4 * bk;
+                    if (n_links) atomicAdd(c + 0, (unsigned long long)n_links);
+                    if (n_safe) atomicAdd(c + 1, (unsigned long long)n_safe);
+                    if (n_pb) atomicAdd(c + 2, (unsigned long long)n_pb);
+                    if (n_pc) atomicAdd(c + 3, (unsigned long long)n_pc);
+                }
+            }
+            const unsigned wl = __reduce_add_sync(FULL, n_links), ws = __reduce_add_sync(FULL, n_safe),
+                           wp = __reduce_add_sync(FULL, n_pb), wc = __reduce_add_sync(FULL, n_pc);
+            if (same && (threadIdx.x & 31) == 0 && bk >= 0) {
+                unsigned long long *c = a.blk_counts + 4 * bk;
+                if (wl) atomicAdd(c + 0, (unsigned long long)wl);
+                if (ws) atomicAdd(c + 1, (unsigned long long)ws);
+                if (wp) atomicAdd(c + 2, (unsigned long long)wp);
+                if (wc) atomicAdd(c + 3, (unsigned long long)wc);
+            }
+        }
         n_links = __reduce_add_sync(FULL, n_links);
         n_safe = __reduce_add_sync(FULL, n_safe);
         n_pb = __reduce_add_sync(FULL, n_pb);
@@ -389,54 +497,25 @@ __global__ void __launch_bounds__(256) k_pairs(const float4 *__restrict__ P4, co
     }
 }
 
-void upload_stencil(const Consts &c, cudaStream_t s) {
-    Stencil st;
-    st.n_off = 0;
-    // home cell first, then the 13 forward neighbours (lexicographically positive (dz, dy, dx))
-    for (int dz = 0; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const bool home = dz == 0 && dy == 0 && dx == 0;
-                const bool fwd = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-                if (!home && !fwd) continue;
-                // a periodic axis with a single cell has no distinct neighbours along it
-                const int d[3] = {dx, dy, dz};
-                bool dup = false;
-                for (int k = 0; k < 3; ++k)
-                    if (c.periodic && c.nc[k] == 1 && d[k] != 0) dup = true;
-                if (dup) continue;
-                if (home) {
-                    // keep the home cell at index 0
-                    for (int m = st.n_off; m > 0; --m)
-                        for (int k = 0; k < 3; ++k) st.off[m][k] = st.off[m - 1][k];
-                    for (int k = 0; k < 3; ++k) st.off[0][k] = d[k];
-                } else {
-                    for (int k = 0; k < 3; ++k) st.off[st.n_off][k] = d[k];
-                }
-                st.n_off++;
-            }
-    PC_CUDA(cudaMemcpyToSymbolAsync(c_stencil, &st, sizeof(st), 0, cudaMemcpyHostToDevice, s));
-}
-
 }  // namespace
 
-void pair_pass_union(const Binned &B, const Consts &c, uint32_t *fof_par, uint32_t *safe_par,
-                     unsigned long long *counts, uint32_t *err, cudaStream_t s) {
-    upload_stencil(c, s);
+void pair_pass_union(const Binned &B, const BlockSet &S, uint32_t *fof_par, uint32_t *safe_par,
+                     unsigned long long *counts, uint32_t *err, cudaStream_t s, unsigned long long *blk_counts) {
     PairArgs a = {};
+    a.blk_counts = blk_counts;
     a.fof_par = fof_par;
     a.safe_par = safe_par;
     a.counts = counts;
     a.err = err;
     const int64_t n = B.n;
-    k_pairs<1, 0><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, c, a);
+    k_pairs<1><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, S.dev.p, S.doff.p, S.nb,
+                                                       a);
     PC_CHECK_LAUNCH();
 }
 
-void pair_pass_emit(const Binned &B, const Consts &c, int mode, const uint32_t *fof_lab, const uint32_t *safe_lab,
+void pair_pass_emit(const Binned &B, const BlockSet &S, const uint32_t *fof_lab, const uint32_t *safe_lab,
                     unsigned long long *A, uint64_t capA, unsigned long long *C, uint64_t capC,
                     unsigned long long *counts, uint32_t *err, cudaStream_t s) {
-    upload_stencil(c, s);
     PairArgs a = {};
     a.fof_lab = fof_lab;
     a.safe_lab = safe_lab;
@@ -447,10 +526,8 @@ void pair_pass_emit(const Binned &B, const Consts &c, int mode, const uint32_t *
     a.counts = counts;
     a.err = err;
     const int64_t n = B.n;
-    const unsigned g = (unsigned)cdiv(n, 256);
-    if (mode == PC_MODE_VP) k_pairs<2, 0><<<g, 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, c, a);
-    else if (mode == PC_MODE_SC) k_pairs<2, 1><<<g, 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, c, a);
-    else k_pairs<2, 2><<<g, 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, c, a);
+    k_pairs<2><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, S.dev.p, S.doff.p, S.nb,
+                                                       a);
     PC_CHECK_LAUNCH();
 }
 

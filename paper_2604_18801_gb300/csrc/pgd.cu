@@ -40,7 +40,9 @@ inline int grid_for(int64_t n, int threads = 256) {
 }
 
 constexpr int PGD_THREADS = 256;
+constexpr int WARPS = PGD_THREADS / 32;
 
+// Per-block PGD constants (one entry per block of the problem set).
 struct PgdConsts {
     int periodic;
     float L[3];
@@ -58,27 +60,28 @@ struct PgdConsts {
     double inv_loss_unit;
 };
 
-struct PgdState {
+// Per-block iteration state.
+struct PgdBlk {
     int32_t t;          // updates done
     int32_t stop;
     int32_t final_buf;
     int32_t converged;
-    uint32_t ticket;
-    uint32_t pad;
     unsigned long long viol, viol0;
     double loss, loss0;
-    double b1p, b2p;    // beta^(t+1) for the update of this launch
+    double b1p, b2p;    // beta^(t+1) for the update of the next launch
     df ibc1, ibc2;      // 1 / (1 - beta^(t+1))
-    int32_t upd_t;      // check index of the last iteration launch
-    int32_t upd_on;     // 1 if that launch's update stands (no stop decided)
+    int32_t upd_t;      // check index of the last launch
+    int32_t upd_on;     // 1 if that launch's update stands
     df upd_ibc1, upd_ibc2;
     unsigned long long lfx, vacc;   // launch accumulators: loss (fixed point), violations
-    unsigned long long work;        // next work item of the launch
 };
 
-struct Partial {
-    double loss;
-    unsigned long long viol;
+struct PgdGlobal {
+    uint32_t ticket;
+    int32_t all_stop;
+    unsigned long long work;        // next work item of the launch
+    int32_t active;                 // blocks still iterating after the last launch
+    int32_t pad;
 };
 
 // ------------------------------------------------------------------ CSR build
@@ -123,33 +126,41 @@ __device__ __forceinline__ float3 canon_dp(const float4 p, const float4 q, int p
 
 __global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, int nb,
                        const uint32_t *__restrict__ dense, const uint32_t *__restrict__ epos,
-                       const float4 *__restrict__ P4, PgdConsts pc_, uint32_t *__restrict__ col) {
+                       const float4 *__restrict__ P4, const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
+                       int nblk, uint32_t *__restrict__ col) {
     const unsigned long long mask = (1ull << nb) - 1ull;
     GRID_STRIDE(t, m) {
         const unsigned long long k = keys[t];
         const uint32_t row = (uint32_t)(k >> nb), nbp = (uint32_t)(k & mask);
-        const float4 p = P4[epos[row]], q = P4[nbp];
-        const float3 d = canon_dp(p, q, pc_.periodic, pc_.L);
-        const bool link = cdist2(d.x, d.y, d.z) <= pc_.b2;
+        const uint32_t pos = epos[row];
+        const BlockDev &B = bt[find_block(off, nblk, pos)];
+        const float4 p = P4[pos], q = P4[nbp];
+        const float3 d = canon_dp(p, q, B.periodic, B.L);
+        const bool link = cdist2(d.x, d.y, d.z) <= B.b2;
         col[t] = dense[nbp] | (link ? 0x80000000u : 0u);
     }
 }
 
 __global__ void k_state_init(const uint32_t *__restrict__ epos, int64_t ne, const float4 *__restrict__ P4,
                              const float *__restrict__ orig, const float *__restrict__ recon,
-                             float4 *__restrict__ PE, float4 *__restrict__ Dhi, float4 *__restrict__ Dlo,
-                             float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
-                             float4 *__restrict__ Vlo, float4 *__restrict__ Q, float4 *__restrict__ Dhi1,
-                             float4 *__restrict__ Dlo1, float4 *__restrict__ Q1, uint8_t *__restrict__ act,
-                             df xi_box) {
+                             const int64_t *__restrict__ off, int nblk, const PgdConsts *__restrict__ CB,
+                             float4 *__restrict__ PE, uint32_t *__restrict__ rb, float4 *__restrict__ Dhi,
+                             float4 *__restrict__ Dlo, float4 *__restrict__ Dhi1, float4 *__restrict__ Dlo1,
+                             float4 *__restrict__ Q, float4 *__restrict__ Q1, float4 *__restrict__ Mhi,
+                             float4 *__restrict__ Mlo, float4 *__restrict__ Vhi, float4 *__restrict__ Vlo,
+                             uint8_t *__restrict__ act, unsigned long long *__restrict__ rows_per_block) {
     GRID_STRIDE(e, ne) {
-        const float4 p = P4[epos[e]];
+        const uint32_t pos = epos[e];
+        const int b = find_block(off, nblk, pos);
+        rb[e] = (uint32_t)b;
+        atomicAdd(rows_per_block + b, 1ull);
+        const float4 p = P4[pos];
         PE[e] = p;
         const int64_t id = (int64_t)__float_as_uint(p.w);
         const float4 q = make_float4(recon[3 * id + 0], recon[3 * id + 1], recon[3 * id + 2], 0.f);   // orig + delta0
         Q[e] = q;
         Q1[e] = q;
-        // delta0 = recon - orig, exactly, as a double-float
+        // delta0 = recon - orig, exactly, as a double-float; both offset buffers start there
         const df dx = two_sum(recon[3 * id + 0], -orig[3 * id + 0]);
         const df dy = two_sum(recon[3 * id + 1], -orig[3 * id + 1]);
         const df dz = two_sum(recon[3 * id + 2], -orig[3 * id + 2]);
@@ -158,9 +169,9 @@ __global__ void k_state_init(const uint32_t *__restrict__ epos, int64_t ne, cons
         Dhi1[e] = make_float4(dx.hi, dy.hi, dz.hi, 0.f);
         Dlo1[e] = make_float4(dx.lo, dy.lo, dz.lo, 0.f);
         // a row must be updated from the first update on if the projection moves it
-        const df nl = df_neg(xi_box);
-        const bool out = df_lt(xi_box, dx) || df_lt(dx, nl) || df_lt(xi_box, dy) || df_lt(dy, nl) ||
-                         df_lt(xi_box, dz) || df_lt(dz, nl);
+        const df xb = CB[b].xi_box, nl = df_neg(xb);
+        const bool out = df_lt(xb, dx) || df_lt(dx, nl) || df_lt(xb, dy) || df_lt(dy, nl) || df_lt(xb, dz) ||
+                         df_lt(dz, nl);
         act[e] = out ? 1 : 0;
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         Mhi[e] = z;
@@ -170,7 +181,7 @@ __global__ void k_state_init(const uint32_t *__restrict__ epos, int64_t ne, cons
     }
 }
 
-// ------------------------------------------------------------------ iteration
+// ------------------------------------------------------------------ helpers
 __device__ __forceinline__ df comp(const float4 &h, const float4 &l, int a) {
     return a == 0 ? df_make(h.x, l.x) : (a == 1 ? df_make(h.y, l.y) : df_make(h.z, l.z));
 }
@@ -182,21 +193,7 @@ __device__ __forceinline__ df df_clamp(df x, df lim) {
     return x;
 }
 
-// ------------------------------------------------------------------ loss reduction
-// The tight loss is accumulated in fixed point: each violated pair adds
-// llrint(v^2 / unit) with unit = xi^2 2^-24 (v <= 2 sqrt3 xi + delta_t, so a term is
-// below 2^28 units and 2^35 terms fit in 63 bits), and the violated pairs are counted.
-// Integer sums do not depend on the order in which warps finish, so the result is
-// deterministic although work items are handed out dynamically.  Warps add into
-// their block's counters, the last warp of a block into the launch counters, and the
-// last block takes the stop decision of Algorithm 1 for check t (at eps_L = 0 the
-// count decides: the loss is zero exactly when no active pair is violated).
-constexpr int WARPS = PGD_THREADS / 32;
-
-struct BlockRed {
-    unsigned long long lfx, viol;
-    unsigned count;
-};
+__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
 #pragma unroll
@@ -204,72 +201,8 @@ __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
     return v;
 }
 
-__device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long long lfx, unsigned long long viol, int t,
-                                                 bool last, const PgdConsts &C, PgdState *st,
-                                                 double *hist_loss, unsigned long long *hist_viol) {
-    const int lane = threadIdx.x & 31;
-    lfx = warp_sum_u(lfx);
-    viol = warp_sum_u(viol);
-    unsigned prev = 0;
-    if (lane == 0) {
-        if (lfx) atomicAdd(&br.lfx, lfx);
-        if (viol) atomicAdd(&br.viol, viol);
-        __threadfence_block();
-        prev = atomicAdd(&br.count, 1u);
-    }
-    prev = __shfl_sync(0xffffffffu, prev, 0);
-    if (prev != WARPS - 1) return;          // not the last warp of this block
-    if (lane != 0) return;
-    __threadfence_block();
-    const unsigned long long bl = atomicAdd(&br.lfx, 0ull), bv = atomicAdd(&br.viol, 0ull);
-    if (bl) atomicAdd(&st->lfx, bl);
-    if (bv) atomicAdd(&st->vacc, bv);
-    __threadfence();
-    const unsigned gprev = atomicAdd(&st->ticket, 1u);
-    if (gprev != gridDim.x - 1) return;     // not the last block
-    __threadfence();
-    const unsigned long long LF = atomicAdd(&st->lfx, 0ull), V = atomicAdd(&st->vacc, 0ull);
-    const double L = (double)LF * C.loss_unit;
-    if (hist_loss) {
-        hist_loss[t] = L;
-        hist_viol[t] = V;
-    }
-    if (t == 0) {
-        st->loss0 = L;
-        st->viol0 = V;
-    }
-    st->loss = L;
-    st->viol = V;
-    const bool replay = C.replay >= 0;
-    const bool conv = C.loss_tol > 0.0 ? (L <= C.loss_tol) : (V == 0);
-    st->upd_t = t;
-    st->upd_ibc1 = st->ibc1;
-    st->upd_ibc2 = st->ibc2;
-    if ((!replay && conv) || last) {
-        st->stop = 1;
-        st->final_buf = t & 1;
-        st->converged = conv ? 1 : 0;
-        st->upd_on = 0;
-    } else {
-        st->upd_on = 1;
-        st->t = t + 1;
-        const double b1 = st->b1p * C.beta1_d, b2 = st->b2p * C.beta2_d;
-        st->b1p = b1;
-        st->b2p = b2;
-        const double i1 = 1.0 / (1.0 - b1), i2 = 1.0 / (1.0 - b2);
-        df x, y;
-        x.hi = (float)i1;
-        x.lo = (float)(i1 - (double)x.hi);
-        y.hi = (float)i2;
-        y.lo = (float)(i2 - (double)y.hi);
-        st->ibc1 = x;
-        st->ibc2 = y;
-    }
-    st->lfx = 0;
-    st->vacc = 0;
-    st->work = 0;
-    st->ticket = 0;
-    __threadfence();
+__device__ __forceinline__ bool is_last(const PgdConsts &C, int t) {
+    return C.replay >= 0 ? (t == C.replay) : (t == C.t_max);
 }
 
 // ------------------------------------------------------------------ pair evaluation
@@ -339,18 +272,6 @@ __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, con
     return true;
 }
 
-__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-
-struct WarpTab {
-    int64_t row[32];                 // the warp's rows: dense index
-    uint32_t qk[96];                 // queued pairs: partner
-    uint8_t qs[96];                  // queued pairs: row slot | link << 7
-    float seg[32][6];                // per-row segment sums of one batch
-    uint32_t segmask;                // rows with a segment in the batch
-};
-
-// Adam step t+1 and projection onto [-xi_box, xi_box] for one row; writes the next
-// offsets, the moments and the next rounded position.
 // A row that has never had a gradient (and needs no projection) has zero moments and an
 // unchanged offset: Adam leaves it where it is, and both offset buffers already hold
 // that value, so nothing is read or written for it.
@@ -393,272 +314,403 @@ __device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 
     Qn[e] = make_float4(qo[0], qo[1], qo[2], 0.f);
 }
 
+// ------------------------------------------------------------------ stop decisions
+// The tight loss is accumulated in fixed point: each violated pair adds llrint(v^2 / unit)
+// with unit = xi^2 2^-24 (v <= 2 sqrt3 xi + delta_t, so a term is below 2^28 units and 2^35
+// terms fit in 63 bits), and the violated pairs are counted.  Integer sums do not depend
+// on the order in which warps finish, so the result is deterministic although work items
+// are handed out dynamically.  The block that finishes the launch last takes, for every
+// block still iterating, the stop decision of Algorithm 1 for its check t (at eps_L = 0
+// the count decides: the loss is zero exactly when no active pair is violated).
+__device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs,
+                              double *hist_loss, unsigned long long *hist_viol) {
+    const int lane = threadIdx.x & 31;
+    int active = 0;
+    for (int b = lane; b < nb; b += 32) {
+        PgdBlk &B = blk[b];
+        if (B.stop) continue;
+        const PgdConsts &C = CB[b];
+        const int t = B.t;
+        const bool last = is_last(C, t);
+        const unsigned long long LF = atomicAdd(&B.lfx, 0ull), V = atomicAdd(&B.vacc, 0ull);
+        const double L = (double)LF * C.loss_unit;
+        if (hist_loss) {
+            hist_loss[t] = L;
+            hist_viol[t] = V;
+        }
+        if (t == 0) {
+            B.loss0 = L;
+            B.viol0 = V;
+        }
+        B.loss = L;
+        B.viol = V;
+        const bool replay = C.replay >= 0;
+        const bool conv = C.loss_tol > 0.0 ? (L <= C.loss_tol) : (V == 0);
+        B.upd_t = t;
+        B.upd_ibc1 = B.ibc1;
+        B.upd_ibc2 = B.ibc2;
+        if ((!replay && conv) || last) {
+            B.stop = 1;
+            B.final_buf = t & 1;
+            B.converged = conv ? 1 : 0;
+            B.upd_on = 0;
+        } else {
+            ++active;
+            B.upd_on = 1;
+            B.t = t + 1;
+            const double b1 = B.b1p * C.beta1_d, b2 = B.b2p * C.beta2_d;
+            B.b1p = b1;
+            B.b2p = b2;
+            const double i1 = 1.0 / (1.0 - b1), i2 = 1.0 / (1.0 - b2);
+            df x, y;
+            x.hi = (float)i1;
+            x.lo = (float)(i1 - (double)x.hi);
+            y.hi = (float)i2;
+            y.lo = (float)(i2 - (double)y.hi);
+            B.ibc1 = x;
+            B.ibc2 = y;
+        }
+        B.lfx = 0;
+        B.vacc = 0;
+    }
+    active = __reduce_add_sync(0xffffffffu, active);
+    if (lane == 0) {
+        gs->active = active;
+        if (active == 0) gs->all_stop = 1;
+        gs->work = 0;
+        gs->ticket = 0;
+    }
+    __threadfence();
+}
+
+struct BlockRed {
+    unsigned long long lfx, viol;
+    unsigned count;
+};
+
+// Warp partials -> block counters -> block 0's launch accumulators (single block), then
+// the last block of the launch takes the decisions.
+template <bool MULTI>
+__device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long long lfx, unsigned long long viol,
+                                                 const PgdConsts *CB, int nb, PgdBlk *blk, PgdGlobal *gs,
+                                                 double *hist_loss, unsigned long long *hist_viol) {
+    const int lane = threadIdx.x & 31;
+    if (!MULTI) {
+        lfx = warp_sum_u(lfx);
+        viol = warp_sum_u(viol);
+    }
+    unsigned prev = 0;
+    if (lane == 0) {
+        if (!MULTI) {
+            if (lfx) atomicAdd(&br.lfx, lfx);
+            if (viol) atomicAdd(&br.viol, viol);
+        }
+        __threadfence_block();
+        prev = atomicAdd(&br.count, 1u);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != WARPS - 1) return;          // not the last warp of this block
+    unsigned gprev = 0;
+    if (lane == 0) {
+        __threadfence_block();
+        if (!MULTI) {
+            const unsigned long long bl = atomicAdd(&br.lfx, 0ull), bv = atomicAdd(&br.viol, 0ull);
+            if (bl) atomicAdd(&blk[0].lfx, bl);
+            if (bv) atomicAdd(&blk[0].vacc, bv);
+        }
+        __threadfence();
+        gprev = atomicAdd(&gs->ticket, 1u);
+    }
+    gprev = __shfl_sync(0xffffffffu, gprev, 0);
+    if (gprev != gridDim.x - 1) return;     // not the last block
+    __threadfence();
+    decide_blocks(CB, nb, blk, gs, hist_loss, hist_viol);
+}
+
+// ------------------------------------------------------------------ iteration kernel
 // Rows with more than HEAVY partners are split into chunks of HEAVY edges.
 constexpr uint32_t HEAVY = 256;
 
 struct HeavyPlan {
-    int64_t n_light_blocks;          // blocks of 8 warps x 32 light rows
     int64_t n_chunks;                // heavy chunks (one warp each)
     const uint32_t *chunk_row;       // row of each chunk
     const uint32_t *chunk_start;     // first edge of each chunk
     float4 *chunk_g;                 // per chunk: gradient partial (hi at 2c, lo at 2c+1)
 };
 
-// One PGD iteration: check t and, unless it is the last check, the update t+1.
+struct PgdBufs {
+    float4 *Dh[2], *Dl[2], *Q[2];
+    float4 *Mh, *Ml, *Vh, *Vl;
+    uint8_t *act;
+};
+
+struct WarpTab {
+    int64_t row[32];                 // the warp's rows: dense index
+    uint32_t qk[96];                 // queued pairs: partner
+    uint8_t qs[96];                  // queued pairs: row slot | link << 7
+};
+
+// One PGD iteration for every block still iterating: check t_b and, unless it is the
+// block's last check, the update t_b + 1.
 //
-// Light warps own 32 consecutive rows (editable particles) and walk the flat range of
-// the light rows' CSR edges 32 at a time; heavy warps take one chunk of HEAVY edges of
-// a heavy row.  The float32 screen on the rounded current positions Q certifies most
-// pairs as satisfied; the others are appended, in edge order, to the warp queue.  Every
-// 32 queued pairs are evaluated in double-float by the 32 lanes together, and a
-// segmented scan (fixed shuffle tree) sums the terms of each row; the row's lane adds
-// its batch sum.  Light lane i then applies Adam to its row; a heavy warp writes its
-// chunk partial, and k_pgd_heavy adds the partials of a heavy row in chunk order.
+// Work items are groups of 32 consecutive light rows (editable particles) or one chunk
+// of HEAVY edges of a heavy row, handed out from a counter.  A light warp walks the
+// flat range of its rows' CSR edges 32 at a time; the float32 screen on the rounded
+// current positions Q certifies most pairs as satisfied and the others are appended,
+// in edge order, to the warp queue.  Every 32 queued pairs are evaluated in
+// double-float by the 32 lanes together; each row then adds its violated pairs one by
+// one in edge order, so a row's gradient does not depend on how rows are grouped into
+// warps, batches or blocks of the problem set.  Light lane i applies Adam to its row;
+// a heavy warp writes its chunk partial and k_pgd_heavy adds the partials of a heavy
+// row in chunk order.  MULTI = false is the single-block specialisation.
+template <bool MULTI>
 __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
-    const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE, int64_t ne,
-    float4 *Dhi0, float4 *Dlo0, float4 *Dhi1, float4 *Dlo1, float4 *Q0, float4 *Q1, float4 *__restrict__ Mhi,
-    float4 *__restrict__ Mlo, float4 *__restrict__ Vhi, float4 *__restrict__ Vlo, uint8_t *__restrict__ act,
-    HeavyPlan H, PgdConsts C,
-    PgdState *st, double *__restrict__ hist_loss,
-    unsigned long long *__restrict__ hist_viol) {
+    const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE,
+    const uint32_t *__restrict__ rb, int64_t ne, PgdBufs Bf, HeavyPlan H, const PgdConsts *__restrict__ CB, int nb,
+    PgdBlk *blk, PgdGlobal *gs, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
     __shared__ int s_stop, s_t;
     __shared__ df s_ibc1, s_ibc2;
     __shared__ WarpTab tab[WARPS];
     __shared__ BlockRed br;
     if (threadIdx.x == 0) {
-        s_stop = st->stop;
-        s_t = st->t;
-        s_ibc1 = st->ibc1;
-        s_ibc2 = st->ibc2;
+        s_stop = gs->all_stop;
+        s_t = blk[0].t;
+        s_ibc1 = blk[0].ibc1;
+        s_ibc2 = blk[0].ibc2;
         br.count = 0;
         br.lfx = 0;
         br.viol = 0;
     }
     __syncthreads();
     if (s_stop) return;
-    const int t = s_t;
-    const bool last = C.replay >= 0 ? (t == C.replay) : (t == C.t_max);
-    const float4 *Dh = (t & 1) ? Dhi1 : Dhi0;
-    const float4 *Dl = (t & 1) ? Dlo1 : Dlo0;
-    const float4 *Qc = (t & 1) ? Q1 : Q0;
-    float4 *Nh = (t & 1) ? Dhi0 : Dhi1;
-    float4 *Nl = (t & 1) ? Dlo0 : Dlo1;
-    float4 *Qn = (t & 1) ? Q0 : Q1;
 
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpTab &T = tab[w];
-    unsigned long long lfx = 0;     // this lane's share of the tight loss, fixed point
+    unsigned long long lfx = 0;     // this lane's share of the tight loss (single block), fixed point
     unsigned long long viol = 0;
-    // work items: 32-row groups of light rows, then chunks of heavy rows; the grid is
-    // persistent (a few blocks per SM) and warps take items round-robin
     const int64_t n_light_warps = (ne + 31) / 32;
     const int64_t n_items = n_light_warps + H.n_chunks;
-    for (;;) {
-    unsigned long long itm = 0;
-    if (lane == 0) itm = atomicAdd(&st->work, 1ull);
-    const int64_t item = (int64_t)__shfl_sync(FULL, itm, 0);
-    if (item >= n_items) break;
-    const bool heavy_warp = item >= n_light_warps;
 
-    // Virtual edge range [0, VT): light warps map v to (row slot, edge) through the
-    // prefix vp of the light rows' degrees; a heavy warp maps v to edge start + v of slot 0.
-    int64_t e = -1;              // row of this lane (light warps) / of slot 0 (heavy warps, lane 0)
-    bool own = false;            // this lane applies Adam to row e
-    uint32_t rp = 0, vp = 0, VT = 0, hstart = 0;
-    int64_t chunk = -1;
-    float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!heavy_warp) {
-        const int64_t r0 = item * 32;
-        e = r0 + lane;
-        const bool have = e < ne;
-        uint32_t deg = 0;
-        if (have) {
-            rp = row_ptr[e];
-            deg = row_ptr[e + 1] - rp;
-            qe = Qc[e];
-            T.row[lane] = e;
-        }
-        const uint32_t ld = deg <= HEAVY ? deg : 0u;
-        own = have && deg <= HEAVY;
-        // exclusive warp scan of the light degrees
-        uint32_t inc = ld;
+    for (;;) {
+        unsigned long long itm = 0;
+        if (lane == 0) itm = atomicAdd(&gs->work, 1ull);
+        const int64_t item = (int64_t)__shfl_sync(FULL, itm, 0);
+        if (item >= n_items) break;
+        const bool heavy_warp = item >= n_light_warps;
+
+        // Virtual edge range [0, VT): light warps map v to (row slot, edge) through the
+        // prefix vp of the light rows' degrees; a heavy warp maps v to edge start + v of slot 0.
+        int64_t e = -1;
+        bool own = false;            // this lane applies Adam to row e
+        uint32_t rp = 0, vp = 0, VT = 0, hstart = 0;
+        int64_t chunk = -1;
+        float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
+        // the row's block: iteration, buffers and screen constants (uniform when !MULTI)
+        int b = 0, tb = s_t;
+        bool bstop = false;
+        if (!heavy_warp) {
+            const int64_t r0 = item * 32;
+            e = r0 + lane;
+            const bool have = e < ne;
+            uint32_t deg = 0;
+            if (have) {
+                if (MULTI) {
+                    b = (int)rb[e];
+                    tb = blk[b].t;
+                    bstop = blk[b].stop != 0;
+                }
+                rp = row_ptr[e];
+                deg = bstop ? 0u : row_ptr[e + 1] - rp;
+                qe = Bf.Q[tb & 1][e];
+                T.row[lane] = e;
+            }
+            const uint32_t ld = deg <= HEAVY ? deg : 0u;
+            own = have && !bstop && deg <= HEAVY;
+            uint32_t inc = ld;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, inc, off);
-            if (lane >= off) inc += y;
-        }
-        vp = inc - ld;
-        VT = __shfl_sync(FULL, inc, 31);
-    } else {
-        chunk = item - n_light_warps;
-        if (chunk < H.n_chunks) {
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, inc, off);
+                if (lane >= off) inc += y;
+            }
+            vp = inc - ld;
+            VT = __shfl_sync(FULL, inc, 31);
+        } else {
+            chunk = item - n_light_warps;
             const uint32_t row = H.chunk_row[chunk];
+            if (MULTI) {
+                b = (int)rb[row];
+                tb = blk[b].t;
+                bstop = blk[b].stop != 0;
+            }
             hstart = H.chunk_start[chunk];
             const uint32_t rend = row_ptr[row + 1];
-            VT = min(HEAVY, rend - hstart);
+            VT = bstop ? 0u : min(HEAVY, rend - hstart);
             e = row;
             if (lane == 0) T.row[0] = row;
-            qe = Qc[row];
-        }
-    }
-    __syncwarp();
-
-    df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of the lane's row
-    int qn = 0;
-    const bool per = C.periodic != 0;
-
-    auto batch = [&](int cnt) {
-        const bool valid = lane < cnt;
-        int s = 32;
-        df gt[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
-        if (valid) {
-            const uint32_t k = T.qk[lane];
-            s = T.qs[lane] & 0x7f;
-            const bool link = (T.qs[lane] >> 7) != 0;
-            const int64_t er = T.row[s];
-            double lt = 0.0;
-            if (eval_pair(PE[er], Dh[er], Dl[er], er, k, link, PE, Dh, Dl, C, gt, lt)) {
-                lfx += (unsigned long long)llrint(lt);
-                viol += (int64_t)k > er ? 1ull : 0ull;
-            }
-        }
-        // segmented inclusive scan over lanes; entries are grouped by row in edge order
-        const int sp = __shfl_up_sync(FULL, s, 1);
-        const bool head = lane == 0 || sp != s;
-        const unsigned hm = __ballot_sync(FULL, head);
-        const int seg0 = 31 - __clz(hm & (0xffffffffu >> (31 - lane)));
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            df y[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                y[a] = df_make(__shfl_up_sync(FULL, gt[a].hi, off), __shfl_up_sync(FULL, gt[a].lo, off));
-            if (lane - off >= seg0) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) gt[a] = df_add(y[a], gt[a]);
-            }
-        }
-        const int sn = __shfl_down_sync(FULL, s, 1);
-        const bool tail = valid && (lane == cnt - 1 || sn != s);
-        if (tail) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                T.seg[s][2 * a] = gt[a].hi;
-                T.seg[s][2 * a + 1] = gt[a].lo;
-            }
-        }
-        const unsigned tm = __ballot_sync(FULL, tail);
-        unsigned mask = 0;
-        for (unsigned b = tm; b; b &= b - 1) {
-            const int src = __ffs(b) - 1;
-            mask |= 1u << __shfl_sync(FULL, s, src);
+            qe = Bf.Q[tb & 1][row];
         }
         __syncwarp();
-        if (mask & (1u << lane)) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], df_make(T.seg[lane][2 * a], T.seg[lane][2 * a + 1]));
-        }
-        __syncwarp();
-    };
+        const PgdConsts &Cl = CB[b];            // this lane's row block
+        const float sl_link = Cl.screen_link, sl_non = Cl.screen_non;
+        const int per_l = Cl.periodic;
+        const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
 
-    // row slot and edge of virtual edge v (light: largest s with vp[s] <= v)
-    auto locate = [&](uint32_t v, int &s, uint32_t &tt) {
-        s = 0;
-        tt = hstart + v;
+        df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of the lane's row
+        int qn = 0;
+
+        auto batch = [&](int cnt) {
+            const bool valid = lane < cnt;
+            int s = 32;
+            df gt[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
+            bool hit = false;
+            if (valid) {
+                const uint32_t k = T.qk[lane];
+                s = T.qs[lane] & 0x7f;
+                const bool link = (T.qs[lane] >> 7) != 0;
+                const int64_t er = T.row[s];
+                const int be = MULTI ? (int)rb[er] : 0;
+                const int te = MULTI ? blk[be].t : s_t;
+                const float4 *Dh = Bf.Dh[te & 1], *Dl = Bf.Dl[te & 1];
+                double lt = 0.0;
+                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, PE, Dh, Dl, CB[be], gt, lt);
+                if (hit) {
+                    const unsigned long long lq = (unsigned long long)llrint(lt);
+                    const unsigned long long vq = (int64_t)k > er ? 1ull : 0ull;
+                    if (MULTI) {
+                        if (lq) atomicAdd(&blk[be].lfx, lq);
+                        if (vq) atomicAdd(&blk[be].vacc, vq);
+                    } else {
+                        lfx += lq;
+                        viol += vq;
+                    }
+                }
+            }
+            // Each row adds its violated pairs one by one in edge order (queue order is
+            // edge order).  The row's owner is lane `slot` (light) or lane 0 (heavy: slot 0).
+            for (unsigned m = __ballot_sync(FULL, hit); m; m &= m - 1) {
+                const int src = __ffs(m) - 1;
+                const int sk = __shfl_sync(FULL, s, src);
+                df y[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    y[a] = df_make(__shfl_sync(FULL, gt[a].hi, src), __shfl_sync(FULL, gt[a].lo, src));
+                if (lane == sk) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], y[a]);
+                }
+            }
+            __syncwarp();
+        };
+
+        // row slot and edge of virtual edge v (light: largest s with vp[s] <= v)
+        auto locate = [&](uint32_t v, int &s, uint32_t &tt) {
+            s = 0;
+            tt = hstart + v;
+            if (!heavy_warp) {
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t y = __shfl_sync(FULL, vp, (s + step) & 31);
+                    if (s + step < 32 && y <= v) s += step;
+                }
+                tt = __shfl_sync(FULL, rp, s) + (v - __shfl_sync(FULL, vp, s));
+            }
+        };
+        auto enqueue = [&](bool need, uint32_t k, int s, bool link) {
+            const unsigned bal = __ballot_sync(FULL, need);
+            if (need) {
+                const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+                T.qk[pos] = k;
+                T.qs[pos] = (uint8_t)(s | (link ? 0x80 : 0));
+            }
+            qn += __popc(bal);
+        };
+        // float32 screen of one edge of row slot s against partner k
+        auto screen = [&](bool ok, int s, uint32_t cv) -> bool {
+            float qx = shfl_f(qe.x, s), qy = shfl_f(qe.y, s), qz = shfl_f(qe.z, s);
+            float slk = sl_link, snn = sl_non, l0 = L0, l1 = L1, l2 = L2;
+            int pr = per_l, tp = tb;
+            if (MULTI) {
+                slk = shfl_f(sl_link, s);
+                snn = shfl_f(sl_non, s);
+                l0 = shfl_f(L0, s);
+                l1 = shfl_f(L1, s);
+                l2 = shfl_f(L2, s);
+                pr = __shfl_sync(FULL, per_l, s);
+                tp = __shfl_sync(FULL, tb, s);
+            }
+            if (!ok) return false;
+            const uint32_t k = cv & 0x7fffffffu;
+            const float4 qk = Bf.Q[tp & 1][k];
+            const bool pp = pr != 0;
+            const float d2 = cdist2(cdiff(qx, qk.x, pp, l0), cdiff(qy, qk.y, pp, l1), cdiff(qz, qk.z, pp, l2));
+            return (cv >> 31) ? !(d2 < slk) : !(d2 > snn);
+        };
+        // two edges per lane per trip: both partner loads are in flight before either is used
+        for (uint32_t base = 0; base < VT; base += 64) {
+            const uint32_t v0 = base + lane, v1 = base + 32 + lane;
+            int s0, s1;
+            uint32_t t0, t1;
+            locate(v0, s0, t0);
+            locate(v1, s1, t1);
+            const bool ok0 = v0 < VT, ok1 = v1 < VT;
+            const uint32_t c0v = ok0 ? col[t0] : 0u, c1v = ok1 ? col[t1] : 0u;
+            const bool n0 = screen(ok0, s0, c0v);
+            const bool n1 = screen(ok1, s1, c1v);
+            enqueue(n0, c0v & 0x7fffffffu, s0, (c0v >> 31) != 0u);
+            enqueue(n1, c1v & 0x7fffffffu, s1, (c1v >> 31) != 0u);
+            __syncwarp();
+            while (qn >= 32) {
+                batch(32);
+                uint32_t mk[2] = {0u, 0u};
+                uint8_t ms[2] = {0, 0};
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (lane + 32 * h < qn - 32) {
+                        mk[h] = T.qk[32 + lane + 32 * h];
+                        ms[h] = T.qs[32 + lane + 32 * h];
+                    }
+                __syncwarp();
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (lane + 32 * h < qn - 32) {
+                        T.qk[lane + 32 * h] = mk[h];
+                        T.qs[lane + 32 * h] = ms[h];
+                    }
+                qn -= 32;
+                __syncwarp();
+            }
+        }
+        if (qn > 0) batch(qn);
+
         if (!heavy_warp) {
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const uint32_t y = __shfl_sync(FULL, vp, (s + step) & 31);
-                if (s + step < 32 && y <= v) s += step;
+            if (own && !is_last(Cl, tb)) {
+                const df i1 = MULTI ? blk[b].ibc1 : s_ibc1, i2 = MULTI ? blk[b].ibc2 : s_ibc2;
+                const int pa = tb & 1;
+                adam_row(e, g, Bf.Dh[pa], Bf.Dl[pa], PE, Bf.act, i1, i2, Cl, Bf.Dh[pa ^ 1], Bf.Dl[pa ^ 1], Bf.Mh,
+                         Bf.Ml, Bf.Vh, Bf.Vl, Bf.Q[pa ^ 1]);
             }
-            tt = __shfl_sync(FULL, rp, s) + (v - __shfl_sync(FULL, vp, s));
+        } else if (lane == 0 && !bstop) {
+            H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, 0.f);
+            H.chunk_g[2 * chunk + 1] = make_float4(g[0].lo, g[1].lo, g[2].lo, 0.f);
         }
-    };
-    auto enqueue = [&](bool need, uint32_t k, int s, bool link) {
-        const unsigned bal = __ballot_sync(FULL, need);
-        if (need) {
-            const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-            T.qk[pos] = k;
-            T.qs[pos] = (uint8_t)(s | (link ? 0x80 : 0));
-        }
-        qn += __popc(bal);
-    };
-    // two edges per lane per trip: both partner loads are in flight before either is used
-    for (uint32_t base = 0; base < VT; base += 64) {
-        const uint32_t v0 = base + lane, v1 = base + 32 + lane;
-        int s0, s1;
-        uint32_t t0, t1;
-        locate(v0, s0, t0);
-        locate(v1, s1, t1);
-        const bool ok0 = v0 < VT, ok1 = v1 < VT;
-        const uint32_t c0v = ok0 ? col[t0] : 0u, c1v = ok1 ? col[t1] : 0u;
-        const uint32_t k0 = c0v & 0x7fffffffu, k1 = c1v & 0x7fffffffu;
-        const float4 q0 = ok0 ? Qc[k0] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 q1 = ok1 ? Qc[k1] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float ax = shfl_f(qe.x, s0), ay = shfl_f(qe.y, s0), az = shfl_f(qe.z, s0);
-        const float bx = shfl_f(qe.x, s1), by = shfl_f(qe.y, s1), bz = shfl_f(qe.z, s1);
-        const bool l0 = (c0v >> 31) != 0u, l1 = (c1v >> 31) != 0u;
-        const float d0 = cdist2(cdiff(ax, q0.x, per, C.L[0]), cdiff(ay, q0.y, per, C.L[1]), cdiff(az, q0.z, per, C.L[2]));
-        const float d1 = cdist2(cdiff(bx, q1.x, per, C.L[0]), cdiff(by, q1.y, per, C.L[1]), cdiff(bz, q1.z, per, C.L[2]));
-        const bool n0 = ok0 && (l0 ? !(d0 < C.screen_link) : !(d0 > C.screen_non));
-        const bool n1 = ok1 && (l1 ? !(d1 < C.screen_link) : !(d1 > C.screen_non));
-        enqueue(n0, k0, s0, l0);
-        enqueue(n1, k1, s1, l1);
         __syncwarp();
-        while (qn >= 32) {
-            batch(32);
-            uint32_t mk[2] = {0u, 0u};
-            uint8_t ms[2] = {0, 0};
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (lane + 32 * h < qn - 32) {
-                    mk[h] = T.qk[32 + lane + 32 * h];
-                    ms[h] = T.qs[32 + lane + 32 * h];
-                }
-            __syncwarp();
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (lane + 32 * h < qn - 32) {
-                    T.qk[lane + 32 * h] = mk[h];
-                    T.qs[lane + 32 * h] = ms[h];
-                }
-            qn -= 32;
-            __syncwarp();
-        }
-    }
-    if (qn > 0) batch(qn);
-
-    if (!heavy_warp) {
-        if (own && !last) adam_row(e, g, Dh, Dl, PE, act, s_ibc1, s_ibc2, C, Nh, Nl, Mhi, Mlo, Vhi, Vlo, Qn);
-    } else if (chunk >= 0 && chunk < H.n_chunks && lane == 0) {
-        H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, 0.f);
-        H.chunk_g[2 * chunk + 1] = make_float4(g[0].lo, g[1].lo, g[2].lo, 0.f);
-    }
-    __syncwarp();
     }   // work items
-    finish_iteration(br, lfx, viol, t, last, C, st, hist_loss, hist_viol);
+    finish_iteration<MULTI>(br, lfx, viol, CB, nb, blk, gs, hist_loss, hist_viol);
 }
 
 // Heavy rows: sum the chunk partials in chunk order and apply Adam (same update as
-// light rows).  Runs after k_pgd_iter of the same iteration, with the step and buffers
-// that launch used (recorded in the state by its last block).
+// light rows), with the check index and step of the iteration launch just finished.
 __global__ void k_pgd_heavy(const uint32_t *__restrict__ hrow, const uint32_t *__restrict__ hc0, int64_t nh,
-                            const float4 *__restrict__ chunk_g, const float4 *__restrict__ PE, float4 *Dhi0,
-                            float4 *Dlo0, float4 *Dhi1, float4 *Dlo1, float4 *Q0, float4 *Q1,
-                            float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
-                            float4 *__restrict__ Vlo, uint8_t *__restrict__ act, PgdConsts C,
-                            const PgdState *st) {
-    if (!st->upd_on) return;
-    const int t = st->upd_t;
-    const df ibc1 = st->upd_ibc1, ibc2 = st->upd_ibc2;
-    const float4 *Dh = (t & 1) ? Dhi1 : Dhi0;
-    const float4 *Dl = (t & 1) ? Dlo1 : Dlo0;
-    float4 *Nh = (t & 1) ? Dhi0 : Dhi1;
-    float4 *Nl = (t & 1) ? Dlo0 : Dlo1;
-    float4 *Qn = (t & 1) ? Q0 : Q1;
+                            const float4 *__restrict__ chunk_g, const float4 *__restrict__ PE,
+                            const uint32_t *__restrict__ rb, PgdBufs Bf, const PgdConsts *__restrict__ CB,
+                            const PgdBlk *__restrict__ blk) {
     GRID_STRIDE(i, nh) {
         const uint32_t e = hrow[i];
+        const int b = (int)rb[e];
+        const PgdBlk &B = blk[b];
+        if (!B.upd_on) continue;
+        const int pa = B.upd_t & 1;
         df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
         for (uint32_t c = hc0[i]; c < hc0[i + 1]; ++c) {
             const float4 h = chunk_g[2 * c], l = chunk_g[2 * c + 1];
@@ -666,7 +718,8 @@ __global__ void k_pgd_heavy(const uint32_t *__restrict__ hrow, const uint32_t *_
             g[1] = df_add(g[1], df_make(h.y, l.y));
             g[2] = df_add(g[2], df_make(h.z, l.z));
         }
-        adam_row(e, g, Dh, Dl, PE, act, ibc1, ibc2, C, Nh, Nl, Mhi, Mlo, Vhi, Vlo, Qn);
+        adam_row(e, g, Bf.Dh[pa], Bf.Dl[pa], PE, Bf.act, B.upd_ibc1, B.upd_ibc2, CB[b], Bf.Dh[pa ^ 1],
+                 Bf.Dl[pa ^ 1], Bf.Mh, Bf.Ml, Bf.Vh, Bf.Vl, Bf.Q[pa ^ 1]);
     }
 }
 
@@ -702,32 +755,30 @@ __global__ void k_copy_recon(const float *__restrict__ recon, float *__restrict_
     GRID_STRIDE(i, m) out[i] = recon[i];
 }
 
-__global__ void k_output(const float4 *__restrict__ PE, int64_t ne, const float4 *Dhi0, const float4 *Dlo0,
-                         const float4 *Dhi1, const float4 *Dlo1, const PgdState *st, float *__restrict__ out) {
-    const int fb = st->final_buf;
-    if (st->t == 0) return;   // no update happened: the reconstruction stands
-    const float4 *Dh = fb ? Dhi1 : Dhi0;
-    const float4 *Dl = fb ? Dlo1 : Dlo0;
+// Corrected output: P + delta of the block's final buffer, rounded once; blocks that
+// stopped at check 0 keep the reconstruction.
+__global__ void k_output(const float4 *__restrict__ PE, const uint32_t *__restrict__ rb, int64_t ne, PgdBufs Bf,
+                         const PgdBlk *__restrict__ blk, float *__restrict__ out) {
     GRID_STRIDE(e, ne) {
-        const float4 p = PE[e], h = Dh[e], l = Dl[e];
+        const PgdBlk &B = blk[rb[e]];
+        if (B.t == 0) continue;
+        const int fb = B.final_buf;
+        const float4 p = PE[e], h = Bf.Dh[fb][e], l = Bf.Dl[fb][e];
         const int64_t id = (int64_t)__float_as_uint(p.w);
         const float pa[3] = {p.x, p.y, p.z}, ha[3] = {h.x, h.y, h.z}, la[3] = {l.x, l.y, l.z};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            // round(p + hi + lo) to float32
             const df s = two_sum(pa[a], ha[a]);
             out[3 * id + a] = __fadd_rn(s.hi, __fadd_rn(s.lo, la[a]));
         }
     }
 }
 
-__global__ void k_delta_out(const float4 *__restrict__ PE, int64_t ne, const float4 *Dhi0, const float4 *Dlo0,
-                            const float4 *Dhi1, const float4 *Dlo1, const PgdState *st, double *__restrict__ out) {
-    const int fb = st->final_buf;
-    const float4 *Dh = fb ? Dhi1 : Dhi0;
-    const float4 *Dl = fb ? Dlo1 : Dlo0;
+__global__ void k_delta_out(const float4 *__restrict__ PE, const uint32_t *__restrict__ rb, int64_t ne, PgdBufs Bf,
+                            const PgdBlk *__restrict__ blk, double *__restrict__ out) {
     GRID_STRIDE(e, ne) {
-        const float4 p = PE[e], h = Dh[e], l = Dl[e];
+        const int fb = blk[rb[e]].final_buf;
+        const float4 p = PE[e], h = Bf.Dh[fb][e], l = Bf.Dl[fb][e];
         const int64_t id = (int64_t)__float_as_uint(p.w);
         out[3 * id + 0] = (double)h.x + (double)l.x;
         out[3 * id + 1] = (double)h.y + (double)l.y;
@@ -751,23 +802,9 @@ double ulp32(double x) {
     return std::ldexp(1.0, e - 24);
 }
 
-}  // namespace
-
-PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const float *orig, const float *recon,
-                  const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s, HostScratch &hs,
-                  double *ms_csr, double *delta_out, double *hist_loss, unsigned long long *hist_viol) {
-    PgdResult res;
-    const int64_t n = B.n;
-    cudaEvent_t e0, e1, e2;
-    PC_CUDA(cudaEventCreate(&e0));
-    PC_CUDA(cudaEventCreate(&e1));
-    PC_CUDA(cudaEventCreate(&e2));
-    PC_CUDA(cudaEventRecord(e0, s));
-    k_copy_recon<<<grid_for(3 * n), 256, 0, s>>>(recon, corrected, 3 * n);
-    PC_CHECK_LAUNCH();
-
-    // ---- constants
+PgdConsts pgd_consts(const Consts &c, const pc_params *p) {
     PgdConsts K;
+    memset(&K, 0, sizeof(K));
     K.periodic = c.periodic;
     for (int a = 0; a < 3; ++a) K.L[a] = c.L[a];
     K.b2 = c.b2;
@@ -795,58 +832,137 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
     K.beta2_d = p->beta2;
     K.loss_unit = c.xi * c.xi * std::ldexp(1.0, -24);
     K.inv_loss_unit = 1.0 / K.loss_unit;
+    return K;
+}
 
-    if (nA == 0) {
-        // nothing to enforce: the reconstruction stands, zero iterations
-        res.converged = true;
-        res.loss_evals = 1;
-        if (delta_out) PC_CUDA(cudaMemsetAsync(delta_out, 0, 3 * n * sizeof(double), s));
-        if (hist_loss) PC_CUDA(cudaMemsetAsync(hist_loss, 0, sizeof(double), s));
-        if (hist_viol) PC_CUDA(cudaMemsetAsync(hist_viol, 0, sizeof(unsigned long long), s));
-        PC_CUDA(cudaEventRecord(e1, s));
-        PC_CUDA(cudaEventRecord(e2, s));
-        PC_CUDA(cudaEventSynchronize(e2));
+}  // namespace
+
+PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
+               const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
+               HostScratch &hs, double *delta_out, double *hist_loss, unsigned long long *hist_viol) {
+    PgdRun run;
+    const int nb = S.nb;
+    run.blocks.assign(nb, PgdResult());
+    const int64_t n = B.n;
+    cudaEvent_t e0, e1, e2, e_it;
+    PC_CUDA(cudaEventCreate(&e0));
+    PC_CUDA(cudaEventCreate(&e1));
+    PC_CUDA(cudaEventCreate(&e2));
+    PC_CUDA(cudaEventCreate(&e_it));
+    PC_CUDA(cudaEventRecord(e0, s));
+    k_copy_recon<<<grid_for(3 * n), 256, 0, s>>>(recon, corrected, 3 * n);
+    PC_CHECK_LAUNCH();
+    if (delta_out) PC_CUDA(cudaMemsetAsync(delta_out, 0, 3 * n * sizeof(double), s));
+
+    // ---- constants and iteration state per block
+    std::vector<PgdConsts> hK(nb);
+    std::vector<PgdBlk> hB(nb);
+    int64_t max_checks = 0;
+    for (int b = 0; b < nb; ++b) {
+        const pc_params *p = &S.prm[b];
+        hK[b] = pgd_consts(cp[b], p);
+        PgdBlk &k = hB[b];
+        memset(&k, 0, sizeof(k));
+        k.b1p = p->beta1;
+        k.b2p = p->beta2;
+        k.ibc1 = df_split(1.0 / (1.0 - p->beta1));
+        k.ibc2 = df_split(1.0 / (1.0 - p->beta2));
+        max_checks = std::max<int64_t>(max_checks, (p->replay_iters >= 0 ? p->replay_iters : p->t_max) + 1);
+    }
+    DBuf<PgdConsts> CB(nb, s);
+    DBuf<PgdBlk> blk(nb, s);
+    DBuf<PgdGlobal> gs(1, s);
+    {
+        const size_t bytes = nb * (sizeof(PgdConsts) + sizeof(PgdBlk)) + sizeof(PgdGlobal);
+        uint8_t *h = (uint8_t *)host_scratch(hs, bytes);
+        memcpy(h, hK.data(), nb * sizeof(PgdConsts));
+        memcpy(h + nb * sizeof(PgdConsts), hB.data(), nb * sizeof(PgdBlk));
+        memset(h + nb * (sizeof(PgdConsts) + sizeof(PgdBlk)), 0, sizeof(PgdGlobal));
+        PC_CUDA(cudaMemcpyAsync(CB.p, h, nb * sizeof(PgdConsts), cudaMemcpyHostToDevice, s));
+        PC_CUDA(cudaMemcpyAsync(blk.p, h + nb * sizeof(PgdConsts), nb * sizeof(PgdBlk), cudaMemcpyHostToDevice, s));
+        PC_CUDA(cudaMemcpyAsync(gs.p, h + nb * (sizeof(PgdConsts) + sizeof(PgdBlk)), sizeof(PgdGlobal),
+                                cudaMemcpyHostToDevice, s));
+        PC_CUDA(cudaStreamSynchronize(s));   // the staging area is reused below
+    }
+
+    auto finish_times = [&]() {
+        float ms1 = 0, ms2 = 0, ms3 = 0;
+        cudaEventElapsedTime(&ms1, e0, e1);
+        cudaEventElapsedTime(&ms2, e1, e2);
+        cudaEventElapsedTime(&ms3, e1, e_it);
+        run.ms_csr = ms1;
+        run.ms = ms2;
+        run.ms_iter = ms3;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaEventDestroy(e2);
-        if (ms_csr) *ms_csr = 0;
-        return res;
+        cudaEventDestroy(e_it);
+    };
+
+    if (nA == 0) {
+        // nothing to enforce anywhere: reconstructions stand, zero iterations
+        for (int b = 0; b < nb; ++b) {
+            run.blocks[b].converged = true;
+            run.blocks[b].loss_evals = 1;
+        }
+        if (hist_loss) PC_CUDA(cudaMemsetAsync(hist_loss, 0, sizeof(double), s));
+        if (hist_viol) PC_CUDA(cudaMemsetAsync(hist_viol, 0, sizeof(unsigned long long), s));
+        PC_CUDA(cudaEventRecord(e1, s));
+        PC_CUDA(cudaEventRecord(e_it, s));
+        PC_CUDA(cudaEventRecord(e2, s));
+        PC_CUDA(cudaEventSynchronize(e2));
+        finish_times();
+        return run;
     }
 
     // ---- E and CSR
-    const int nb = std::max(1, ceil_log2((uint64_t)n));
+    const int nbits = std::max(1, ceil_log2((uint64_t)n));
     DBuf<uint32_t> mark(n, s), dense(n, s), tot(1, s);
     PC_CUDA(cudaMemsetAsync(mark.p, 0, n * sizeof(uint32_t), s));
     k_mark<<<grid_for(nA), 256, 0, s>>>(A, nA, mark.p);
     PC_CHECK_LAUNCH();
     scan_exclusive_u32(mark.p, dense.p, n, tot.p, s);
     const int64_t ne = *(uint32_t *)read_back(hs, tot.p, sizeof(uint32_t), s);
-    res.n_editable = ne;
     DBuf<uint32_t> epos(ne, s);
     k_epos<<<grid_for(n), 256, 0, s>>>(mark.p, dense.p, n, epos.p);
     PC_CHECK_LAUNCH();
     mark.release();
     const int64_t m = 2 * nA;
     DBuf<unsigned long long> keys(m, s);
-    k_dir_keys<<<grid_for(nA), 256, 0, s>>>(A, nA, dense.p, nb, keys.p);
+    k_dir_keys<<<grid_for(nA), 256, 0, s>>>(A, nA, dense.p, nbits, keys.p);
     PC_CHECK_LAUNCH();
-    radix_sort_u64((uint64_t *)keys.p, nullptr, m, nb + std::max(1, ceil_log2((uint64_t)ne)), s);
+    radix_sort_u64((uint64_t *)keys.p, nullptr, m, nbits + std::max(1, ceil_log2((uint64_t)ne)), s);
     DBuf<uint32_t> row_ptr(ne + 1, s), col(m, s);
-    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nb, ne, row_ptr.p);
+    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbits, ne, row_ptr.p);
     PC_CHECK_LAUNCH();
-    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nb, dense.p, epos.p, B.P4.p, K, col.p);
+    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbits, dense.p, epos.p, B.P4.p, S.dev.p, S.doff.p, nb, col.p);
     PC_CHECK_LAUNCH();
     keys.release();
     dense.release();
     DBuf<float4> PE(ne, s), Dh0(ne, s), Dl0(ne, s), Dh1(ne, s), Dl1(ne, s), Mh(ne, s), Ml(ne, s), Vh(ne, s),
         Vl(ne, s), Q0(ne, s), Q1(ne, s);
     DBuf<uint8_t> act(ne, s);
-    k_state_init<<<grid_for(ne), 256, 0, s>>>(epos.p, ne, B.P4.p, orig, recon, PE.p, Dh0.p, Dl0.p, Mh.p, Ml.p, Vh.p,
-                                              Vl.p, Q0.p, Dh1.p, Dl1.p, Q1.p, act.p, K.xi_box);
+    DBuf<uint32_t> rb(ne, s);
+    DBuf<unsigned long long> rows_pb(nb, s);
+    PC_CUDA(cudaMemsetAsync(rows_pb.p, 0, nb * sizeof(unsigned long long), s));
+    k_state_init<<<grid_for(ne), 256, 0, s>>>(epos.p, ne, B.P4.p, orig, recon, S.doff.p, nb, CB.p, PE.p, rb.p, Dh0.p,
+                                              Dl0.p, Dh1.p, Dl1.p, Q0.p, Q1.p, Mh.p, Ml.p, Vh.p, Vl.p, act.p,
+                                              rows_pb.p);
     PC_CHECK_LAUNCH();
     epos.release();
+    PgdBufs Bf;
+    Bf.Dh[0] = Dh0.p;
+    Bf.Dh[1] = Dh1.p;
+    Bf.Dl[0] = Dl0.p;
+    Bf.Dl[1] = Dl1.p;
+    Bf.Q[0] = Q0.p;
+    Bf.Q[1] = Q1.p;
+    Bf.Mh = Mh.p;
+    Bf.Ml = Ml.p;
+    Bf.Vh = Vh.p;
+    Bf.Vl = Vl.p;
+    Bf.act = act.p;
 
-    // ---- state
     // heavy rows (more than HEAVY partners) are split into chunks of HEAVY edges
     DBuf<uint32_t> nchunk(ne, s), isheavy(ne, s), c0(ne, s), hpos(ne, s), tot2(2, s);
     k_heavy_count<<<grid_for(ne), 256, 0, s>>>(row_ptr.p, ne, nchunk.p, isheavy.p);
@@ -869,90 +985,73 @@ PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const fl
     c0.release();
     hpos.release();
     HeavyPlan HP;
-    HP.n_light_blocks = cdiv(ne, PGD_THREADS);      // one row per lane, 32 rows per warp
     HP.n_chunks = n_chunks;
     HP.chunk_row = chunk_row.p;
     HP.chunk_start = chunk_start.p;
     HP.chunk_g = chunk_g.p;
     const int64_t n_items = cdiv(ne, 32) + n_chunks;
     const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS), (int64_t)num_sms() * 4));
-
-    DBuf<PgdState> st(1, s);
-    const int64_t hist_n = (p->replay_iters >= 0 ? p->replay_iters : p->t_max) + 1;
-    DBuf<double> hl_own(hist_loss ? 0 : hist_n, s);
-    DBuf<unsigned long long> hv_own(hist_viol ? 0 : hist_n, s);
-    double *hl_p = hist_loss ? hist_loss : hl_own.p;
-    unsigned long long *hv_p = hist_viol ? hist_viol : hv_own.p;
-    PgdState h0;
-    memset(&h0, 0, sizeof(h0));
-    h0.b1p = p->beta1;
-    h0.b2p = p->beta2;
-    h0.ibc1 = df_split(1.0 / (1.0 - p->beta1));
-    h0.ibc2 = df_split(1.0 / (1.0 - p->beta2));
-    PgdState *hs0 = (PgdState *)host_scratch(hs, sizeof(PgdState));
-    *hs0 = h0;
-    PC_CUDA(cudaMemcpyAsync(st.p, hs0, sizeof(PgdState), cudaMemcpyHostToDevice, s));
     PC_CUDA(cudaEventRecord(e1, s));
 
     auto launch_iter = [&]() {
-        k_pgd_iter<<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Dh0.p, Dl0.p, Dh1.p, Dl1.p, Q0.p, Q1.p, Mh.p,
-                                                 Ml.p, Vh.p, Vl.p, act.p, HP, K, st.p, hl_p, hv_p);
+        if (nb == 1)
+            k_pgd_iter<false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, rb.p, ne, Bf, HP, CB.p, nb,
+                                                           blk.p, gs.p, hist_loss, hist_viol);
+        else
+            k_pgd_iter<true><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, rb.p, ne, Bf, HP, CB.p, nb, blk.p,
+                                                          gs.p, nullptr, nullptr);
+        PC_CHECK_LAUNCH();
         if (n_heavy > 0) {
+            k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, rb.p, Bf, CB.p,
+                                                          blk.p);
             PC_CHECK_LAUNCH();
-            k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, Dh0.p, Dl0.p, Dh1.p,
-                                                          Dl1.p, Q0.p, Q1.p, Mh.p, Ml.p, Vh.p, Vl.p, act.p, K, st.p);
         }
     };
 
     // ---- iterations: launch in growing chunks, poll the device stop flag between chunks
     int64_t launched = 0;
-    const int64_t max_launch = hist_n + 1;
+    const int64_t max_launch = max_checks + 1;
     int chunk = 4;
     for (;;) {
-        for (int k = 0; k < chunk && launched < max_launch; ++k, ++launched) {
-            launch_iter();
-            PC_CHECK_LAUNCH();
-        }
-        const PgdState *h = (const PgdState *)read_back(hs, st.p, sizeof(PgdState), s);
-        if (h->stop) break;
+        for (int k = 0; k < chunk && launched < max_launch; ++k, ++launched) launch_iter();
+        const PgdGlobal *h = (const PgdGlobal *)read_back(hs, gs.p, sizeof(PgdGlobal), s);
+        if (h->all_stop) break;
         if (launched >= max_launch) {
             set_error("PGD loop did not reach its stop decision");
             throw Fail{PC_ETIMEOUT};
         }
         chunk = std::min(chunk * 2, 256);
     }
-    cudaEvent_t e_it;
-    PC_CUDA(cudaEventCreate(&e_it));
     PC_CUDA(cudaEventRecord(e_it, s));
-    k_output<<<grid_for(ne), 256, 0, s>>>(PE.p, ne, Dh0.p, Dl0.p, Dh1.p, Dl1.p, st.p, corrected);
+    k_output<<<grid_for(ne), 256, 0, s>>>(PE.p, rb.p, ne, Bf, blk.p, corrected);
     PC_CHECK_LAUNCH();
     if (delta_out) {
-        PC_CUDA(cudaMemsetAsync(delta_out, 0, 3 * n * sizeof(double), s));
-        k_delta_out<<<grid_for(ne), 256, 0, s>>>(PE.p, ne, Dh0.p, Dl0.p, Dh1.p, Dl1.p, st.p, delta_out);
+        k_delta_out<<<grid_for(ne), 256, 0, s>>>(PE.p, rb.p, ne, Bf, blk.p, delta_out);
         PC_CHECK_LAUNCH();
     }
     PC_CUDA(cudaEventRecord(e2, s));
-    const PgdState *h = (const PgdState *)read_back(hs, st.p, sizeof(PgdState), s);
-    res.iters = h->t;
-    res.loss_evals = h->t + 1;
-    res.viol0 = (int64_t)h->viol0;
-    res.viol_final = (int64_t)h->viol;
-    res.loss0 = h->loss0;
-    res.loss_final = h->loss;
-    res.converged = h->converged != 0;
-    float ms1 = 0, ms2 = 0, ms3 = 0;
-    cudaEventElapsedTime(&ms1, e0, e1);
-    cudaEventElapsedTime(&ms2, e1, e2);
-    cudaEventElapsedTime(&ms3, e1, e_it);
-    cudaEventDestroy(e_it);
-    res.ms = ms2;
-    res.ms_iter = ms3;
-    res.launches = launched;
-    if (ms_csr) *ms_csr = ms1;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
-    return res;
+    const size_t rb_bytes = nb * sizeof(PgdBlk) + nb * sizeof(unsigned long long);
+    uint8_t *h = (uint8_t *)host_scratch(hs, rb_bytes);
+    PC_CUDA(cudaMemcpyAsync(h, blk.p, nb * sizeof(PgdBlk), cudaMemcpyDeviceToHost, s));
+    PC_CUDA(cudaMemcpyAsync(h + nb * sizeof(PgdBlk), rows_pb.p, nb * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s));
+    PC_CUDA(cudaStreamSynchronize(s));
+    const PgdBlk *hb = (const PgdBlk *)h;
+    const unsigned long long *rows = (const unsigned long long *)(h + nb * sizeof(PgdBlk));
+    for (int b = 0; b < nb; ++b) {
+        PgdResult &r = run.blocks[b];
+        r.iters = hb[b].t;
+        r.loss_evals = hb[b].t + 1;
+        r.viol0 = (int64_t)hb[b].viol0;
+        r.viol_final = (int64_t)hb[b].viol;
+        r.loss0 = hb[b].loss0;
+        r.loss_final = hb[b].loss;
+        r.converged = hb[b].converged != 0;
+        r.n_editable = (int64_t)rows[b];
+    }
+    run.launches = launched;
+    finish_times();
+    return run;
 }
 
 }  // namespace pc

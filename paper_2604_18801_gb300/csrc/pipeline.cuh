@@ -1,6 +1,8 @@
 // Host-side interfaces between the translation units of libpc (internal).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace pc {
@@ -11,39 +13,85 @@ struct Inspect {
     float maxabs = 0.f;    // max |coordinate| over orig and recon
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};  // bounding box of orig
 };
-// Validates finiteness, |recon - orig| <= xi (float64 compare) and the periodic box;
-// recon may be null (labels only).  Synchronises the stream.
-Inspect inspect_inputs(const float *orig, const float *recon, int64_t n, const pc_params *p,
-                       cudaStream_t s, HostScratch &hs);
 
 // Derived constants; `window` = false sizes the grid for links only (FoF labels).
 Consts make_consts(const pc_params *p, const Inspect &ins, int64_t n, bool window);
 
+// ---------------------------------------------------------------- blocks
+// A problem set is one or more independent blocks of particles, concatenated:
+// block b owns ids (and, after binning, sorted positions) [off_b, off_b + n_b).
+// Every kernel finds the block of an index by binary search over the offsets and
+// reads that block's constants from the device table; blocks never interact.
+struct BlockDev {
+    int64_t off, n, cell_base;   // particle range; first global cell of the block's grid
+    double origin[3], inv_w[3];  // grid
+    float b2, lo2, hi2, L[3];    // link-test bounds, periodic lengths
+    int nc[3];
+    int periodic, mode;
+};
+
+__device__ __forceinline__ int find_block(const int64_t *__restrict__ off, int nb, int64_t i) {
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct BlockSet {
+    int nb = 0;
+    int64_t n = 0;                   // all particles
+    std::vector<pc_params> prm;      // per block
+    std::vector<int64_t> off;        // nb + 1 offsets
+    std::vector<Inspect> ins;
+    std::vector<Consts> c;
+    int64_t ncells = 0;              // all blocks' cells
+    int key_bits = 0;
+    DBuf<BlockDev> dev;              // nb entries
+    DBuf<int64_t> doff;              // nb + 1 offsets
+    void release_to_default_stream() {
+        dev.s = 0;
+        doff.s = 0;
+    }
+};
+// Per-block validation and statistics (finiteness, |recon - orig| <= xi in float64,
+// periodic boxes, max |coordinate|, bounding box); recon may be null.  Uploads the
+// offsets.  Synchronises the stream.
+void inspect_blocks(const float *orig, const float *recon, BlockSet &S, cudaStream_t s, HostScratch &hs);
+// Per-block constants (window or links only), global cell bases, device table.
+void setup_blocks(BlockSet &S, bool window, cudaStream_t s);
+
 // ---------------------------------------------------------------- binning
-constexpr int CHUNK = 128;   // particles of one home cell handled by one CTA
 struct Binned {
     int64_t n = 0;
-    DBuf<uint32_t> keys;        // sorted cell keys
+    DBuf<uint32_t> keys;        // sorted cell keys (block cell base + local cell)
     DBuf<uint32_t> order;       // sorted position -> particle id
     DBuf<float4> P4;            // sorted original positions, w = id bits
     DBuf<uint32_t> cell_start;  // ncells + 1
-    DBuf<uint32_t> items;       // first sorted position of each home chunk
-    int64_t n_items = 0;
+    void release_to_default_stream() {
+        keys.s = 0;
+        order.s = 0;
+        P4.s = 0;
+        cell_start.s = 0;
+    }
 };
-void bin_particles(const float *orig, int64_t n, const Consts &c, Binned &B, cudaStream_t s, HostScratch &hs);
+void bin_particles(const float *orig, const BlockSet &S, Binned &B, cudaStream_t s, HostScratch &hs);
 
 // ---------------------------------------------------------------- pair search
 enum { CNT_LINKS = 0, CNT_SAFE = 1, CNT_PB = 2, CNT_PC = 3, CNT_A = 4, CNT_C = 5, CNT_N = 8 };
 // Pass 1: union-find over links (fof_par) and safe links (safe_par), class counts.
-void pair_pass_union(const Binned &B, const Consts &c, uint32_t *fof_par, uint32_t *safe_par,
-                     unsigned long long *counts, uint32_t *err, cudaStream_t s);
-// Pass 2: emission of selected pairs as (min_pos << 32 | max_pos):
+void pair_pass_union(const Binned &B, const BlockSet &S, uint32_t *fof_par, uint32_t *safe_par,
+                     unsigned long long *counts, uint32_t *err, cudaStream_t s,
+                     unsigned long long *blk_counts = nullptr);
+// Pass 2: emission of selected pairs as (min_pos << 32 | max_pos), by each block's mode:
 //   VP: all vulnerable pairs -> A;  SC: vulnerable pairs joining different safe components -> A;
 //   HF: potentially created pairs joining different halos -> A, potentially broken links
 //       joining different safe components -> C (spanning-forest candidates).
-void pair_pass_emit(const Binned &B, const Consts &c, int mode, const uint32_t *fof_lab,
-                    const uint32_t *safe_lab, unsigned long long *A, uint64_t capA, unsigned long long *C,
-                    uint64_t capC, unsigned long long *counts, uint32_t *err, cudaStream_t s);
+void pair_pass_emit(const Binned &B, const BlockSet &S, const uint32_t *fof_lab, const uint32_t *safe_lab,
+                    unsigned long long *A, uint64_t capA, unsigned long long *C, uint64_t capC,
+                    unsigned long long *counts, uint32_t *err, cudaStream_t s);
 // Union-find helpers (labels = smallest id of the set)
 void uf_init(uint32_t *par, int64_t n, cudaStream_t s);
 void uf_flatten(uint32_t *par, int64_t n, cudaStream_t s);
@@ -52,26 +100,32 @@ void uf_flatten(uint32_t *par, int64_t n, cudaStream_t s);
 // HF spanning forest: Boruvka on safe-component supernodes over candidate links C
 // (key: float32 bits of d2, then (i, j) ids).  Appends the forest links to A
 // (positions) starting at *nA; returns the number of forest links.
-int64_t halo_forest(const Binned &B, const Consts &c, const uint32_t *safe_lab, const unsigned long long *C,
+int64_t halo_forest(const Binned &B, const BlockSet &S, const uint32_t *safe_lab, const unsigned long long *C,
                     int64_t nC, unsigned long long *A, int64_t nA, uint32_t *err, cudaStream_t s,
                     HostScratch &hs);
 // Canonical export: (i, j) ids with i < j sorted by (i, j), and the link flag.
-void export_pairs(const Binned &B, const Consts &c, const unsigned long long *A, int64_t nA, uint32_t *i_out,
+void export_pairs(const Binned &B, const BlockSet &S, const unsigned long long *A, int64_t nA, uint32_t *i_out,
                   uint32_t *j_out, uint8_t *link_out, cudaStream_t s);
 
 // ---------------------------------------------------------------- PGD (pgd.cu)
-struct PgdResult {
+struct PgdResult {       // per block
     int64_t iters = 0, loss_evals = 0, viol0 = 0, viol_final = 0, n_editable = 0;
     double loss0 = 0, loss_final = 0;
     bool converged = false;
+};
+struct PgdRun {
+    std::vector<PgdResult> blocks;
     double ms = 0;        // iterations + output
     double ms_iter = 0;   // iteration launches only
+    double ms_csr = 0;    // CSR and state build
     int64_t launches = 0;
 };
-PgdResult run_pgd(const Binned &B, const Consts &c, const pc_params *p, const float *orig, const float *recon,
-                  const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s, HostScratch &hs,
-                  double *ms_csr, double *delta_out = nullptr, double *hist_loss = nullptr,
-                  unsigned long long *hist_viol = nullptr);
+// PGD for every block of the set; `cp` holds each block's PGD constants (built from
+// orig and recon).  The history outputs require a single block.
+PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
+               const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
+               HostScratch &hs, double *delta_out = nullptr, double *hist_loss = nullptr,
+               unsigned long long *hist_viol = nullptr);
 
 // ---------------------------------------------------------------- host scratch
 void *host_scratch(HostScratch &hs, size_t bytes);

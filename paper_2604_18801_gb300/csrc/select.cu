@@ -55,7 +55,7 @@ inline int grid_for(int64_t n, int threads = 256) {
 #define GRID_STRIDE(i, n) \
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-__device__ __forceinline__ float pair_d2(const float4 p, const float4 q, const Consts &c) {
+__device__ __forceinline__ float pair_d2(const float4 p, const float4 q, const BlockDev &c) {
     const bool per = c.periodic != 0;
     return cdist2(cdiff(p.x, q.x, per, c.L[0]), cdiff(p.y, q.y, per, c.L[1]), cdiff(p.z, q.z, per, c.L[2]));
 }
@@ -75,12 +75,13 @@ __global__ void k_id_keys(const unsigned long long *__restrict__ P, int64_t m, c
 // Per ranked candidate: msf key, supernode endpoints.
 __global__ void k_forest_setup(const unsigned long long *__restrict__ C, const uint32_t *__restrict__ rank_to_c,
                                int64_t m, const float4 *__restrict__ P4, const uint32_t *__restrict__ safe_lab,
-                               Consts c, unsigned long long *__restrict__ ekey, uint32_t *__restrict__ eu,
+                               const BlockDev *__restrict__ bt, const int64_t *__restrict__ off, int nb,
+                               unsigned long long *__restrict__ ekey, uint32_t *__restrict__ eu,
                                uint32_t *__restrict__ ev) {
     GRID_STRIDE(q, m) {
         const unsigned long long pk = C[rank_to_c[q]];
         const float4 p = P4[pk >> 32], r = P4[pk & 0xffffffffull];
-        const float d2 = pair_d2(p, r, c);
+        const float d2 = pair_d2(p, r, bt[find_block(off, nb, (int64_t)(pk >> 32))]);
         ekey[q] = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned long long)q;
         eu[q] = safe_lab[__float_as_uint(p.w)];
         ev[q] = safe_lab[__float_as_uint(r.w)];
@@ -139,12 +140,14 @@ __global__ void k_fill_u64(unsigned long long *p, unsigned long long v, int64_t 
 
 // export: id pair key + link flag
 __global__ void k_export_keys(const unsigned long long *__restrict__ A, int64_t m, const float4 *__restrict__ P4,
-                              Consts c, int nb, unsigned long long *__restrict__ keys, uint32_t *__restrict__ link) {
+                              const BlockDev *__restrict__ bt, const int64_t *__restrict__ off, int nblk, int nb,
+                              unsigned long long *__restrict__ keys, uint32_t *__restrict__ link) {
     GRID_STRIDE(r, m) {
         const unsigned long long pk = A[r];
         const float4 p = P4[pk >> 32], q = P4[pk & 0xffffffffull];
         const uint32_t i = __float_as_uint(p.w), j = __float_as_uint(q.w);
         keys[r] = ((unsigned long long)min(i, j) << nb) | max(i, j);
+        const BlockDev &c = bt[find_block(off, nblk, (int64_t)(pk >> 32))];
         link[r] = pair_d2(p, q, c) <= c.b2 ? 1u : 0u;
     }
 }
@@ -162,7 +165,7 @@ __global__ void k_export_split(const unsigned long long *__restrict__ keys, cons
 
 }  // namespace
 
-int64_t halo_forest(const Binned &B, const Consts &c, const uint32_t *safe_lab, const unsigned long long *C,
+int64_t halo_forest(const Binned &B, const BlockSet &S, const uint32_t *safe_lab, const unsigned long long *C,
                     int64_t nC, unsigned long long *A, int64_t nA, uint32_t *err, cudaStream_t s,
                     HostScratch &hs) {
     if (nC <= 0) return 0;
@@ -177,7 +180,8 @@ int64_t halo_forest(const Binned &B, const Consts &c, const uint32_t *safe_lab, 
     keys.release();
     DBuf<unsigned long long> ekey(nC, s), best(n, s), picked(1, s);
     DBuf<uint32_t> eu(nC, s), ev(nC, s), ru(nC, s), rv(nC, s), sel(nC, s), sup(n, s);
-    k_forest_setup<<<grid_for(nC), 256, 0, s>>>(C, rank_to_c.p, nC, B.P4.p, safe_lab, c, ekey.p, eu.p, ev.p);
+    k_forest_setup<<<grid_for(nC), 256, 0, s>>>(C, rank_to_c.p, nC, B.P4.p, safe_lab, S.dev.p, S.doff.p, S.nb,
+                                                ekey.p, eu.p, ev.p);
     PC_CHECK_LAUNCH();
     iota_u32(sup.p, n, s);
     k_fill_u64<<<grid_for(n), 256, 0, s>>>(best.p, ~0ull, n);
@@ -201,14 +205,14 @@ int64_t halo_forest(const Binned &B, const Consts &c, const uint32_t *safe_lab, 
     return (int64_t) * (uint32_t *)read_back(hs, tot.p, sizeof(uint32_t), s);
 }
 
-void export_pairs(const Binned &B, const Consts &c, const unsigned long long *A, int64_t nA, uint32_t *i_out,
+void export_pairs(const Binned &B, const BlockSet &S, const unsigned long long *A, int64_t nA, uint32_t *i_out,
                   uint32_t *j_out, uint8_t *link_out, cudaStream_t s) {
     if (nA <= 0) return;
     const int nb = std::max(1, ceil_log2((uint64_t)B.n));
     DBuf<unsigned long long> keys(nA, s);
     DBuf<uint32_t> link(nA, s), di(nA, s), dj(nA, s);
     DBuf<uint8_t> dl(nA, s);
-    k_export_keys<<<grid_for(nA), 256, 0, s>>>(A, nA, B.P4.p, c, nb, keys.p, link.p);
+    k_export_keys<<<grid_for(nA), 256, 0, s>>>(A, nA, B.P4.p, S.dev.p, S.doff.p, S.nb, nb, keys.p, link.p);
     PC_CHECK_LAUNCH();
     radix_sort_u64((uint64_t *)keys.p, link.p, nA, 2 * nb, s);
     k_export_split<<<grid_for(nA), 256, 0, s>>>(keys.p, link.p, nA, nb, di.p, dj.p, dl.p);

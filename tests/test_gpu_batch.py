@@ -1,0 +1,75 @@
+"""Batched form: independent blocks corrected together equal each block corrected alone.
+
+Blocks never interact and every row's gradient is summed in a fixed order of its own
+edges, so the batched result must be bit-identical to pc_correct on each block.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_18801_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _blocks():
+    return [synth.hacc_box(eps_over_b=0.5, mode="HF", seed=31, n=3000),
+            synth.md_box(n_clusters=20, eps_over_b=0.3, mode="SC", seed=32),
+            synth.tiny_cosmo(seed=33, n=2048, mode="VP"),
+            synth.fluid_box(n=5000, eps_over_b=0.5, seed=34, mode="HF"),
+            synth.hacc_box(eps_over_b=0.1, mode="VP", seed=35, n=1500),
+            synth.md_box(n_clusters=7, eps_over_b=0.3, mode="HF", seed=36)]
+
+
+def test_batch_equals_blocks_alone(cuda):
+    import torch
+    import paper_2604_18801_gb300 as pc
+    ws = _blocks()
+    orig = torch.from_numpy(np.concatenate([w.orig for w in ws])).to(cuda)
+    recon = torch.from_numpy(np.concatenate([w.recon for w in ws])).to(cuda)
+    sizes = [w.n for w in ws]
+    prms = [w.params() for w in ws]
+    out, stats, code = pc.correct_batch(orig, recon, sizes, prms)
+    assert code == 0
+    at = 0
+    for w, st in zip(ws, stats):
+        o = orig[at:at + w.n].contiguous()
+        r = recon[at:at + w.n].contiguous()
+        alone, sa, ca = pc.correct(o, r, w.params())
+        assert ca == 0 and st["converged"] == 1
+        assert st["iters"] == sa["iters"] and st["n_active"] == sa["n_active"] and st["n_editable"] == sa["n_editable"]
+        assert st["n_vulnerable"] == sa["n_vulnerable"] and st["viol0"] == sa["viol0"]
+        assert torch.equal(out[at:at + w.n], alone)
+        at += w.n
+
+
+def test_batch_membership_is_exact(cuda):
+    import torch
+    import paper_2604_18801_gb300 as pc
+    ws = _blocks()
+    orig = torch.from_numpy(np.concatenate([w.orig for w in ws])).to(cuda)
+    recon = torch.from_numpy(np.concatenate([w.recon for w in ws])).to(cuda)
+    out, stats, code = pc.correct_batch(orig, recon, [w.n for w in ws], [w.params() for w in ws])
+    at = 0
+    for w in ws:
+        c = out[at:at + w.n].contiguous()
+        r = recon[at:at + w.n].contiguous()
+        dec = pc.apply_edits(r, pc.encode_edits(r, c, w.params())).cpu().numpy()
+        assert np.abs(dec.astype(np.float64) - w.orig).max() <= w.xi
+        lab0, _, _ = oracle.fof_labels(w.orig, **w.params())
+        lab1, _, _ = oracle.fof_labels(dec, **w.params())
+        assert np.array_equal(lab0, lab1)
+        at += w.n
+
+
+def test_batch_rejects_bad_tiling_and_names_the_block(cuda):
+    import torch
+    import paper_2604_18801_gb300 as pc
+    ws = _blocks()[:2]
+    orig = torch.from_numpy(np.concatenate([w.orig for w in ws])).to(cuda)
+    recon = torch.from_numpy(np.concatenate([w.recon for w in ws])).to(cuda)
+    bad = recon.clone()
+    bad[ws[0].n + 3, 1] += 3 * ws[1].xi
+    with pytest.raises(pc.PcError) as e:
+        pc.correct_batch(orig, bad, [w.n for w in ws], [w.params() for w in ws])
+    assert e.value.code == -2 and "block 1" in str(e.value)

@@ -137,8 +137,9 @@ def test_correct_halo_forest_converged_parity(cuda, name):
 
 
 @pytest.mark.parametrize("name,mode,R", [("cosmo4096", 0, 10), ("cosmo4096", 1, 10), ("cosmo4096", 0, 30),
-                                         ("cosmo4096", 2, 5), ("md300", 0, 20), ("hacc32k", 2, 3),
-                                         ("hacc32k", 0, 3), ("fluid20k", 1, 10)])
+                                         ("cosmo4096", 2, 5), ("md300", 2, 40), ("hacc32k", 2, 3),
+                                         ("hacc32k", 0, 3), ("hacc32k", 1, 5), ("fluid20k", 1, 10),
+                                         ("fluid20k", 0, 10), ("fluid20k", 2, 20)])
 def test_correct_replayed_iterations_parity(cuda, name, mode, R):
     import paper_2604_18801_gb300 as pc
     w = W_(name)
@@ -147,8 +148,22 @@ def test_correct_replayed_iterations_parity(cuda, name, mode, R):
     assert st["iters"] == R
     ai, aj, al, _ = oracle.select(w.orig, **prm)
     _, delta, ed, ost = oracle.pgd(w.orig, w.recon, ai, aj, al, **prm)
+    # the case is well conditioned: the oracle agrees with itself under reversed summation order
+    _, delta_rev, _, _ = oracle.pgd(w.orig, w.recon, ai[::-1], aj[::-1], al[::-1], **prm)
+    assert np.abs(delta - delta_rev).max() <= 1e-7 * w.xi
     assert ost["iters"] == R and st["viol0"] == ost["viol0"]
     _check_coords(corr.cpu().numpy(), w, delta, ed, R)
+
+
+def test_ill_conditioned_case_is_detected():
+    # md300 in VP mode: reversing the float64 pair order alone moves the oracle by > 1e-7 xi
+    # within 3 iterations, so no pair of implementations can be held to 1e-6 xi there.
+    w = W_("md300")
+    prm = w.params(mode=0, replay_iters=3)
+    ai, aj, al, _ = oracle.select(w.orig, **prm)
+    _, d1, _, _ = oracle.pgd(w.orig, w.recon, ai, aj, al, **prm)
+    _, d2, _, _ = oracle.pgd(w.orig, w.recon, ai[::-1], aj[::-1], al[::-1], **prm)
+    assert np.abs(d1 - d2).max() > 1e-7 * w.xi
 
 
 @pytest.mark.parametrize("name,mode", [("cosmo4096", 0), ("cosmo4096", 1), ("fluid20k", 0), ("md300", 1),
