@@ -72,10 +72,18 @@ typedef struct {
     double loss_tol;       /* eps_L: stop when the tight loss <= loss_tol (default 0)     */
     int32_t replay_iters;  /* >= 0: run exactly this many updates, ignore the loss (-1 off) */
     int32_t cell_cap_log2; /* tuning: at most 2^cell_cap_log2 grid cells (0 = default 27)   */
+    int32_t stall_patience;/* stall reset (not in the paper; 0 = off): after this many checks
+                              without progress, the next check puts every editable endpoint
+                              of a violated pair back at its original position with cleared
+                              Adam moments.  Progress: the loss in units of xi^2 2^-24,
+                              summed per violated pair after rounding to an integer, is 0 or
+                              below best - floor(best / 1024).                            */
+    int32_t pad_;
 } pc_params;
 
-/* Fills defaults: m=16, t_max=10000, alpha_rel=0.05, beta=(0.9,0.999), eps_rel=1e-8,
- * loss_tol=0, replay_iters=-1, cell_cap_log2=0, unit box, non-periodic, mode VP. */
+/* Fills defaults: m=16, t_max=10000, alpha_rel=0.2, beta=(0.9,0.999), eps_rel=2e-6,
+ * loss_tol=0, replay_iters=-1, cell_cap_log2=0, stall_patience=100, unit box,
+ * non-periodic, mode VP. */
 void pc_params_default(pc_params *p);
 
 typedef struct pc_ctx pc_ctx;

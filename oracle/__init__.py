@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("box_hi", C.c_double * 3), ("periodic", C.c_int32), ("mode", C.c_int32),
                 ("m_bits", C.c_int32), ("t_max", C.c_int32), ("alpha_rel", C.c_double),
                 ("beta1", C.c_double), ("beta2", C.c_double), ("eps_rel", C.c_double),
-                ("loss_tol", C.c_double), ("replay_iters", C.c_int32), ("pad_", C.c_int32)]
+                ("loss_tol", C.c_double), ("replay_iters", C.c_int32), ("stall_patience", C.c_int32)]
 
 
 class Consts(C.Structure):
@@ -62,7 +62,7 @@ class PgdStats(C.Structure):
 
 DEFAULTS = dict(b=1.0, xi=0.1, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), periodic=0,
                 mode=0, m_bits=16, t_max=10000, alpha_rel=0.2, beta1=0.9, beta2=0.999,
-                eps_rel=2e-6, loss_tol=0.0, replay_iters=-1)
+                eps_rel=2e-6, loss_tol=0.0, replay_iters=-1, stall_patience=100)
 
 
 def make_params(**kw) -> Params:

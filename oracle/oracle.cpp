@@ -44,6 +44,19 @@
 //  * When a pair's current distance is at most b * 2^-30 (coincident points:
 //    the quantizer lattice makes them common, and rounding turns an exact
 //    zero into noise), its gradient direction is the original separation.
+//  * Stall reset (not in the paper).  The loss is non-convex (the false-link
+//    term), and at large xi / b PGD can settle in a local minimum where a few
+//    non-link pairs sit well inside b with an endpoint on the box.  The original
+//    positions P satisfy every constraint (Sec. 3.4), so: the loss of each check
+//    is also measured in fixed point, as the sum over violated pairs of
+//    llrint(v^2 / (xi^2 2^-24)); a check makes progress when that value is
+//    zero or below best - floor(best / 1024), and its value then becomes best
+//    (best starts at check 0).  After stall_patience consecutive checks
+//    without progress, the next check resets every editable particle that is
+//    an endpoint of a violated pair to its original position (delta = 0) and
+//    clears its Adam moments instead of taking its Adam step; the other
+//    particles take their step.  The check after a reset starts a new best.
+//    stall_patience = 0 turns this off.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -68,7 +81,7 @@ typedef struct {
     double eps_rel;      // Adam epsilon / xi
     double loss_tol;     // convergence threshold eps_L
     int32_t replay_iters;// >= 0: run exactly this many updates, ignoring the loss
-    int32_t pad_;
+    int32_t stall_patience; // checks without progress before a stall reset (0 = never)
 } or_params;
 
 // Derived constants (float32 link-test bounds and float64 PGD constants).
@@ -386,9 +399,12 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             delta[3 * e + d] = (double)recon[3 * E[e] + d] - (double)orig[3 * E[e] + d];
 
     // Tight loss of Eq. 3 and (optionally) its gradient with respect to delta.
-    auto evaluate = [&](bool want_grad, double *loss, int64_t *viol) {
+    const double inv_unit = 1.0 / (p->xi * p->xi * std::ldexp(1.0, -24));
+    std::vector<uint8_t> hit(ne);   // editable particle is an endpoint of a violated pair
+    auto evaluate = [&](bool want_grad, double *loss, int64_t *viol, int64_t *lfx) {
         double L = 0.0;
-        int64_t nv = 0;
+        int64_t nv = 0, fx = 0;
+        std::fill(hit.begin(), hit.end(), 0);
         if (want_grad) std::fill(g.begin(), g.end(), 0.0);
         for (int64_t k = 0; k < na; ++k) {
             const int64_t a = idx[A[k].i], b = idx[A[k].j];
@@ -400,6 +416,8 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             if (!(viol_amt > 0.0)) continue;
             L += viol_amt * viol_amt;
             nv += 1;
+            fx += (int64_t)std::llrint(viol_amt * viol_amt * inv_unit);
+            hit[a] = hit[b] = 1;
             if (!want_grad) continue;
             double u[3];
             if (dh > c.tau) {
@@ -418,6 +436,7 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
         }
         *loss = L;
         *viol = nv;
+        *lfx = fx;
     };
 
     int64_t t = 0;        // updates done
@@ -425,11 +444,15 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
     double L = 0.0;
     int64_t nv = 0;
     double b1t = 1.0, b2t = 1.0;
+    int64_t lfx = 0;          // fixed-point loss of the last check
+    int64_t best = 0;         // lowest fixed-point loss that counted as progress
+    int64_t since = 0;        // checks since then
+    bool reset_now = false;   // this check resets the endpoints of violated pairs
     for (;;) {
         const bool replay = p->replay_iters >= 0;
         const bool last = replay ? (t == p->replay_iters) : (t == p->t_max);
         const bool need_grad = !last;
-        evaluate(need_grad, &L, &nv);
+        evaluate(need_grad, &L, &nv, &lfx);
         st->loss_evals += 1;
         if (t == 0) {
             st->loss0 = L;
@@ -445,12 +468,32 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
         b1t *= p->beta1;
         b2t *= p->beta2;
         for (int64_t q = 0; q < 3 * ne; ++q) {
+            if (reset_now && hit[q / 3]) {
+                delta[q] = 0.0;
+                m[q] = 0.0;
+                v[q] = 0.0;
+                continue;
+            }
             m[q] = p->beta1 * m[q] + (1.0 - p->beta1) * g[q];
             v[q] = p->beta2 * v[q] + (1.0 - p->beta2) * g[q] * g[q];
             const double mh = m[q] / (1.0 - b1t);
             const double vh = v[q] / (1.0 - b2t);
             double dq = delta[q] - c.alpha * mh / (std::sqrt(vh) + c.eps_adam);
             delta[q] = std::min(c.xi_box, std::max(-c.xi_box, dq));
+        }
+        // stall rule on the loss of the check just taken (t now counts its update)
+        if (reset_now) {
+            reset_now = false;
+            best = INT64_MAX;
+            since = 0;
+        } else if (t == 1) {
+            best = lfx;
+        } else if (lfx == 0 || lfx < best - best / 1024) {
+            best = lfx;
+            since = 0;
+        } else if (p->stall_patience > 0 && ++since >= p->stall_patience) {
+            reset_now = true;
+            since = 0;
         }
     }
     if (p->replay_iters >= 0) converged = (L <= p->loss_tol);

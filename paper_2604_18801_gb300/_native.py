@@ -27,7 +27,8 @@ class Params(C.Structure):
     _fields_ = [("b", C.c_double), ("xi", C.c_double), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
                 ("periodic", C.c_int32), ("mode", C.c_int32), ("m_bits", C.c_int32), ("t_max", C.c_int32),
                 ("alpha_rel", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps_rel", C.c_double),
-                ("loss_tol", C.c_double), ("replay_iters", C.c_int32), ("cell_cap_log2", C.c_int32)]
+                ("loss_tol", C.c_double), ("replay_iters", C.c_int32), ("cell_cap_log2", C.c_int32),
+                ("stall_patience", C.c_int32), ("pad_", C.c_int32)]
 
 
 class SelectStats(C.Structure):

@@ -52,7 +52,7 @@ void check_params(const pc_params *p, int64_t n, bool need_pgd) {
         if (p->m_bits < 2 || p->m_bits > 32) fail(PC_EINVAL, "m_bits must be in [2, 32]");
         if (p->t_max < 0) fail(PC_EINVAL, "t_max must be >= 0");
         if (!(p->alpha_rel > 0.0) || !(p->beta1 >= 0.0 && p->beta1 < 1.0) || !(p->beta2 >= 0.0 && p->beta2 < 1.0) ||
-            !(p->eps_rel > 0.0) || !(p->loss_tol >= 0.0))
+            !(p->eps_rel > 0.0) || !(p->loss_tol >= 0.0) || p->stall_patience < 0)
             fail(PC_EINVAL, "bad Adam parameters");
     }
 }
@@ -412,6 +412,8 @@ void pc_params_default(pc_params *p) {
     p->loss_tol = 0.0;
     p->replay_iters = -1;
     p->cell_cap_log2 = 0;
+    p->stall_patience = 100;
+    p->pad_ = 0;
 }
 
 const char *pc_last_error(void) { return g_err.c_str(); }

@@ -58,6 +58,8 @@ struct PgdConsts {
     double beta1_d, beta2_d;
     double loss_unit;    // xi^2 2^-24: fixed-point unit of the loss
     double inv_loss_unit;
+    int stall_patience;  // checks without progress of the fixed-point loss before a reset (0 = off)
+    int pad;
 };
 
 // Per-block iteration state.
@@ -73,6 +75,11 @@ struct PgdBlk {
     int32_t upd_t;      // check index of the last launch
     int32_t upd_on;     // 1 if that launch's update stands
     df upd_ibc1, upd_ibc2;
+    int32_t reset;      // this launch resets the endpoints of violated pairs (stall rule)
+    int32_t upd_reset;  // the value of reset for the launch just finished (heavy rows)
+    unsigned long long best;        // lowest fixed-point loss that counted as progress
+    int32_t since;                  // checks since then
+    int32_t pad;
     unsigned long long lfx, vacc;   // launch accumulators: loss (fixed point), violations
 };
 
@@ -274,16 +281,28 @@ __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, con
 
 // A row that has never had a gradient (and needs no projection) has zero moments and an
 // unchanged offset: Adam leaves it where it is, and both offset buffers already hold
-// that value, so nothing is read or written for it.
+// that value, so nothing is read or written for it.  A reset row (stall rule) returns
+// to its original position with cleared moments instead of taking its step.
 __device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 *Dh, const float4 *Dl,
                                          const float4 *__restrict__ PE, uint8_t *__restrict__ act, const df ibc1,
-                                         const df ibc2, const PgdConsts &C, float4 *Nh, float4 *Nl,
+                                         const df ibc2, bool reset, const PgdConsts &C, float4 *Nh, float4 *Nl,
                                          float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
                                          float4 *__restrict__ Vlo, float4 *Qn) {
     const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
     const bool was = act[e] != 0;
-    if (!was && gz) return;
+    if (!was && gz && !reset) return;
     if (!was) act[e] = 1;
+    if (reset) {
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), pe = PE[e];
+        Nh[e] = z4;
+        Nl[e] = z4;
+        Mhi[e] = z4;
+        Mlo[e] = z4;
+        Vhi[e] = z4;
+        Vlo[e] = z4;
+        Qn[e] = make_float4(pe.x, pe.y, pe.z, 0.f);
+        return;
+    }
     const float4 deh = Dh[e], del = Dl[e], pe = PE[e];
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 mh4 = was ? Mhi[e] : z4, ml4 = was ? Mlo[e] : z4, vh4 = was ? Vhi[e] : z4, vl4 = was ? Vlo[e] : z4;
@@ -349,6 +368,7 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
         B.upd_t = t;
         B.upd_ibc1 = B.ibc1;
         B.upd_ibc2 = B.ibc2;
+        B.upd_reset = B.reset;
         if ((!replay && conv) || last) {
             B.stop = 1;
             B.final_buf = t & 1;
@@ -369,6 +389,22 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
             y.lo = (float)(i2 - (double)y.hi);
             B.ibc1 = x;
             B.ibc2 = y;
+            // stall rule on the loss of check t: progress is a fixed-point loss of zero or
+            // below best - floor(best / 1024); stall_patience checks without progress make
+            // the next launch reset the endpoints of its violated pairs
+            if (B.reset) {
+                B.reset = 0;
+                B.best = ~0ull;
+                B.since = 0;
+            } else if (t == 0) {
+                B.best = LF;
+            } else if (LF == 0 || LF < B.best - B.best / 1024) {
+                B.best = LF;
+                B.since = 0;
+            } else if (C.stall_patience > 0 && ++B.since >= C.stall_patience) {
+                B.reset = 1;
+                B.since = 0;
+            }
         }
         B.lfx = 0;
         B.vacc = 0;
@@ -468,7 +504,7 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
     const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE,
     const uint32_t *__restrict__ rb, int64_t ne, PgdBufs Bf, HeavyPlan H, const PgdConsts *__restrict__ CB, int nb,
     PgdBlk *blk, PgdGlobal *gs, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
-    __shared__ int s_stop, s_t;
+    __shared__ int s_stop, s_t, s_reset;
     __shared__ df s_ibc1, s_ibc2;
     __shared__ WarpTab tab[WARPS];
     __shared__ BlockRed br;
@@ -477,6 +513,7 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
         s_t = blk[0].t;
         s_ibc1 = blk[0].ibc1;
         s_ibc2 = blk[0].ibc2;
+        s_reset = blk[0].reset;
         br.count = 0;
         br.lfx = 0;
         br.viol = 0;
@@ -557,6 +594,7 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
         const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
 
         df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of the lane's row
+        bool rv = false;             // the lane's row has a violated pair
         int qn = 0;
 
         auto batch = [&](int cnt) {
@@ -598,6 +636,7 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
                 if (lane == sk) {
 #pragma unroll
                     for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], y[a]);
+                    rv = true;
                 }
             }
             __syncwarp();
@@ -686,12 +725,13 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
         if (!heavy_warp) {
             if (own && !is_last(Cl, tb)) {
                 const df i1 = MULTI ? blk[b].ibc1 : s_ibc1, i2 = MULTI ? blk[b].ibc2 : s_ibc2;
+                const bool rs = rv && (MULTI ? blk[b].reset != 0 : s_reset != 0);
                 const int pa = tb & 1;
-                adam_row(e, g, Bf.Dh[pa], Bf.Dl[pa], PE, Bf.act, i1, i2, Cl, Bf.Dh[pa ^ 1], Bf.Dl[pa ^ 1], Bf.Mh,
+                adam_row(e, g, Bf.Dh[pa], Bf.Dl[pa], PE, Bf.act, i1, i2, rs, Cl, Bf.Dh[pa ^ 1], Bf.Dl[pa ^ 1], Bf.Mh,
                          Bf.Ml, Bf.Vh, Bf.Vl, Bf.Q[pa ^ 1]);
             }
         } else if (lane == 0 && !bstop) {
-            H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, 0.f);
+            H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, rv ? 1.f : 0.f);
             H.chunk_g[2 * chunk + 1] = make_float4(g[0].lo, g[1].lo, g[2].lo, 0.f);
         }
         __syncwarp();
@@ -712,13 +752,16 @@ __global__ void k_pgd_heavy(const uint32_t *__restrict__ hrow, const uint32_t *_
         if (!B.upd_on) continue;
         const int pa = B.upd_t & 1;
         df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
+        bool rv = false;
         for (uint32_t c = hc0[i]; c < hc0[i + 1]; ++c) {
             const float4 h = chunk_g[2 * c], l = chunk_g[2 * c + 1];
+            rv |= h.w != 0.f;
             g[0] = df_add(g[0], df_make(h.x, l.x));
             g[1] = df_add(g[1], df_make(h.y, l.y));
             g[2] = df_add(g[2], df_make(h.z, l.z));
         }
-        adam_row(e, g, Bf.Dh[pa], Bf.Dl[pa], PE, Bf.act, B.upd_ibc1, B.upd_ibc2, CB[b], Bf.Dh[pa ^ 1],
+        adam_row(e, g, Bf.Dh[pa], Bf.Dl[pa], PE, Bf.act, B.upd_ibc1, B.upd_ibc2, rv && B.upd_reset != 0, CB[b],
+                 Bf.Dh[pa ^ 1],
                  Bf.Dl[pa ^ 1], Bf.Mh, Bf.Ml, Bf.Vh, Bf.Vl, Bf.Q[pa ^ 1]);
     }
 }
@@ -832,6 +875,7 @@ PgdConsts pgd_consts(const Consts &c, const pc_params *p) {
     K.beta2_d = p->beta2;
     K.loss_unit = c.xi * c.xi * std::ldexp(1.0, -24);
     K.inv_loss_unit = 1.0 / K.loss_unit;
+    K.stall_patience = p->stall_patience;
     return K;
 }
 

@@ -268,13 +268,20 @@ def tiny_cosmo(seed: int = 0, n: int = 32768, mode: str = "VP") -> Workload:
                      eps_over_b=0.25, seed=seed, mode=mode, name=f"cosmo{n}_eps0.25b_{mode}")
 
 
-def hacc_box(eps_over_b: float = 0.1, mode: str = "HF", seed: int = 1, n: int = 256 ** 3) -> Workload:
+def hacc_box(eps_over_b: float = 0.1, mode: str = "HF", seed: int = 1, n: int = 256 ** 3,
+             ref_n: int = 256 ** 3) -> Workload:
     """HACC-shaped periodic unit box: 20,000 halos per 256^3 particles holding 55%,
-    sigma log-uniform [0.002, 0.02], counts ~ n^-1.9 truncated to [20, 0.001 N],
-    b = 0.2 / N^(1/3)."""
-    nh = max(1, round(20000 * n / 256 ** 3))
-    return cosmo_box(n=n, n_halos=nh, halo_frac=0.55, sigma_lo=0.002, sigma_hi=0.02,
-                     alpha=-1.9, nmin=20, nmax=max(21.0, 0.001 * n), eps_over_b=eps_over_b,
+    sigma log-uniform [0.002, 0.02], counts ~ n^-1.9 truncated to [20, 0.001 * 256^3],
+    b = 0.2 / N^(1/3).
+
+    For n < ref_n the box stands for a sub-volume of the ref_n-particle box scaled to
+    unit side: the halo count scales with n / ref_n and the halo widths scale with
+    the mean spacing, (ref_n / n)^(1/3), so halo widths in units of b, the member-count
+    law and the halo fraction are those of the full box."""
+    nh = max(1, round(20000 * n / ref_n))
+    zoom = (ref_n / n) ** (1.0 / 3.0)
+    return cosmo_box(n=n, n_halos=nh, halo_frac=0.55, sigma_lo=0.002 * zoom, sigma_hi=0.02 * zoom,
+                     alpha=-1.9, nmin=20, nmax=0.001 * ref_n, eps_over_b=eps_over_b,
                      seed=seed, mode=mode, name=f"hacc{n}_eps{eps_over_b:g}b_{mode}")
 
 

@@ -31,13 +31,17 @@ def test_param_defaults():
     p = _native.make_params()
     assert p.m_bits == 16 and p.t_max == 10000 and p.replay_iters == -1
     assert abs(p.beta1 - 0.9) < 1e-15 and abs(p.beta2 - 0.999) < 1e-15 and p.loss_tol == 0.0
+    import oracle
+    for k in ("m_bits", "t_max", "alpha_rel", "beta1", "beta2", "eps_rel", "loss_tol", "replay_iters",
+              "stall_patience"):
+        assert getattr(p, k) == oracle.DEFAULTS[k], k
     q = _native.make_params(b=0.5, xi=0.1, mode=2, box_hi=(2, 3, 4))
     assert q.b == 0.5 and q.mode == 2 and list(q.box_hi) == [2.0, 3.0, 4.0]
 
 
 def test_struct_sizes_match_the_header():
     # pc_params: 2+3+3 doubles, 4 ints, 5 doubles, 2 ints
-    assert C.sizeof(_native.Params) == 8 * 8 + 4 * 4 + 5 * 8 + 2 * 4
+    assert C.sizeof(_native.Params) == 8 * 8 + 4 * 4 + 5 * 8 + 4 * 4
     assert C.sizeof(_native.SelectStats) == 10 * 8 + 8
     assert C.sizeof(_native.CorrectStats) == 4 * 8 + 2 * 8 + 3 * 8 + 8 + 3 * 8 + 8
 

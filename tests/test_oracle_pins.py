@@ -184,7 +184,7 @@ def test_mode_hierarchy_and_definitions():
 
 
 # ----------------------------------------------------------------- PGD step: torch autograd + torch Adam
-def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps, periodic):
+def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps, periodic, stall=0):
     import torch
     o = torch.tensor(orig, dtype=torch.float64)
     E = np.unique(np.concatenate([ai, aj]))
@@ -203,6 +203,8 @@ def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps
     delta = torch.tensor(recon[E].astype(np.float64) - orig[E].astype(np.float64), requires_grad=True)
     opt = torch.optim.Adam([delta], lr=alpha_rel * xi, betas=(0.9, 0.999), eps=eps_rel * xi)
     thr_l, thr_n = consts["thr_link"], consts["thr_non"]
+    unit = xi * xi * 2.0 ** -24
+    best, since, reset_now, resets = None, 0, False, 0
     for _ in range(steps):
         opt.zero_grad()
         r = dp + delta[a] - delta[b]
@@ -217,7 +219,28 @@ def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps
         opt.step()
         with torch.no_grad():
             delta.clamp_(-consts["xi_box"], consts["xi_box"])
-    return E, delta.detach().numpy()
+            # stall rule: a reset check puts the endpoints of its violated pairs back at the
+            # original positions with cleared moments; the fixed-point loss measures progress
+            vv = torch.clamp(v, min=0.0)
+            hit = torch.zeros(len(E), dtype=torch.bool)
+            hit[a[vv > 0]] = True
+            hit[b[vv > 0]] = True
+            if reset_now:
+                st = opt.state[delta]
+                delta[hit] = 0.0
+                st["exp_avg"][hit] = 0.0
+                st["exp_avg_sq"][hit] = 0.0
+                resets += int(hit.any())
+            fx = int(np.rint((vv * vv * (1.0 / unit)).numpy()).sum())
+        if reset_now:
+            reset_now, best, since = False, None, 0
+        elif best is None or fx == 0 or fx < best - best // 1024:
+            best, since = fx, 0
+        elif stall > 0:
+            since += 1
+            if since >= stall:
+                reset_now, since = True, 0
+    return E, delta.detach().numpy(), resets
 
 
 @pytest.mark.parametrize("mode", [0, 2])
@@ -231,9 +254,44 @@ def test_pgd_matches_torch_autograd_and_adam(mode):
     _, delta, ed, st = oracle.pgd(w.orig, w.recon, ai, aj, al, **dict(kw, replay_iters=steps))
     assert st["iters"] == steps
     d = oracle.DEFAULTS
-    E, dref = _torch_pgd(w.orig, w.recon, ai, aj, al, c, w.xi, d["alpha_rel"], d["eps_rel"], steps, True)
+    E, dref, _ = _torch_pgd(w.orig, w.recon, ai, aj, al, c, w.xi, d["alpha_rel"], d["eps_rel"], steps, True)
     assert np.array_equal(np.flatnonzero(ed), E)
     assert np.abs(delta[E] - dref).max() <= 1e-9 * w.xi
+
+
+def test_stall_reset_matches_torch_adam_with_resets():
+    # With a patience of one check the stall rule fires early; torch.optim.Adam whose
+    # parameters and moments are cleared on the same rows must give the same offsets.
+    w = synth.tiny_cosmo(seed=9, n=600)
+    kw = w.params(mode=0, stall_patience=1)
+    ai, aj, al, _ = oracle.select(w.orig, **kw)
+    c = oracle.constants(w.orig, w.recon, **kw)
+    steps = 16
+    _, delta, _, _ = oracle.pgd(w.orig, w.recon, ai, aj, al, **dict(kw, replay_iters=steps))
+    _, plain, _, _ = oracle.pgd(w.orig, w.recon, ai, aj, al, **dict(kw, replay_iters=steps, stall_patience=0))
+    d = oracle.DEFAULTS
+    E, dref, resets = _torch_pgd(w.orig, w.recon, ai, aj, al, c, w.xi, d["alpha_rel"], d["eps_rel"], steps, True,
+                                 stall=1)
+    assert resets >= 1
+    assert np.abs(delta[E] - plain[E]).max() > 1e-3 * w.xi
+    assert np.abs(delta[E] - dref).max() <= 1e-9 * w.xi
+
+
+def test_stall_reset_escapes_a_local_minimum():
+    # A 1,915-particle HACC-shaped block at eps = 0.5 b: plain Adam-PGD settles with one
+    # non-link pair well inside b and an endpoint on the box (the false-link term makes
+    # the loss non-convex, Sec. 3.4); the stall rule returns such endpoints to their
+    # original positions, which satisfy every constraint, and the run converges with the
+    # membership and the box of Eq. 2 intact after encoding.
+    w = synth.hacc_box(eps_over_b=0.5, mode="HF", seed=3004, n=1915)
+    stuck, st0 = oracle.correct(w.orig, w.recon, **w.params(stall_patience=0, t_max=3000))
+    assert st0["converged"] == 0 and st0["viol_final"] >= 1
+    corr, st = oracle.correct(w.orig, w.recon, **w.params())
+    assert st["converged"] == 1 and st["iters"] < 1000
+    kw = w.params()
+    dec = oracle.decode(w.recon, oracle.encode(w.recon, corr, **kw))
+    assert np.abs(dec.astype(np.float64) - w.orig).max() <= w.xi
+    assert np.array_equal(oracle.fof_labels(dec, **kw)[0], oracle.fof_labels(w.orig, **kw)[0])
 
 
 def test_adam_first_step_is_alpha():
