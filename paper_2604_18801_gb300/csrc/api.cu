@@ -15,6 +15,7 @@ static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(int64_t k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
 
 size_t encode_edits(const float *recon, const float *corr, int64_t n, const pc_params *p, uint8_t *out, size_t cap,
                     cudaStream_t s, HostScratch &hs);
@@ -22,6 +23,9 @@ void apply_edits(const float *recon, int64_t n, const uint8_t *in, size_t nbytes
                  HostScratch &hs);
 
 namespace {
+
+// PGD iterations run as replays of a CUDA graph holding this many iteration launches.
+constexpr int PGD_GRAPH_LAUNCHES = 8;
 
 double ulp32(double x) {
     int e = 0;
@@ -352,7 +356,7 @@ void correct_blocks(pc_ctx *ctx, const float *orig, const float *recon, BlockSet
                                     "xi too small for float32 coordinates of this magnitude (empty projection box)");
         }
         PgdRun r = run_pgd(h->B, h->S, cp, orig, recon, h->A.p, h->nA, corrected, s, ctx->hs, delta_dev, hist_loss,
-                           (unsigned long long *)hist_viol);
+                           (unsigned long long *)hist_viol, PGD_GRAPH_LAUNCHES);
         all_converged = true;
         for (int b = 0; b < V.nb; ++b) {
             const PgdResult &pr = r.blocks[b];

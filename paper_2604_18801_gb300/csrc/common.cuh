@@ -27,6 +27,7 @@ struct Fail {
         }                                                                                   \
     } while (0)
 void count_launch();
+void add_launches(int64_t k);   // graph replays (k > 0) and captured launches that did not run (k < 0)
 #define PC_CHECK_LAUNCH()             \
     do {                              \
         ::pc::count_launch();         \

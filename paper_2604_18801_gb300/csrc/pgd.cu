@@ -89,7 +89,73 @@ struct PgdGlobal {
     unsigned long long work;        // next work item of the launch
     int32_t active;                 // blocks still iterating after the last launch
     int32_t pad;
+    unsigned long long n_items;     // work items of the blocks still iterating (problem sets)
 };
+
+// Work of one block of a problem set: its rows [row0, row0 + nrows) form ceil(nrows / 32)
+// light items (groups of 32 rows that never straddle two blocks; the heavy rows among
+// them have no light edges), followed by its heavy chunks [ch0, ch0 + nch).
+struct BlkWork {
+    uint32_t row0, nrows, ch0, nch;
+};
+
+// Items of the blocks still iterating, for the next launch: active block k is act_blk[k]
+// and owns the work items [act_pref[k], act_pref[k + 1]).
+struct WorkTab {
+    const BlkWork *bw;
+    uint32_t *act_blk;
+    unsigned long long *act_pref;
+};
+
+// One warp: rebuild the table from the stop flags (blocks in ascending order).
+__device__ void build_worktab(int nb, const PgdBlk *blk, const WorkTab wt, PgdGlobal *gs) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long carry = 0;
+    int cnt = 0;
+    for (int base = 0; base < nb; base += 32) {
+        const int b = base + lane;
+        const bool a = b < nb && !blk[b].stop;
+        unsigned long long it = 0;
+        if (a) {
+            const BlkWork w = wt.bw[b];
+            it = (unsigned long long)((w.nrows + 31u) >> 5) + w.nch;
+        }
+        unsigned long long inc = it;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, a);
+        if (a) {
+            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+            wt.act_blk[pos] = (uint32_t)b;
+            wt.act_pref[pos] = carry + inc - it;
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+        cnt += __popc(bal);
+    }
+    if (lane == 0) {
+        wt.act_pref[cnt] = carry;
+        gs->n_items = carry;
+        gs->active = cnt;
+    }
+}
+
+__global__ void k_worktab_init(int nb, const PgdBlk *blk, const WorkTab wt, PgdGlobal *gs) {
+    if (threadIdx.x < 32) build_worktab(nb, blk, wt, gs);
+}
+
+// Per-block row and chunk ranges (rows are in sorted-position order, so every block owns
+// a contiguous range of rows, and chunks follow their rows).
+__global__ void k_blk_work(const int64_t *__restrict__ row_off, const uint32_t *__restrict__ c0, int64_t ne,
+                           int64_t n_chunks, int nb, BlkWork *__restrict__ bw) {
+    GRID_STRIDE(b, nb) {
+        const int64_t r0 = row_off[b], r1 = row_off[b + 1];
+        const uint32_t h0 = r0 < ne ? c0[r0] : (uint32_t)n_chunks, h1 = r1 < ne ? c0[r1] : (uint32_t)n_chunks;
+        bw[b] = BlkWork{(uint32_t)r0, (uint32_t)(r1 - r0), h0, h1 - h0};
+    }
+}
 
 // ------------------------------------------------------------------ CSR build
 __global__ void k_mark(const unsigned long long *__restrict__ A, int64_t m, uint32_t *__restrict__ mark) {
@@ -342,7 +408,7 @@ __device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 
 // block still iterating, the stop decision of Algorithm 1 for its check t (at eps_L = 0
 // the count decides: the loss is zero exactly when no active pair is violated).
 __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs,
-                              double *hist_loss, unsigned long long *hist_viol) {
+                              double *hist_loss, unsigned long long *hist_viol, const WorkTab *wt) {
     const int lane = threadIdx.x & 31;
     int active = 0;
     for (int b = lane; b < nb; b += 32) {
@@ -410,6 +476,11 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
         B.vacc = 0;
     }
     active = __reduce_add_sync(0xffffffffu, active);
+    if (wt) {
+        __syncwarp();
+        __threadfence_block();
+        build_worktab(nb, blk, *wt, gs);
+    }
     if (lane == 0) {
         gs->active = active;
         if (active == 0) gs->all_stop = 1;
@@ -429,7 +500,8 @@ struct BlockRed {
 template <bool MULTI>
 __device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long long lfx, unsigned long long viol,
                                                  const PgdConsts *CB, int nb, PgdBlk *blk, PgdGlobal *gs,
-                                                 double *hist_loss, unsigned long long *hist_viol) {
+                                                 double *hist_loss, unsigned long long *hist_viol,
+                                                 const WorkTab &wt) {
     const int lane = threadIdx.x & 31;
     if (!MULTI) {
         lfx = warp_sum_u(lfx);
@@ -460,7 +532,7 @@ __device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long lon
     gprev = __shfl_sync(0xffffffffu, gprev, 0);
     if (gprev != gridDim.x - 1) return;     // not the last block
     __threadfence();
-    decide_blocks(CB, nb, blk, gs, hist_loss, hist_viol);
+    decide_blocks(CB, nb, blk, gs, hist_loss, hist_viol, MULTI ? &wt : nullptr);
 }
 
 // ------------------------------------------------------------------ iteration kernel
@@ -498,18 +570,23 @@ struct WarpTab {
 // one in edge order, so a row's gradient does not depend on how rows are grouped into
 // warps, batches or blocks of the problem set.  Light lane i applies Adam to its row;
 // a heavy warp writes its chunk partial and k_pgd_heavy adds the partials of a heavy
-// row in chunk order.  MULTI = false is the single-block specialisation.
+// row in chunk order.  MULTI = false is the single-block specialisation; with MULTI the
+// items come from the table of blocks still iterating, so a block that has stopped
+// costs nothing in later launches, and the rows of one item share a block.
 template <bool MULTI>
 __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
     const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE,
-    const uint32_t *__restrict__ rb, int64_t ne, PgdBufs Bf, HeavyPlan H, const PgdConsts *__restrict__ CB, int nb,
-    PgdBlk *blk, PgdGlobal *gs, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
-    __shared__ int s_stop, s_t, s_reset;
+    int64_t ne, PgdBufs Bf, HeavyPlan H, const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs,
+    const WorkTab wt, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
+    __shared__ int s_stop, s_t, s_reset, s_nact;
+    __shared__ unsigned long long s_items;
     __shared__ df s_ibc1, s_ibc2;
     __shared__ WarpTab tab[WARPS];
     __shared__ BlockRed br;
     if (threadIdx.x == 0) {
         s_stop = gs->all_stop;
+        s_nact = gs->active;
+        s_items = gs->n_items;
         s_t = blk[0].t;
         s_ibc1 = blk[0].ibc1;
         s_ibc2 = blk[0].ibc2;
@@ -527,14 +604,13 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
     unsigned long long lfx = 0;     // this lane's share of the tight loss (single block), fixed point
     unsigned long long viol = 0;
     const int64_t n_light_warps = (ne + 31) / 32;
-    const int64_t n_items = n_light_warps + H.n_chunks;
+    const int64_t n_items = MULTI ? (int64_t)s_items : n_light_warps + H.n_chunks;
 
     for (;;) {
         unsigned long long itm = 0;
         if (lane == 0) itm = atomicAdd(&gs->work, 1ull);
         const int64_t item = (int64_t)__shfl_sync(FULL, itm, 0);
         if (item >= n_items) break;
-        const bool heavy_warp = item >= n_light_warps;
 
         // Virtual edge range [0, VT): light warps map v to (row slot, edge) through the
         // prefix vp of the light rows' degrees; a heavy warp maps v to edge start + v of slot 0.
@@ -543,20 +619,52 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
         uint32_t rp = 0, vp = 0, VT = 0, hstart = 0;
         int64_t chunk = -1;
         float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
-        // the row's block: iteration, buffers and screen constants (uniform when !MULTI)
+        // the item's block: iteration, buffers and screen constants (one block per item)
         int b = 0, tb = s_t;
         bool bstop = false;
+        int64_t r0 = 0, item_chunk = 0;
+        int cnt = 0;
+        bool heavy_warp;
+        if (MULTI) {
+            // active block of the item: largest k with act_pref[k] <= item
+            int kk = 0;
+            if (lane == 0) {
+                int lo = 0, hi = s_nact - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (wt.act_pref[mid] <= (unsigned long long)item) lo = mid;
+                    else hi = mid - 1;
+                }
+                kk = lo;
+            }
+            kk = __shfl_sync(FULL, kk, 0);
+            b = (int)wt.act_blk[kk];
+            const int64_t j = item - (int64_t)wt.act_pref[kk];
+            const BlkWork bw = wt.bw[b];
+            const int64_t nl = (bw.nrows + 31u) >> 5;
+            heavy_warp = j >= nl;
+            if (!heavy_warp) {
+                r0 = (int64_t)bw.row0 + 32 * j;
+                cnt = (int)min((int64_t)32, (int64_t)bw.nrows - 32 * j);
+            } else {
+                item_chunk = (int64_t)bw.ch0 + (j - nl);
+            }
+            tb = blk[b].t;
+            bstop = blk[b].stop != 0;
+        } else {
+            heavy_warp = item >= n_light_warps;
+            if (!heavy_warp) {
+                r0 = item * 32;
+                cnt = (int)min((int64_t)32, ne - r0);
+            } else {
+                item_chunk = item - n_light_warps;
+            }
+        }
         if (!heavy_warp) {
-            const int64_t r0 = item * 32;
             e = r0 + lane;
-            const bool have = e < ne;
+            const bool have = lane < cnt;
             uint32_t deg = 0;
             if (have) {
-                if (MULTI) {
-                    b = (int)rb[e];
-                    tb = blk[b].t;
-                    bstop = blk[b].stop != 0;
-                }
                 rp = row_ptr[e];
                 deg = bstop ? 0u : row_ptr[e + 1] - rp;
                 qe = Bf.Q[tb & 1][e];
@@ -573,13 +681,8 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
             vp = inc - ld;
             VT = __shfl_sync(FULL, inc, 31);
         } else {
-            chunk = item - n_light_warps;
+            chunk = item_chunk;
             const uint32_t row = H.chunk_row[chunk];
-            if (MULTI) {
-                b = (int)rb[row];
-                tb = blk[b].t;
-                bstop = blk[b].stop != 0;
-            }
             hstart = H.chunk_start[chunk];
             const uint32_t rend = row_ptr[row + 1];
             VT = bstop ? 0u : min(HEAVY, rend - hstart);
@@ -588,7 +691,7 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
             qe = Bf.Q[tb & 1][row];
         }
         __syncwarp();
-        const PgdConsts &Cl = CB[b];            // this lane's row block
+        const PgdConsts &Cl = CB[b];            // the item's block
         const float sl_link = Cl.screen_link, sl_non = Cl.screen_non;
         const int per_l = Cl.periodic;
         const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
@@ -607,21 +710,12 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
                 s = T.qs[lane] & 0x7f;
                 const bool link = (T.qs[lane] >> 7) != 0;
                 const int64_t er = T.row[s];
-                const int be = MULTI ? (int)rb[er] : 0;
-                const int te = MULTI ? blk[be].t : s_t;
-                const float4 *Dh = Bf.Dh[te & 1], *Dl = Bf.Dl[te & 1];
+                const float4 *Dh = Bf.Dh[tb & 1], *Dl = Bf.Dl[tb & 1];
                 double lt = 0.0;
-                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, PE, Dh, Dl, CB[be], gt, lt);
+                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, PE, Dh, Dl, Cl, gt, lt);
                 if (hit) {
-                    const unsigned long long lq = (unsigned long long)llrint(lt);
-                    const unsigned long long vq = (int64_t)k > er ? 1ull : 0ull;
-                    if (MULTI) {
-                        if (lq) atomicAdd(&blk[be].lfx, lq);
-                        if (vq) atomicAdd(&blk[be].vacc, vq);
-                    } else {
-                        lfx += lq;
-                        viol += vq;
-                    }
+                    lfx += (unsigned long long)llrint(lt);
+                    viol += (int64_t)k > er ? 1ull : 0ull;
                 }
             }
             // Each row adds its violated pairs one by one in edge order (queue order is
@@ -667,23 +761,12 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
         // float32 screen of one edge of row slot s against partner k
         auto screen = [&](bool ok, int s, uint32_t cv) -> bool {
             float qx = shfl_f(qe.x, s), qy = shfl_f(qe.y, s), qz = shfl_f(qe.z, s);
-            float slk = sl_link, snn = sl_non, l0 = L0, l1 = L1, l2 = L2;
-            int pr = per_l, tp = tb;
-            if (MULTI) {
-                slk = shfl_f(sl_link, s);
-                snn = shfl_f(sl_non, s);
-                l0 = shfl_f(L0, s);
-                l1 = shfl_f(L1, s);
-                l2 = shfl_f(L2, s);
-                pr = __shfl_sync(FULL, per_l, s);
-                tp = __shfl_sync(FULL, tb, s);
-            }
             if (!ok) return false;
             const uint32_t k = cv & 0x7fffffffu;
-            const float4 qk = Bf.Q[tp & 1][k];
-            const bool pp = pr != 0;
-            const float d2 = cdist2(cdiff(qx, qk.x, pp, l0), cdiff(qy, qk.y, pp, l1), cdiff(qz, qk.z, pp, l2));
-            return (cv >> 31) ? !(d2 < slk) : !(d2 > snn);
+            const float4 qk = Bf.Q[tb & 1][k];
+            const bool pp = per_l != 0;
+            const float d2 = cdist2(cdiff(qx, qk.x, pp, L0), cdiff(qy, qk.y, pp, L1), cdiff(qz, qk.z, pp, L2));
+            return (cv >> 31) ? !(d2 < sl_link) : !(d2 > sl_non);
         };
         // two edges per lane per trip: both partner loads are in flight before either is used
         for (uint32_t base = 0; base < VT; base += 64) {
@@ -734,9 +817,19 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
             H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, rv ? 1.f : 0.f);
             H.chunk_g[2 * chunk + 1] = make_float4(g[0].lo, g[1].lo, g[2].lo, 0.f);
         }
+        if (MULTI) {
+            // the item's loss and violations belong to its block
+            const unsigned long long il = warp_sum_u(lfx), iv = warp_sum_u(viol);
+            if (lane == 0 && !bstop) {
+                if (il) atomicAdd(&blk[b].lfx, il);
+                if (iv) atomicAdd(&blk[b].vacc, iv);
+            }
+            lfx = 0;
+            viol = 0;
+        }
         __syncwarp();
     }   // work items
-    finish_iteration<MULTI>(br, lfx, viol, CB, nb, blk, gs, hist_loss, hist_viol);
+    finish_iteration<MULTI>(br, lfx, viol, CB, nb, blk, gs, hist_loss, hist_viol, wt);
 }
 
 // Heavy rows: sum the chunk partials in chunk order and apply Adam (same update as
@@ -800,9 +893,10 @@ __global__ void k_copy_recon(const float *__restrict__ recon, float *__restrict_
 
 // Corrected output: P + delta of the block's final buffer, rounded once; blocks that
 // stopped at check 0 keep the reconstruction.
-__global__ void k_output(const float4 *__restrict__ PE, const uint32_t *__restrict__ rb, int64_t ne, PgdBufs Bf,
-                         const PgdBlk *__restrict__ blk, float *__restrict__ out) {
-    GRID_STRIDE(e, ne) {
+__global__ void k_output(const float4 *__restrict__ PE, const uint32_t *__restrict__ rb, int64_t e0, int64_t cnt,
+                         PgdBufs Bf, const PgdBlk *__restrict__ blk, float *__restrict__ out) {
+    GRID_STRIDE(i, cnt) {
+        const int64_t e = e0 + i;
         const PgdBlk &B = blk[rb[e]];
         if (B.t == 0) continue;
         const int fb = B.final_buf;
@@ -881,27 +975,76 @@ PgdConsts pgd_consts(const Consts &c, const pc_params *p) {
 
 }  // namespace
 
-PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
-               const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
-               HostScratch &hs, double *delta_out, double *hist_loss, unsigned long long *hist_viol) {
-    PgdRun run;
+// ------------------------------------------------------------------ resumable solver
+struct PgdSolver::Impl {
+    cudaStream_t s = 0;
+    int nb = 0;
+    int64_t ne = 0, n_heavy = 0, max_checks = 0;
+    int nblk = 1;
+    double *hist_loss = nullptr;
+    unsigned long long *hist_viol = nullptr;
+    DBuf<PgdConsts> CB;
+    DBuf<PgdBlk> blk;
+    DBuf<PgdGlobal> gs;
+    DBuf<uint32_t> row_ptr, col, rb, chunk_row, chunk_start, hrow, hc0;
+    DBuf<float4> PE, Dh0, Dl0, Dh1, Dl1, Mh, Ml, Vh, Vl, Q0, Q1, chunk_g;
+    DBuf<uint8_t> act;
+    DBuf<BlkWork> bw;
+    DBuf<uint32_t> act_blk;
+    DBuf<unsigned long long> act_pref;
+    WorkTab wt{};
+    PgdBufs Bf;
+    HeavyPlan HP;
+    std::vector<int64_t> row_off;            // rows of block b: [row_off[b], row_off[b+1])
+    // status copies
+    uint8_t *pin = nullptr;                  // nb PgdBlk + one PgdGlobal, pinned
+    cudaEvent_t ev = nullptr;
+    bool posted = false;
+    // graph of `graph_k` iteration launches
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_k = 0;
+    int kernels_per_iter = 1;
+
+    void launch_iter() {
+        if (nb == 1)
+            k_pgd_iter<false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, CB.p, nb, blk.p, gs.p,
+                                                           wt, hist_loss, hist_viol);
+        else
+            k_pgd_iter<true><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, CB.p, nb, blk.p, gs.p,
+                                                          wt, nullptr, nullptr);
+        PC_CHECK_LAUNCH();
+        if (n_heavy > 0) {
+            k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, rb.p, Bf, CB.p,
+                                                          blk.p);
+            PC_CHECK_LAUNCH();
+        }
+    }
+    ~Impl() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev) cudaEventDestroy(ev);
+        if (pin) cudaFreeHost(pin);
+    }
+};
+
+PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
+                     const float *recon, const unsigned long long *A, int64_t nA, cudaStream_t s, HostScratch &hs,
+                     double *hist_loss, unsigned long long *hist_viol)
+    : im(new Impl()) {
+    Impl &I = *im;
+    I.s = s;
     const int nb = S.nb;
-    run.blocks.assign(nb, PgdResult());
+    I.nb = nb;
+    I.hist_loss = hist_loss;
+    I.hist_viol = hist_viol;
     const int64_t n = B.n;
-    cudaEvent_t e0, e1, e2, e_it;
-    PC_CUDA(cudaEventCreate(&e0));
-    PC_CUDA(cudaEventCreate(&e1));
-    PC_CUDA(cudaEventCreate(&e2));
-    PC_CUDA(cudaEventCreate(&e_it));
-    PC_CUDA(cudaEventRecord(e0, s));
-    k_copy_recon<<<grid_for(3 * n), 256, 0, s>>>(recon, corrected, 3 * n);
-    PC_CHECK_LAUNCH();
-    if (delta_out) PC_CUDA(cudaMemsetAsync(delta_out, 0, 3 * n * sizeof(double), s));
+    PC_CUDA(cudaEventCreateWithFlags(&I.ev, cudaEventDisableTiming));
+    PC_CUDA(cudaMallocHost((void **)&I.pin, nb * sizeof(PgdBlk) + sizeof(PgdGlobal)));
 
     // ---- constants and iteration state per block
     std::vector<PgdConsts> hK(nb);
     std::vector<PgdBlk> hB(nb);
-    int64_t max_checks = 0;
     for (int b = 0; b < nb; ++b) {
         const pc_params *p = &S.prm[b];
         hK[b] = pgd_consts(cp[b], p);
@@ -911,53 +1054,25 @@ PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp
         k.b2p = p->beta2;
         k.ibc1 = df_split(1.0 / (1.0 - p->beta1));
         k.ibc2 = df_split(1.0 / (1.0 - p->beta2));
-        max_checks = std::max<int64_t>(max_checks, (p->replay_iters >= 0 ? p->replay_iters : p->t_max) + 1);
+        I.max_checks = std::max<int64_t>(I.max_checks, (p->replay_iters >= 0 ? p->replay_iters : p->t_max) + 1);
     }
-    DBuf<PgdConsts> CB(nb, s);
-    DBuf<PgdBlk> blk(nb, s);
-    DBuf<PgdGlobal> gs(1, s);
+    I.CB.alloc(nb, s);
+    I.blk.alloc(nb, s);
+    I.gs.alloc(1, s);
     {
         const size_t bytes = nb * (sizeof(PgdConsts) + sizeof(PgdBlk)) + sizeof(PgdGlobal);
         uint8_t *h = (uint8_t *)host_scratch(hs, bytes);
         memcpy(h, hK.data(), nb * sizeof(PgdConsts));
         memcpy(h + nb * sizeof(PgdConsts), hB.data(), nb * sizeof(PgdBlk));
         memset(h + nb * (sizeof(PgdConsts) + sizeof(PgdBlk)), 0, sizeof(PgdGlobal));
-        PC_CUDA(cudaMemcpyAsync(CB.p, h, nb * sizeof(PgdConsts), cudaMemcpyHostToDevice, s));
-        PC_CUDA(cudaMemcpyAsync(blk.p, h + nb * sizeof(PgdConsts), nb * sizeof(PgdBlk), cudaMemcpyHostToDevice, s));
-        PC_CUDA(cudaMemcpyAsync(gs.p, h + nb * (sizeof(PgdConsts) + sizeof(PgdBlk)), sizeof(PgdGlobal),
+        PC_CUDA(cudaMemcpyAsync(I.CB.p, h, nb * sizeof(PgdConsts), cudaMemcpyHostToDevice, s));
+        PC_CUDA(cudaMemcpyAsync(I.blk.p, h + nb * sizeof(PgdConsts), nb * sizeof(PgdBlk), cudaMemcpyHostToDevice, s));
+        PC_CUDA(cudaMemcpyAsync(I.gs.p, h + nb * (sizeof(PgdConsts) + sizeof(PgdBlk)), sizeof(PgdGlobal),
                                 cudaMemcpyHostToDevice, s));
         PC_CUDA(cudaStreamSynchronize(s));   // the staging area is reused below
     }
-
-    auto finish_times = [&]() {
-        float ms1 = 0, ms2 = 0, ms3 = 0;
-        cudaEventElapsedTime(&ms1, e0, e1);
-        cudaEventElapsedTime(&ms2, e1, e2);
-        cudaEventElapsedTime(&ms3, e1, e_it);
-        run.ms_csr = ms1;
-        run.ms = ms2;
-        run.ms_iter = ms3;
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaEventDestroy(e2);
-        cudaEventDestroy(e_it);
-    };
-
-    if (nA == 0) {
-        // nothing to enforce anywhere: reconstructions stand, zero iterations
-        for (int b = 0; b < nb; ++b) {
-            run.blocks[b].converged = true;
-            run.blocks[b].loss_evals = 1;
-        }
-        if (hist_loss) PC_CUDA(cudaMemsetAsync(hist_loss, 0, sizeof(double), s));
-        if (hist_viol) PC_CUDA(cudaMemsetAsync(hist_viol, 0, sizeof(unsigned long long), s));
-        PC_CUDA(cudaEventRecord(e1, s));
-        PC_CUDA(cudaEventRecord(e_it, s));
-        PC_CUDA(cudaEventRecord(e2, s));
-        PC_CUDA(cudaEventSynchronize(e2));
-        finish_times();
-        return run;
-    }
+    I.row_off.assign(nb + 1, 0);
+    if (nA == 0) return;
 
     // ---- E and CSR
     const int nbits = std::max(1, ceil_log2((uint64_t)n));
@@ -967,6 +1082,7 @@ PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp
     PC_CHECK_LAUNCH();
     scan_exclusive_u32(mark.p, dense.p, n, tot.p, s);
     const int64_t ne = *(uint32_t *)read_back(hs, tot.p, sizeof(uint32_t), s);
+    I.ne = ne;
     DBuf<uint32_t> epos(ne, s);
     k_epos<<<grid_for(n), 256, 0, s>>>(mark.p, dense.p, n, epos.p);
     PC_CHECK_LAUNCH();
@@ -976,114 +1092,209 @@ PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp
     k_dir_keys<<<grid_for(nA), 256, 0, s>>>(A, nA, dense.p, nbits, keys.p);
     PC_CHECK_LAUNCH();
     radix_sort_u64((uint64_t *)keys.p, nullptr, m, nbits + std::max(1, ceil_log2((uint64_t)ne)), s);
-    DBuf<uint32_t> row_ptr(ne + 1, s), col(m, s);
-    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbits, ne, row_ptr.p);
+    I.row_ptr.alloc(ne + 1, s);
+    I.col.alloc(m, s);
+    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbits, ne, I.row_ptr.p);
     PC_CHECK_LAUNCH();
-    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbits, dense.p, epos.p, B.P4.p, S.dev.p, S.doff.p, nb, col.p);
+    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbits, dense.p, epos.p, B.P4.p, S.dev.p, S.doff.p, nb, I.col.p);
     PC_CHECK_LAUNCH();
     keys.release();
     dense.release();
-    DBuf<float4> PE(ne, s), Dh0(ne, s), Dl0(ne, s), Dh1(ne, s), Dl1(ne, s), Mh(ne, s), Ml(ne, s), Vh(ne, s),
-        Vl(ne, s), Q0(ne, s), Q1(ne, s);
-    DBuf<uint8_t> act(ne, s);
-    DBuf<uint32_t> rb(ne, s);
+    for (DBuf<float4> *d : {&I.PE, &I.Dh0, &I.Dl0, &I.Dh1, &I.Dl1, &I.Mh, &I.Ml, &I.Vh, &I.Vl, &I.Q0, &I.Q1})
+        d->alloc(ne, s);
+    I.act.alloc(ne, s);
+    I.rb.alloc(ne, s);
     DBuf<unsigned long long> rows_pb(nb, s);
     PC_CUDA(cudaMemsetAsync(rows_pb.p, 0, nb * sizeof(unsigned long long), s));
-    k_state_init<<<grid_for(ne), 256, 0, s>>>(epos.p, ne, B.P4.p, orig, recon, S.doff.p, nb, CB.p, PE.p, rb.p, Dh0.p,
-                                              Dl0.p, Dh1.p, Dl1.p, Q0.p, Q1.p, Mh.p, Ml.p, Vh.p, Vl.p, act.p,
-                                              rows_pb.p);
+    k_state_init<<<grid_for(ne), 256, 0, s>>>(epos.p, ne, B.P4.p, orig, recon, S.doff.p, nb, I.CB.p, I.PE.p, I.rb.p,
+                                              I.Dh0.p, I.Dl0.p, I.Dh1.p, I.Dl1.p, I.Q0.p, I.Q1.p, I.Mh.p, I.Ml.p,
+                                              I.Vh.p, I.Vl.p, I.act.p, rows_pb.p);
     PC_CHECK_LAUNCH();
     epos.release();
-    PgdBufs Bf;
-    Bf.Dh[0] = Dh0.p;
-    Bf.Dh[1] = Dh1.p;
-    Bf.Dl[0] = Dl0.p;
-    Bf.Dl[1] = Dl1.p;
-    Bf.Q[0] = Q0.p;
-    Bf.Q[1] = Q1.p;
-    Bf.Mh = Mh.p;
-    Bf.Ml = Ml.p;
-    Bf.Vh = Vh.p;
-    Bf.Vl = Vl.p;
-    Bf.act = act.p;
+    // rows per block -> row offsets (rows are in sorted-position order, blocks own contiguous ranges)
+    const unsigned long long *rows =
+        (const unsigned long long *)read_back(hs, rows_pb.p, nb * sizeof(unsigned long long), s);
+    for (int b = 0; b < nb; ++b) I.row_off[b + 1] = I.row_off[b] + (int64_t)rows[b];
+    PgdBufs &Bf = I.Bf;
+    Bf.Dh[0] = I.Dh0.p;
+    Bf.Dh[1] = I.Dh1.p;
+    Bf.Dl[0] = I.Dl0.p;
+    Bf.Dl[1] = I.Dl1.p;
+    Bf.Q[0] = I.Q0.p;
+    Bf.Q[1] = I.Q1.p;
+    Bf.Mh = I.Mh.p;
+    Bf.Ml = I.Ml.p;
+    Bf.Vh = I.Vh.p;
+    Bf.Vl = I.Vl.p;
+    Bf.act = I.act.p;
 
     // heavy rows (more than HEAVY partners) are split into chunks of HEAVY edges
     DBuf<uint32_t> nchunk(ne, s), isheavy(ne, s), c0(ne, s), hpos(ne, s), tot2(2, s);
-    k_heavy_count<<<grid_for(ne), 256, 0, s>>>(row_ptr.p, ne, nchunk.p, isheavy.p);
+    k_heavy_count<<<grid_for(ne), 256, 0, s>>>(I.row_ptr.p, ne, nchunk.p, isheavy.p);
     PC_CHECK_LAUNCH();
     scan_exclusive_u32(nchunk.p, c0.p, ne, tot2.p, s);
     scan_exclusive_u32(isheavy.p, hpos.p, ne, tot2.p + 1, s);
     uint32_t tots[2];
     memcpy(tots, read_back(hs, tot2.p, 2 * sizeof(uint32_t), s), sizeof(tots));
-    const int64_t n_chunks = tots[0], n_heavy = tots[1];
-    DBuf<uint32_t> chunk_row(n_chunks, s), chunk_start(n_chunks, s), hrow(n_heavy, s), hc0(n_heavy + 1, s);
-    DBuf<float4> chunk_g(2 * n_chunks, s);
-    if (n_heavy > 0) {
-        k_heavy_fill<<<grid_for(ne), 256, 0, s>>>(row_ptr.p, ne, nchunk.p, c0.p, isheavy.p, hpos.p, chunk_row.p,
-                                                  chunk_start.p, hrow.p, hc0.p);
+    const int64_t n_chunks = tots[0];
+    I.n_heavy = tots[1];
+    I.chunk_row.alloc(n_chunks, s);
+    I.chunk_start.alloc(n_chunks, s);
+    I.hrow.alloc(I.n_heavy, s);
+    I.hc0.alloc(I.n_heavy + 1, s);
+    I.chunk_g.alloc(2 * n_chunks, s);
+    if (I.n_heavy > 0) {
+        k_heavy_fill<<<grid_for(ne), 256, 0, s>>>(I.row_ptr.p, ne, nchunk.p, c0.p, isheavy.p, hpos.p, I.chunk_row.p,
+                                                  I.chunk_start.p, I.hrow.p, I.hc0.p);
         PC_CHECK_LAUNCH();
-        PC_CUDA(cudaMemcpyAsync(hc0.p + n_heavy, tot2.p, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+        PC_CUDA(cudaMemcpyAsync(I.hc0.p + I.n_heavy, tot2.p, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     }
-    nchunk.release();
-    isheavy.release();
-    c0.release();
-    hpos.release();
-    HeavyPlan HP;
-    HP.n_chunks = n_chunks;
-    HP.chunk_row = chunk_row.p;
-    HP.chunk_start = chunk_start.p;
-    HP.chunk_g = chunk_g.p;
-    const int64_t n_items = cdiv(ne, 32) + n_chunks;
-    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS), (int64_t)num_sms() * 4));
-    PC_CUDA(cudaEventRecord(e1, s));
-
-    auto launch_iter = [&]() {
-        if (nb == 1)
-            k_pgd_iter<false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, rb.p, ne, Bf, HP, CB.p, nb,
-                                                           blk.p, gs.p, hist_loss, hist_viol);
-        else
-            k_pgd_iter<true><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, rb.p, ne, Bf, HP, CB.p, nb, blk.p,
-                                                          gs.p, nullptr, nullptr);
+    I.kernels_per_iter = I.n_heavy > 0 ? 2 : 1;
+    if (nb > 1) {
+        // work table of the blocks still iterating (all of them before the first launch)
+        DBuf<int64_t> roff(nb + 1, s);
+        PC_CUDA(cudaMemcpyAsync(roff.p, I.row_off.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        I.bw.alloc(nb, s);
+        I.act_blk.alloc(nb, s);
+        I.act_pref.alloc(nb + 1, s);
+        k_blk_work<<<grid_for(nb), 256, 0, s>>>(roff.p, c0.p, ne, n_chunks, nb, I.bw.p);
         PC_CHECK_LAUNCH();
-        if (n_heavy > 0) {
-            k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, rb.p, Bf, CB.p,
-                                                          blk.p);
-            PC_CHECK_LAUNCH();
-        }
-    };
-
-    // ---- iterations: launch in growing chunks, poll the device stop flag between chunks
-    int64_t launched = 0;
-    const int64_t max_launch = max_checks + 1;
-    int chunk = 4;
-    for (;;) {
-        for (int k = 0; k < chunk && launched < max_launch; ++k, ++launched) launch_iter();
-        const PgdGlobal *h = (const PgdGlobal *)read_back(hs, gs.p, sizeof(PgdGlobal), s);
-        if (h->all_stop) break;
-        if (launched >= max_launch) {
-            set_error("PGD loop did not reach its stop decision");
-            throw Fail{PC_ETIMEOUT};
-        }
-        chunk = std::min(chunk * 2, 256);
+        I.wt = WorkTab{I.bw.p, I.act_blk.p, I.act_pref.p};
+        k_worktab_init<<<1, 32, 0, s>>>(nb, I.blk.p, I.wt, I.gs.p);
+        PC_CHECK_LAUNCH();
+        PC_CUDA(cudaStreamSynchronize(s));   // roff is released on return
     }
-    PC_CUDA(cudaEventRecord(e_it, s));
-    k_output<<<grid_for(ne), 256, 0, s>>>(PE.p, rb.p, ne, Bf, blk.p, corrected);
+    I.HP.n_chunks = n_chunks;
+    I.HP.chunk_row = I.chunk_row.p;
+    I.HP.chunk_start = I.chunk_start.p;
+    I.HP.chunk_g = I.chunk_g.p;
+    const int64_t n_items = cdiv(ne, 32) + nb + n_chunks;
+    I.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS), (int64_t)num_sms() * 4));
+}
+
+PgdSolver::~PgdSolver() { delete im; }
+
+bool PgdSolver::empty() const { return im->ne == 0; }
+int64_t PgdSolver::max_launches() const { return im->max_checks + 1; }
+int64_t PgdSolver::rows() const { return im->ne; }
+
+void PgdSolver::capture(int k) {
+    Impl &I = *im;
+    if (I.ne == 0 || k < 1) return;
+    if (I.exec) {
+        cudaGraphExecDestroy(I.exec);
+        I.exec = nullptr;
+    }
+    if (I.graph) {
+        cudaGraphDestroy(I.graph);
+        I.graph = nullptr;
+    }
+    // capture on a private stream (the legacy default stream cannot be captured); nothing
+    // runs during capture, and the graph is replayed on the solver's stream
+    cudaStream_t cs = nullptr;
+    PC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const cudaStream_t run_s = I.s;
+    I.s = cs;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        try {
+            for (int j = 0; j < k; ++j) I.launch_iter();
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            I.s = run_s;
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        e = cudaStreamEndCapture(cs, &I.graph);
+    }
+    I.s = run_s;
+    cudaStreamDestroy(cs);
+    PC_CUDA(e);
+    PC_CUDA(cudaGraphInstantiate(&I.exec, I.graph, 0));
+    add_launches(-(int64_t)k * I.kernels_per_iter);   // captured, not run
+    I.graph_k = k;
+}
+
+int64_t PgdSolver::launch(int k) {
+    Impl &I = *im;
+    if (I.ne == 0) return 0;
+    int64_t done = 0;
+    if (I.exec) {
+        for (; done + I.graph_k <= k || done == 0; done += I.graph_k) {
+            PC_CUDA(cudaGraphLaunch(I.exec, I.s));
+            add_launches((int64_t)I.graph_k * I.kernels_per_iter);
+        }
+    } else {
+        for (; done < k; ++done) I.launch_iter();
+    }
+    launches += done;
+    return done;
+}
+
+void PgdSolver::post_status() {
+    Impl &I = *im;
+    PC_CUDA(cudaMemcpyAsync(I.pin, I.blk.p, I.nb * sizeof(PgdBlk), cudaMemcpyDeviceToHost, I.s));
+    PC_CUDA(cudaMemcpyAsync(I.pin + I.nb * sizeof(PgdBlk), I.gs.p, sizeof(PgdGlobal), cudaMemcpyDeviceToHost, I.s));
+    PC_CUDA(cudaEventRecord(I.ev, I.s));
+    I.posted = true;
+}
+
+bool PgdSolver::status_ready() const {
+    if (!im->posted) return false;
+    const cudaError_t e = cudaEventQuery(im->ev);
+    if (e == cudaErrorNotReady) return false;
+    PC_CUDA(e);
+    return true;
+}
+
+void PgdSolver::wait_status() const {
+    if (!im->posted) return;
+    PC_CUDA(cudaEventSynchronize(im->ev));
+}
+
+bool PgdSolver::all_stopped() const {
+    if (im->ne == 0) return true;
+    return ((const PgdGlobal *)(im->pin + im->nb * sizeof(PgdBlk)))->all_stop != 0;
+}
+
+bool PgdSolver::block_stopped(int b) const {
+    if (im->ne == 0) return true;
+    return ((const PgdBlk *)im->pin)[b].stop != 0;
+}
+
+void PgdSolver::output(float *corrected, int b) {
+    Impl &I = *im;
+    if (I.ne == 0) return;
+    const int64_t e0 = b < 0 ? 0 : I.row_off[b], e1 = b < 0 ? I.ne : I.row_off[b + 1];
+    if (e1 <= e0) return;
+    k_output<<<grid_for(e1 - e0), 256, 0, I.s>>>(I.PE.p, I.rb.p, e0, e1 - e0, I.Bf, I.blk.p, corrected);
     PC_CHECK_LAUNCH();
-    if (delta_out) {
-        k_delta_out<<<grid_for(ne), 256, 0, s>>>(PE.p, rb.p, ne, Bf, blk.p, delta_out);
-        PC_CHECK_LAUNCH();
+}
+
+void PgdSolver::delta_out(double *d) {
+    Impl &I = *im;
+    if (I.ne == 0) return;
+    k_delta_out<<<grid_for(I.ne), 256, 0, I.s>>>(I.PE.p, I.rb.p, I.ne, I.Bf, I.blk.p, d);
+    PC_CHECK_LAUNCH();
+}
+
+void PgdSolver::results(std::vector<PgdResult> &out) {
+    Impl &I = *im;
+    out.assign(I.nb, PgdResult());
+    if (I.ne == 0) {
+        for (auto &r : out) {
+            r.converged = true;
+            r.loss_evals = 1;
+        }
+        return;
     }
-    PC_CUDA(cudaEventRecord(e2, s));
-    const size_t rb_bytes = nb * sizeof(PgdBlk) + nb * sizeof(unsigned long long);
-    uint8_t *h = (uint8_t *)host_scratch(hs, rb_bytes);
-    PC_CUDA(cudaMemcpyAsync(h, blk.p, nb * sizeof(PgdBlk), cudaMemcpyDeviceToHost, s));
-    PC_CUDA(cudaMemcpyAsync(h + nb * sizeof(PgdBlk), rows_pb.p, nb * sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, s));
-    PC_CUDA(cudaStreamSynchronize(s));
-    const PgdBlk *hb = (const PgdBlk *)h;
-    const unsigned long long *rows = (const unsigned long long *)(h + nb * sizeof(PgdBlk));
-    for (int b = 0; b < nb; ++b) {
-        PgdResult &r = run.blocks[b];
+    post_status();
+    wait_status();
+    const PgdBlk *hb = (const PgdBlk *)I.pin;
+    for (int b = 0; b < I.nb; ++b) {
+        PgdResult &r = out[b];
         r.iters = hb[b].t;
         r.loss_evals = hb[b].t + 1;
         r.viol0 = (int64_t)hb[b].viol0;
@@ -1091,10 +1302,64 @@ PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp
         r.loss0 = hb[b].loss0;
         r.loss_final = hb[b].loss;
         r.converged = hb[b].converged != 0;
-        r.n_editable = (int64_t)rows[b];
+        r.n_editable = I.row_off[b + 1] - I.row_off[b];
     }
-    run.launches = launched;
-    finish_times();
+}
+
+PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
+               const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
+               HostScratch &hs, double *delta_out, double *hist_loss, unsigned long long *hist_viol, int graph_k) {
+    PgdRun run;
+    const int64_t n = B.n;
+    cudaEvent_t ev[4];
+    for (auto &e : ev) PC_CUDA(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int k = 0; k < 4; ++k) cudaEventDestroy(e[k]);
+        }
+    } guard{ev};
+    PC_CUDA(cudaEventRecord(ev[0], s));
+    k_copy_recon<<<grid_for(3 * n), 256, 0, s>>>(recon, corrected, 3 * n);
+    PC_CHECK_LAUNCH();
+    if (delta_out) PC_CUDA(cudaMemsetAsync(delta_out, 0, 3 * n * sizeof(double), s));
+    PgdSolver sol(B, S, cp, orig, recon, A, nA, s, hs, hist_loss, hist_viol);
+    PC_CUDA(cudaEventRecord(ev[1], s));
+    if (sol.empty()) {
+        // nothing to enforce anywhere: reconstructions stand, zero iterations
+        if (hist_loss) PC_CUDA(cudaMemsetAsync(hist_loss, 0, sizeof(double), s));
+        if (hist_viol) PC_CUDA(cudaMemsetAsync(hist_viol, 0, sizeof(unsigned long long), s));
+    } else {
+        if (graph_k > 0) sol.capture(graph_k);
+        // iterations: launch in growing chunks, poll the device stop flags between chunks
+        const int64_t max_launch = sol.max_launches();
+        int64_t launched = 0;
+        int chunk = graph_k > 0 ? graph_k : 4;
+        for (;;) {
+            launched += sol.launch(chunk);
+            sol.post_status();
+            sol.wait_status();
+            if (sol.all_stopped()) break;
+            if (launched >= max_launch) {
+                set_error("PGD loop did not reach its stop decision");
+                throw Fail{PC_ETIMEOUT};
+            }
+            chunk = std::min(chunk * 2, 256);
+        }
+    }
+    PC_CUDA(cudaEventRecord(ev[2], s));
+    sol.output(corrected);
+    if (delta_out) sol.delta_out(delta_out);
+    PC_CUDA(cudaEventRecord(ev[3], s));
+    sol.results(run.blocks);
+    float ms[3] = {0, 0, 0};
+    cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+    cudaEventElapsedTime(&ms[1], ev[1], ev[3]);
+    cudaEventElapsedTime(&ms[2], ev[1], ev[2]);
+    run.ms_csr = ms[0];
+    run.ms = ms[1];
+    run.ms_iter = ms[2];
+    run.launches = sol.launches;
     return run;
 }
 

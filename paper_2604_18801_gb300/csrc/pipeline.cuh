@@ -120,12 +120,46 @@ struct PgdRun {
     double ms_csr = 0;    // CSR and state build
     int64_t launches = 0;
 };
+// Resumable PGD over every block of a set (Algorithm 1, the loop).  The constructor
+// builds E, the CSR of A and the iteration state on stream s (it synchronises s a few
+// times); launch() enqueues iteration launches, replaying a captured CUDA graph when
+// capture() was called; each block stops on its own check (its later launches return
+// at once), so launching past a stop is harmless.  The history outputs require a
+// single block.  Not thread safe; every call works on stream s.
+class PgdSolver {
+  public:
+    PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
+              const float *recon, const unsigned long long *A, int64_t nA, cudaStream_t s, HostScratch &hs,
+              double *hist_loss = nullptr, unsigned long long *hist_viol = nullptr);
+    ~PgdSolver();
+    PgdSolver(const PgdSolver &) = delete;
+    PgdSolver &operator=(const PgdSolver &) = delete;
+    bool empty() const;                 // no active pair in any block
+    int64_t rows() const;               // |E| over all blocks
+    int64_t max_launches() const;       // launches after which every block has stopped
+    void capture(int k);                // capture k iteration launches into a graph
+    int64_t launch(int k);              // enqueue >= k launches (whole graphs when captured); returns the count
+    void post_status();                 // enqueue a copy of the stop flags to pinned memory
+    bool status_ready() const;          // that copy has landed
+    void wait_status() const;
+    bool all_stopped() const;           // from the last landed copy
+    bool block_stopped(int b) const;
+    void output(float *corrected, int b = -1);   // P + delta of the final buffer: every block, or block b
+    void delta_out(double *delta);
+    void results(std::vector<PgdResult> &out);   // per block; synchronises
+    int64_t launches = 0;
+  private:
+    struct Impl;
+    Impl *im;
+};
+
 // PGD for every block of the set; `cp` holds each block's PGD constants (built from
-// orig and recon).  The history outputs require a single block.
+// orig and recon).  The history outputs require a single block.  graph_k > 0 runs the
+// iterations as replays of a CUDA graph of graph_k launches.
 PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
                const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
                HostScratch &hs, double *delta_out = nullptr, double *hist_loss = nullptr,
-               unsigned long long *hist_viol = nullptr);
+               unsigned long long *hist_viol = nullptr, int graph_k = 0);
 
 // ---------------------------------------------------------------- host scratch
 void *host_scratch(HostScratch &hs, size_t bytes);
