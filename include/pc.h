@@ -225,6 +225,67 @@ pc_status pc_apply_edits(pc_ctx *ctx, const float *recon_dev, int64_t n, const u
 pc_status pc_apply_edits_static(const float *recon_dev, int64_t n, const uint8_t *stream_dev, size_t nbytes,
                                 float *out_dev, void *stream);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop around pc_correct (not part of the paper).  A server owns one worker
+ * thread on the context's device.  Submitted jobs wait in FIFO order until they can be
+ * admitted: the jobs admitted together form a cohort that is set up in one pass
+ * (validation, binning, pair-search count pass), admitted to the rest (selection, PGD)
+ * only when the device-memory estimate from its counts fits the budget, and then
+ * iterates on its own stream, replaying a CUDA graph of PGD launches, while later
+ * cohorts are admitted and set up beside it (continuous batching: work of jobs that
+ * arrived at different times overlaps on the device).  A job finishes as soon as its own
+ * block stops: its corrected coordinates are copied out and, when asked, its edit
+ * stream is encoded.  Every job's result is bit-identical to pc_correct (and
+ * pc_encode_edits) on that job alone, whatever it was batched with.
+ *
+ * Buffers of a job are device buffers on the server's device; the caller keeps them
+ * valid, and its inputs ready and unchanged, from submission until the job is DONE or
+ * ERROR.  Thread safe: submit, poll and wait may be called from any thread. */
+typedef struct pc_server pc_server;
+
+typedef enum { PC_JOB_PENDING = 0, PC_JOB_RUNNING = 1, PC_JOB_DONE = 2, PC_JOB_ERROR = 3 } pc_job_state;
+
+typedef struct {
+    const float *orig_dev;    /* n x 3 original coordinates                              */
+    const float *recon_dev;   /* n x 3 reconstruction, |recon - orig| <= xi                */
+    int64_t n;
+    pc_params params;
+    float *corrected_dev;     /* n x 3 output                                             */
+    uint8_t *stream_dev;      /* edit stream output, or NULL for none                     */
+    size_t stream_cap;        /* bytes available at stream_dev                             */
+} pc_job;
+
+typedef struct {
+    int32_t state;            /* pc_job_state                                              */
+    int32_t status;           /* once DONE or ERROR: PC_OK, PC_WARN_NOT_CONVERGED or an error */
+    int64_t submit_ns;        /* steady-clock times of submission, admission and completion */
+    int64_t start_ns;
+    int64_t done_ns;
+    uint64_t stream_bytes;    /* size of the edit stream written (0 without one)            */
+    int32_t cohort_jobs;      /* jobs set up together with this one                        */
+    int32_t pad_;
+    pc_correct_stats stats;
+    char error[160];          /* message of an ERROR                                       */
+} pc_job_result;
+
+/* mem_budget: device bytes the server's jobs may hold at once (0 = 40 GiB); max_slots:
+ * jobs resident at once (0 = 256); max_cohort_particles: particles admitted together in
+ * one cohort (0 = 2^24).  A job whose estimate alone exceeds the budget ends in ERROR
+ * with PC_ENOMEM. */
+pc_status pc_server_create(pc_ctx *ctx, size_t mem_budget, int32_t max_slots, int64_t max_cohort_particles,
+                           pc_server **out);
+/* Finishes every submitted job, then stops the worker and frees the server. */
+void pc_server_destroy(pc_server *srv);
+/* Queues a job (parameters are checked at once: PC_EINVAL, no ticket).  Never blocks. */
+pc_status pc_serve_submit(pc_server *srv, const pc_job *job, uint64_t *ticket);
+/* Current state of a job (PC_EBUSY for an unknown ticket). */
+pc_status pc_serve_poll(pc_server *srv, uint64_t ticket, pc_job_result *res);
+/* Waits until the job is DONE or ERROR, at most timeout_ms (< 0: no limit); PC_ETIMEOUT
+ * when the time ran out (res then holds the current state). */
+pc_status pc_serve_wait(pc_server *srv, uint64_t ticket, int64_t timeout_ms, pc_job_result *res);
+/* Server counters: jobs submitted, finished, cohorts formed, peak estimated bytes. */
+pc_status pc_serve_counters(pc_server *srv, int64_t out[4]);
+
 #ifdef __cplusplus
 }
 #endif

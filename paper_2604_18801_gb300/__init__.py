@@ -8,6 +8,8 @@ step of the method runs in the library's CUDA kernels:
 * :func:`select_constraints`    -- vulnerable pairs and the active set A (Sec. 3.1-3.2)
 * :func:`correct`               -- projected Adam descent on the tight loss (Alg. 1, Eq. 3)
 * :func:`encode_edits` / :func:`apply_edits` -- edit stream and decoder (Sec. 3.3)
+* :func:`correct_batch`         -- many independent blocks in one pass (batching layer)
+* :class:`Server`               -- request loop with continuous batching (serving layer)
 """
 from __future__ import annotations
 
@@ -19,8 +21,7 @@ from . import _native
 from ._native import PcError, make_params, struct_dict
 
 __all__ = ["Context", "fof_labels", "select_constraints", "Constraints", "correct", "correct_detail", "correct_batch",
-           "encode_edits",
-           "apply_edits", "PcError", "make_params", "default_context"]
+           "encode_edits", "apply_edits", "Server", "PcError", "make_params", "default_context"]
 
 MODES = {"VP": 0, "SC": 1, "HF": 2}
 
@@ -227,3 +228,96 @@ def apply_edits(recon: torch.Tensor, stream: torch.Tensor, out: torch.Tensor = N
                                                stream.numel(), out.data_ptr(), _stream(recon.device)),
                   "pc_apply_edits")
     return out
+
+
+class Server:
+    """Request loop of the library (pc_server_*): jobs are admitted under a device-memory
+    budget, set up together as they arrive and iterate side by side; each job's result is
+    bit-identical to :func:`correct` (and :func:`encode_edits`) on that job alone.
+
+    The tensors of a submitted job are kept referenced here until the job is finished."""
+
+    def __init__(self, mem_budget: int = 0, max_slots: int = 0, max_cohort_particles: int = 0,
+                 ctx: Context = None, device: int = 0):
+        self.ctx = ctx or default_context(device)
+        self.device = torch.device("cuda", self.ctx.device)
+        h = C.c_void_p()
+        _native.check(_native.lib().pc_server_create(self.ctx.h, int(mem_budget), int(max_slots),
+                                                     int(max_cohort_particles), C.byref(h)), "pc_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, orig: torch.Tensor, recon: torch.Tensor, params, out: torch.Tensor = None,
+               stream_cap: int = 0) -> int:
+        """Queues one job; returns its ticket.  stream_cap > 0 also asks for the edit stream
+        (a uint8 buffer of that many bytes, see :meth:`result`).  The inputs must be ready
+        (the current stream is synchronised here)."""
+        _xyz(orig, "orig")
+        _xyz(recon, "recon")
+        out = torch.empty_like(orig) if out is None else _xyz(out, "out")
+        buf = torch.empty(int(stream_cap), dtype=torch.uint8, device=orig.device) if stream_cap > 0 else None
+        torch.cuda.current_stream(orig.device).synchronize()
+        j = _native.Job()
+        j.orig_dev, j.recon_dev, j.n = orig.data_ptr(), recon.data_ptr(), orig.shape[0]
+        j.params = _params(params)
+        j.corrected_dev = out.data_ptr()
+        j.stream_dev = buf.data_ptr() if buf is not None else None
+        j.stream_cap = int(stream_cap)
+        t = C.c_uint64(0)
+        _native.check(_native.lib().pc_serve_submit(self.h, C.byref(j), C.byref(t)), "pc_serve_submit")
+        self._keep[t.value] = (orig, recon, out, buf)
+        return t.value
+
+    def _res(self, r) -> dict:
+        d = {k: getattr(r, k) for k in ("status", "submit_ns", "start_ns", "done_ns", "stream_bytes", "cohort_jobs")}
+        d["state"] = _native.JOB_STATES[r.state]
+        d["stats"] = struct_dict(r.stats)
+        d["error"] = r.error.decode(errors="replace")
+        return d
+
+    def poll(self, ticket: int) -> dict:
+        r = _native.JobResult()
+        _native.check(_native.lib().pc_serve_poll(self.h, ticket, C.byref(r)), "pc_serve_poll")
+        return self._res(r)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        r = _native.JobResult()
+        code = _native.lib().pc_serve_wait(self.h, ticket, int(timeout_ms), C.byref(r))
+        if code == -6:
+            return self._res(r)
+        _native.check(code, "pc_serve_wait")
+        return self._res(r)
+
+    def result(self, ticket: int, release: bool = True, timeout_ms: int = 600000):
+        """(corrected, edit stream or None, result dict) of a finished job; TimeoutError if
+        the job has not finished within timeout_ms."""
+        d = self.wait(ticket, timeout_ms)
+        if d["state"] not in ("DONE", "ERROR"):
+            raise TimeoutError(f"job {ticket} still {d['state']} after {timeout_ms} ms")
+        orig, recon, out, buf = self._keep[ticket] if not release else self._keep.pop(ticket)
+        if buf is not None:
+            buf = buf[: d["stream_bytes"]]
+        return out, buf, d
+
+    def counters(self) -> dict:
+        a = (C.c_int64 * 4)()
+        _native.check(_native.lib().pc_serve_counters(self.h, a), "pc_serve_counters")
+        return dict(submitted=a[0], finished=a[1], cohorts=a[2], peak_bytes=a[3])
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            _native.lib().pc_server_destroy(self.h)
+            self.h = C.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -49,6 +49,20 @@ class Block(C.Structure):
     _fields_ = [("offset", C.c_int64), ("n", C.c_int64), ("params", Params)]
 
 
+class Job(C.Structure):
+    _fields_ = [("orig_dev", C.c_void_p), ("recon_dev", C.c_void_p), ("n", C.c_int64), ("params", Params),
+                ("corrected_dev", C.c_void_p), ("stream_dev", C.c_void_p), ("stream_cap", C.c_size_t)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("submit_ns", C.c_int64), ("start_ns", C.c_int64),
+                ("done_ns", C.c_int64), ("stream_bytes", C.c_uint64), ("cohort_jobs", C.c_int32),
+                ("pad_", C.c_int32), ("stats", CorrectStats), ("error", C.c_char * 160)]
+
+
+JOB_STATES = {0: "PENDING", 1: "RUNNING", 2: "DONE", 3: "ERROR"}
+
+
 def struct_dict(s) -> dict:
     return {k: getattr(s, k) for k, _ in s._fields_ if not k.endswith("_")}
 
@@ -84,8 +98,16 @@ def lib():
         L.pc_correct_batch.argtypes = [vp, vp, vp, C.POINTER(Block), C.c_int32, vp, C.POINTER(CorrectStats), vp]
         L.pc_encode_edits.argtypes = [vp, vp, vp, i64, P, vp, sz, C.POINTER(sz), vp]
         L.pc_apply_edits.argtypes = [vp, vp, i64, vp, sz, vp, vp]
+        L.pc_server_create.argtypes = [vp, sz, C.c_int32, i64, C.POINTER(vp)]
+        L.pc_server_destroy.argtypes = [vp]
+        L.pc_server_destroy.restype = None
+        L.pc_serve_submit.argtypes = [vp, C.POINTER(Job), C.POINTER(C.c_uint64)]
+        L.pc_serve_poll.argtypes = [vp, C.c_uint64, C.POINTER(JobResult)]
+        L.pc_serve_wait.argtypes = [vp, C.c_uint64, i64, C.POINTER(JobResult)]
+        L.pc_serve_counters.argtypes = [vp, C.POINTER(i64)]
         for f in ("pc_ctx_create", "pc_fof_labels", "pc_select_constraints", "pc_constraints_copy", "pc_correct",
-                  "pc_correct_detail", "pc_correct_batch",
+                  "pc_correct_detail", "pc_correct_batch", "pc_server_create", "pc_serve_submit", "pc_serve_poll",
+                  "pc_serve_wait", "pc_serve_counters",
                   "pc_encode_edits", "pc_apply_edits"):
             getattr(L, f).restype = C.c_int
         _lib = L

@@ -33,6 +33,8 @@ double ulp32(double x) {
     return std::ldexp(1.0, e - 24);
 }
 
+}  // namespace
+
 void fail(pc_status st, const std::string &msg) {
     set_error(msg);
     throw Fail{st};
@@ -67,7 +69,16 @@ void check_inspect(const Inspect &ins) {
     if (ins.err & ERR_BOUND) fail(PC_EBOUND, "some |recon - orig| exceeds xi");
 }
 
-}  // namespace
+void check_block_inputs(const BlockSet &S) {
+    for (int b = 0; b < S.nb; ++b) {
+        try {
+            check_inspect(S.ins[b]);
+        } catch (const Fail &f) {
+            if (S.nb > 1) set_error("block " + std::to_string(b) + ": " + pc_last_error());
+            throw;
+        }
+    }
+}
 
 // Constants of Sec. 3.1 and Sec. 3.3 and the cell grid (see include/pc.h for the readings).
 Consts make_consts(const pc_params *p, const Inspect &ins, int64_t n, bool window) {
@@ -169,13 +180,9 @@ struct pc_ctx {
     HostScratch hs;
 };
 
-struct pc_constraints {
-    BlockSet S;
-    Binned B;
-    DBuf<unsigned long long> A;     // active pairs (min_pos << 32 | max_pos)
-    int64_t nA = 0;
-    std::vector<pc_select_stats> stats;   // per block
-};
+struct pc_constraints : pc::Selection {};
+
+int pc::ctx_device(const pc_ctx *ctx) { return ctx->device; }
 
 namespace {
 
@@ -209,80 +216,90 @@ void release_to_default_stream(pc_constraints *h) {
     h->A.s = 0;
 }
 
-void check_block_inputs(const BlockSet &S) {
-    for (int b = 0; b < S.nb; ++b) {
-        try {
-            check_inspect(S.ins[b]);
-        } catch (const Fail &f) {
-            if (S.nb > 1) set_error("block " + std::to_string(b) + ": " + pc_last_error());
-            throw;
-        }
-    }
-}
+}  // namespace
 
-// Binning, pair search, union-find and selection for every block of S (Sec. 3.2, 3.3).
-// S.prm and S.off must be set; fills S and the handle.
-void do_select(pc_ctx *ctx, const float *orig, cudaStream_t s, pc_constraints *h) {
-    BlockSet &S = h->S;
+namespace pc {
+
+// Count pass of the selection (Sec. 3.2): binning, pair search pass 1 (union-find over
+// links and safe links, class counts).  S.prm and S.off must be set.
+void select_count(HostScratch &hs, const float *orig, cudaStream_t s, Selection &h) {
+    BlockSet &S = h.S;
     const int nb = S.nb;
     const int64_t n = S.n;
-    cudaEvent_t e0, e1;
-    PC_CUDA(cudaEventCreate(&e0));
-    PC_CUDA(cudaEventCreate(&e1));
-    PC_CUDA(cudaEventRecord(e0, s));
-    inspect_blocks(orig, nullptr, S, s, ctx->hs);
+    PC_CUDA(cudaEventCreate(&h.ev0));
+    PC_CUDA(cudaEventRecord(h.ev0, s));
+    inspect_blocks(orig, nullptr, S, s, hs);
     check_block_inputs(S);
     setup_blocks(S, true, s);
-    bin_particles(orig, S, h->B, s, ctx->hs);
-    bool any_fof = false, any_safe = false;
+    bin_particles(orig, S, h.B, s, hs);
+    h.any_fof = h.any_safe = false;
     for (int b = 0; b < nb; ++b) {
-        any_fof |= S.prm[b].mode == PC_MODE_HF;
-        any_safe |= S.prm[b].mode != PC_MODE_VP;
+        h.any_fof |= S.prm[b].mode == PC_MODE_HF;
+        h.any_safe |= S.prm[b].mode != PC_MODE_VP;
     }
-    DBuf<unsigned long long> counts(CNT_N, s), bc(4 * nb + nb, s);
-    DBuf<uint32_t> err(1, s);
-    PC_CUDA(cudaMemsetAsync(counts.p, 0, CNT_N * sizeof(unsigned long long), s));
-    PC_CUDA(cudaMemsetAsync(bc.p, 0, 5 * nb * sizeof(unsigned long long), s));
-    PC_CUDA(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s));
-    DBuf<uint32_t> fof, safe;
-    if (any_fof) {
-        fof.alloc(n, s);
-        uf_init(fof.p, n, s);
+    h.counts.alloc(CNT_N, s);
+    h.bc.alloc(5 * nb, s);
+    h.err.alloc(1, s);
+    PC_CUDA(cudaMemsetAsync(h.counts.p, 0, CNT_N * sizeof(unsigned long long), s));
+    PC_CUDA(cudaMemsetAsync(h.bc.p, 0, 5 * nb * sizeof(unsigned long long), s));
+    PC_CUDA(cudaMemsetAsync(h.err.p, 0, sizeof(uint32_t), s));
+    if (h.any_fof) {
+        h.fof.alloc(n, s);
+        uf_init(h.fof.p, n, s);
     }
-    if (any_safe) {
-        safe.alloc(n, s);
-        uf_init(safe.p, n, s);
+    if (h.any_safe) {
+        h.safe.alloc(n, s);
+        uf_init(h.safe.p, n, s);
     }
-    pair_pass_union(h->B, S, fof.p, safe.p, counts.p, err.p, s, nb > 1 ? bc.p : nullptr);
-    if (fof.p) uf_flatten(fof.p, n, s);
-    if (safe.p) uf_flatten(safe.p, n, s);
-    unsigned long long cnt[CNT_N];
-    memcpy(cnt, read_back(ctx->hs, counts.p, sizeof(cnt), s), sizeof(cnt));
-    const uint32_t e1v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
-    if (e1v & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
+    pair_pass_union(h.B, S, h.fof.p, h.safe.p, h.counts.p, h.err.p, s, nb > 1 ? h.bc.p : nullptr);
+    if (h.fof.p) uf_flatten(h.fof.p, n, s);
+    if (h.safe.p) uf_flatten(h.safe.p, n, s);
+    memcpy(h.cnt, read_back(hs, h.counts.p, sizeof(h.cnt), s), sizeof(h.cnt));
+    const uint32_t ev = *(uint32_t *)read_back(hs, h.err.p, sizeof(uint32_t), s);
+    if (ev & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
+}
+
+// Device bytes the emission, the spanning forest and the PGD state will take on top of
+// the count pass (an upper estimate from the class counts).
+int64_t select_more_bytes(const Selection &h) {
+    const int64_t capA = (int64_t)(h.cnt[CNT_PB] + h.cnt[CNT_PC]), pb = (int64_t)h.cnt[CNT_PB];
+    const int64_t rows = std::min<int64_t>(h.S.n, 2 * capA);
+    int64_t b = 8 * capA;                       // A
+    if (h.any_fof) b += 8 * pb + 24 * pb;       // C and the forest temporaries
+    b += 48 * capA;                             // directed keys (sorted twice) and columns
+    b += 200 * rows + 16 * h.S.n;               // PGD state per row, marks and dense map
+    return b;
+}
+
+// Emission pass and the spanning forest (Sec. 3.2), per-block statistics.
+void select_emit(HostScratch &hs, cudaStream_t s, Selection &h) {
+    BlockSet &S = h.S;
+    const int nb = S.nb;
+    const int64_t n = S.n;
+    const unsigned long long *cnt = h.cnt;
     const uint64_t capA = std::max<uint64_t>(1, cnt[CNT_PB] + cnt[CNT_PC]);
-    const uint64_t capC = any_fof ? std::max<uint64_t>(1, cnt[CNT_PB]) : 0;
-    h->A.alloc(capA, s);
+    const uint64_t capC = h.any_fof ? std::max<uint64_t>(1, cnt[CNT_PB]) : 0;
+    h.A.alloc(capA, s);
     DBuf<unsigned long long> C(capC, s);
-    pair_pass_emit(h->B, S, fof.p, safe.p, h->A.p, capA, C.p, capC, counts.p, err.p, s);
+    pair_pass_emit(h.B, S, h.fof.p, h.safe.p, h.A.p, capA, C.p, capC, h.counts.p, h.err.p, s);
     unsigned long long cnt2[CNT_N];
-    memcpy(cnt2, read_back(ctx->hs, counts.p, sizeof(cnt2), s), sizeof(cnt2));
-    const uint32_t e2v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
+    memcpy(cnt2, read_back(hs, h.counts.p, sizeof(cnt2), s), sizeof(cnt2));
+    const uint32_t e2v = *(uint32_t *)read_back(hs, h.err.p, sizeof(uint32_t), s);
     if (e2v & ERR_INDEX) fail(PC_ECUDA, "pair emission overflowed its count");
     int64_t nA = (int64_t)cnt2[CNT_A];
     int64_t n_forest = 0;
-    if (any_fof) {
-        n_forest = halo_forest(h->B, S, safe.p, C.p, (int64_t)cnt2[CNT_C], h->A.p, nA, err.p, s, ctx->hs);
+    if (h.any_fof) {
+        n_forest = halo_forest(h.B, S, h.safe.p, C.p, (int64_t)cnt2[CNT_C], h.A.p, nA, h.err.p, s, hs);
         nA += n_forest;
-        const uint32_t e3v = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
+        const uint32_t e3v = *(uint32_t *)read_back(hs, h.err.p, sizeof(uint32_t), s);
         if (e3v & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
     }
-    h->nA = nA;
+    h.nA = nA;
     // statistics per block
-    h->stats.assign(nb, pc_select_stats());
-    for (auto &st : h->stats) memset(&st, 0, sizeof(st));
+    h.stats.assign(nb, pc_select_stats());
+    for (auto &st : h.stats) memset(&st, 0, sizeof(st));
     if (nb == 1) {
-        pc_select_stats &st = h->stats[0];
+        pc_select_stats &st = h.stats[0];
         st.n_links = (int64_t)cnt[CNT_LINKS];
         st.n_safe = (int64_t)cnt[CNT_SAFE];
         st.n_pb = (int64_t)cnt[CNT_PB];
@@ -290,18 +307,18 @@ void do_select(pc_ctx *ctx, const float *orig, cudaStream_t s, pc_constraints *h
         st.n_vulnerable = (int64_t)(cnt[CNT_PB] + cnt[CNT_PC]);
         st.n_active = nA;
         st.n_forest = n_forest;
-        if (fof.p) st.n_halos = count_roots(fof.p, n, s, ctx->hs);
-        if (safe.p) st.n_safe_comps = count_roots(safe.p, n, s, ctx->hs);
+        if (h.fof.p) st.n_halos = count_roots(h.fof.p, n, s, hs);
+        if (h.safe.p) st.n_safe_comps = count_roots(h.safe.p, n, s, hs);
     } else {
         if (nA > 0) {
             const int g = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nA, 256), (int64_t)num_sms() * 8));
-            k_pairs_per_block<<<g, 256, 0, s>>>(h->A.p, nA, S.doff.p, nb, bc.p + 4 * nb);
+            k_pairs_per_block<<<g, 256, 0, s>>>(h.A.p, nA, S.doff.p, nb, h.bc.p + 4 * nb);
             PC_CHECK_LAUNCH();
         }
         const unsigned long long *hc =
-            (const unsigned long long *)read_back(ctx->hs, bc.p, 5 * nb * sizeof(unsigned long long), s);
+            (const unsigned long long *)read_back(hs, h.bc.p, 5 * nb * sizeof(unsigned long long), s);
         for (int b = 0; b < nb; ++b) {
-            pc_select_stats &st = h->stats[b];
+            pc_select_stats &st = h.stats[b];
             st.n_links = (int64_t)hc[4 * b + 0];
             st.n_safe = (int64_t)hc[4 * b + 1];
             st.n_pb = (int64_t)hc[4 * b + 2];
@@ -310,13 +327,32 @@ void do_select(pc_ctx *ctx, const float *orig, cudaStream_t s, pc_constraints *h
             st.n_active = (int64_t)hc[4 * nb + b];
         }
     }
+    h.fof.release();
+    h.safe.release();
+    h.counts.release();
+    h.bc.release();
+    h.err.release();
+    cudaEvent_t e1;
+    PC_CUDA(cudaEventCreate(&e1));
     PC_CUDA(cudaEventRecord(e1, s));
     PC_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    for (auto &st : h->stats) st.ms = ms;
-    cudaEventDestroy(e0);
+    cudaEventElapsedTime(&ms, h.ev0, e1);
+    for (auto &st : h.stats) st.ms = ms;
     cudaEventDestroy(e1);
+    cudaEventDestroy(h.ev0);
+    h.ev0 = nullptr;
+}
+
+}  // namespace pc
+
+namespace {
+
+// Binning, pair search, union-find and selection for every block of S (Sec. 3.2, 3.3).
+// S.prm and S.off must be set; fills S and the handle.
+void do_select(pc_ctx *ctx, const float *orig, cudaStream_t s, pc_constraints *h) {
+    select_count(ctx->hs, orig, s, *h);
+    select_emit(ctx->hs, s, *h);
 }
 
 void single_block(BlockSet &S, int64_t n, const pc_params *p) {

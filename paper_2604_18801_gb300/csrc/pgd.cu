@@ -1306,6 +1306,25 @@ void PgdSolver::results(std::vector<PgdResult> &out) {
     }
 }
 
+void PgdSolver::block_result(int b, PgdResult &r) const {
+    const Impl &I = *im;
+    r = PgdResult();
+    if (I.ne == 0) {
+        r.converged = true;
+        r.loss_evals = 1;
+        return;
+    }
+    const PgdBlk &B = ((const PgdBlk *)I.pin)[b];
+    r.iters = B.t;
+    r.loss_evals = B.t + 1;
+    r.viol0 = (int64_t)B.viol0;
+    r.viol_final = (int64_t)B.viol;
+    r.loss0 = B.loss0;
+    r.loss_final = B.loss;
+    r.converged = B.converged != 0;
+    r.n_editable = I.row_off[b + 1] - I.row_off[b];
+}
+
 PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
                const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
                HostScratch &hs, double *delta_out, double *hist_loss, unsigned long long *hist_viol, int graph_k) {

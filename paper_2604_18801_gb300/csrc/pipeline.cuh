@@ -147,6 +147,7 @@ class PgdSolver {
     void output(float *corrected, int b = -1);   // P + delta of the final buffer: every block, or block b
     void delta_out(double *delta);
     void results(std::vector<PgdResult> &out);   // per block; synchronises
+    void block_result(int b, PgdResult &r) const;  // block b, from the last landed status copy
     int64_t launches = 0;
   private:
     struct Impl;
@@ -160,6 +161,42 @@ PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp
                const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
                HostScratch &hs, double *delta_out = nullptr, double *hist_loss = nullptr,
                unsigned long long *hist_viol = nullptr, int graph_k = 0);
+
+// ---------------------------------------------------------------- selection (api.cu)
+int ctx_device(const pc_ctx *ctx);
+void fail(pc_status st, const std::string &msg);                 // set_error + throw
+void check_params(const pc_params *p, int64_t n, bool need_pgd);  // PC_EINVAL on bad parameters
+void check_inspect(const Inspect &ins);                           // PC_EINVAL / PC_EBOUND on bad input
+void check_block_inputs(const BlockSet &S);                       // the same, naming the block
+Consts make_consts(const pc_params *p, const Inspect &ins, int64_t n, bool window);
+
+// Selected constraints of a block set, resident on the device.
+struct Selection {
+    BlockSet S;
+    Binned B;
+    DBuf<unsigned long long> A;           // active pairs (min_pos << 32 | max_pos)
+    int64_t nA = 0;
+    std::vector<pc_select_stats> stats;   // per block
+    // between the count and the emission passes
+    DBuf<unsigned long long> counts, bc;
+    DBuf<uint32_t> err, fof, safe;
+    unsigned long long cnt[CNT_N] = {};
+    bool any_fof = false, any_safe = false;
+    cudaEvent_t ev0 = nullptr;
+    ~Selection() {
+        if (ev0) cudaEventDestroy(ev0);
+    }
+};
+// Count pass (binning, pass 1 of the pair search): S.prm and S.off must be set.
+void select_count(HostScratch &hs, const float *orig, cudaStream_t s, Selection &h);
+// Device bytes that select_emit and the PGD state will add (upper estimate from the counts).
+int64_t select_more_bytes(const Selection &h);
+// Emission pass, halo forest, per-block statistics; releases the count-pass temporaries.
+void select_emit(HostScratch &hs, cudaStream_t s, Selection &h);
+
+// Edit stream (edits.cu)
+size_t encode_edits(const float *recon, const float *corr, int64_t n, const pc_params *p, uint8_t *out, size_t cap,
+                    cudaStream_t s, HostScratch &hs);
 
 // ---------------------------------------------------------------- host scratch
 void *host_scratch(HostScratch &hs, size_t bytes);

@@ -22,7 +22,8 @@ def test_library_exports_every_declared_symbol():
     path = _build.build()
     lib = C.CDLL(path)
     syms = declared_symbols()
-    assert {"pc_correct", "pc_fof_labels", "pc_select_constraints", "pc_encode_edits", "pc_apply_edits"} <= syms
+    assert {"pc_correct", "pc_fof_labels", "pc_select_constraints", "pc_encode_edits", "pc_apply_edits",
+            "pc_correct_batch", "pc_server_create", "pc_serve_submit", "pc_serve_poll", "pc_serve_wait"} <= syms
     missing = [s for s in syms if not hasattr(lib, s)]
     assert not missing, missing
 
@@ -40,10 +41,43 @@ def test_param_defaults():
 
 
 def test_struct_sizes_match_the_header():
-    # pc_params: 2+3+3 doubles, 4 ints, 5 doubles, 2 ints
+    # pc_params: 2+3+3 doubles, 4 ints, 5 doubles, 4 ints
     assert C.sizeof(_native.Params) == 8 * 8 + 4 * 4 + 5 * 8 + 4 * 4
     assert C.sizeof(_native.SelectStats) == 10 * 8 + 8
     assert C.sizeof(_native.CorrectStats) == 4 * 8 + 2 * 8 + 3 * 8 + 8 + 3 * 8 + 8
+
+
+def test_struct_layouts_match_a_c_compiler(tmp_path):
+    # sizes and field offsets as a C compiler lays out include/pc.h
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    checks = [("pc_params", _native.Params, ["b", "xi", "periodic", "t_max", "alpha_rel", "loss_tol", "replay_iters",
+                                              "stall_patience"]),
+              ("pc_select_stats", _native.SelectStats, ["n_links", "ms"]),
+              ("pc_correct_stats", _native.CorrectStats, ["converged", "ms_setup", "pgd_launches"]),
+              ("pc_block", _native.Block, ["n", "params"]),
+              ("pc_job", _native.Job, ["n", "params", "corrected_dev", "stream_cap"]),
+              ("pc_job_result", _native.JobResult, ["done_ns", "stream_bytes", "cohort_jobs", "stats", "error"])]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pc.h"', "int main(void) {"]
+    for cname, _, fields in checks:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for _, cls, fields in checks:
+        want.append(C.sizeof(cls))
+        want += [getattr(cls, f).offset for f in fields]
+    assert got == want
 
 
 def test_product_path_has_no_oracle_import():
