@@ -14,6 +14,8 @@ reports membership_exact (a run that loses membership does not count).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--eps 0.1] [--modes VP,SC,HF]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample (CPU baseline arm)
+  python bench.py --workload batch       # 512 mixed blocks in one batched pass vs one at a time
+  python bench.py --workload serve       # 2,000 requests, Poisson arrivals, p50/p99 latency
 
 N > 1 (torchrun) runs independent replicas, one per GPU: the method has no
 data exchange on one node; value = all ranks' particles / max elapsed.
@@ -49,6 +51,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--cpu-side", type=float, default=0.33, help="side of the sub-cube the CPU baseline corrects")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"])
+    ap.add_argument("--blocks", type=int, default=512, help="batch: number of blocks")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
+    ap.add_argument("--load", type=float, default=0.8, help="serve: arrival rate / batched capacity")
+    ap.add_argument("--procs", type=int, default=0, help="host processes generating inputs (0 = all cores)")
     return ap.parse_args()
 
 
@@ -135,8 +142,235 @@ def cpu_baseline(w, modes, side):
                       f"{dt:.1f} s single-threaded"}
 
 
+def _gen(spec):
+    from paper_2604_18801_gb300 import synth
+    w = synth.make_request(spec)
+    return spec["k"], w
+
+
+def generate(specs, procs):
+    """Draws the workloads of `specs` in a pool of spawned processes (before any CUDA call)."""
+    import multiprocessing as mp
+    procs = procs or min(32, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        got = dict(pool.imap_unordered(_gen, specs, chunksize=1))
+    return [got[s["k"]] for s in specs]
+
+
+def block_specs(nb, seed=3, lo=1e3, hi=1e6):
+    """The mixed blocks of the batched form: log-uniform sizes, half HACC-shaped and half
+    MD-like, eps in {0.1 b, 0.5 b}, modes drawn from VP/SC/HF (the draws of synth.mixed_blocks)."""
+    import math
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(lo), math.log(hi), nb)).astype(np.int64)
+    eps = rng.choice([0.1, 0.5], nb)
+    modes = rng.choice(["VP", "SC", "HF"], nb)
+    return [dict(k=k, kind=("hacc", "md")[k % 2], n=int(sizes[k]), eps=float(eps[k]), mode=str(modes[k]),
+                 seed=1000 * seed + k) for k in range(nb)]
+
+
+def membership_ok(pc, torch, o, r, corr, stream, prm, xi) -> bool:
+    dec = pc.apply_edits(r, stream)
+    l0, _ = pc.fof_labels(o, prm)
+    l1, _ = pc.fof_labels(dec, prm)
+    return bool(torch.equal(l0, l1)) and float((dec.double() - o.double()).abs().max()) <= xi
+
+
+def run_batch(a):
+    """Batched form: every block corrected in one pass (pc_correct_batch, CUDA-graph PGD)
+    and its edit stream encoded, against the same blocks one at a time."""
+    specs = block_specs(a.blocks)
+    t = time.perf_counter()
+    ws = generate(specs, a.procs)
+    gen_s = time.perf_counter() - t
+    import numpy as np
+    import torch
+    import paper_2604_18801_gb300 as pc
+    from paper_2604_18801_gb300 import _native
+    dev = torch.device("cuda", 0)
+    orig = torch.from_numpy(np.concatenate([w.orig for w in ws])).to(dev)
+    recon = torch.from_numpy(np.concatenate([w.recon for w in ws])).to(dev)
+    sizes = [w.n for w in ws]
+    prms = [w.params() for w in ws]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    n = int(offs[-1])
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        out, stats, code = pc.correct_batch(orig, recon, sizes, prms)
+        streams = [pc.encode_edits(recon[offs[k]:offs[k + 1]], out[offs[k]:offs[k + 1]], prms[k])
+                   for k in range(len(ws))]
+        return out, stats, code, streams
+
+    def one_at_a_time():
+        res = []
+        for k in range(len(ws)):
+            o, r = orig[offs[k]:offs[k + 1]], recon[offs[k]:offs[k + 1]]
+            c, st, code = pc.correct(o, r, prms[k])
+            res.append((c, pc.encode_edits(r, c, prms[k]), code))
+        return res
+
+    for _ in range(max(3, a.warmup)):
+        res = step()
+    launches0 = _native.lib().pc_kernel_launches()
+    clk = Clocks(0)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        res = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    launches = _native.lib().pc_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1) / a.steps
+    value = n / (ms / 1e3) / 1e6
+    # one at a time (same work, same encodes)
+    one_at_a_time()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    seq = one_at_a_time()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_ms = e0.elapsed_time(e1)
+    out, stats, code, streams = res
+    same = all(torch.equal(out[offs[k]:offs[k + 1]], seq[k][0]) and torch.equal(streams[k], seq[k][1])
+               for k in range(len(ws)))
+    exact = code == 0 and all(membership_ok(pc, torch, orig[offs[k]:offs[k + 1]], recon[offs[k]:offs[k + 1]],
+                                            out[offs[k]:offs[k + 1]], streams[k], prms[k], ws[k].xi)
+                              for k in range(len(ws)))
+    line = {"metric": "corrected Mparticles/s, batched blocks (exact membership)", "value": round(value, 3),
+            "unit": "Mparticles/s", "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 data, double-float PGD", "data": "synthetic",
+            "config": {"workload": f"batch{len(ws)}_hacc+md_eps0.1|0.5b_VP|SC|HF", "n_particles": n,
+                       "blocks": len(ws), "block_sizes": "log-uniform 1e3-1e6", "parallelism": "replicas1",
+                       "l2": "inputs (2 x %d MB) larger than L2" % (n * 12 // 2 ** 20)},
+            "membership_exact": bool(exact), "same_as_one_at_a_time": bool(same),
+            "one_at_a_time": {"value": round(n / (seq_ms / 1e3) / 1e6, 3), "unit": "Mparticles/s",
+                              "ms": round(seq_ms, 3)},
+            "speedup_vs_one_at_a_time": round(seq_ms / ms, 3),
+            "max_iters": max(st["iters"] for st in stats), "sum_iters": sum(st["iters"] for st in stats),
+            "pgd_launches": stats[0]["pgd_launches"], "ms_setup": round(stats[0]["ms_setup"], 3),
+            "ms_pgd": round(stats[0]["ms_pgd"], 3), "gpu_launches": int(launches // a.steps),
+            "clocks": clocks, "generate_s": round(gen_s, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(a):
+    """Serving form: requests from the HACC-shaped, MD-like and fluid generators arrive as
+    a Poisson stream at `load` x the batched capacity (the server's throughput with every
+    request submitted at once) and go through pc_server; latency is submission to
+    completion.  One at a time = the same requests served by pc_correct + pc_encode_edits
+    in arrival order (a FIFO queue replayed with their measured times)."""
+    import math
+    import threading
+    import numpy as np
+    from paper_2604_18801_gb300 import synth
+    specs = synth.serve_requests(n_req=a.requests)
+    t = time.perf_counter()
+    ws = generate(specs, a.procs)
+    gen_s = time.perf_counter() - t
+    import torch
+    import paper_2604_18801_gb300 as pc
+    dev = torch.device("cuda", 0)
+    dat = [(torch.from_numpy(w.orig).to(dev), torch.from_numpy(w.recon).to(dev)) for w in ws]
+    prms = [w.params() for w in ws]
+    caps = [64 + (w.n + 7) // 8 + 12 * w.n for w in ws]
+    n_tot = sum(w.n for w in ws)
+    torch.cuda.synchronize(dev)
+    # one at a time: service time of each request alone
+    for k in range(min(3, len(ws))):
+        c, st, code = pc.correct(dat[k][0], dat[k][1], prms[k])
+        pc.encode_edits(dat[k][1], c, prms[k])
+    svc = []
+    for k, w in enumerate(ws):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        c, st, code = pc.correct(dat[k][0], dat[k][1], prms[k])
+        s = pc.encode_edits(dat[k][1], c, prms[k])
+        torch.cuda.synchronize(dev)
+        svc.append(time.perf_counter() - t0)
+    seq_rate = n_tot / sum(svc)
+    # capacity of the server: every request submitted at once (saturated), same budget
+    with pc.Server(mem_budget=40 << 30, max_slots=256) as cap_srv:
+        tk = [cap_srv.submit(dat[k][0], dat[k][1], prms[k], stream_cap=caps[k]) for k in range(len(ws))]
+        rs = [cap_srv.result(t)[2] for t in tk]
+    cap_rate = n_tot / ((max(d["done_ns"] for d in rs) - min(d["submit_ns"] for d in rs)) / 1e9)
+    del rs
+    # Poisson arrivals at load x capacity (particles/s) -> requests/s
+    rng = np.random.default_rng(7)
+    lam = a.load * cap_rate / (n_tot / len(ws))
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, len(ws)))
+    srv = pc.Server(mem_budget=40 << 30, max_slots=256)
+    tickets = [None] * len(ws)
+
+    def client():
+        t_start = time.perf_counter()
+        for k in range(len(ws)):
+            d = arrivals[k] - (time.perf_counter() - t_start)
+            if d > 0:
+                time.sleep(d)
+            tickets[k] = srv.submit(dat[k][0], dat[k][1], prms[k], stream_cap=caps[k])
+
+    clk = Clocks(0)
+    clk.start()
+    th = threading.Thread(target=client)
+    t_begin = time.perf_counter()
+    th.start()
+    th.join()
+    results = [srv.result(tk, release=False) for tk in tickets]
+    t_end = time.perf_counter()
+    clocks = clk.stop()
+    lat = np.array([(d["done_ns"] - d["submit_ns"]) / 1e6 for _, _, d in results])
+    first = min(d["submit_ns"] for _, _, d in results)
+    last = max(d["done_ns"] for _, _, d in results)
+    served_rate = n_tot / ((last - first) / 1e9)
+    ok = all(d["state"] == "DONE" and d["status"] == 0 for _, _, d in results)
+    # exactness and equality with the request alone, checked after the run
+    exact, same = ok, True
+    for k in range(len(ws)):
+        out, stream, d = results[k]
+        if k % 10 == 0:
+            c, st, code = pc.correct(dat[k][0], dat[k][1], prms[k])
+            same &= bool(torch.equal(out, c))
+        exact &= membership_ok(pc, torch, dat[k][0], dat[k][1], out, stream, prms[k], ws[k].xi)
+    counters = srv.counters()
+    srv.close()
+    # one at a time under the same arrivals: FIFO queue with the measured service times
+    fin, seq_lat = 0.0, []
+    for k in range(len(ws)):
+        fin = max(fin, arrivals[k]) + svc[k]
+        seq_lat.append((fin - arrivals[k]) * 1e3)
+    seq_lat = np.array(seq_lat)
+    line = {"metric": "served Mparticles/s at %g x batched capacity (exact membership); p50/p99 latency" % a.load,
+            "value": round(served_rate / 1e6, 3), "unit": "Mparticles/s", "n_gpus": 1, "steps": 1, "warmup": 3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 data, double-float PGD", "data": "synthetic",
+            "config": {"workload": f"serve{len(ws)}_hacc|md|fluid_eps0.1|0.5b_VP|SC|HF", "requests": len(ws),
+                       "n_particles": n_tot, "sizes": "log-uniform 1e3-2e6", "arrivals": "Poisson",
+                       "load": a.load, "mem_budget_gb": 40, "parallelism": "replicas1"},
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                           "p99": round(float(np.percentile(lat, 99)), 3), "max": round(float(lat.max()), 3)},
+            "capacity_saturated": round(cap_rate / 1e6, 3), "arrival_rate_req_s": round(lam, 3),
+            "one_at_a_time": {"value": round(seq_rate / 1e6, 3), "unit": "Mparticles/s",
+                              "p50": round(float(np.percentile(seq_lat, 50)), 3),
+                              "p99": round(float(np.percentile(seq_lat, 99)), 3)},
+            "membership_exact": bool(exact), "same_as_alone_sampled": bool(same), "all_done": bool(ok),
+            "cohorts": counters["cohorts"], "peak_estimated_gb": round(counters["peak_bytes"] / 2 ** 30, 2),
+            "wall_s": round(t_end - t_begin, 2), "clocks": clocks, "generate_s": round(gen_s, 1)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.workload == "batch":
+        return run_batch(a)
+    if a.workload == "serve":
+        return run_serve(a)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

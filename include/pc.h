@@ -55,7 +55,7 @@ typedef enum {
 
 typedef enum { PC_MODE_VP = 0, PC_MODE_SC = 1, PC_MODE_HF = 2 } pc_mode;
 
-/* Parameters: the REQUIRE line of Algorithm 1 plus the Adam moments (Sec. 4.1). */
+/* Parameters: the REQUIRE line of Algorithm 1 plus the Adam moments (Sec. 4.2). */
 typedef struct {
     double b;              /* linking length b > 0                                        */
     double xi;             /* pointwise bound xi >= 0 (error of the base compressor)       */

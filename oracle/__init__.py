@@ -141,6 +141,17 @@ def dist2(P, i, j, **kw) -> np.float32:
 CLS_SAFE, CLS_PB, CLS_PC = 1, 2, 3
 
 
+def classify(P, i, j, **kw) -> np.ndarray:
+    """Class of each pair (i[k], j[k]): 0 far, 1 safe, 2 potentially broken, 3 potentially created."""
+    p, pp = _f32(P)
+    i = np.ascontiguousarray(i, np.uint32)
+    j = np.ascontiguousarray(j, np.uint32)
+    out = np.empty(len(i), np.uint8)
+    lib().or_classify(pp, p.shape[0], C.byref(make_params(**kw)), _ptr(i, C.c_uint32), _ptr(j, C.c_uint32),
+                      len(i), _ptr(out, C.c_uint8))
+    return out
+
+
 def pairs(P, brute=False, **kw):
     """All classified pairs (i < j) sorted by (i, j): returns (i, j, cls)."""
     p, pp = _f32(P)

@@ -31,7 +31,7 @@
 //    tight margin is delta_t = 2 sqrt3 (eps_q + u) + b 2^-20.  With these the
 //    decoded output stays within xi and keeps the untightened loss at zero.
 //  * Learning rate and Adam epsilon are scaled to the error bound:
-//    alpha = alpha_rel * xi, eps_adam = eps_rel * xi (Sec. 4.1 gives them in
+//    alpha = alpha_rel * xi, eps_adam = eps_rel * xi (Sec. 4.2 gives them in
 //    unstated data units).
 //  * Halo forest: the spanning forest kept is the unique minimum spanning
 //    forest under the key (float32 bits of d2, i, j) (Sec. 3.2 leaves the
@@ -47,8 +47,8 @@
 //  * Stall reset (not in the paper).  The loss is non-convex (the false-link
 //    term), and at large xi / b PGD can settle in a local minimum where a few
 //    non-link pairs sit well inside b with an endpoint on the box.  The original
-//    positions P satisfy every constraint (Sec. 3.4), so: the loss of each check
-//    is also measured in fixed point, as the sum over violated pairs of
+//    positions P satisfy every constraint (Sec. 3.3, convergence analysis), so:
+//    the loss of each check is also measured in fixed point, as the sum over violated pairs of
 //    llrint(v^2 / (xi^2 2^-24)); a check makes progress when that value is
 //    zero or below best - floor(best / 1024), and its value then becomes best
 //    (best starts at check 0).  After stall_patience consecutive checks
@@ -544,6 +544,14 @@ float or_dist2(const float *P, int64_t i, int64_t j, const or_params *p) {
     float L[3];
     for (int k = 0; k < 3; ++k) L[k] = (float)(p->box_hi[k] - p->box_lo[k]);
     return cdist2(P, i, j, p->periodic, L);
+}
+
+// Class of each listed pair (0 far, 1 safe, 2 potentially broken, 3 potentially created),
+// one by one, with the constants of the whole point set (Sec. 3.1).
+void or_classify(const float *P, int64_t n, const or_params *p, const uint32_t *ai, const uint32_t *aj,
+                 int64_t m, uint8_t *cls) {
+    or_consts c = make_consts(p, P, nullptr, n);
+    for (int64_t k = 0; k < m; ++k) cls[k] = (uint8_t)classify(cdist2(P, ai[k], aj[k], p->periodic, c.L), c);
 }
 
 // Every pair with a class (safe, potentially broken, potentially created), sorted by (i, j).

@@ -1,5 +1,5 @@
 // Projected gradient descent on the tightened loss (Algorithm 1, Eq. 3,
-// Sec. 3.3 "Gradient descent and projection", Adam as in Sec. 4.1).
+// Sec. 3.3 "Gradient descent and projection", Adam as in Sec. 4.2).
 //
 // Layout.  The editable set E = endpoints(A) is numbered in cell order (dense
 // index e), so neighbouring particles sit close in memory.  A is stored as a

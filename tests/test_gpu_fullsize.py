@@ -1,0 +1,82 @@
+"""Full-size checks on the HACC-shaped 256^3 box (16.8M particles, eps = 0.1 b) in the
+launch configuration the benchmark times.
+
+The oracle cannot run the whole pipeline at this size in test time, so it checks what it
+can compute one by one or as a property that holds at any size:
+
+* for sampled particles, the oracle classifies the pair with every other particle of the
+  box; the vulnerable partners (potentially broken or created) must be exactly the
+  partners the GPU put in the vulnerable-pair set, with the same link flag;
+* after correction, encoding and decoding, the oracle counts the active pairs of the mode
+  whose link state changed (must be none; for VP, A = V holds every pair that could flip,
+  so the link set itself is unchanged) and decodes the edit stream itself (must equal the
+  GPU decoder bit for bit); every decoded coordinate stays within xi of the original, and
+  the friends-of-friends labels of the decoded data equal those of the original.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_18801_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def box():
+    return synth.hacc_box(eps_over_b=0.1, mode="VP", seed=1)
+
+
+def test_vulnerable_pairs_of_sampled_particles(cuda, box):
+    import torch
+    import paper_2604_18801_gb300 as pc
+    w = box
+    kw = w.params(mode=0)
+    o = torch.from_numpy(w.orig).to(cuda)
+    cons = pc.select_constraints(o, kw)
+    gi, gj, gl = [x.cpu().numpy() for x in cons.pairs()]
+    cons.close()
+    assert len(gi) == cons.stats["n_vulnerable"] > 10 ** 7
+    rng = np.random.default_rng(5)
+    # half the sample from particles that have vulnerable pairs, half uniformly
+    with_pairs = np.unique(np.concatenate([gi[:: max(1, len(gi) // 5000)], gj[:: max(1, len(gj) // 5000)]]))
+    sample = np.concatenate([rng.choice(with_pairs, 24, replace=False), rng.choice(w.n, 24, replace=False)])
+    everyone = np.arange(w.n, dtype=np.uint32)
+    for i in sample:
+        others = everyone[everyone != i]
+        cls = oracle.classify(w.orig, np.full(len(others), i, np.uint32), others, **kw)
+        vul = cls >= oracle.CLS_PB
+        want = np.sort(others[vul])
+        want_link = cls[vul][np.argsort(others[vul])] == oracle.CLS_PB
+        m1, m2 = gi == i, gj == i
+        got = np.concatenate([gj[m1], gi[m2]])
+        got_link = np.concatenate([gl[m1], gl[m2]]).astype(bool)
+        order = np.argsort(got)
+        assert np.array_equal(got[order], want), f"particle {i}"
+        assert np.array_equal(got_link[order], want_link), f"particle {i}"
+
+
+@pytest.mark.parametrize("mode", ["VP", "SC", "HF"])
+def test_full_size_correction_keeps_every_active_link_state(cuda, box, mode):
+    import torch
+    import paper_2604_18801_gb300 as pc
+    w = box
+    kw = w.params(mode=synth.MODES[mode])
+    o = torch.from_numpy(w.orig).to(cuda)
+    r = torch.from_numpy(w.recon).to(cuda)
+    cons = pc.select_constraints(o, kw)
+    ai, aj, al = [x.cpu().numpy() for x in cons.pairs()]
+    corr, st, code = pc.correct(o, r, kw, constraints=cons)
+    cons.close()
+    assert code == 0 and st["converged"] == 1 and len(ai) == st["n_active"]
+    stream = pc.encode_edits(r, corr, kw)
+    dec = pc.apply_edits(r, stream)
+    dec_h = dec.cpu().numpy()
+    assert np.abs(dec_h.astype(np.float64) - w.orig).max() <= w.xi
+    # the oracle's own decoder gives the same coordinates
+    assert np.array_equal(oracle.decode(w.recon, stream.cpu().numpy().tobytes()), dec_h)
+    # every active pair keeps its original link state after decoding
+    assert oracle.count_flips(dec_h, ai, aj, al, **kw) == 0
+    l0, n0 = pc.fof_labels(o, kw)
+    l1, n1 = pc.fof_labels(dec, kw)
+    assert n0 == n1 and torch.equal(l0, l1)

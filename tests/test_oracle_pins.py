@@ -100,6 +100,11 @@ def test_grid_search_equals_brute_force(periodic, clumpy, xi):
     assert len(gi) > 100
     for a, b_ in ((gi, bi), (gj, bj), (gc, bc), (gi, ni), (gj, nj), (gc, nc)):
         assert np.array_equal(a, b_)
+    # one-by-one classification of every pair agrees with the brute-force list
+    iu, ju = np.triu_indices(n, 1)
+    cls = oracle.classify(P, iu, ju, **kw)
+    keep = cls > 0
+    assert np.array_equal(iu[keep], ni) and np.array_equal(ju[keep], nj) and np.array_equal(cls[keep], nc)
 
 
 @pytest.mark.parametrize("periodic", [True, False])
@@ -280,7 +285,7 @@ def test_stall_reset_matches_torch_adam_with_resets():
 def test_stall_reset_escapes_a_local_minimum():
     # A 1,915-particle HACC-shaped block at eps = 0.5 b: plain Adam-PGD settles with one
     # non-link pair well inside b and an endpoint on the box (the false-link term makes
-    # the loss non-convex, Sec. 3.4); the stall rule returns such endpoints to their
+    # the loss non-convex, Sec. 3.3); the stall rule returns such endpoints to their
     # original positions, which satisfy every constraint, and the run converges with the
     # membership and the box of Eq. 2 intact after encoding.
     w = synth.hacc_box(eps_over_b=0.5, mode="HF", seed=3004, n=1915)
