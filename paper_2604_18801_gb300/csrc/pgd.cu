@@ -1264,6 +1264,15 @@ bool PgdSolver::block_stopped(int b) const {
     return ((const PgdBlk *)im->pin)[b].stop != 0;
 }
 
+int64_t PgdSolver::active_rows() const {
+    if (im->ne == 0) return 0;
+    const PgdBlk *hb = (const PgdBlk *)im->pin;
+    int64_t r = 0;
+    for (int b = 0; b < im->nb; ++b)
+        if (!hb[b].stop) r += im->row_off[b + 1] - im->row_off[b];
+    return r;
+}
+
 void PgdSolver::output(float *corrected, int b) {
     Impl &I = *im;
     if (I.ne == 0) return;

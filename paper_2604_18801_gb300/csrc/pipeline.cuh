@@ -144,6 +144,7 @@ class PgdSolver {
     void wait_status() const;
     bool all_stopped() const;           // from the last landed copy
     bool block_stopped(int b) const;
+    int64_t active_rows() const;        // rows of the blocks not stopped, from the last landed copy
     void output(float *corrected, int b = -1);   // P + delta of the final buffer: every block, or block b
     void delta_out(double *delta);
     void results(std::vector<PgdResult> &out);   // per block; synchronises

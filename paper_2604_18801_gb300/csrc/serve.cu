@@ -1,13 +1,16 @@
 // Request loop: pc_server_* and pc_serve_* (include/pc.h).  Not part of the paper.
 //
-// One worker thread per server.  Jobs are admitted in FIFO order into cohorts; a cohort
-// gathers its jobs' inputs into one block set (one block per job), runs the count pass
-// of the selection, waits until the memory its counts call for fits the budget, selects
-// its constraints and builds a PgdSolver whose iterations replay a CUDA graph on the
-// cohort's own stream.  The worker interleaves: admitting and setting up new cohorts,
-// launching iteration chunks of the running ones, and finishing each job as soon as its
-// block has stopped (output rows of that block, copy-out, optional edit stream).
-// Blocks of a set never interact, so a job's result does not depend on its cohort.
+// Two threads per server.  The setup thread admits jobs in FIFO order into cohorts: a
+// cohort gathers its jobs' inputs into one block set (one block per job), runs the
+// count pass of the selection, waits until the memory its counts call for fits the
+// budget, selects its constraints, builds a PgdSolver whose iterations replay a CUDA
+// graph on the cohort's own stream, and hands the cohort to the run thread.  The run
+// thread launches iteration chunks and finishes each job as soon as its block has
+// stopped (output rows of that block, copy-out, optional edit stream).  Chunks go to
+// the oldest cohorts first: a younger cohort waits while the cohorts ahead of it keep
+// enough rows in flight to fill the GPU, so large early jobs are not starved by the
+// stream of later ones.  Blocks of a set never interact, so a job's result does not
+// depend on its cohort.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -26,6 +29,7 @@ namespace {
 
 constexpr int GRAPH_LAUNCHES = 8;     // iteration launches per captured graph
 constexpr int MAX_CHUNK = 64;         // launches between two status polls
+constexpr int64_t SATURATE_ROWS = int64_t(1) << 21;   // rows in flight that fill the GPU
 
 int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -52,6 +56,8 @@ struct Cohort {
     std::vector<char> finished;
     int chunk = GRAPH_LAUNCHES;
     int64_t launched = 0;
+    bool in_flight = false;              // a chunk and its status copy are queued
+    int64_t rows = 0;                    // rows of the blocks still iterating (last status)
     ~Cohort() {
         // release device memory on the cohort's stream before the stream goes away
         sol.reset();
@@ -74,18 +80,19 @@ struct pc_server {
     int64_t budget = 0;
     int max_slots = 0;
     int64_t max_cohort_n = 0;
-    std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    bool stopping = false;
+    std::mutex mu;                                         // everything below up to the threads
+    std::condition_variable cv_setup, cv_run, cv_done;
+    bool stopping = false, setup_exited = false;
     uint64_t next_ticket = 1;
     std::map<uint64_t, std::unique_ptr<pc::Job>> jobs;   // every job ever submitted
-    std::deque<pc::Job *> pending;                         // FIFO, under mu
-    // worker-only state
-    std::vector<std::unique_ptr<pc::Cohort>> cohorts;
-    pc::HostScratch hs;
-    int64_t used = 0, peak = 0, resident_jobs = 0;
+    std::deque<pc::Job *> pending;                         // FIFO
+    std::vector<std::unique_ptr<pc::Cohort>> ready;       // set up, not yet taken by the run thread
+    int64_t used = 0, peak = 0, resident_jobs = 0;         // memory estimate and jobs of live cohorts
     int64_t n_submitted = 0, n_finished = 0, n_cohorts = 0;
-    std::thread worker;
+    // thread-owned
+    std::vector<std::unique_ptr<pc::Cohort>> running;     // run thread, oldest first
+    pc::HostScratch hs_setup, hs_run;
+    std::thread setup_thr, run_thr;
 };
 
 namespace pc {
@@ -152,13 +159,13 @@ void setup_count(pc_server *srv, Cohort &c) {
     }
     S.off[nb] = at;
     PC_CUDA(cudaMemcpyAsync(c.corr.p, c.recon.p, 12 * c.n, cudaMemcpyDeviceToDevice, c.s));
-    select_count(srv->hs, c.orig.p, c.s, *c.sel);
+    select_count(srv->hs_setup, c.orig.p, c.s, *c.sel);
     c.bytes2 = select_more_bytes(*c.sel);
 }
 
 // Selection, PGD state and the captured graph; the first chunk is launched.
 void setup_run(pc_server *srv, Cohort &c) {
-    select_emit(srv->hs, c.s, *c.sel);
+    select_emit(srv->hs_setup, c.s, *c.sel);
     BlockSet &S = c.sel->S;
     // PGD constants need M over orig and recon of each block
     BlockSet V;
@@ -166,10 +173,10 @@ void setup_run(pc_server *srv, Cohort &c) {
     V.n = S.n;
     V.prm = S.prm;
     V.off = S.off;
-    inspect_blocks(c.orig.p, c.recon.p, V, c.s, srv->hs);
+    inspect_blocks(c.orig.p, c.recon.p, V, c.s, srv->hs_setup);
     std::vector<Consts> cp(V.nb);
     for (int b = 0; b < V.nb; ++b) cp[b] = make_consts(&V.prm[b], V.ins[b], V.off[b + 1] - V.off[b], true);
-    c.sol.reset(new PgdSolver(c.sel->B, S, cp, c.orig.p, c.recon.p, c.sel->A.p, c.sel->nA, c.s, srv->hs));
+    c.sol.reset(new PgdSolver(c.sel->B, S, cp, c.orig.p, c.recon.p, c.sel->A.p, c.sel->nA, c.s, srv->hs_setup));
     // the solver keeps what it needs: cell lists and pairs go back to the pool
     c.sel->A.release();
     c.sel->B.keys.release();
@@ -191,6 +198,8 @@ void setup_run(pc_server *srv, Cohort &c) {
         c.launched += c.sol->launch(c.chunk);
     }
     c.sol->post_status();
+    c.in_flight = true;
+    c.rows = c.sol->rows();
     c.state = C_RUNNING;
 }
 
@@ -218,7 +227,7 @@ void finish_job(pc_server *srv, Cohort &c, int b) {
     st.pgd_launches = c.launched;
     if (sp.stream_dev) {
         j->res.stream_bytes = encode_edits(sp.recon_dev, sp.corrected_dev, sp.n, &sp.params, sp.stream_dev,
-                                           sp.stream_cap, c.s, srv->hs);
+                                           sp.stream_cap, c.s, srv->hs_run);
     } else {
         PC_CUDA(cudaStreamSynchronize(c.s));
     }
@@ -226,10 +235,8 @@ void finish_job(pc_server *srv, Cohort &c, int b) {
     publish(srv, j, PC_JOB_DONE, r.converged ? PC_OK : PC_WARN_NOT_CONVERGED, nullptr);
 }
 
-// One look at a running cohort; returns true if anything happened.
-bool progress(pc_server *srv, Cohort &c) {
-    if (!c.sol->empty() && !c.sol->status_ready()) return false;
-    if (c.sol->empty()) c.sol->wait_status();
+// Finishes the jobs whose blocks have stopped, from the landed status copy.
+void finish_stopped(pc_server *srv, Cohort &c) {
     for (size_t b = 0; b < c.jobs.size(); ++b) {
         if (c.finished[b] || !c.sol->block_stopped((int)b)) continue;
         try {
@@ -239,17 +246,7 @@ bool progress(pc_server *srv, Cohort &c) {
             publish(srv, c.jobs[b], PC_JOB_ERROR, f.st, pc_last_error());
         }
     }
-    bool all = true;
-    for (char f : c.finished) all &= f != 0;
-    if (all) return true;
-    if (c.launched >= c.sol->max_launches()) {
-        fail_cohort(srv, c, PC_ETIMEOUT, "PGD loop did not reach its stop decision");
-        return true;
-    }
-    c.launched += c.sol->launch(c.chunk);
-    c.sol->post_status();
-    c.chunk = std::min(c.chunk * 2, MAX_CHUNK);
-    return true;
+    c.rows = c.sol->active_rows();
 }
 
 bool cohort_done(const Cohort &c) {
@@ -259,134 +256,206 @@ bool cohort_done(const Cohort &c) {
     return true;
 }
 
-// Forms and counts one cohort from the head of the queue; returns true if it did.
-bool admit(pc_server *srv) {
+void release(pc_server *srv, const Cohort &c) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->used -= c.bytes1 + (c.state == C_RUNNING ? c.bytes2 : 0);
+    srv->resident_jobs -= (int64_t)c.jobs.size();
+    srv->cv_setup.notify_all();
+}
+
+// ----------------------------------------------------------------------------- setup thread
+// Takes the next cohort's jobs from the head of the queue (under srv->mu); empty when
+// the queue is empty or memory and slots are short.
+std::vector<Job *> take_jobs(pc_server *srv, int64_t &n) {
     std::vector<Job *> take;
-    int64_t n = 0;
-    {
-        std::lock_guard<std::mutex> lk(srv->mu);
-        while (!srv->pending.empty()) {
-            Job *j = srv->pending.front();
-            if (srv->resident_jobs + (int64_t)take.size() >= srv->max_slots) break;
-            const int64_t nn = n + j->spec.n;
-            if (!take.empty() && nn > srv->max_cohort_n) break;
-            if (!take.empty() && srv->used + count_pass_bytes(nn) > srv->budget) break;
-            if (take.empty() && srv->used + count_pass_bytes(j->spec.n) > srv->budget) {
-                if (count_pass_bytes(j->spec.n) > srv->budget) {
-                    // can never fit
-                    srv->pending.pop_front();
-                    j->res.state = PC_JOB_ERROR;
-                    j->res.status = PC_ENOMEM;
-                    std::strncpy(j->res.error, "job does not fit the server's memory budget", sizeof(j->res.error) - 1);
-                    j->res.done_ns = now_ns();
-                    ++srv->n_finished;
-                    srv->cv_done.notify_all();
-                    continue;
-                }
-                break;   // wait for memory
+    n = 0;
+    while (!srv->pending.empty()) {
+        Job *j = srv->pending.front();
+        if (srv->resident_jobs + (int64_t)take.size() >= srv->max_slots) break;
+        const int64_t nn = n + j->spec.n;
+        if (!take.empty() && nn > srv->max_cohort_n) break;
+        if (srv->used + count_pass_bytes(nn) > srv->budget) {
+            if (take.empty() && count_pass_bytes(j->spec.n) > srv->budget) {
+                // can never fit
+                srv->pending.pop_front();
+                j->res.state = PC_JOB_ERROR;
+                j->res.status = PC_ENOMEM;
+                std::strncpy(j->res.error, "job does not fit the server's memory budget", sizeof(j->res.error) - 1);
+                j->res.done_ns = now_ns();
+                ++srv->n_finished;
+                srv->cv_done.notify_all();
+                continue;
             }
-            srv->pending.pop_front();
-            take.push_back(j);
-            n = nn;
+            break;   // wait for memory
         }
+        srv->pending.pop_front();
+        take.push_back(j);
+        n = nn;
     }
-    if (take.empty()) return false;
-    // validate each job alone; failures end here
-    std::vector<Job *> ok;
+    if (!take.empty()) {
+        srv->used += count_pass_bytes(n);
+        srv->resident_jobs += (int64_t)take.size();
+        ++srv->n_cohorts;
+        srv->peak = std::max(srv->peak, srv->used);
+    }
+    return take;
+}
+
+void setup_main(pc_server *srv) {
+    cudaSetDevice(srv->device);
     cudaStream_t vs = nullptr;
-    PC_CUDA(cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking));
-    for (Job *j : take) {
-        try {
-            validate(j, vs, srv->hs);
-            ok.push_back(j);
-        } catch (const Fail &f) {
-            publish(srv, j, PC_JOB_ERROR, f.st, pc_last_error());
+    cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking);
+    for (;;) {
+        std::vector<Job *> take;
+        int64_t n = 0;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            for (;;) {
+                take = take_jobs(srv, n);
+                if (!take.empty()) break;
+                if (srv->stopping && srv->pending.empty()) break;
+                srv->cv_setup.wait_for(lk, std::chrono::milliseconds(1));
+            }
+            if (take.empty()) break;
         }
-    }
-    cudaStreamSynchronize(vs);
-    cudaStreamDestroy(vs);
-    if (ok.empty()) return true;
-    std::unique_ptr<Cohort> c(new Cohort());
-    c->jobs = ok;
-    c->n = 0;
-    for (Job *j : ok) c->n += j->spec.n;
-    c->bytes1 = count_pass_bytes(c->n);
-    srv->used += c->bytes1;
-    srv->resident_jobs += (int64_t)ok.size();
-    ++srv->n_cohorts;
-    try {
-        setup_count(srv, *c);
-    } catch (const Fail &f) {
+        const int64_t bytes1 = count_pass_bytes(n);
+        // validate each job alone; failures end here
+        std::vector<Job *> ok;
+        for (Job *j : take) {
+            try {
+                validate(j, vs, srv->hs_setup);
+                ok.push_back(j);
+            } catch (const Fail &f) {
+                publish(srv, j, PC_JOB_ERROR, f.st, pc_last_error());
+            }
+        }
+        std::unique_ptr<Cohort> c(new Cohort());
+        c->jobs = ok;
+        c->bytes1 = bytes1;
+        for (Job *j : ok) c->n += j->spec.n;
+        if (ok.size() < take.size()) {
+            // the failed jobs give back their slots (their bytes stay with the cohort's estimate)
+            std::lock_guard<std::mutex> lk(srv->mu);
+            srv->resident_jobs -= (int64_t)(take.size() - ok.size());
+        }
+        if (ok.empty()) {
+            release(srv, *c);
+            continue;
+        }
         c->finished.assign(c->jobs.size(), 0);
-        fail_cohort(srv, *c, f.st, pc_last_error());
-    }
-    srv->peak = std::max(srv->peak, srv->used);
-    srv->cohorts.push_back(std::move(c));
-    return true;
-}
-
-void retire_finished(pc_server *srv) {
-    for (size_t k = 0; k < srv->cohorts.size();) {
-        Cohort &c = *srv->cohorts[k];
-        if (cohort_done(c)) {
-            srv->used -= c.bytes1 + (c.state == C_RUNNING ? c.bytes2 : 0);
-            srv->resident_jobs -= (int64_t)c.jobs.size();
-            srv->cohorts.erase(srv->cohorts.begin() + k);
-        } else {
-            ++k;
+        try {
+            setup_count(srv, *c);
+        } catch (const Fail &f) {
+            fail_cohort(srv, *c, f.st, pc_last_error());
+            release(srv, *c);
+            continue;
         }
+        // the rest of the cohort's memory, once it fits
+        bool fits = true;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            while (srv->used + c->bytes2 > srv->budget) {
+                if (srv->resident_jobs == (int64_t)c->jobs.size()) {   // nothing else will free memory
+                    fits = false;
+                    break;
+                }
+                srv->cv_setup.wait_for(lk, std::chrono::milliseconds(1));
+            }
+            if (fits) {
+                srv->used += c->bytes2;
+                srv->peak = std::max(srv->peak, srv->used);
+            }
+        }
+        if (!fits) {
+            fail_cohort(srv, *c, PC_ENOMEM, "cohort does not fit the server's memory budget");
+            release(srv, *c);
+            continue;
+        }
+        try {
+            setup_run(srv, *c);
+        } catch (const Fail &f) {
+            c->state = C_RUNNING;
+            fail_cohort(srv, *c, f.st, pc_last_error());
+            release(srv, *c);
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            srv->ready.push_back(std::move(c));
+        }
+        srv->cv_run.notify_all();
     }
+    cudaStreamDestroy(vs);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->setup_exited = true;
+    srv->cv_run.notify_all();
 }
 
-void worker_main(pc_server *srv) {
+// ----------------------------------------------------------------------------- run thread
+void run_main(pc_server *srv) {
     cudaSetDevice(srv->device);
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(srv->mu);
-            if (srv->stopping && srv->pending.empty() && srv->cohorts.empty()) break;
+            for (auto &c : srv->ready) srv->running.push_back(std::move(c));
+            srv->ready.clear();
+            if (srv->setup_exited && srv->running.empty()) break;
         }
         bool did = false;
-        // counted cohorts move on when their estimate fits (or fail if it never can)
-        for (auto &cp : srv->cohorts) {
+        // land status copies and finish stopped jobs
+        for (auto &cp : srv->running) {
             Cohort &c = *cp;
-            if (c.state != C_COUNTED || cohort_done(c)) continue;
-            bool others = false;
-            for (auto &o : srv->cohorts)
-                if (o.get() != &c && o->state == C_RUNNING && !cohort_done(*o)) others = true;
-            if (srv->used + c.bytes2 > srv->budget) {
-                if (!others) {
-                    c.finished.assign(c.jobs.size(), 0);
-                    fail_cohort(srv, c, PC_ENOMEM, "cohort does not fit the server's memory budget");
-                    did = true;
-                }
-                continue;
-            }
-            srv->used += c.bytes2;
-            srv->peak = std::max(srv->peak, srv->used);
+            if (!c.in_flight) continue;
             try {
-                setup_run(srv, c);
+                if (!c.sol->empty() && !c.sol->status_ready()) continue;
+                if (c.sol->empty()) c.sol->wait_status();
+                c.in_flight = false;
+                finish_stopped(srv, c);
             } catch (const Fail &f) {
-                c.state = C_RUNNING;
-                if (c.finished.empty()) c.finished.assign(c.jobs.size(), 0);
                 fail_cohort(srv, c, f.st, pc_last_error());
             }
             did = true;
         }
-        for (auto &cp : srv->cohorts) {
+        // oldest first: launch while the rows in flight do not fill the GPU
+        int64_t rows = 0;
+        for (auto &cp : srv->running)
+            if (cp->in_flight) rows += cp->rows;
+        bool first = true;
+        for (auto &cp : srv->running) {
             Cohort &c = *cp;
-            if (c.state != C_RUNNING || cohort_done(c)) continue;
+            if (cohort_done(c)) continue;
+            const bool oldest = first;
+            first = false;
+            if (c.in_flight) continue;
+            if (!oldest && rows + c.rows > SATURATE_ROWS) continue;
             try {
-                did |= progress(srv, c);
+                if (c.launched >= c.sol->max_launches()) {
+                    fail_cohort(srv, c, PC_ETIMEOUT, "PGD loop did not reach its stop decision");
+                    continue;
+                }
+                c.launched += c.sol->launch(c.chunk);
+                c.sol->post_status();
+                c.in_flight = true;
+                c.chunk = std::min(c.chunk * 2, MAX_CHUNK);
+                rows += c.rows;
             } catch (const Fail &f) {
                 fail_cohort(srv, c, f.st, pc_last_error());
+            }
+            did = true;
+        }
+        // retire finished cohorts (their memory goes back to the pool and the budget)
+        for (size_t k = 0; k < srv->running.size();) {
+            if (cohort_done(*srv->running[k]) && !srv->running[k]->in_flight) {
+                release(srv, *srv->running[k]);
+                srv->running.erase(srv->running.begin() + k);
                 did = true;
+            } else {
+                ++k;
             }
         }
-        retire_finished(srv);
-        did |= admit(srv);
         if (!did) {
             std::unique_lock<std::mutex> lk(srv->mu);
-            srv->cv_work.wait_for(lk, std::chrono::microseconds(50));
+            srv->cv_run.wait_for(lk, std::chrono::microseconds(50));
         }
     }
 }
@@ -425,7 +494,8 @@ pc_status pc_server_create(pc_ctx *ctx, size_t mem_budget, int32_t max_slots, in
         s->budget = mem_budget ? (int64_t)mem_budget : ((int64_t)40 << 30);
         s->max_slots = max_slots ? max_slots : 256;
         s->max_cohort_n = max_cohort_particles ? max_cohort_particles : ((int64_t)1 << 24);
-        s->worker = std::thread(worker_main, s);
+        s->setup_thr = std::thread(setup_main, s);
+        s->run_thr = std::thread(run_main, s);
         *out = s;
         return PC_OK;
     });
@@ -437,9 +507,12 @@ void pc_server_destroy(pc_server *srv) {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->stopping = true;
     }
-    srv->cv_work.notify_all();
-    if (srv->worker.joinable()) srv->worker.join();
-    if (srv->hs.p) cudaFreeHost(srv->hs.p);
+    srv->cv_setup.notify_all();
+    srv->cv_run.notify_all();
+    if (srv->setup_thr.joinable()) srv->setup_thr.join();
+    if (srv->run_thr.joinable()) srv->run_thr.join();
+    if (srv->hs_setup.p) cudaFreeHost(srv->hs_setup.p);
+    if (srv->hs_run.p) cudaFreeHost(srv->hs_run.p);
     delete srv;
 }
 
@@ -463,7 +536,7 @@ pc_status pc_serve_submit(pc_server *srv, const pc_job *job, uint64_t *ticket) {
             srv->jobs[j->ticket] = std::move(j);
             ++srv->n_submitted;
         }
-        srv->cv_work.notify_all();
+        srv->cv_setup.notify_all();
         return PC_OK;
     });
 }
