@@ -36,6 +36,11 @@ sys.path.insert(0, ROOT)
 
 MODES = {"VP": 0, "SC": 1, "HF": 2}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# DRAM bytes (read + write) per algorithmic byte of k_pgd_iter, from the ncu capture in
+# profiles/k_pgd_iter_hacc4194304_eps0.1b_VP.md (475.2 MB for 322.2 MB); the kernel's traffic
+# grows with |E| and |A|, so a full-size launch's traffic is this ratio times its bytes.
+PGD_TRAFFIC_RATIO = 475.2 / 322.2
+PGD_TRAFFIC_SOURCE = "profiles/k_pgd_iter_hacc4194304_eps0.1b_VP.md (scaled by algorithmic bytes)"
 
 
 def parse():
@@ -476,7 +481,8 @@ def main():
     achieved = bytes_it / (ms_it / 1e3) / 1e9 if ms_it > 0 else 0.0
     peak = float(pk["hbm_gbs"])
     roofline = {"kernel": "k_pgd_iter", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": int(PGD_TRAFFIC_RATIO * bytes_it / max(1, launches_it)), "traffic_source": PGD_TRAFFIC_SOURCE,
                 "peak_kind": pk_kind, "avg_launch_us": round(1e3 * ms_it / max(1, launches_it), 2),
                 "launches_per_step": launches_it,
                 "bytes_per_launch": int(bytes_it / max(1, launches_it))}

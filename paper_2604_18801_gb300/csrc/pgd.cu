@@ -556,6 +556,8 @@ struct WarpTab {
     int64_t row[32];                 // the warp's rows: dense index
     uint32_t qk[96];                 // queued pairs: partner
     uint8_t qs[96];                  // queued pairs: row slot | link << 7
+    unsigned own[32];                // per row slot: this batch's violated entries of that row
+    float gt[6][32];                 // this batch's gradient terms (x hi, x lo, y hi, ...) by entry
 };
 
 // One PGD iteration for every block still iterating: check t_b and, unless it is the
@@ -719,19 +721,27 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
                 }
             }
             // Each row adds its violated pairs one by one in edge order (queue order is
-            // edge order).  The row's owner is lane `slot` (light) or lane 0 (heavy: slot 0).
-            for (unsigned m = __ballot_sync(FULL, hit); m; m &= m - 1) {
-                const int src = __ffs(m) - 1;
-                const int sk = __shfl_sync(FULL, s, src);
-                df y[3];
+            // edge order).  The row's owner is lane `slot` (light) or lane 0 (heavy: slot 0):
+            // the entries of a slot are found with one match, and every owner walks its own
+            // entries while the others walk theirs.
+            if (hit) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    y[a] = df_make(__shfl_sync(FULL, gt[a].hi, src), __shfl_sync(FULL, gt[a].lo, src));
-                if (lane == sk) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], y[a]);
-                    rv = true;
+                for (int a = 0; a < 3; ++a) {
+                    T.gt[2 * a][lane] = gt[a].hi;
+                    T.gt[2 * a + 1][lane] = gt[a].lo;
                 }
+            }
+            const unsigned hm = __ballot_sync(FULL, hit);
+            T.own[lane] = 0u;
+            const unsigned same = __match_any_sync(FULL, s);
+            __syncwarp();
+            if (hit) T.own[s] = same & hm;   // the entries of one slot all write the same mask
+            __syncwarp();
+            for (unsigned mine = T.own[lane]; mine; mine &= mine - 1) {
+                const int i = __ffs(mine) - 1;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], df_make(T.gt[2 * a][i], T.gt[2 * a + 1][i]));
+                rv = true;
             }
             __syncwarp();
         };
