@@ -546,6 +546,15 @@ struct HeavyPlan {
     float4 *chunk_g;                 // per chunk: gradient partial (hi at 2c, lo at 2c+1)
 };
 
+// The light rows' edges, in row order, apart from the heavy rows': a group of 32 rows
+// owns the contiguous range [ptr[r0], ptr[r0 + 32]), and each edge carries the slot of
+// its row within the group, so a warp maps an edge to its row without a search.
+struct LightPlan {
+    const uint32_t *ptr;             // per row: first light edge (heavy rows own none)
+    const uint32_t *col;             // partner | link << 31
+    const uint8_t *slot;             // row - first row of its 32-row group
+};
+
 struct PgdBufs {
     float4 *Dh[2], *Dl[2], *Q[2];
     float4 *Mh, *Ml, *Vh, *Vl;
@@ -556,6 +565,7 @@ struct WarpTab {
     int64_t row[32];                 // the warp's rows: dense index
     uint32_t qk[96];                 // queued pairs: partner
     uint8_t qs[96];                  // queued pairs: row slot | link << 7
+    float4 q[32];                    // the rows' rounded current positions
     unsigned own[32];                // per row slot: this batch's violated entries of that row
     float gt[6][32];                 // this batch's gradient terms (x hi, x lo, y hi, ...) by entry
 };
@@ -578,7 +588,8 @@ struct WarpTab {
 template <bool MULTI>
 __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
     const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE,
-    int64_t ne, PgdBufs Bf, HeavyPlan H, const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs,
+    int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP, const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk,
+    PgdGlobal *gs,
     const WorkTab wt, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
     __shared__ int s_stop, s_t, s_reset, s_nact;
     __shared__ unsigned long long s_items;
@@ -614,11 +625,11 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
         const int64_t item = (int64_t)__shfl_sync(FULL, itm, 0);
         if (item >= n_items) break;
 
-        // Virtual edge range [0, VT): light warps map v to (row slot, edge) through the
-        // prefix vp of the light rows' degrees; a heavy warp maps v to edge start + v of slot 0.
+        // Edge range [ebase, ebase + VT): a light warp's rows' light edges (each with its
+        // row's slot), or one heavy chunk (slot 0).
         int64_t e = -1;
         bool own = false;            // this lane applies Adam to row e
-        uint32_t rp = 0, vp = 0, VT = 0, hstart = 0;
+        uint32_t VT = 0, ebase = 0;
         int64_t chunk = -1;
         float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
         // the item's block: iteration, buffers and screen constants (one block per item)
@@ -667,30 +678,31 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
             const bool have = lane < cnt;
             uint32_t deg = 0;
             if (have) {
-                rp = row_ptr[e];
-                deg = bstop ? 0u : row_ptr[e + 1] - rp;
+                deg = row_ptr[e + 1] - row_ptr[e];
                 qe = Bf.Q[tb & 1][e];
                 T.row[lane] = e;
+                T.q[lane] = qe;
             }
-            const uint32_t ld = deg <= HEAVY ? deg : 0u;
             own = have && !bstop && deg <= HEAVY;
-            uint32_t inc = ld;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, inc, off);
-                if (lane >= off) inc += y;
+            uint32_t lb = 0, le = 0;
+            if (lane == 0) {
+                lb = LP.ptr[r0];
+                le = LP.ptr[r0 + cnt];
             }
-            vp = inc - ld;
-            VT = __shfl_sync(FULL, inc, 31);
+            ebase = __shfl_sync(FULL, lb, 0);
+            VT = bstop ? 0u : __shfl_sync(FULL, le, 0) - ebase;
         } else {
             chunk = item_chunk;
             const uint32_t row = H.chunk_row[chunk];
-            hstart = H.chunk_start[chunk];
+            ebase = H.chunk_start[chunk];
             const uint32_t rend = row_ptr[row + 1];
-            VT = bstop ? 0u : min(HEAVY, rend - hstart);
+            VT = bstop ? 0u : min(HEAVY, rend - ebase);
             e = row;
-            if (lane == 0) T.row[0] = row;
             qe = Bf.Q[tb & 1][row];
+            if (lane == 0) {
+                T.row[0] = row;
+                T.q[0] = qe;
+            }
         }
         __syncwarp();
         const PgdConsts &Cl = CB[b];            // the item's block
@@ -746,19 +758,6 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
             __syncwarp();
         };
 
-        // row slot and edge of virtual edge v (light: largest s with vp[s] <= v)
-        auto locate = [&](uint32_t v, int &s, uint32_t &tt) {
-            s = 0;
-            tt = hstart + v;
-            if (!heavy_warp) {
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const uint32_t y = __shfl_sync(FULL, vp, (s + step) & 31);
-                    if (s + step < 32 && y <= v) s += step;
-                }
-                tt = __shfl_sync(FULL, rp, s) + (v - __shfl_sync(FULL, vp, s));
-            }
-        };
         auto enqueue = [&](bool need, uint32_t k, int s, bool link) {
             const unsigned bal = __ballot_sync(FULL, need);
             if (need) {
@@ -769,24 +768,26 @@ __global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
             qn += __popc(bal);
         };
         // float32 screen of one edge of row slot s against partner k
+        const float4 *Qc = Bf.Q[tb & 1];
         auto screen = [&](bool ok, int s, uint32_t cv) -> bool {
-            float qx = shfl_f(qe.x, s), qy = shfl_f(qe.y, s), qz = shfl_f(qe.z, s);
             if (!ok) return false;
+            const float4 qr = T.q[s];
             const uint32_t k = cv & 0x7fffffffu;
-            const float4 qk = Bf.Q[tb & 1][k];
+            const float4 qk = Qc[k];
             const bool pp = per_l != 0;
-            const float d2 = cdist2(cdiff(qx, qk.x, pp, L0), cdiff(qy, qk.y, pp, L1), cdiff(qz, qk.z, pp, L2));
+            const float d2 =
+                cdist2(cdiff(qr.x, qk.x, pp, L0), cdiff(qr.y, qk.y, pp, L1), cdiff(qr.z, qk.z, pp, L2));
             return (cv >> 31) ? !(d2 < sl_link) : !(d2 > sl_non);
         };
+        const uint32_t *ecol = heavy_warp ? col : LP.col;
         // two edges per lane per trip: both partner loads are in flight before either is used
         for (uint32_t base = 0; base < VT; base += 64) {
             const uint32_t v0 = base + lane, v1 = base + 32 + lane;
-            int s0, s1;
-            uint32_t t0, t1;
-            locate(v0, s0, t0);
-            locate(v1, s1, t1);
             const bool ok0 = v0 < VT, ok1 = v1 < VT;
-            const uint32_t c0v = ok0 ? col[t0] : 0u, c1v = ok1 ? col[t1] : 0u;
+            const uint32_t t0 = ebase + v0, t1 = ebase + v1;
+            const uint32_t c0v = ok0 ? ecol[t0] : 0u, c1v = ok1 ? ecol[t1] : 0u;
+            const int s0 = (ok0 && !heavy_warp) ? (int)LP.slot[t0] : 0;
+            const int s1 = (ok1 && !heavy_warp) ? (int)LP.slot[t1] : 0;
             const bool n0 = screen(ok0, s0, c0v);
             const bool n1 = screen(ok1, s1, c1v);
             enqueue(n0, c0v & 0x7fffffffu, s0, (c0v >> 31) != 0u);
@@ -897,6 +898,32 @@ __global__ void k_heavy_fill(const uint32_t *__restrict__ row_ptr, int64_t ne, c
     }
 }
 
+// Light edge plan: degrees of the light rows, then their edges with each row's slot in its
+// 32-row group (groups start at the first row of their block).
+__global__ void k_light_deg(const uint32_t *__restrict__ row_ptr, int64_t ne, uint32_t *__restrict__ ldeg) {
+    GRID_STRIDE(e, ne) {
+        const uint32_t d = row_ptr[e + 1] - row_ptr[e];
+        ldeg[e] = d <= HEAVY ? d : 0u;
+    }
+}
+
+__global__ void k_light_fill(const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
+                             const uint32_t *__restrict__ lptr, int64_t ne, const uint32_t *__restrict__ rb,
+                             const int64_t *__restrict__ roff, uint32_t *__restrict__ lcol,
+                             uint8_t *__restrict__ lslot) {
+    GRID_STRIDE(e, ne) {
+        const uint32_t a = row_ptr[e], d = row_ptr[e + 1] - a;
+        if (d > HEAVY) continue;
+        const int64_t r0 = roff ? roff[rb[e]] : 0;
+        const uint8_t sl = (uint8_t)((e - r0) & 31);
+        const uint32_t o = lptr[e];
+        for (uint32_t k = 0; k < d; ++k) {
+            lcol[o + k] = col[a + k];
+            lslot[o + k] = sl;
+        }
+    }
+}
+
 __global__ void k_copy_recon(const float *__restrict__ recon, float *__restrict__ out, int64_t m) {
     GRID_STRIDE(i, m) out[i] = recon[i];
 }
@@ -996,7 +1023,9 @@ struct PgdSolver::Impl {
     DBuf<PgdConsts> CB;
     DBuf<PgdBlk> blk;
     DBuf<PgdGlobal> gs;
-    DBuf<uint32_t> row_ptr, col, rb, chunk_row, chunk_start, hrow, hc0;
+    DBuf<uint32_t> row_ptr, col, rb, chunk_row, chunk_start, hrow, hc0, lptr, lcol;
+    DBuf<uint8_t> lslot;
+    LightPlan LP{};
     DBuf<float4> PE, Dh0, Dl0, Dh1, Dl1, Mh, Ml, Vh, Vl, Q0, Q1, chunk_g;
     DBuf<uint8_t> act;
     DBuf<BlkWork> bw;
@@ -1018,11 +1047,11 @@ struct PgdSolver::Impl {
 
     void launch_iter() {
         if (nb == 1)
-            k_pgd_iter<false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, CB.p, nb, blk.p, gs.p,
-                                                           wt, hist_loss, hist_viol);
+            k_pgd_iter<false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p,
+                                                           gs.p, wt, hist_loss, hist_viol);
         else
-            k_pgd_iter<true><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, CB.p, nb, blk.p, gs.p,
-                                                          wt, nullptr, nullptr);
+            k_pgd_iter<true><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p,
+                                                          gs.p, wt, nullptr, nullptr);
         PC_CHECK_LAUNCH();
         if (n_heavy > 0) {
             k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, rb.p, Bf, CB.p,
@@ -1160,10 +1189,28 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
         PC_CUDA(cudaMemcpyAsync(I.hc0.p + I.n_heavy, tot2.p, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     }
     I.kernels_per_iter = I.n_heavy > 0 ? 2 : 1;
+    DBuf<int64_t> roff;
+    if (nb > 1) {
+        roff.alloc(nb + 1, s);
+        PC_CUDA(cudaMemcpyAsync(roff.p, I.row_off.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    // light edge plan
+    {
+        DBuf<uint32_t> ldeg(ne, s);
+        I.lptr.alloc(ne + 1, s);
+        k_light_deg<<<grid_for(ne), 256, 0, s>>>(I.row_ptr.p, ne, ldeg.p);
+        PC_CHECK_LAUNCH();
+        scan_exclusive_u32(ldeg.p, I.lptr.p, ne, I.lptr.p + ne, s);
+        const uint32_t n_light = *(const uint32_t *)read_back(hs, I.lptr.p + ne, sizeof(uint32_t), s);
+        I.lcol.alloc(std::max<uint32_t>(1, n_light), s);
+        I.lslot.alloc(std::max<uint32_t>(1, n_light), s);
+        k_light_fill<<<grid_for(ne), 256, 0, s>>>(I.row_ptr.p, I.col.p, I.lptr.p, ne, I.rb.p, roff.p, I.lcol.p,
+                                                  I.lslot.p);
+        PC_CHECK_LAUNCH();
+        I.LP = LightPlan{I.lptr.p, I.lcol.p, I.lslot.p};
+    }
     if (nb > 1) {
         // work table of the blocks still iterating (all of them before the first launch)
-        DBuf<int64_t> roff(nb + 1, s);
-        PC_CUDA(cudaMemcpyAsync(roff.p, I.row_off.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         I.bw.alloc(nb, s);
         I.act_blk.alloc(nb, s);
         I.act_pref.alloc(nb + 1, s);
