@@ -8,8 +8,10 @@
 // error bounds for basic building blocks of double-word arithmetic", ACM TOMS
 // 44(2), 2017 (relative errors of a few 2^-48).  Every float32 operation is
 // written with a round-to-nearest intrinsic so the compiler cannot contract
-// or reorder it; division and square root of the leading term are the IEEE
-// float32 operations.
+// or reorder it.  Division and square root take their leading term from the
+// hardware's approximate reciprocal and reciprocal square root (a few ulps);
+// the correction computed from the exact remainder then gives about 2^-44
+// relative, and every operation stays an odd function of its inputs.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -84,23 +86,26 @@ __device__ __forceinline__ df df_mul_f(df x, float y) {
     return fast_two_sum(p.hi, c);
 }
 
-// double-word / double-word: quotient of the leading terms, then one correction
-// from the exact remainder x - q*y.
+// double-word / double-word: approximate quotient of the leading terms, then one
+// correction from the remainder x - q*y (formed with an exact product).
 __device__ __forceinline__ df df_div(df x, df y) {
-    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const float ry = __fdividef(1.f, y.hi);
+    const float q1 = __fmul_rn(x.hi, ry);
     const df r = df_sub(x, df_mul_f(y, q1));
-    const float q2 = __fdiv_rn(r.hi, y.hi);
+    const float q2 = __fmul_rn(r.hi, ry);
     return fast_two_sum(q1, q2);
 }
 
-// square root of a non-negative double-word: s = sqrt(hi), then the Newton
-// correction (x - s^2) / (2 s) with x - s^2 formed exactly.
+// square root of a non-negative double-word: s ~ sqrt(hi) from the approximate
+// reciprocal square root, then the Newton correction (x - s^2) / (2 s) with x - s^2
+// formed exactly.
 __device__ __forceinline__ df df_sqrt(df x) {
     if (!(x.hi > 0.f)) return df_make(0.f, 0.f);
-    const float s = __fsqrt_rn(x.hi);
+    const float rs = rsqrtf(x.hi);
+    const float s = __fmul_rn(x.hi, rs);
     const df s2 = two_prod(s, s);
     const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, s2.hi), s2.lo), x.lo);
-    const float c = __fdiv_rn(r, __fmul_rn(2.f, s));
+    const float c = __fmul_rn(__fmul_rn(r, rs), 0.5f);
     return fast_two_sum(s, c);
 }
 

@@ -41,6 +41,7 @@ inline int grid_for(int64_t n, int threads = 256) {
 
 constexpr int PGD_THREADS = 256;
 constexpr int WARPS = PGD_THREADS / 32;
+constexpr int PGD_BLOCKS_PER_SM = 4;   // resident CTAs of the persistent iteration grid
 
 // Per-block PGD constants (one entry per block of the problem set).
 struct PgdConsts {
@@ -279,31 +280,12 @@ __device__ __forceinline__ bool is_last(const PgdConsts &C, int t) {
 }
 
 // ------------------------------------------------------------------ pair evaluation
-// r = dp + (eh + el) - (kh + kl) formed without rounding: Shewchuk's grow-expansion
-// (each input added through a chain of TwoSums) gives a nonoverlapping expansion whose
-// components sum to r exactly; the largest component plus the rounded sum of the rest
-// is r to about 2^-48 relative, and an exact zero stays exactly zero.
+// r = dp + ((eh + el) - (kh + kl)) in double-float: the offset difference with one
+// double-word add, then the original separation.  Every step is an odd function of its
+// inputs under round-to-nearest, so r(k, e) = -r(e, k) exactly and mirror-image pairs
+// give exactly opposite terms; an exact zero stays exactly zero.
 __device__ __forceinline__ df exact_r(float dp, float eh, float el, float kh, float kl) {
-    float h[5];
-    h[0] = dp;
-    int m = 1;
-    const float in[4] = {eh, el, -kh, -kl};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float q = in[j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (i < m) {
-                const df t = two_sum(q, h[i]);
-                h[i] = t.lo;
-                q = t.hi;
-            }
-        }
-        h[m] = q;
-        ++m;
-    }
-    const float rest = __fadd_rn(h[3], __fadd_rn(h[2], __fadd_rn(h[1], h[0])));
-    return fast_two_sum(h[4], rest);
+    return df_add_f(df_add(df_make(eh, el), df_make(-kh, -kl)), dp);
 }
 
 // Violated amount of Eq. 3 for one active pair (row e, partner k) at the current
@@ -586,7 +568,7 @@ struct WarpTab {
 // items come from the table of blocks still iterating, so a block that has stopped
 // costs nothing in later launches, and the rows of one item share a block.
 template <bool MULTI>
-__global__ void __launch_bounds__(PGD_THREADS, 4) k_pgd_iter(
+__global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
     const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE,
     int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP, const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk,
     PgdGlobal *gs,
@@ -1226,7 +1208,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     I.HP.chunk_start = I.chunk_start.p;
     I.HP.chunk_g = I.chunk_g.p;
     const int64_t n_items = cdiv(ne, 32) + nb + n_chunks;
-    I.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS), (int64_t)num_sms() * 4));
+    I.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS), (int64_t)num_sms() * PGD_BLOCKS_PER_SM));
 }
 
 PgdSolver::~PgdSolver() { delete im; }
