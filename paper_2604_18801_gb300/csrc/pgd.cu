@@ -541,6 +541,11 @@ struct PgdBufs {
     float4 *Dh[2], *Dl[2], *Q[2];
     float4 *Mh, *Ml, *Vh, *Vl;
     uint8_t *act;
+    // buffer i of a ping-pong pair, chosen without indexing the parameter array at run
+    // time (which would copy it to local memory)
+    __device__ __forceinline__ float4 *dh(int i) const { return i ? Dh[1] : Dh[0]; }
+    __device__ __forceinline__ float4 *dl(int i) const { return i ? Dl[1] : Dl[0]; }
+    __device__ __forceinline__ float4 *q(int i) const { return i ? Q[1] : Q[0]; }
 };
 
 struct WarpTab {
@@ -661,7 +666,7 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
             uint32_t deg = 0;
             if (have) {
                 deg = row_ptr[e + 1] - row_ptr[e];
-                qe = Bf.Q[tb & 1][e];
+                qe = Bf.q(tb & 1)[e];
                 T.row[lane] = e;
                 T.q[lane] = qe;
             }
@@ -680,7 +685,7 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
             const uint32_t rend = row_ptr[row + 1];
             VT = bstop ? 0u : min(HEAVY, rend - ebase);
             e = row;
-            qe = Bf.Q[tb & 1][row];
+            qe = Bf.q(tb & 1)[row];
             if (lane == 0) {
                 T.row[0] = row;
                 T.q[0] = qe;
@@ -706,7 +711,7 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
                 s = T.qs[lane] & 0x7f;
                 const bool link = (T.qs[lane] >> 7) != 0;
                 const int64_t er = T.row[s];
-                const float4 *Dh = Bf.Dh[tb & 1], *Dl = Bf.Dl[tb & 1];
+                const float4 *Dh = Bf.dh(tb & 1), *Dl = Bf.dl(tb & 1);
                 double lt = 0.0;
                 hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, PE, Dh, Dl, Cl, gt, lt);
                 if (hit) {
@@ -750,7 +755,7 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
             qn += __popc(bal);
         };
         // float32 screen of one edge of row slot s against partner k
-        const float4 *Qc = Bf.Q[tb & 1];
+        const float4 *Qc = Bf.q(tb & 1);
         auto screen = [&](bool ok, int s, uint32_t cv) -> bool {
             if (!ok) return false;
             const float4 qr = T.q[s];
@@ -803,8 +808,8 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
                 const df i1 = MULTI ? blk[b].ibc1 : s_ibc1, i2 = MULTI ? blk[b].ibc2 : s_ibc2;
                 const bool rs = rv && (MULTI ? blk[b].reset != 0 : s_reset != 0);
                 const int pa = tb & 1;
-                adam_row(e, g, Bf.Dh[pa], Bf.Dl[pa], PE, Bf.act, i1, i2, rs, Cl, Bf.Dh[pa ^ 1], Bf.Dl[pa ^ 1], Bf.Mh,
-                         Bf.Ml, Bf.Vh, Bf.Vl, Bf.Q[pa ^ 1]);
+                adam_row(e, g, Bf.dh(pa), Bf.dl(pa), PE, Bf.act, i1, i2, rs, Cl, Bf.dh(pa ^ 1), Bf.dl(pa ^ 1), Bf.Mh,
+                         Bf.Ml, Bf.Vh, Bf.Vl, Bf.q(pa ^ 1));
             }
         } else if (lane == 0 && !bstop) {
             H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, rv ? 1.f : 0.f);
@@ -846,9 +851,9 @@ __global__ void k_pgd_heavy(const uint32_t *__restrict__ hrow, const uint32_t *_
             g[1] = df_add(g[1], df_make(h.y, l.y));
             g[2] = df_add(g[2], df_make(h.z, l.z));
         }
-        adam_row(e, g, Bf.Dh[pa], Bf.Dl[pa], PE, Bf.act, B.upd_ibc1, B.upd_ibc2, rv && B.upd_reset != 0, CB[b],
-                 Bf.Dh[pa ^ 1],
-                 Bf.Dl[pa ^ 1], Bf.Mh, Bf.Ml, Bf.Vh, Bf.Vl, Bf.Q[pa ^ 1]);
+        adam_row(e, g, Bf.dh(pa), Bf.dl(pa), PE, Bf.act, B.upd_ibc1, B.upd_ibc2, rv && B.upd_reset != 0, CB[b],
+                 Bf.dh(pa ^ 1),
+                 Bf.dl(pa ^ 1), Bf.Mh, Bf.Ml, Bf.Vh, Bf.Vl, Bf.q(pa ^ 1));
     }
 }
 
@@ -919,7 +924,7 @@ __global__ void k_output(const float4 *__restrict__ PE, const uint32_t *__restri
         const PgdBlk &B = blk[rb[e]];
         if (B.t == 0) continue;
         const int fb = B.final_buf;
-        const float4 p = PE[e], h = Bf.Dh[fb][e], l = Bf.Dl[fb][e];
+        const float4 p = PE[e], h = Bf.dh(fb)[e], l = Bf.dl(fb)[e];
         const int64_t id = (int64_t)__float_as_uint(p.w);
         const float pa[3] = {p.x, p.y, p.z}, ha[3] = {h.x, h.y, h.z}, la[3] = {l.x, l.y, l.z};
 #pragma unroll
@@ -934,7 +939,7 @@ __global__ void k_delta_out(const float4 *__restrict__ PE, const uint32_t *__res
                             const PgdBlk *__restrict__ blk, double *__restrict__ out) {
     GRID_STRIDE(e, ne) {
         const int fb = blk[rb[e]].final_buf;
-        const float4 p = PE[e], h = Bf.Dh[fb][e], l = Bf.Dl[fb][e];
+        const float4 p = PE[e], h = Bf.dh(fb)[e], l = Bf.dl(fb)[e];
         const int64_t id = (int64_t)__float_as_uint(p.w);
         out[3 * id + 0] = (double)h.x + (double)l.x;
         out[3 * id + 1] = (double)h.y + (double)l.y;
