@@ -396,7 +396,7 @@ def main():
             times.append(cb["value"])
         v = statistics.median(times)
         cb["value"] = v
-        print(json.dumps({"impl": "reference", "metric": "corrected Mparticles/s", "value": v,
+        print(json.dumps({"impl": "reference", "metric": "corrected Mparticles/s (exact membership)", "value": v,
                           "unit": "Mparticles/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
                           "higher_is_better": True, "scaling": "weak", "dtype": "f64", "data": "synthetic",
                           "config": {"workload": workload, "sample": cb["sample"]}, "cpu_baseline": cb,
