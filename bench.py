@@ -147,6 +147,20 @@ def cpu_baseline(w, modes, side):
                       f"{dt:.1f} s single-threaded"}
 
 
+def job_throughput(ms: float, units: int, device=None):
+    """Whole-job throughput of N replicas: every rank processed `units` particles in `ms`
+    of its own timed region; the job's time is the slowest rank's (max over ranks).
+    Returns (max ms, Mparticles/s over all ranks)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, units * world / (ms_max / 1e3) / 1e6
+
+
 def _gen(spec):
     from paper_2604_18801_gb300 import synth
     w = synth.make_request(spec)
@@ -455,12 +469,8 @@ def main():
         dist.barrier()
     launches = _native.lib().pc_kernel_launches() - launches0
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, value = job_throughput(ms, w.n * len(modes) * a.steps, dev)
     per_step = ms_max / a.steps
-    value = w.n * len(modes) * a.steps * world / (ms_max / 1e3) / 1e6
 
     # exact membership of the decoded output (not timed)
     lab0, _ = pc.fof_labels(o, prms[modes[0]])
