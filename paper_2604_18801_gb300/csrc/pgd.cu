@@ -331,17 +331,21 @@ __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, con
 // unchanged offset: Adam leaves it where it is, and both offset buffers already hold
 // that value, so nothing is read or written for it.  A reset row (stall rule) returns
 // to its original position with cleared moments instead of taking its step.
-__device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 *Dh, const float4 *Dl,
-                                         const float4 *__restrict__ PE, uint8_t *__restrict__ act, const df ibc1,
-                                         const df ibc2, bool reset, const PgdConsts &C, float4 *Nh, float4 *Nl,
-                                         float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
-                                         float4 *__restrict__ Vlo, float4 *Qn) {
+// The row's state as loaded: offset (hi, lo), original position, moments (hi, lo).
+struct RowState {
+    float4 dh, dl, pe, mh, ml, vh, vl;
+};
+
+__device__ __forceinline__ void adam_core(int64_t e, const df g[3], const RowState &S, bool was,
+                                          uint8_t *__restrict__ act, const df ibc1, const df ibc2, bool reset,
+                                          const PgdConsts &C, float4 *Nh, float4 *Nl, float4 *__restrict__ Mhi,
+                                          float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
+                                          float4 *__restrict__ Vlo, float4 *Qn) {
     const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
-    const bool was = act[e] != 0;
     if (!was && gz && !reset) return;
     if (!was) act[e] = 1;
     if (reset) {
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), pe = PE[e];
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), pe = S.pe;
         Nh[e] = z4;
         Nl[e] = z4;
         Mhi[e] = z4;
@@ -351,9 +355,9 @@ __device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 
         Qn[e] = make_float4(pe.x, pe.y, pe.z, 0.f);
         return;
     }
-    const float4 deh = Dh[e], del = Dl[e], pe = PE[e];
+    const float4 deh = S.dh, del = S.dl, pe = S.pe;
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 mh4 = was ? Mhi[e] : z4, ml4 = was ? Mlo[e] : z4, vh4 = was ? Vhi[e] : z4, vl4 = was ? Vlo[e] : z4;
+    const float4 mh4 = was ? S.mh : z4, ml4 = was ? S.ml : z4, vh4 = was ? S.vh : z4, vl4 = was ? S.vl : z4;
     df nd[3], nm[3], nv[3];
     float qo[3];
     const float pa[3] = {pe.x, pe.y, pe.z};
@@ -380,6 +384,36 @@ __device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 
     Vlo[e] = make_float4(nv[0].lo, nv[1].lo, nv[2].lo, 0.f);
     Qn[e] = make_float4(qo[0], qo[1], qo[2], 0.f);
 }
+
+// Adam on one row, loading its state from global memory.
+__device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 *Dh, const float4 *Dl,
+                                         const float4 *__restrict__ PE, uint8_t *__restrict__ act, const df ibc1,
+                                         const df ibc2, bool reset, const PgdConsts &C, float4 *Nh, float4 *Nl,
+                                         float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
+                                         float4 *__restrict__ Vlo, float4 *Qn) {
+    const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
+    const bool was = act[e] != 0;
+    if (!was && gz && !reset) return;
+    RowState S;
+    S.dh = Dh[e];
+    S.dl = Dl[e];
+    S.pe = PE[e];
+    if (was) {
+        S.mh = Mhi[e];
+        S.ml = Mlo[e];
+        S.vh = Vhi[e];
+        S.vl = Vlo[e];
+    }
+    adam_core(e, g, S, was, act, ibc1, ibc2, reset, C, Nh, Nl, Mhi, Mlo, Vhi, Vlo, Qn);
+}
+
+// 16-byte asynchronous copies from global to shared memory (not cached in L1).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ stop decisions
 // The tight loss is accumulated in fixed point: each violated pair adds llrint(v^2 / unit)
@@ -549,6 +583,7 @@ struct PgdBufs {
 };
 
 struct WarpTab {
+    float4 st[7][32];                // the rows' state for Adam, fetched while the edges are walked
     int64_t row[32];                 // the warp's rows: dense index
     uint32_t qk[96];                 // queued pairs: partner
     uint8_t qs[96];                  // queued pairs: row slot | link << 7
@@ -616,6 +651,7 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
         // row's slot), or one heavy chunk (slot 0).
         int64_t e = -1;
         bool own = false;            // this lane applies Adam to row e
+        bool upd = false, was = false;   // ... at this launch; the row had a gradient before
         uint32_t VT = 0, ebase = 0;
         int64_t chunk = -1;
         float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -671,6 +707,22 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
                 T.q[lane] = qe;
             }
             own = have && !bstop && deg <= HEAVY;
+            // the row's Adam state travels to shared memory while the edges are walked
+            upd = own && !is_last(CB[b], tb);
+            if (upd) {
+                const int pa = tb & 1;
+                was = Bf.act[e] != 0;
+                cp_async16(&T.st[0][lane], Bf.dh(pa) + e);
+                cp_async16(&T.st[1][lane], Bf.dl(pa) + e);
+                cp_async16(&T.st[2][lane], PE + e);
+                if (was) {
+                    cp_async16(&T.st[3][lane], Bf.Mh + e);
+                    cp_async16(&T.st[4][lane], Bf.Ml + e);
+                    cp_async16(&T.st[5][lane], Bf.Vh + e);
+                    cp_async16(&T.st[6][lane], Bf.Vl + e);
+                }
+            }
+            cp_async_commit();
             uint32_t lb = 0, le = 0;
             if (lane == 0) {
                 lb = LP.ptr[r0];
@@ -804,12 +856,23 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
         if (qn > 0) batch(qn);
 
         if (!heavy_warp) {
-            if (own && !is_last(Cl, tb)) {
+            cp_async_wait_all();
+            if (upd) {
                 const df i1 = MULTI ? blk[b].ibc1 : s_ibc1, i2 = MULTI ? blk[b].ibc2 : s_ibc2;
                 const bool rs = rv && (MULTI ? blk[b].reset != 0 : s_reset != 0);
                 const int pa = tb & 1;
-                adam_row(e, g, Bf.dh(pa), Bf.dl(pa), PE, Bf.act, i1, i2, rs, Cl, Bf.dh(pa ^ 1), Bf.dl(pa ^ 1), Bf.Mh,
-                         Bf.Ml, Bf.Vh, Bf.Vl, Bf.q(pa ^ 1));
+                RowState S;
+                S.dh = T.st[0][lane];
+                S.dl = T.st[1][lane];
+                S.pe = T.st[2][lane];
+                if (was) {
+                    S.mh = T.st[3][lane];
+                    S.ml = T.st[4][lane];
+                    S.vh = T.st[5][lane];
+                    S.vl = T.st[6][lane];
+                }
+                adam_core(e, g, S, was, Bf.act, i1, i2, rs, Cl, Bf.dh(pa ^ 1), Bf.dl(pa ^ 1), Bf.Mh, Bf.Ml, Bf.Vh,
+                          Bf.Vl, Bf.q(pa ^ 1));
             }
         } else if (lane == 0 && !bstop) {
             H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, rv ? 1.f : 0.f);
