@@ -211,10 +211,13 @@ def run_batch(a):
     orig = torch.from_numpy(np.concatenate([w.orig for w in ws])).to(dev)
     recon = torch.from_numpy(np.concatenate([w.recon for w in ws])).to(dev)
     sizes = [w.n for w in ws]
-    prms = [w.params() for w in ws]
     offs = np.concatenate([[0], np.cumsum(sizes)])
     n = int(offs[-1])
     stream = torch.cuda.current_stream(dev)
+    # autotuner (not timed): cell factor of the fastest selection on the largest block
+    kbig = int(np.argmax(sizes))
+    cell_factor, tune_ms = pc.autotune_cells(orig[offs[kbig]:offs[kbig + 1]], ws[kbig].params())
+    prms = [w.params(cell_factor=cell_factor) for w in ws]
 
     def step():
         out, stats, code = pc.correct_batch(orig, recon, sizes, prms)
@@ -267,6 +270,7 @@ def run_batch(a):
             "dtype": "f32 data, double-float PGD", "data": "synthetic",
             "config": {"workload": f"batch{len(ws)}_hacc+md_eps0.1|0.5b_VP|SC|HF", "n_particles": n,
                        "blocks": len(ws), "block_sizes": "log-uniform 1e3-1e6", "parallelism": "replicas1",
+                       "cell_factor": cell_factor, "autotune_ms": {str(k): round(v, 2) for k, v in tune_ms.items()},
                        "l2": "inputs (2 x %d MB) larger than L2" % (n * 12 // 2 ** 20)},
             "membership_exact": bool(exact), "same_as_one_at_a_time": bool(same),
             "one_at_a_time": {"value": round(n / (seq_ms / 1e3) / 1e6, 3), "unit": "Mparticles/s",

@@ -71,19 +71,21 @@ typedef struct {
     double eps_rel;        /* Adam epsilon in units of xi (1e-8)                           */
     double loss_tol;       /* eps_L: stop when the tight loss <= loss_tol (default 0)     */
     int32_t replay_iters;  /* >= 0: run exactly this many updates, ignore the loss (-1 off) */
-    int32_t cell_cap_log2; /* tuning: at most 2^cell_cap_log2 grid cells (0 = default 27)   */
+    int32_t cell_cap_log2; /* tuning: at most 2^cell_cap_log2 grid cells (0: cell_factor)    */
     int32_t stall_patience;/* stall reset (not in the paper; 0 = off): after this many checks
                               without progress, the next check puts every editable endpoint
                               of a violated pair back at its original position with cleared
                               Adam moments.  Progress: the loss in units of xi^2 2^-24,
                               summed per violated pair after rounding to an integer, is 0 or
                               below best - floor(best / 1024).                            */
-    int32_t pad_;
+    int32_t cell_factor;   /* tuning: at most cell_factor * n grid cells, within [2^16, 2^28]
+                              (0 = 8); cells are never smaller than the pair reach.  Only
+                              speed depends on it (pc_autotune_cells picks one).          */
 } pc_params;
 
 /* Fills defaults: m=16, t_max=10000, alpha_rel=0.2, beta=(0.9,0.999), eps_rel=2e-6,
- * loss_tol=0, replay_iters=-1, cell_cap_log2=0, stall_patience=100, unit box,
- * non-periodic, mode VP. */
+ * loss_tol=0, replay_iters=-1, cell_cap_log2=0, stall_patience=100, cell_factor=0,
+ * unit box, non-periodic, mode VP. */
 void pc_params_default(pc_params *p);
 
 typedef struct pc_ctx pc_ctx;
@@ -186,6 +188,14 @@ typedef struct {
 } pc_block;
 pc_status pc_correct_batch(pc_ctx *ctx, const float *orig_dev, const float *recon_dev, const pc_block *blocks,
                            int32_t nblocks, float *corrected_dev, pc_correct_stats *stats, void *stream);
+
+/* Autotuner for the cell grid (not part of the paper): runs the selection (binning, pair
+ * search, union-find, selection) on the given point set once per candidate cell factor
+ * (2, 4, 8, 16, 32 cells per particle), twice each, and returns in *best the factor with
+ * the shortest time (CUDA events on the stream).  ms (host, may be NULL) receives the 5
+ * times.  The selected pairs do not depend on the factor, only the time does. */
+pc_status pc_autotune_cells(pc_ctx *ctx, const float *xyz_dev, int64_t n, const pc_params *params, int32_t *best,
+                            double *ms, void *stream);
 
 /* Edit stream v1 (Algorithm 1 last lines; Sec. 3.3).  Little endian:
  *   0  "PCE1" | 4 u32 version=1 | 8 u64 n | 16 u32 m | 20 u32 mode | 24 u32 periodic | 28 u32 0

@@ -21,7 +21,7 @@ from . import _native
 from ._native import PcError, make_params, struct_dict
 
 __all__ = ["Context", "fof_labels", "select_constraints", "Constraints", "correct", "correct_detail", "correct_batch",
-           "encode_edits", "apply_edits", "Server", "PcError", "make_params", "default_context"]
+           "encode_edits", "apply_edits", "Server", "autotune_cells", "PcError", "make_params", "default_context"]
 
 MODES = {"VP": 0, "SC": 1, "HF": 2}
 
@@ -198,6 +198,19 @@ def correct_batch(orig: torch.Tensor, recon: torch.Tensor, sizes, params_list, o
                                           _stream(orig.device))
     _native.check(code, "pc_correct_batch", allow_warn=True)
     return out, [struct_dict(st) for st in stats], code
+
+
+def autotune_cells(xyz: torch.Tensor, params, ctx: Context = None):
+    """Cell factor (cells per particle) with the fastest selection on this point set, and
+    the time of each candidate {2, 4, 8, 16, 32} in ms.  Results never depend on it."""
+    _xyz(xyz, "xyz")
+    ctx = ctx or default_context(xyz.device.index)
+    p = _params(params)
+    best = C.c_int32(0)
+    ms = (C.c_double * 5)()
+    _native.check(_native.lib().pc_autotune_cells(ctx.h, xyz.data_ptr(), xyz.shape[0], C.byref(p), C.byref(best), ms,
+                                                  _stream(xyz.device)), "pc_autotune_cells")
+    return int(best.value), dict(zip((2, 4, 8, 16, 32), list(ms)))
 
 
 def encode_edits(recon: torch.Tensor, corrected: torch.Tensor, params, ctx: Context = None) -> torch.Tensor:

@@ -125,7 +125,7 @@ Consts make_consts(const pc_params *p, const Inspect &ins, int64_t n, bool windo
     }
     int64_t cap;
     if (p->cell_cap_log2 > 0) cap = (int64_t)1 << std::min(p->cell_cap_log2, 30);
-    else cap = std::max<int64_t>(1 << 16, std::min<int64_t>((int64_t)1 << 27, 8 * n));
+    else cap = std::max<int64_t>(1 << 16, std::min<int64_t>((int64_t)1 << 28, (p->cell_factor > 0 ? p->cell_factor : 8) * n));
     for (int guard = 0; guard < 64 && (int64_t)nc[0] * nc[1] * nc[2] > cap; ++guard) {
         const double f = std::cbrt((double)cap / ((double)nc[0] * nc[1] * nc[2]));
         for (int k = 0; k < 3; ++k) {
@@ -453,7 +453,7 @@ void pc_params_default(pc_params *p) {
     p->replay_iters = -1;
     p->cell_cap_log2 = 0;
     p->stall_patience = 100;
-    p->pad_ = 0;
+    p->cell_factor = 0;
 }
 
 const char *pc_last_error(void) { return g_err.c_str(); }
@@ -608,6 +608,45 @@ pc_status pc_correct_batch(pc_ctx *ctx, const float *orig, const float *recon, c
         correct_blocks(ctx, orig, recon, std::move(S), nullptr, corrected, nullptr, nullptr, nullptr, stats, conv,
                        (cudaStream_t)stream);
         return conv ? PC_OK : PC_WARN_NOT_CONVERGED;
+    });
+}
+
+pc_status pc_autotune_cells(pc_ctx *ctx, const float *xyz, int64_t n, const pc_params *p, int32_t *best, double *ms,
+                            void *stream) {
+    return guarded([&]() -> pc_status {
+        use_device(ctx);
+        check_params(p, n, false);
+        if (!xyz || !best) fail(PC_EINVAL, "NULL argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        static const int32_t cand[5] = {2, 4, 8, 16, 32};
+        cudaEvent_t e0, e1;
+        PC_CUDA(cudaEventCreate(&e0));
+        PC_CUDA(cudaEventCreate(&e1));
+        double best_ms = 1e300;
+        *best = 8;
+        for (int c = 0; c < 5; ++c) {
+            pc_params q = *p;
+            q.cell_factor = cand[c];
+            q.cell_cap_log2 = 0;
+            float t = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {   // the first run warms the pool
+                pc_constraints h;
+                single_block(h.S, n, &q);
+                PC_CUDA(cudaEventRecord(e0, s));
+                do_select(ctx, xyz, s, &h);
+                PC_CUDA(cudaEventRecord(e1, s));
+                PC_CUDA(cudaEventSynchronize(e1));
+                PC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            }
+            if (ms) ms[c] = t;
+            if (t < best_ms) {
+                best_ms = t;
+                *best = cand[c];
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return PC_OK;
     });
 }
 

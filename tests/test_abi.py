@@ -56,7 +56,7 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
         import pytest
         pytest.skip("no C compiler")
     checks = [("pc_params", _native.Params, ["b", "xi", "periodic", "t_max", "alpha_rel", "loss_tol", "replay_iters",
-                                              "stall_patience"]),
+                                              "stall_patience", "cell_factor"]),
               ("pc_select_stats", _native.SelectStats, ["n_links", "ms"]),
               ("pc_correct_stats", _native.CorrectStats, ["converged", "ms_setup", "pgd_launches"]),
               ("pc_block", _native.Block, ["n", "params"]),

@@ -73,3 +73,22 @@ def test_batch_rejects_bad_tiling_and_names_the_block(cuda):
     with pytest.raises(pc.PcError) as e:
         pc.correct_batch(orig, bad, [w.n for w in ws], [w.params() for w in ws])
     assert e.value.code == -2 and "block 1" in str(e.value)
+
+
+def test_cell_factor_changes_speed_only(cuda):
+    # the autotuner's knob: the selected pairs are the same for every cell factor
+    import torch
+    import paper_2604_18801_gb300 as pc
+    w = synth.hacc_box(eps_over_b=0.5, mode="SC", seed=61, n=60000)
+    o = torch.from_numpy(w.orig).to(cuda)
+    best, ms = pc.autotune_cells(o, w.params())
+    assert best in (2, 4, 8, 16, 32) and all(v > 0 for v in ms.values())
+    ref = None
+    for f in (2, 8, 32):
+        cons = pc.select_constraints(o, w.params(cell_factor=f))
+        got = [x.cpu().numpy() for x in cons.pairs()]
+        cons.close()
+        if ref is None:
+            ref = got
+        else:
+            assert all(np.array_equal(a, b) for a, b in zip(ref, got))
