@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
-    ap.add_argument("--cpu-side", type=float, default=0.33, help="side of the sub-cube the CPU baseline corrects")
+    ap.add_argument("--cpu-side", type=float, default=0.25, help="side of the sub-cube the CPU baseline corrects")
     ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"])
     ap.add_argument("--blocks", type=int, default=512, help="batch: number of blocks")
     ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
@@ -301,7 +301,9 @@ def run_serve(a):
     import paper_2604_18801_gb300 as pc
     dev = torch.device("cuda", 0)
     dat = [(torch.from_numpy(w.orig).to(dev), torch.from_numpy(w.recon).to(dev)) for w in ws]
-    prms = [w.params() for w in ws]
+    kbig = max(range(len(ws)), key=lambda k: ws[k].n)
+    cell_factor, _ = pc.autotune_cells(dat[kbig][0], ws[kbig].params())
+    prms = [w.params(cell_factor=cell_factor) for w in ws]
     caps = [64 + (w.n + 7) // 8 + 12 * w.n for w in ws]
     n_tot = sum(w.n for w in ws)
     torch.cuda.synchronize(dev)
@@ -375,7 +377,7 @@ def run_serve(a):
             "dtype": "f32 data, double-float PGD", "data": "synthetic",
             "config": {"workload": f"serve{len(ws)}_hacc|md|fluid_eps0.1|0.5b_VP|SC|HF", "requests": len(ws),
                        "n_particles": n_tot, "sizes": "log-uniform 1e3-2e6", "arrivals": "Poisson",
-                       "load": a.load, "mem_budget_gb": 40, "parallelism": "replicas1"},
+                       "load": a.load, "mem_budget_gb": 40, "parallelism": "replicas1", "cell_factor": cell_factor},
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                            "p99": round(float(np.percentile(lat, 99)), 3), "max": round(float(lat.max()), 3)},
             "capacity_saturated": round(cap_rate / 1e6, 3), "arrival_rate_req_s": round(lam, 3),
@@ -437,7 +439,9 @@ def main():
     w = synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n)
     o = torch.from_numpy(w.orig).to(dev)
     r = torch.from_numpy(w.recon).to(dev)
-    prms = {m: w.params(mode=MODES[m]) for m in modes}
+    # autotuner (not timed): cells per particle of the fastest selection on this machine
+    cell_factor, tune_ms = pc.autotune_cells(o, w.params(mode=MODES[modes[0]]))
+    prms = {m: w.params(mode=MODES[m], cell_factor=cell_factor) for m in modes}
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -529,6 +533,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 data, double-float PGD",
         "data": "synthetic",
         "config": {"workload": workload, "n_particles": w.n, "b": w.b, "xi": w.xi, "modes": modes,
+                   "cell_factor": cell_factor,
                    "parallelism": f"replicas{world}", "l2": "inputs (2 x 201 MB) and PGD state larger than L2"},
         "membership_exact": exact,
         "per_mode": {m: {k: last[m][k] for k in ("iters", "n_vulnerable", "n_active", "n_editable", "viol0",

@@ -113,8 +113,14 @@ void publish(pc_server *srv, Job *j, int32_t state, int32_t status, const char *
     srv->cv_done.notify_all();
 }
 
-// Device bytes of the count pass for n particles (gathered inputs, binning, labels).
-int64_t count_pass_bytes(int64_t n) { return 176 * n + (int64_t)(1 << 20); }
+// Device bytes of a job's count pass: gathered inputs, binning, labels, and the cell table
+// (4 B per cell, at most cell_factor cells per particle).
+int64_t count_pass_bytes(const pc_job &sp) {
+    const int64_t f = sp.params.cell_factor > 0 ? sp.params.cell_factor : 8;
+    const int64_t cells = sp.params.cell_cap_log2 > 0 ? ((int64_t)1 << std::min(sp.params.cell_cap_log2, 30))
+                                                      : std::min<int64_t>((int64_t)1 << 28, f * sp.n);
+    return 176 * sp.n + 4 * std::max<int64_t>(cells, 1 << 16) + (int64_t)(1 << 20);
+}
 
 // Validates one job alone (finiteness, |recon - orig| <= xi, periodic box); throws Fail.
 void validate(Job *j, cudaStream_t s, HostScratch &hs) {
@@ -266,16 +272,17 @@ void release(pc_server *srv, const Cohort &c) {
 // ----------------------------------------------------------------------------- setup thread
 // Takes the next cohort's jobs from the head of the queue (under srv->mu); empty when
 // the queue is empty or memory and slots are short.
-std::vector<Job *> take_jobs(pc_server *srv, int64_t &n) {
+std::vector<Job *> take_jobs(pc_server *srv, int64_t &n, int64_t &bytes) {
     std::vector<Job *> take;
     n = 0;
+    bytes = 0;
     while (!srv->pending.empty()) {
         Job *j = srv->pending.front();
         if (srv->resident_jobs + (int64_t)take.size() >= srv->max_slots) break;
-        const int64_t nn = n + j->spec.n;
+        const int64_t nn = n + j->spec.n, bj = count_pass_bytes(j->spec);
         if (!take.empty() && nn > srv->max_cohort_n) break;
-        if (srv->used + count_pass_bytes(nn) > srv->budget) {
-            if (take.empty() && count_pass_bytes(j->spec.n) > srv->budget) {
+        if (srv->used + bytes + bj > srv->budget) {
+            if (take.empty() && bj > srv->budget) {
                 // can never fit
                 srv->pending.pop_front();
                 j->res.state = PC_JOB_ERROR;
@@ -291,9 +298,10 @@ std::vector<Job *> take_jobs(pc_server *srv, int64_t &n) {
         srv->pending.pop_front();
         take.push_back(j);
         n = nn;
+        bytes += bj;
     }
     if (!take.empty()) {
-        srv->used += count_pass_bytes(n);
+        srv->used += bytes;
         srv->resident_jobs += (int64_t)take.size();
         ++srv->n_cohorts;
         srv->peak = std::max(srv->peak, srv->used);
@@ -307,18 +315,17 @@ void setup_main(pc_server *srv) {
     cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking);
     for (;;) {
         std::vector<Job *> take;
-        int64_t n = 0;
+        int64_t n = 0, bytes1 = 0;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             for (;;) {
-                take = take_jobs(srv, n);
+                take = take_jobs(srv, n, bytes1);
                 if (!take.empty()) break;
                 if (srv->stopping && srv->pending.empty()) break;
                 srv->cv_setup.wait_for(lk, std::chrono::milliseconds(1));
             }
             if (take.empty()) break;
         }
-        const int64_t bytes1 = count_pass_bytes(n);
         // validate each job alone; failures end here
         std::vector<Job *> ok;
         for (Job *j : take) {
