@@ -46,7 +46,8 @@ enum CohortState { C_COUNTED, C_RUNNING };
 
 struct Cohort {
     std::vector<Job *> jobs;
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr;            // high priority: PGD state, iterations, finishing jobs
+    cudaStream_t s_setup = nullptr;      // low priority: gathering, binning, pair search, selection
     CohortState state = C_COUNTED;
     int64_t n = 0;
     int64_t bytes1 = 0, bytes2 = 0;      // estimates: count pass, the rest
@@ -59,16 +60,18 @@ struct Cohort {
     bool in_flight = false;              // a chunk and its status copy are queued
     int64_t rows = 0;                    // rows of the blocks still iterating (last status)
     ~Cohort() {
-        // release device memory on the cohort's stream before the stream goes away
+        // everything queued on the run stream finishes before the setup stream's buffers go
+        if (s) cudaStreamSynchronize(s);
         sol.reset();
         sel.reset();
         orig.release();
         recon.release();
         corr.release();
-        if (s) {
-            cudaStreamSynchronize(s);
-            cudaStreamDestroy(s);
+        if (s_setup) {
+            cudaStreamSynchronize(s_setup);
+            cudaStreamDestroy(s_setup);
         }
+        if (s) cudaStreamDestroy(s);
     }
 };
 
@@ -144,10 +147,15 @@ void fail_cohort(pc_server *srv, Cohort &c, pc_status st, const char *msg) {
 // Gathers the jobs' inputs and runs the count pass.
 void setup_count(pc_server *srv, Cohort &c) {
     const int nb = (int)c.jobs.size();
-    PC_CUDA(cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking));
-    c.orig.alloc(3 * c.n, c.s);
-    c.recon.alloc(3 * c.n, c.s);
-    c.corr.alloc(3 * c.n, c.s);
+    // iterations of running cohorts take precedence over the setup of new ones
+    int least = 0, greatest = 0;
+    PC_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    PC_CUDA(cudaStreamCreateWithPriority(&c.s, cudaStreamNonBlocking, greatest));
+    PC_CUDA(cudaStreamCreateWithPriority(&c.s_setup, cudaStreamNonBlocking, least));
+    const cudaStream_t ss = c.s_setup;
+    c.orig.alloc(3 * c.n, ss);
+    c.recon.alloc(3 * c.n, ss);
+    c.corr.alloc(3 * c.n, ss);
     c.sel.reset(new Selection());
     BlockSet &S = c.sel->S;
     S.nb = nb;
@@ -159,19 +167,20 @@ void setup_count(pc_server *srv, Cohort &c) {
         const pc_job &sp = c.jobs[b]->spec;
         S.prm[b] = sp.params;
         S.off[b] = at;
-        PC_CUDA(cudaMemcpyAsync(c.orig.p + 3 * at, sp.orig_dev, 12 * sp.n, cudaMemcpyDeviceToDevice, c.s));
-        PC_CUDA(cudaMemcpyAsync(c.recon.p + 3 * at, sp.recon_dev, 12 * sp.n, cudaMemcpyDeviceToDevice, c.s));
+        PC_CUDA(cudaMemcpyAsync(c.orig.p + 3 * at, sp.orig_dev, 12 * sp.n, cudaMemcpyDeviceToDevice, ss));
+        PC_CUDA(cudaMemcpyAsync(c.recon.p + 3 * at, sp.recon_dev, 12 * sp.n, cudaMemcpyDeviceToDevice, ss));
         at += sp.n;
     }
     S.off[nb] = at;
-    PC_CUDA(cudaMemcpyAsync(c.corr.p, c.recon.p, 12 * c.n, cudaMemcpyDeviceToDevice, c.s));
-    select_count(srv->hs_setup, c.orig.p, c.s, *c.sel);
+    PC_CUDA(cudaMemcpyAsync(c.corr.p, c.recon.p, 12 * c.n, cudaMemcpyDeviceToDevice, ss));
+    select_count(srv->hs_setup, c.orig.p, ss, *c.sel);
     c.bytes2 = select_more_bytes(*c.sel);
 }
 
 // Selection, PGD state and the captured graph; the first chunk is launched.
 void setup_run(pc_server *srv, Cohort &c) {
-    select_emit(srv->hs_setup, c.s, *c.sel);
+    const cudaStream_t ss = c.s_setup;
+    select_emit(srv->hs_setup, ss, *c.sel);
     BlockSet &S = c.sel->S;
     // PGD constants need M over orig and recon of each block
     BlockSet V;
@@ -179,10 +188,24 @@ void setup_run(pc_server *srv, Cohort &c) {
     V.n = S.n;
     V.prm = S.prm;
     V.off = S.off;
-    inspect_blocks(c.orig.p, c.recon.p, V, c.s, srv->hs_setup);
+    inspect_blocks(c.orig.p, c.recon.p, V, ss, srv->hs_setup);
     std::vector<Consts> cp(V.nb);
     for (int b = 0; b < V.nb; ++b) cp[b] = make_consts(&V.prm[b], V.ins[b], V.off[b + 1] - V.off[b], true);
-    c.sol.reset(new PgdSolver(c.sel->B, S, cp, c.orig.p, c.recon.p, c.sel->A.p, c.sel->nA, c.s, srv->hs_setup));
+    // the run stream starts after the setup stream's work, and the setup stream frees the
+    // selection's buffers only after the solver has read them
+    cudaEvent_t ev = nullptr;
+    PC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PC_CUDA(cudaEventRecord(ev, ss));
+    PC_CUDA(cudaStreamWaitEvent(c.s, ev, 0));
+    try {
+        c.sol.reset(new PgdSolver(c.sel->B, S, cp, c.orig.p, c.recon.p, c.sel->A.p, c.sel->nA, c.s, srv->hs_setup));
+    } catch (...) {
+        cudaEventDestroy(ev);
+        throw;
+    }
+    PC_CUDA(cudaEventRecord(ev, c.s));
+    PC_CUDA(cudaStreamWaitEvent(ss, ev, 0));
+    cudaEventDestroy(ev);
     // the solver keeps what it needs: cell lists and pairs go back to the pool
     c.sel->A.release();
     c.sel->B.keys.release();
