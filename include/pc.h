@@ -197,6 +197,31 @@ pc_status pc_correct_batch(pc_ctx *ctx, const float *orig_dev, const float *reco
 pc_status pc_autotune_cells(pc_ctx *ctx, const float *xyz_dev, int64_t n, const pc_params *params, int32_t *best,
                             double *ms, void *stream);
 
+/* Cluster-query metrics of Sec. 4.1 ("Metrics"), for judging an iteration-capped
+ * correction (Sec. 4.2 uses a 100-iteration limit).  lab0 / lab1: friends-of-friends
+ * labels (smallest id of the component, as pc_fof_labels gives them) of the original and
+ * of the decoded data, n entries each on the device.  A halo is a component with at least
+ * min_members particles; a particle outside every halo shares a halo with no other.
+ *   tp, fp, fn, tn: particle pairs by halo co-membership (same in both / merged /
+ *                   split / different in both), exact integers;
+ *   ari = 2 (tp tn - fp fn) / ((tp + fn)(fn + tn) + (tp + fp)(fp + tn));
+ *   mwm_iou = sum_i |H_i| max_j |H_i and H'_j| / |H_i or H'_j| / sum_i |H_i| over original
+ *             halos H_i and decoded halos H'_j (a halo with no overlap scores 0);
+ *   halos0 / halos1 / members0: halo counts and particles in original halos.
+ * With n_bins > 0 the halo mass functions dn/dlog10 M (mass = members) of both sides are
+ * written to hmf0 / hmf1 (host, n_bins each) over n_bins equal-width bins of log10 M from
+ * log10(min_members) to log10 of the largest original halo (edges: host, n_bins + 1),
+ * normalised by volume and bin width.  Synchronises the stream. */
+typedef struct {
+    uint64_t tp, fp, fn, tn;
+    double ari, mwm_iou;
+    int64_t halos0, halos1, members0;
+    int64_t pad_;
+} pc_cluster_metrics_t;
+pc_status pc_cluster_metrics(pc_ctx *ctx, const int32_t *lab0_dev, const int32_t *lab1_dev, int64_t n,
+                             int32_t min_members, int32_t n_bins, double volume, pc_cluster_metrics_t *out,
+                             double *hmf0, double *hmf1, double *bin_edges, void *stream);
+
 /* Edit stream v1 (Algorithm 1 last lines; Sec. 3.3).  Little endian:
  *   0  "PCE1" | 4 u32 version=1 | 8 u64 n | 16 u32 m | 20 u32 mode | 24 u32 periodic | 28 u32 0
  *   32 f64 xi | 40 u64 flagged | 48 u64 flag_bytes=ceil(n/8) | 56 u64 code_bytes

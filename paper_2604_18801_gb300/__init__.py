@@ -21,7 +21,8 @@ from . import _native
 from ._native import PcError, make_params, struct_dict
 
 __all__ = ["Context", "fof_labels", "select_constraints", "Constraints", "correct", "correct_detail", "correct_batch",
-           "encode_edits", "apply_edits", "Server", "autotune_cells", "PcError", "make_params", "default_context"]
+           "encode_edits", "apply_edits", "Server", "autotune_cells", "cluster_metrics", "PcError", "make_params",
+           "default_context"]
 
 MODES = {"VP": 0, "SC": 1, "HF": 2}
 
@@ -211,6 +212,29 @@ def autotune_cells(xyz: torch.Tensor, params, ctx: Context = None):
     _native.check(_native.lib().pc_autotune_cells(ctx.h, xyz.data_ptr(), xyz.shape[0], C.byref(p), C.byref(best), ms,
                                                   _stream(xyz.device)), "pc_autotune_cells")
     return int(best.value), dict(zip((2, 4, 8, 16, 32), list(ms)))
+
+
+def cluster_metrics(lab0: torch.Tensor, lab1: torch.Tensor, min_members: int = 20, n_bins: int = 50,
+                    volume: float = 1.0, ctx: Context = None) -> dict:
+    """ARI, MWM-IoU and halo mass functions (Sec. 4.1) between two labelings of the same
+    particles (int32 CUDA tensors, "smallest id of the component" as fof_labels gives)."""
+    for t, nm in ((lab0, "lab0"), (lab1, "lab1")):
+        if not (t.is_cuda and t.dtype == torch.int32 and t.dim() == 1 and t.is_contiguous()):
+            raise ValueError(f"{nm} must be a contiguous int32 CUDA vector")
+    if lab0.shape != lab1.shape:
+        raise ValueError("labelings differ in length")
+    ctx = ctx or default_context(lab0.device.index)
+    m = _native.ClusterMetrics()
+    nb = max(0, int(n_bins))
+    h0, h1, ed = (C.c_double * max(1, nb))(), (C.c_double * max(1, nb))(), (C.c_double * (nb + 1))()
+    _native.check(_native.lib().pc_cluster_metrics(ctx.h, lab0.data_ptr(), lab1.data_ptr(), lab0.shape[0],
+                                                   int(min_members), nb, float(volume), C.byref(m),
+                                                   h0 if nb else None, h1 if nb else None, ed if nb else None,
+                                                   _stream(lab0.device)), "pc_cluster_metrics")
+    d = struct_dict(m)
+    if nb:
+        d["hmf0"], d["hmf1"], d["bin_edges"] = list(h0)[:nb], list(h1)[:nb], list(ed)
+    return d
 
 
 def encode_edits(recon: torch.Tensor, corrected: torch.Tensor, params, ctx: Context = None) -> torch.Tensor:

@@ -63,6 +63,12 @@ class JobResult(C.Structure):
 JOB_STATES = {0: "PENDING", 1: "RUNNING", 2: "DONE", 3: "ERROR"}
 
 
+class ClusterMetrics(C.Structure):
+    _fields_ = [("tp", C.c_uint64), ("fp", C.c_uint64), ("fn", C.c_uint64), ("tn", C.c_uint64),
+                ("ari", C.c_double), ("mwm_iou", C.c_double), ("halos0", C.c_int64), ("halos1", C.c_int64),
+                ("members0", C.c_int64), ("pad_", C.c_int64)]
+
+
 def struct_dict(s) -> dict:
     return {k: getattr(s, k) for k, _ in s._fields_ if not k.endswith("_")}
 
@@ -99,6 +105,8 @@ def lib():
         L.pc_encode_edits.argtypes = [vp, vp, vp, i64, P, vp, sz, C.POINTER(sz), vp]
         L.pc_apply_edits.argtypes = [vp, vp, i64, vp, sz, vp, vp]
         L.pc_autotune_cells.argtypes = [vp, vp, i64, P, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
+        L.pc_cluster_metrics.argtypes = [vp, vp, vp, i64, C.c_int32, C.c_int32, C.c_double,
+                                         C.POINTER(ClusterMetrics), vp, vp, vp, vp]
         L.pc_server_create.argtypes = [vp, sz, C.c_int32, i64, C.POINTER(vp)]
         L.pc_server_destroy.argtypes = [vp]
         L.pc_server_destroy.restype = None
@@ -107,7 +115,8 @@ def lib():
         L.pc_serve_wait.argtypes = [vp, C.c_uint64, i64, C.POINTER(JobResult)]
         L.pc_serve_counters.argtypes = [vp, C.POINTER(i64)]
         for f in ("pc_ctx_create", "pc_fof_labels", "pc_select_constraints", "pc_constraints_copy", "pc_correct",
-                  "pc_correct_detail", "pc_correct_batch", "pc_autotune_cells", "pc_server_create", "pc_serve_submit",
+                  "pc_correct_detail", "pc_correct_batch", "pc_autotune_cells", "pc_cluster_metrics",
+                  "pc_server_create", "pc_serve_submit",
                   "pc_serve_poll",
                   "pc_serve_wait", "pc_serve_counters",
                   "pc_encode_edits", "pc_apply_edits"):

@@ -61,7 +61,8 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
               ("pc_correct_stats", _native.CorrectStats, ["converged", "ms_setup", "pgd_launches"]),
               ("pc_block", _native.Block, ["n", "params"]),
               ("pc_job", _native.Job, ["n", "params", "corrected_dev", "stream_cap"]),
-              ("pc_job_result", _native.JobResult, ["done_ns", "stream_bytes", "cohort_jobs", "stats", "error"])]
+              ("pc_job_result", _native.JobResult, ["done_ns", "stream_bytes", "cohort_jobs", "stats", "error"]),
+              ("pc_cluster_metrics_t", _native.ClusterMetrics, ["tn", "ari", "mwm_iou", "members0"])]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pc.h"', "int main(void) {"]
     for cname, _, fields in checks:
         lines.append(f'printf("%zu\\n", sizeof({cname}));')
