@@ -553,6 +553,32 @@ def main():
         exact &= bool(torch.equal(lab0, lab1)) and bool(
             (dec.double() - o.double()).abs().max().item() <= w.xi) and res[m][3] == 0
 
+    # lossless stage (not timed in the step): canonical Huffman container of each mode's
+    # stream, its size, and the median time of an encode and a decode call
+    lossless = {}
+    for m in modes:
+        s_ = res[m][1]
+        blob = pc.huff_encode(s_)
+        ok = bool(torch.equal(pc.huff_decode(blob), s_))
+        te, td = [], []
+        for _ in range(5):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            pc.huff_encode(s_)
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            pc.huff_decode(blob)
+            torch.cuda.synchronize(dev)
+            te.append((t1 - t0) * 1e3)
+            td.append((time.perf_counter() - t1) * 1e3)
+        e_ms, d_ms = statistics.median(te), statistics.median(td)
+        lossless[m] = {"stream_bytes": int(s_.numel()), "container_bytes": int(blob.numel()),
+                       "ratio": round(s_.numel() / blob.numel(), 3),
+                       "bits_per_particle": round(8 * blob.numel() / w.n, 3),
+                       "encode_ms": round(e_ms, 3), "decode_ms": round(d_ms, 3),
+                       "encode_gbs": round(s_.numel() / e_ms / 1e6, 2), "decode_gbs": round(s_.numel() / d_ms / 1e6, 2),
+                       "roundtrip_exact": ok}
+
     # roofline of the dominant kernel (the PGD iteration): algorithmic bytes per launch =
     # 112 B per editable particle + 8 B per active pair; duration from the in-library events
     last = stats[-1]
@@ -603,6 +629,7 @@ def main():
         "per_mode": {m: {k: last[m][k] for k in ("iters", "n_vulnerable", "n_active", "n_editable", "viol0",
                                                    "ms_setup", "ms_pgd")} for m in modes},
         "roofline": roofline,
+        "lossless": lossless,
         "e2e": {"value": round(e2e_v, 3), "unit": "Mparticles/s",
                 "h2d_bytes_per_step": int(ho.numel() * 4 + hr.numel() * 4), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

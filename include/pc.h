@@ -260,6 +260,38 @@ pc_status pc_apply_edits(pc_ctx *ctx, const float *recon_dev, int64_t n, const u
 pc_status pc_apply_edits_static(const float *recon_dev, int64_t n, const uint8_t *stream_dev, size_t nbytes,
                                 float *out_dev, void *stream);
 
+/* Lossless stage (Algorithm 1, last line; Sec. 3.3 "Compaction, quantization, and
+ * lossless compression"): canonical Huffman coding of an edit stream v1.  The paper
+ * follows the Huffman stage with ZSTD; that stage is not part of this container.
+ * Container "PCH1", little endian:
+ *   0  "PCH1" | 4 u32 version=1 | 8 u64 raw_bytes | 16 u32 n_lanes | 20 u32 chunk=4096
+ *   24 u32 max_len=15 | 28 u32 0 | 32..95 the stream's 64-byte header, verbatim
+ *   96 per lane: u64 n_syms | u64 bit_len | u64 n_chunks=ceil(n_syms/4096) |
+ *      256 x u8 code length (0 = unused symbol) | n_chunks x u64 bit offset of the chunk |
+ *      ceil(bit_len/32) x u32 words
+ * Lane 0 holds the flag bytes, lane 1 + k byte k of every code (k < ceil(m/8)).  Each
+ * lane has its own code: Huffman lengths (ties taken in order of node id: symbols 0..255,
+ * then merged nodes in order of creation) limited to 15 bits (deepest codes folded to 15
+ * and the Kraft sum restored by deepening the deepest shorter codes; lengths then dealt
+ * from longest to shortest in ascending (frequency, -symbol) order), canonical codes in
+ * (length, symbol) order, bits written most significant first from bit 31 of each word.
+ * A lane with one distinct symbol codes it with one bit.
+ *
+ * pc_huff_encode: in_dev is a device copy of an edit stream of nbytes bytes (PC_EFORMAT
+ * if it is not one).  With out_dev NULL only *out_bytes is computed; else cap must be at
+ * least that size (PC_EINVAL otherwise) and the container is written to out_dev.
+ * pc_huff_decode: in_dev is a device copy of a container of nbytes bytes; *out_bytes is
+ * set to the stream's size and, with out_dev non-NULL (cap at least that size), the
+ * stream is written there.  PC_EFORMAT on a malformed container or an invalid code.
+ * The container's buffer (out_dev of the encoder, in_dev of the decoder) must be 4-byte
+ * aligned (PC_EINVAL otherwise; cudaMalloc'd pointers are): its words are read and
+ * written as u32, and lanes after the first start at 4-byte boundaries.
+ * Both synchronise the stream and hold no memory after they return. */
+pc_status pc_huff_encode(pc_ctx *ctx, const uint8_t *in_dev, size_t nbytes, uint8_t *out_dev, size_t cap,
+                         size_t *out_bytes, void *stream);
+pc_status pc_huff_decode(pc_ctx *ctx, const uint8_t *in_dev, size_t nbytes, uint8_t *out_dev, size_t cap,
+                         size_t *out_bytes, void *stream);
+
 /* ------------------------------------------------------------------ serving
  * A request loop around pc_correct (not part of the paper).  A server owns one worker
  * thread on the context's device.  Submitted jobs wait in FIFO order until they can be

@@ -127,21 +127,22 @@ def encode_lane(sym: np.ndarray) -> bytes:
     for c in range(nchunks):
         offsets[c] = total
         total += int(lens[c * CHUNK:(c + 1) * CHUNK].sum())
+    # bit j of the lane is bit (len - 1 - k) of the code of the symbol whose code starts
+    # at position j - k; the bit string is then cut into big-endian 32-bit words
     nwords = (total + 31) // 32
-    words = [0] * nwords
-    pos = 0
-    for s in sym.tolist():
-        ln, cd = lengths[s], codes[s]
-        for k in range(ln - 1, -1, -1):
-            if (cd >> k) & 1:
-                words[pos >> 5] |= 1 << (31 - (pos & 31))
-            pos += 1
+    bits = np.zeros(32 * nwords, np.uint8)
+    start = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64) if n else np.zeros(0, np.int64)
+    cd = np.array(codes, np.int64)[sym]
+    for k in range(MAX_LEN):
+        has = lens > k
+        bits[start[has] + k] = (cd[has] >> (lens[has] - 1 - k)) & 1
+    words = np.packbits(bits).view(">u4").astype(np.uint32) if nwords else np.zeros(0, np.uint32)
     out = bytearray()
     out += int(n).to_bytes(8, "little") + int(total).to_bytes(8, "little") + int(nchunks).to_bytes(8, "little")
     out += bytes(lengths)
     for o in offsets:
         out += int(o).to_bytes(8, "little")
-    out += np.array(words, np.uint32).astype("<u4").tobytes()
+    out += words.astype("<u4").tobytes()
     return bytes(out)
 
 

@@ -21,7 +21,7 @@ from . import _native
 from ._native import PcError, make_params, struct_dict
 
 __all__ = ["Context", "fof_labels", "select_constraints", "Constraints", "correct", "correct_detail", "correct_batch",
-           "encode_edits", "apply_edits", "Server", "autotune_cells", "cluster_metrics", "PcError", "make_params",
+           "encode_edits", "apply_edits", "huff_encode", "huff_decode", "Server", "autotune_cells", "cluster_metrics", "PcError", "make_params",
            "default_context"]
 
 MODES = {"VP": 0, "SC": 1, "HF": 2}
@@ -265,6 +265,30 @@ def apply_edits(recon: torch.Tensor, stream: torch.Tensor, out: torch.Tensor = N
                                                stream.numel(), out.data_ptr(), _stream(recon.device)),
                   "pc_apply_edits")
     return out
+
+
+def _huff(fn: str, data: torch.Tensor, ctx: Context) -> torch.Tensor:
+    if not (data.is_cuda and data.dtype == torch.uint8 and data.is_contiguous() and data.dim() == 1):
+        raise ValueError("input must be a contiguous 1-D uint8 CUDA tensor")
+    ctx = ctx or default_context(data.device.index)
+    f = getattr(_native.lib(), fn)
+    nb = C.c_size_t(0)
+    s = _stream(data.device)
+    _native.check(f(ctx.h, data.data_ptr(), data.numel(), None, 0, C.byref(nb), s), fn)
+    out = torch.empty(nb.value, dtype=torch.uint8, device=data.device)
+    _native.check(f(ctx.h, data.data_ptr(), data.numel(), out.data_ptr(), nb.value, C.byref(nb), s), fn)
+    return out
+
+
+def huff_encode(stream: torch.Tensor, ctx: Context = None) -> torch.Tensor:
+    """Lossless stage: an edit stream (uint8 CUDA tensor) to a "PCH1" container of
+    per-lane canonical Huffman codes (uint8 CUDA tensor)."""
+    return _huff("pc_huff_encode", stream, ctx)
+
+
+def huff_decode(blob: torch.Tensor, ctx: Context = None) -> torch.Tensor:
+    """Inverse of :func:`huff_encode`: the edit stream, byte for byte."""
+    return _huff("pc_huff_decode", blob, ctx)
 
 
 class Server:

@@ -104,6 +104,8 @@ def lib():
         L.pc_correct_batch.argtypes = [vp, vp, vp, C.POINTER(Block), C.c_int32, vp, C.POINTER(CorrectStats), vp]
         L.pc_encode_edits.argtypes = [vp, vp, vp, i64, P, vp, sz, C.POINTER(sz), vp]
         L.pc_apply_edits.argtypes = [vp, vp, i64, vp, sz, vp, vp]
+        L.pc_huff_encode.argtypes = [vp, vp, sz, vp, sz, C.POINTER(sz), vp]
+        L.pc_huff_decode.argtypes = [vp, vp, sz, vp, sz, C.POINTER(sz), vp]
         L.pc_autotune_cells.argtypes = [vp, vp, i64, P, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
         L.pc_cluster_metrics.argtypes = [vp, vp, vp, i64, C.c_int32, C.c_int32, C.c_double,
                                          C.POINTER(ClusterMetrics), vp, vp, vp, vp]
@@ -119,7 +121,7 @@ def lib():
                   "pc_server_create", "pc_serve_submit",
                   "pc_serve_poll",
                   "pc_serve_wait", "pc_serve_counters",
-                  "pc_encode_edits", "pc_apply_edits"):
+                  "pc_encode_edits", "pc_apply_edits", "pc_huff_encode", "pc_huff_decode"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
