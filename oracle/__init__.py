@@ -99,6 +99,9 @@ def lib():
             L.or_pgd.argtypes = [f32p, f32p, C.c_int64, P, u32p, u32p, u8p, C.c_int64, f32p,
                                  f64p, i32p, C.POINTER(PgdStats)]
             L.or_pgd.restype = C.c_int32
+            L.or_pgd_thr.argtypes = [f32p, f32p, C.c_int64, P, u32p, u32p, u8p, f64p, C.c_int64, f32p,
+                                     f64p, i32p, C.POINTER(PgdStats)]
+            L.or_pgd_thr.restype = C.c_int32
             L.or_encode.argtypes = [f32p, f32p, C.c_int64, P, u8p, C.c_int64]
             L.or_encode.restype = C.c_int64
             L.or_decode.argtypes = [f32p, C.c_int64, u8p, C.c_int64, f32p]
@@ -211,6 +214,43 @@ def pgd(orig, recon, ai, aj, alink, **kw):
     rc = lib().or_pgd(op, rp, n, C.byref(make_params(**kw)), _ptr(ai, C.c_uint32),
                       _ptr(aj, C.c_uint32), _ptr(al, C.c_uint8), len(ai), _ptr(out, C.c_float),
                       _ptr(delta, C.c_double), _ptr(ed, C.c_int32), C.byref(st))
+    if rc != 0:
+        raise ValueError("oracle: empty projection box (xi too small for float32 coordinates)")
+    return out, delta, ed.astype(bool), st.as_dict()
+
+
+def select_multi(P, b_list, mode=None, **kw):
+    """Union of the active sets of several linking lengths (Sec. 1 and Sec. 5: a range of
+    thresholds is supported by enforcing the union of their selected pairs).  Returns
+    (ai, aj, alink, ab) in threshold order, then (i, j) order: alink is the link flag
+    at the pair's own linking length ab."""
+    out = [[], [], [], []]
+    for b in b_list:
+        ai, aj, al, _ = select(P, mode=mode, **dict(kw, b=b))
+        out[0].append(ai)
+        out[1].append(aj)
+        out[2].append(al)
+        out[3].append(np.full(len(ai), float(b)))
+    return tuple(np.concatenate(x) for x in out)
+
+
+def pgd_multi(orig, recon, ai, aj, alink, ab, **kw):
+    """PGD on an active set whose pairs carry their own linking length ab (the union of
+    several thresholds): (corrected f32, delta f64 (n,3), editable mask, stats)."""
+    o, op = _f32(orig)
+    r, rp = _f32(recon)
+    n = o.shape[0]
+    ai = np.ascontiguousarray(ai, np.uint32)
+    aj = np.ascontiguousarray(aj, np.uint32)
+    al = np.ascontiguousarray(alink, np.uint8)
+    ab = np.ascontiguousarray(ab, np.float64)
+    out = np.empty_like(o)
+    delta = np.zeros((n, 3), np.float64)
+    ed = np.zeros(n, np.int32)
+    st = PgdStats()
+    rc = lib().or_pgd_thr(op, rp, n, C.byref(make_params(**kw)), _ptr(ai, C.c_uint32), _ptr(aj, C.c_uint32),
+                          _ptr(al, C.c_uint8), _ptr(ab, C.c_double), len(ai), _ptr(out, C.c_float),
+                          _ptr(delta, C.c_double), _ptr(ed, C.c_int32), C.byref(st))
     if rc != 0:
         raise ValueError("oracle: empty projection box (xi too small for float32 coordinates)")
     return out, delta, ed.astype(bool), st.as_dict()

@@ -365,10 +365,13 @@ double norm3(const double r[3]) {
 }
 
 // Projected gradient descent with Adam on the tightened loss (Algorithm 1, Eq. 3),
-// in float64 on offsets delta = P_hat - P of the editable particles.
+// in float64 on offsets delta = P_hat - P of the editable particles.  ab (may be NULL)
+// gives each active pair its own linking length: several thresholds are supported by
+// enforcing the union of their selected pairs (Sec. 1 and Sec. 5), each pair with the
+// constraint and the margin of its own threshold.
 void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Active> &A,
          const or_params *p, const or_consts &c, float *corrected, double *delta_out,
-         int32_t *editable_out, or_pgd_stats *st) {
+         int32_t *editable_out, or_pgd_stats *st, const double *ab = nullptr) {
     std::memset(st, 0, sizeof(*st));
     // E = endpoints(A), ascending id (Algorithm 1).
     std::vector<int64_t> idx(n, -1);
@@ -392,6 +395,15 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
     for (int64_t k = 0; k < na; ++k)
         for (int d = 0; d < 3; ++d)
             dp[3 * k + d] = (double)cdiff(orig[3 * A[k].i + d], orig[3 * A[k].j + d], p->periodic, c.L[d]);
+    // Per pair: thresholds of Eq. 3 (b -/+ dt with the pair's b) and the coincidence radius.
+    std::vector<double> thr_link(na, c.thr_link), thr_non(na, c.thr_non), tau(na, c.tau);
+    if (ab)
+        for (int64_t k = 0; k < na; ++k) {
+            const double dt = 2.0 * std::sqrt(3.0) * (c.eps_q + c.u) + ab[k] * std::ldexp(1.0, -20);
+            thr_link[k] = ab[k] - dt;
+            thr_non[k] = ab[k] + dt;
+            tau[k] = std::ldexp(ab[k], -30);
+        }
     // P_hat starts at the base reconstruction: delta0 = recon - orig (exact in float64).
     std::vector<double> delta(3 * ne), m(3 * ne, 0.0), v(3 * ne, 0.0), g(3 * ne);
     for (int64_t e = 0; e < ne; ++e)
@@ -412,7 +424,7 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             for (int d = 0; d < 3; ++d) r[d] = offset(dp[3 * k + d], delta[3 * a + d], delta[3 * b + d]);
             const double dh = norm3(r);
             // link: penalise d_hat > b - dt;  non-link: penalise d_hat < b + dt
-            const double viol_amt = A[k].link ? dh - c.thr_link : c.thr_non - dh;
+            const double viol_amt = A[k].link ? dh - thr_link[k] : thr_non[k] - dh;
             if (!(viol_amt > 0.0)) continue;
             L += viol_amt * viol_amt;
             nv += 1;
@@ -420,7 +432,7 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             hit[a] = hit[b] = 1;
             if (!want_grad) continue;
             double u[3];
-            if (dh > c.tau) {
+            if (dh > tau[k]) {
                 for (int d = 0; d < 3; ++d) u[d] = r[d] / dh;
             } else {
                 const double n0 = std::sqrt(dp[3 * k] * dp[3 * k] + dp[3 * k + 1] * dp[3 * k + 1] +
@@ -618,18 +630,27 @@ int64_t or_select(const float *P, int64_t n, const or_params *p, int32_t mode,
     return na;
 }
 
-// PGD on a given active set (Algorithm 1 loop).  delta_out (n*3 doubles, may be NULL)
-// receives the float64 offsets of editable particles; editable_out (n ints, may be NULL)
-// marks E.  Returns 0, or -1 when the box is empty (xi too small for float32 coordinates).
-int32_t or_pgd(const float *orig, const float *recon, int64_t n, const or_params *p,
-               const uint32_t *ai, const uint32_t *aj, const uint8_t *alink, int64_t na,
-               float *corrected, double *delta_out, int32_t *editable_out, or_pgd_stats *st) {
+// PGD on a given active set (Algorithm 1 loop) with a linking length per active pair
+// (ab may be NULL: p->b for every pair); alink[k] is the pair's link flag at its own
+// linking length.  delta_out (n*3 doubles, may be NULL) receives the float64 offsets of
+// editable particles; editable_out (n ints, may be NULL) marks E.  Returns 0, or -1 when
+// the box is empty (xi too small for float32 coordinates).
+int32_t or_pgd_thr(const float *orig, const float *recon, int64_t n, const or_params *p,
+                   const uint32_t *ai, const uint32_t *aj, const uint8_t *alink, const double *ab, int64_t na,
+                   float *corrected, double *delta_out, int32_t *editable_out, or_pgd_stats *st) {
     or_consts c = make_consts(p, orig, recon, n);
     if (!(c.xi_box > 0.0)) return -1;
     std::vector<Active> A(na);
     for (int64_t k = 0; k < na; ++k) A[k] = {ai[k], aj[k], alink[k]};
-    pgd(orig, recon, n, A, p, c, corrected, delta_out, editable_out, st);
+    pgd(orig, recon, n, A, p, c, corrected, delta_out, editable_out, st, ab);
     return 0;
+}
+
+// The same with p->b for every pair.
+int32_t or_pgd(const float *orig, const float *recon, int64_t n, const or_params *p,
+               const uint32_t *ai, const uint32_t *aj, const uint8_t *alink, int64_t na,
+               float *corrected, double *delta_out, int32_t *editable_out, or_pgd_stats *st) {
+    return or_pgd_thr(orig, recon, n, p, ai, aj, alink, nullptr, na, corrected, delta_out, editable_out, st);
 }
 
 // Edit stream (Algorithm 1 last lines, Sec. 3.3): flags + m-bit codes; format v1:

@@ -207,7 +207,9 @@ def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps
     link = torch.tensor(alink.astype(bool))
     delta = torch.tensor(recon[E].astype(np.float64) - orig[E].astype(np.float64), requires_grad=True)
     opt = torch.optim.Adam([delta], lr=alpha_rel * xi, betas=(0.9, 0.999), eps=eps_rel * xi)
-    thr_l, thr_n = consts["thr_link"], consts["thr_non"]
+    # scalars, or one threshold per pair (several linking lengths)
+    thr_l = torch.as_tensor(consts["thr_link"], dtype=torch.float64)
+    thr_n = torch.as_tensor(consts["thr_non"], dtype=torch.float64)
     unit = xi * xi * 2.0 ** -24
     best, since, reset_now, resets = None, 0, False, 0
     for _ in range(steps):
