@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--eps", type=float, default=0.1, help="eps / b")
     ap.add_argument("--modes", default="VP,SC,HF")
+    ap.add_argument("--base", default="quant", choices=["quant", "morton"],
+                    help="base-compressor stand-in: global quantizer or the Morton-order baseline (Sec. 4.1)")
     ap.add_argument("--n", type=int, default=256 ** 3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -464,13 +466,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     modes = [m.strip() for m in a.modes.split(",") if m.strip()]
-    workload = f"hacc{a.n}_eps{a.eps:g}b_{'+'.join(modes)}"
+    workload = f"hacc{a.n}_eps{a.eps:g}b_{'+'.join(modes)}" + ("" if a.base == "quant" else "_" + a.base)
 
     if a.impl == "reference":
         if rank != 0:
             return
         from paper_2604_18801_gb300 import synth
-        w = synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n)
+        w = synth.with_base(synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n), a.base)
         for _ in range(a.warmup):
             pass
         times = []
@@ -500,7 +502,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    w = synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n)
+    w = synth.with_base(synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n), a.base)
     o = torch.from_numpy(w.orig).to(dev)
     r = torch.from_numpy(w.recon).to(dev)
     # autotuner (not timed): cells per particle of the fastest selection on this machine
@@ -622,7 +624,7 @@ def main():
         "n_gpus": world, "steps": a.steps, "warmup": max(3, a.warmup), "ms_per_step": round(per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 data, double-float PGD",
         "data": "synthetic",
-        "config": {"workload": workload, "n_particles": w.n, "b": w.b, "xi": w.xi, "modes": modes,
+        "config": {"workload": workload, "n_particles": w.n, "b": w.b, "xi": w.xi, "modes": modes, "base": a.base,
                    "cell_factor": cell_factor,
                    "parallelism": f"replicas{world}", "l2": "inputs (2 x 201 MB) and PGD state larger than L2"},
         "membership_exact": exact,

@@ -18,6 +18,12 @@ them with the shapes, densities and structure described there:
   1 + 0.8 sin(2 pi x) cos(2 pi y) (FPM-like).
 * ``quantize_recon`` -- the absolute-error quantizer x' = 2e*round(x/2e) used
   as the base compressor (|x' - x| <= e per coordinate).
+* ``morton_recon`` -- the Morton-order baseline of Sec. 4.1: particles visited cell
+  by cell in Morton order inside each cell, each coordinate predicted by the
+  previous particle's reconstruction (first order) and the residual quantized in
+  bins of 2e; the first particle of a cell is kept exact.  Its errors lie on a
+  lattice whose offset changes from cell to cell.  ``with_base`` swaps it in,
+  with cells holding 64 particles on average.
 
 Every function takes an explicit seed and returns float32 arrays of shape
 (N, 3), C-contiguous (x, y, z per particle).  Particle order is shuffled so
@@ -34,6 +40,8 @@ import numpy as np
 __all__ = [
     "Workload",
     "quantize_recon",
+    "morton_recon",
+    "with_base",
     "cosmo_box",
     "md_clusters",
     "fluid_box",
@@ -92,6 +100,77 @@ def quantize_recon(x: np.ndarray, eps: float) -> np.ndarray:
         r[bad] = np.nextafter(r[bad], x[bad])
     assert np.all(np.abs(r.astype(np.float64) - x64) <= eps)
     return np.ascontiguousarray(r)
+
+
+def _fix_bound(r: np.ndarray, x: np.ndarray, eps: float) -> np.ndarray:
+    """Moves float32 values one ulp toward x where rounding broke |r - x| <= eps."""
+    bad = np.abs(r.astype(np.float64) - x.astype(np.float64)) > eps
+    if np.any(bad):
+        r[bad] = np.nextafter(r[bad], x[bad])
+    return r
+
+
+def morton_order(x: np.ndarray, cell: float, lo, hi) -> np.ndarray:
+    """Particle order of the Morton baseline: by cell (row-major over the grid of cubes
+    of side ``cell`` from ``lo``), then by the 10-bit-per-axis Morton code of the
+    position inside the cell, then by id."""
+    x64 = x.astype(np.float64)
+    lo = np.asarray(lo, np.float64)
+    ncell = np.maximum(1, np.ceil((np.asarray(hi, np.float64) - lo) / cell)).astype(np.int64)
+    c = np.clip(np.floor((x64 - lo) / cell).astype(np.int64), 0, ncell - 1)
+    lin = (c[:, 0] * ncell[1] + c[:, 1]) * ncell[2] + c[:, 2]
+    f = np.clip(((x64 - lo) / cell - c) * 1024.0, 0, 1023).astype(np.int64)
+    code = np.zeros(len(x), np.int64)
+    for bit in range(10):
+        for ax in range(3):
+            code |= ((f[:, ax] >> bit) & 1) << (3 * bit + (2 - ax))
+    return np.lexsort((np.arange(len(x)), code, lin)), lin
+
+
+def morton_recon(x: np.ndarray, eps: float, cell: float, lo, hi) -> np.ndarray:
+    """Morton-order baseline (Sec. 4.1) as a base-compressor stand-in.
+
+    In the order of ``morton_order``, the first particle of each cell is kept exact;
+    every later coordinate is predicted by the previous particle's reconstruction p
+    and reconstructed as p + 2 eps * round((x - p) / (2 eps)) (float64, rounded to
+    float32; a value that rounding moved beyond eps is moved one ulp back).  The loop
+    runs over the rank inside a cell, vectorised across cells."""
+    order, lin = morton_order(x, cell, lo, hi)
+    xs = x[order]
+    ls = lin[order]
+    n = len(x)
+    rs = np.empty_like(xs)
+    first = np.ones(n, bool)
+    first[1:] = ls[1:] != ls[:-1]
+    start = np.maximum.accumulate(np.where(first, np.arange(n), 0))
+    rank = np.arange(n) - start
+    rs[first] = xs[first]
+    step = 2.0 * float(eps)
+    by_rank = np.argsort(rank, kind="stable")
+    bounds = np.searchsorted(rank[by_rank], np.arange(int(rank.max()) + 2 if n else 1))
+    for k in range(1, len(bounds) - 1):
+        sel = by_rank[bounds[k]:bounds[k + 1]]
+        p = rs[sel - 1].astype(np.float64)
+        v = (p + step * np.round((xs[sel].astype(np.float64) - p) / step)).astype(np.float32)
+        rs[sel] = _fix_bound(v, xs[sel], eps)
+    out = np.empty_like(x)
+    out[order] = rs
+    assert np.all(np.abs(out.astype(np.float64) - x.astype(np.float64)) <= eps)
+    return np.ascontiguousarray(out)
+
+
+def with_base(w: "Workload", base: str, cell_particles: int = 64) -> "Workload":
+    """The same workload with the reconstruction of another base-compressor stand-in:
+    "quant" (the global quantizer) or "morton" (cubic cells holding ``cell_particles``
+    particles on average)."""
+    if base == "quant":
+        return w
+    if base != "morton":
+        raise ValueError(f"unknown base compressor {base!r}")
+    vol = float(np.prod(np.asarray(w.box_hi, np.float64) - np.asarray(w.box_lo, np.float64)))
+    cell = (vol * cell_particles / max(1, w.n)) ** (1.0 / 3.0)
+    recon = morton_recon(w.orig, w.xi, cell, w.box_lo, w.box_hi)
+    return dataclasses.replace(w, recon=recon, name=w.name + "_morton")
 
 
 def _wrap_unit(x: np.ndarray) -> np.ndarray:

@@ -11,7 +11,10 @@ can compute one by one or as a property that holds at any size:
   whose link state changed (must be none; for VP, A = V holds every pair that could flip,
   so the link set itself is unchanged) and decodes the edit stream itself (must equal the
   GPU decoder bit for bit); every decoded coordinate stays within xi of the original, and
-  the friends-of-friends labels of the decoded data equal those of the original.
+  the friends-of-friends labels of the decoded data equal those of the original;
+* the lossless container of each stream equals the oracle's byte for byte;
+* the box reconstructed by the Morton-order baseline instead of the quantizer converges
+  in HF mode with the same guarantees.
 """
 import numpy as np
 import pytest
@@ -75,7 +78,35 @@ def test_full_size_correction_keeps_every_active_link_state(cuda, box, mode):
     assert np.abs(dec_h.astype(np.float64) - w.orig).max() <= w.xi
     # the oracle's own decoder gives the same coordinates
     assert np.array_equal(oracle.decode(w.recon, stream.cpu().numpy().tobytes()), dec_h)
+    # the lossless container equals the oracle's and decodes to the stream
+    from oracle import huffman
+    blob = pc.huff_encode(stream)
+    assert bytes(blob.cpu().numpy()) == huffman.encode(stream.cpu().numpy().tobytes())
+    assert torch.equal(pc.huff_decode(blob), stream)
     # every active pair keeps its original link state after decoding
+    assert oracle.count_flips(dec_h, ai, aj, al, **kw) == 0
+    l0, n0 = pc.fof_labels(o, kw)
+    l1, n1 = pc.fof_labels(dec, kw)
+    assert n0 == n1 and torch.equal(l0, l1)
+
+
+def test_full_size_morton_baseline_halo_forest(cuda, box):
+    """The same box reconstructed by the Morton-order baseline (Sec. 4.1): HF correction
+    converges, keeps every active link state and gives the original labels."""
+    import torch
+    import paper_2604_18801_gb300 as pc
+    w = synth.with_base(box, "morton")
+    kw = w.params(mode=2)
+    o = torch.from_numpy(w.orig).to(cuda)
+    r = torch.from_numpy(w.recon).to(cuda)
+    cons = pc.select_constraints(o, kw)
+    ai, aj, al = [x.cpu().numpy() for x in cons.pairs()]
+    corr, st, code = pc.correct(o, r, kw, constraints=cons)
+    cons.close()
+    assert code == 0 and st["converged"] == 1
+    dec = pc.apply_edits(r, pc.huff_decode(pc.huff_encode(pc.encode_edits(r, corr, kw))))
+    dec_h = dec.cpu().numpy()
+    assert np.abs(dec_h.astype(np.float64) - w.orig).max() <= w.xi
     assert oracle.count_flips(dec_h, ai, aj, al, **kw) == 0
     l0, n0 = pc.fof_labels(o, kw)
     l1, n1 = pc.fof_labels(dec, kw)
