@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--cpu-side", type=float, default=0.25, help="side of the sub-cube the CPU baseline corrects")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve", "capped"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve", "capped", "multi"])
     ap.add_argument("--t-max", type=int, default=100, help="capped: iteration cap (Sec. 4.2 uses 100)")
     ap.add_argument("--blocks", type=int, default=512, help="batch: number of blocks")
     ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
@@ -454,12 +454,84 @@ def run_capped(a):
     print(json.dumps(line), flush=True)
 
 
+def run_multi(a):
+    """Several linking lengths at once (Sec. 1 and Sec. 5: the union of the pairs each
+    length selects) on the 256^3 box: pc_correct_multi with b x {0.8, 1, 1.25} per mode,
+    timed with the edit stream; the labels at every length must equal the original's.
+    Beside it, the three single-length corrections one after another."""
+    import torch
+    import paper_2604_18801_gb300 as pc
+    from paper_2604_18801_gb300 import synth
+    dev = torch.device("cuda", 0)
+    w = synth.with_base(synth.hacc_box(eps_over_b=a.eps, mode="VP", seed=a.seed, n=a.n), a.base)
+    o = torch.from_numpy(w.orig).to(dev)
+    r = torch.from_numpy(w.recon).to(dev)
+    modes = [m.strip() for m in a.modes.split(",") if m.strip()]
+    bl = [f * w.b for f in (0.8, 1.0, 1.25)]
+    cell_factor, _ = pc.autotune_cells(o, w.params(mode=MODES[modes[0]], b=bl[-1]))
+    base = w.params(cell_factor=cell_factor)
+    stream = torch.cuda.current_stream(dev)
+    per_mode, total_ms, single_ms, exact = {}, 0.0, 0.0, True
+    for m in modes:
+        prm = dict(base, mode=MODES[m])
+
+        def timed(fn):
+            for _ in range(max(1, a.warmup)):
+                res = fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(a.steps):
+                res = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / a.steps, res
+
+        def multi():
+            corr, st, code = pc.correct_multi(o, r, prm, bl)
+            return corr, st, code, pc.encode_edits(r, corr, prm)
+
+        def singles():
+            out = []
+            for b in bl:
+                corr, st, code = pc.correct(o, r, dict(prm, b=b))
+                out.append(pc.encode_edits(r, corr, dict(prm, b=b)))
+            return out
+
+        ms, (corr, st, code, s_) = timed(multi)
+        ms1, _ = timed(singles)
+        total_ms += ms
+        single_ms += ms1
+        dec = pc.apply_edits(r, s_)
+        ok = code == 0 and bool((dec.double() - o.double()).abs().max().item() <= w.xi)
+        for b in bl:
+            kb = dict(prm, b=b)
+            ok &= bool(torch.equal(pc.fof_labels(o, kb)[0], pc.fof_labels(dec, kb)[0]))
+        exact &= ok
+        per_mode[m] = {"ms": round(ms, 2), "iters": st["iters"], "n_active": st["n_active"],
+                       "n_editable": st["n_editable"], "viol0": st["viol0"], "membership_exact_all_b": ok,
+                       "stream_bytes": int(s_.numel()), "three_single_length_runs_ms": round(ms1, 2)}
+    line = {"metric": "multi-threshold corrected Mparticles/s (3 linking lengths, exact membership at each)",
+            "value": round(w.n * len(modes) / (total_ms / 1e3) / 1e6, 3), "unit": "Mparticles/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": max(1, a.warmup), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 data, double-float PGD", "data": "synthetic",
+            "config": {"workload": f"hacc{w.n}_eps{a.eps:g}b_{'+'.join(modes)}_b0.8-1-1.25"
+                                   + ("" if a.base == "quant" else "_" + a.base),
+                       "n_particles": w.n, "b_list": bl, "cell_factor": cell_factor, "base": a.base},
+            "membership_exact": exact,
+            "single_length_runs_value": round(w.n * len(modes) / (single_ms / 1e3) / 1e6, 3),
+            "per_mode": per_mode}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.workload == "batch":
         return run_batch(a)
     if a.workload == "capped":
         return run_capped(a)
+    if a.workload == "multi":
+        return run_multi(a)
     if a.workload == "serve":
         return run_serve(a)
     rank = int(os.environ.get("RANK", "0"))

@@ -222,6 +222,21 @@ pc_status pc_cluster_metrics(pc_ctx *ctx, const int32_t *lab0_dev, const int32_t
                              int32_t min_members, int32_t n_bins, double volume, pc_cluster_metrics_t *out,
                              double *hmf0, double *hmf1, double *bin_edges, void *stream);
 
+/* Several linking lengths at once (Sec. 1 and Sec. 5: a range of thresholds is
+ * supported by enforcing the union of the pairs each threshold selects).  b_list holds
+ * n_b linking lengths (1 <= n_b <= 4), finite, positive and strictly ascending;
+ * params->b is ignored, every other field applies to each length (mode, xi, box, m,
+ * Adam, stop rule).  For each length the active pairs are selected as by
+ * pc_select_constraints; a pair active at several lengths is enforced once at each, with
+ * the link flag and the thresholds b -/+ delta_t of Eq. 3 of that length.  After
+ * convergence the friends-of-friends labels at every length are those of orig.
+ * stats: n_vulnerable and n_active are summed over the lengths; the other fields are as
+ * for pc_correct.  n_b = 1 is pc_correct with b = b_list[0].  At most 2^29 editable
+ * particles with n_b > 1 (PC_EINVAL otherwise).  Synchronises the stream. */
+pc_status pc_correct_multi(pc_ctx *ctx, const float *orig_dev, const float *recon_dev, int64_t n,
+                           const pc_params *params, const double *b_list, int32_t n_b, float *corrected_dev,
+                           pc_correct_stats *stats, void *stream);
+
 /* Edit stream v1 (Algorithm 1 last lines; Sec. 3.3).  Little endian:
  *   0  "PCE1" | 4 u32 version=1 | 8 u64 n | 16 u32 m | 20 u32 mode | 24 u32 periodic | 28 u32 0
  *   32 f64 xi | 40 u64 flagged | 48 u64 flag_bytes=ceil(n/8) | 56 u64 code_bytes

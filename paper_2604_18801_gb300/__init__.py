@@ -21,6 +21,7 @@ from . import _native
 from ._native import PcError, make_params, struct_dict
 
 __all__ = ["Context", "fof_labels", "select_constraints", "Constraints", "correct", "correct_detail", "correct_batch",
+           "correct_multi",
            "encode_edits", "apply_edits", "huff_encode", "huff_decode", "Server", "autotune_cells", "cluster_metrics", "PcError", "make_params",
            "default_context"]
 
@@ -145,6 +146,26 @@ def correct(orig: torch.Tensor, recon: torch.Tensor, params, constraints: Constr
                                     constraints.h if constraints is not None else None, out.data_ptr(),
                                     C.byref(st), _stream(orig.device))
     _native.check(code, "pc_correct", allow_warn=True)
+    return out, struct_dict(st), code
+
+
+def correct_multi(orig: torch.Tensor, recon: torch.Tensor, params, b_list, out: torch.Tensor = None,
+                  ctx: Context = None):
+    """Correction for several linking lengths at once (the union of their active sets):
+    returns (corrected (N,3) float32 CUDA tensor, stats dict, status code).  params' b is
+    ignored; b_list holds 1 to 4 ascending lengths."""
+    _xyz(orig, "orig")
+    _xyz(recon, "recon")
+    if recon.shape != orig.shape:
+        raise ValueError("orig and recon differ in shape")
+    ctx = ctx or default_context(orig.device.index)
+    p = _params(params)
+    bl = (C.c_double * len(b_list))(*[float(b) for b in b_list])
+    out = torch.empty_like(orig) if out is None else _xyz(out, "out")
+    st = _native.CorrectStats()
+    code = _native.lib().pc_correct_multi(ctx.h, orig.data_ptr(), recon.data_ptr(), orig.shape[0], C.byref(p), bl,
+                                          len(b_list), out.data_ptr(), C.byref(st), _stream(orig.device))
+    _native.check(code, "pc_correct_multi", allow_warn=True)
     return out, struct_dict(st), code
 
 

@@ -101,6 +101,8 @@ def lib():
         L.pc_constraints_free.restype = None
         L.pc_correct.argtypes = [vp, vp, vp, i64, P, vp, vp, C.POINTER(CorrectStats), vp]
         L.pc_correct_detail.argtypes = [vp, vp, vp, i64, P, vp, vp, vp, vp, vp, C.POINTER(CorrectStats), vp]
+        L.pc_correct_multi.argtypes = [vp, vp, vp, i64, P, C.POINTER(C.c_double), C.c_int32, vp,
+                                       C.POINTER(CorrectStats), vp]
         L.pc_correct_batch.argtypes = [vp, vp, vp, C.POINTER(Block), C.c_int32, vp, C.POINTER(CorrectStats), vp]
         L.pc_encode_edits.argtypes = [vp, vp, vp, i64, P, vp, sz, C.POINTER(sz), vp]
         L.pc_apply_edits.argtypes = [vp, vp, i64, vp, sz, vp, vp]
@@ -117,7 +119,7 @@ def lib():
         L.pc_serve_wait.argtypes = [vp, C.c_uint64, i64, C.POINTER(JobResult)]
         L.pc_serve_counters.argtypes = [vp, C.POINTER(i64)]
         for f in ("pc_ctx_create", "pc_fof_labels", "pc_select_constraints", "pc_constraints_copy", "pc_correct",
-                  "pc_correct_detail", "pc_correct_batch", "pc_autotune_cells", "pc_cluster_metrics",
+                  "pc_correct_detail", "pc_correct_batch", "pc_correct_multi", "pc_autotune_cells", "pc_cluster_metrics",
                   "pc_server_create", "pc_serve_submit",
                   "pc_serve_poll",
                   "pc_serve_wait", "pc_serve_counters",

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 
@@ -572,6 +573,97 @@ pc_status pc_correct_detail(pc_ctx *ctx, const float *orig, const float *recon, 
         bool conv = false;
         correct_blocks(ctx, orig, recon, std::move(S), given, corrected, delta_dev, hist_loss, hist_viol, stats, conv,
                        (cudaStream_t)stream);
+        return conv ? PC_OK : PC_WARN_NOT_CONVERGED;
+    });
+}
+
+pc_status pc_correct_multi(pc_ctx *ctx, const float *orig, const float *recon, int64_t n, const pc_params *p,
+                           const double *b_list, int32_t n_b, float *corrected, pc_correct_stats *stats,
+                           void *stream) {
+    return guarded([&]() -> pc_status {
+        use_device(ctx);
+        if (!p || !b_list) fail(PC_EINVAL, "NULL argument");
+        if (n_b < 1 || n_b > 4) fail(PC_EINVAL, "n_b must be in [1, 4]");
+        for (int k = 0; k < n_b; ++k)
+            if (!(std::isfinite(b_list[k]) && b_list[k] > 0.0) || (k > 0 && !(b_list[k] > b_list[k - 1])))
+                fail(PC_EINVAL, "linking lengths must be finite, positive and strictly ascending");
+        std::vector<pc_params> prm(n_b, *p);
+        for (int k = 0; k < n_b; ++k) {
+            prm[k].b = b_list[k];
+            check_params(&prm[k], n, true);
+        }
+        if (!orig || !recon || !corrected) fail(PC_EINVAL, "NULL buffer");
+        const cudaStream_t s = (cudaStream_t)stream;
+        bool conv = false;
+        if (n_b == 1) {
+            BlockSet S;
+            single_block(S, n, &prm[0]);
+            correct_blocks(ctx, orig, recon, std::move(S), nullptr, corrected, nullptr, nullptr, nullptr, stats, conv,
+                           s);
+            return conv ? PC_OK : PC_WARN_NOT_CONVERGED;
+        }
+        // validation against the reconstruction (bound, finiteness, box; the largest M)
+        BlockSet V;
+        single_block(V, n, &prm[n_b - 1]);
+        inspect_blocks(orig, recon, V, s, ctx->hs);
+        check_block_inputs(V);
+        ThrSet ts;
+        for (int k = 0; k < n_b; ++k) {
+            ts.c.push_back(make_consts(&prm[k], V.ins[0], n, true));
+            if (!(ts.c[k].xi_box_d > 0.0))
+                fail(PC_EINVAL, "xi too small for float32 coordinates of this magnitude (empty projection box)");
+        }
+        // the selection of every linking length; the binning of the largest is the base
+        std::vector<std::unique_ptr<pc_constraints>> sel(n_b);
+        int64_t total = 0, n_vul = 0;
+        double ms_sel = 0.0;
+        for (int k = 0; k < n_b; ++k) {
+            sel[k].reset(new pc_constraints());
+            single_block(sel[k]->S, n, &prm[k]);
+            do_select(ctx, orig, s, sel[k].get());
+            total += sel[k]->nA;
+            n_vul += sel[k]->stats[0].n_vulnerable;
+            ms_sel += sel[k]->stats[0].ms;
+        }
+        if (total >= ((int64_t)1 << 31)) fail(PC_EINVAL, "several linking lengths: too many active pairs");
+        const pc_constraints &base = *sel[n_b - 1];
+        // the union: a pair active at two lengths is enforced twice, once at each
+        DBuf<unsigned long long> U(std::max<int64_t>(1, total), s);
+        DBuf<uint8_t> T(std::max<int64_t>(1, total), s);
+        {
+            DBuf<uint32_t> inv(n, s);
+            inverse_order(base.B, inv.p, s);
+            int64_t at = 0;
+            for (int k = 0; k < n_b; ++k) {
+                remap_pairs(sel[k]->A.p, sel[k]->nA, sel[k]->B.order.p, inv.p, (uint8_t)k, U.p + at, T.p + at, s);
+                at += sel[k]->nA;
+            }
+        }
+        for (int k = 0; k + 1 < n_b; ++k) sel[k].reset();   // freed in stream order
+        ts.Athr = T.p;
+        const std::vector<Consts> cp{ts.c[n_b - 1]};
+        PgdRun r = run_pgd(base.B, base.S, cp, orig, recon, U.p, total, corrected, s, ctx->hs, nullptr, nullptr,
+                           nullptr, PGD_GRAPH_LAUNCHES, &ts);
+        const PgdResult &pr = r.blocks[0];
+        conv = pr.converged;
+        if (stats) {
+            pc_correct_stats &st = *stats;
+            memset(&st, 0, sizeof(st));
+            st.iters = pr.iters;
+            st.loss_evals = pr.loss_evals;
+            st.viol0 = pr.viol0;
+            st.viol_final = pr.viol_final;
+            st.loss0 = pr.loss0;
+            st.loss_final = pr.loss_final;
+            st.n_vulnerable = n_vul;
+            st.n_active = total;
+            st.n_editable = pr.n_editable;
+            st.converged = pr.converged ? 1 : 0;
+            st.ms_setup = ms_sel + r.ms_csr;
+            st.ms_pgd = r.ms;
+            st.ms_pgd_iter = r.ms_iter;
+            st.pgd_launches = r.launches;
+        }
         return conv ? PC_OK : PC_WARN_NOT_CONVERGED;
     });
 }

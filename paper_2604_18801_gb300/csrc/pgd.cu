@@ -4,7 +4,8 @@
 // Layout.  The editable set E = endpoints(A) is numbered in cell order (dense
 // index e), so neighbouring particles sit close in memory.  A is stored as a
 // CSR by endpoint: row e lists every active partner k of e (col = k | link
-// bit << 31), rows sorted by the partner's position.  State per editable
+// bit << 31; with several linking lengths, k | threshold index << 29 | link << 31),
+// rows sorted by the partner's position.  State per editable
 // particle, float4 each (w unused): original position PE (w = id bits); the
 // offset delta = P_hat - P as a double-float (hi, lo) and its float32 rounding
 // Q = fl(P + delta), both in two ping-pong buffers; the Adam moments m, v as
@@ -43,15 +44,21 @@ constexpr int PGD_THREADS = 256;
 constexpr int WARPS = PGD_THREADS / 32;
 constexpr int PGD_BLOCKS_PER_SM = 4;   // resident CTAs of the persistent iteration grid
 
-// Per-block PGD constants (one entry per block of the problem set).
+// Linking lengths of one problem: one, or up to MAX_THR enforced together (the union of
+// their active pairs, Sec. 1 and Sec. 5); a CSR entry then carries its pair's index.
+constexpr int MAX_THR = 4;
+
+// Per-block PGD constants (one entry per block of the problem set).  The threshold arrays
+// are indexed by the pair's linking length (entry 0 alone with one).
 struct PgdConsts {
     int periodic;
     float L[3];
     float b2;
-    float screen_link;   // link pair certainly satisfied when float32 d2 < screen_link
-    float screen_non;    // non-link pair certainly satisfied when float32 d2 > screen_non
-    float tau;           // coincidence radius b * 2^-30 for the gradient direction
-    df thr_link, thr_non, xi_box, alpha, eps_adam;
+    float screen_link[MAX_THR];   // link pair certainly satisfied when float32 d2 < screen_link
+    float screen_non[MAX_THR];    // non-link pair certainly satisfied when float32 d2 > screen_non
+    float tau[MAX_THR];           // coincidence radius b * 2^-30 for the gradient direction
+    df thr_link[MAX_THR], thr_non[MAX_THR];   // b -/+ delta_t of Eq. 3
+    df xi_box, alpha, eps_adam;
     df beta1, one_m_beta1, beta2, one_m_beta2;
     int t_max;
     int replay;
@@ -174,13 +181,16 @@ __global__ void k_epos(const uint32_t *__restrict__ mark, const uint32_t *__rest
     }
 }
 
-__global__ void k_dir_keys(const unsigned long long *__restrict__ A, int64_t m, const uint32_t *__restrict__ dense,
-                           int nb, unsigned long long *__restrict__ keys) {
+// Directed keys (row << nb | partner position) << tb | threshold index (tb = 0: one
+// linking length; tb = 2: Athr gives each pair's index).
+__global__ void k_dir_keys(const unsigned long long *__restrict__ A, const uint8_t *__restrict__ Athr, int64_t m,
+                           const uint32_t *__restrict__ dense, int nb, int tb, unsigned long long *__restrict__ keys) {
     GRID_STRIDE(r, m) {
         const unsigned long long pk = A[r];
         const uint32_t ki = (uint32_t)(pk >> 32), kj = (uint32_t)(pk & 0xffffffffull);
-        keys[2 * r] = ((unsigned long long)dense[ki] << nb) | kj;
-        keys[2 * r + 1] = ((unsigned long long)dense[kj] << nb) | ki;
+        const unsigned long long t = tb ? (unsigned long long)Athr[r] : 0ull;
+        keys[2 * r] = ((((unsigned long long)dense[ki] << nb) | kj) << tb) | t;
+        keys[2 * r + 1] = ((((unsigned long long)dense[kj] << nb) | ki) << tb) | t;
     }
 }
 
@@ -188,7 +198,7 @@ __global__ void k_row_bounds(const unsigned long long *__restrict__ keys, int64_
                              uint32_t *__restrict__ row_ptr) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= m; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t prev = t == 0 ? -1 : (int64_t)(keys[t - 1] >> nb);
-        const int64_t cur = t == m ? nrows : (int64_t)(keys[t] >> nb);
+        const int64_t cur = t == m ? nrows : (int64_t)(keys[t] >> nb);   // nb: all bits below the row
         for (int64_t r = prev + 1; r <= cur; ++r) row_ptr[r] = (uint32_t)t;
     }
 }
@@ -198,20 +208,28 @@ __device__ __forceinline__ float3 canon_dp(const float4 p, const float4 q, int p
     return make_float3(cdiff(p.x, q.x, per, L[0]), cdiff(p.y, q.y, per, L[1]), cdiff(p.z, q.z, per, L[2]));
 }
 
-__global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, int nb,
+// Squared linking lengths of the thresholds of a multi-threshold problem (float32).
+struct ThrB2 {
+    float b2[MAX_THR];
+};
+
+__global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, int nb, int tb, ThrB2 tb2,
                        const uint32_t *__restrict__ dense, const uint32_t *__restrict__ epos,
                        const float4 *__restrict__ P4, const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
                        int nblk, uint32_t *__restrict__ col) {
     const unsigned long long mask = (1ull << nb) - 1ull;
     GRID_STRIDE(t, m) {
         const unsigned long long k = keys[t];
-        const uint32_t row = (uint32_t)(k >> nb), nbp = (uint32_t)(k & mask);
+        const uint32_t ti = (uint32_t)(k & ((1ull << tb) - 1ull));
+        const uint32_t row = (uint32_t)(k >> (nb + tb)), nbp = (uint32_t)((k >> tb) & mask);
         const uint32_t pos = epos[row];
         const BlockDev &B = bt[find_block(off, nblk, pos)];
         const float4 p = P4[pos], q = P4[nbp];
         const float3 d = canon_dp(p, q, B.periodic, B.L);
-        const bool link = cdist2(d.x, d.y, d.z) <= B.b2;
-        col[t] = dense[nbp] | (link ? 0x80000000u : 0u);
+        // the link flag at the pair's own linking length
+        const float b2 = tb ? (ti == 0 ? tb2.b2[0] : ti == 1 ? tb2.b2[1] : ti == 2 ? tb2.b2[2] : tb2.b2[3]) : B.b2;
+        const bool link = cdist2(d.x, d.y, d.z) <= b2;
+        col[t] = dense[nbp] | (ti << 29) | (link ? 0x80000000u : 0u);
     }
 }
 
@@ -291,7 +309,7 @@ __device__ __forceinline__ df exact_r(float dp, float eh, float el, float kh, fl
 // Violated amount of Eq. 3 for one active pair (row e, partner k) at the current
 // offsets, in double-float, and the gradient term d/d(delta_e) of max(0, v)^2.
 __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, const float4 del, int64_t e, uint32_t k,
-                                          bool link, const float4 *__restrict__ PE, const float4 *Dh,
+                                          bool link, int ti, const float4 *__restrict__ PE, const float4 *Dh,
                                           const float4 *Dl, const PgdConsts &C, df g[3], double &lt) {
     const float4 pk = __ldg(PE + k);
     const float4 dkh = Dh[k], dkl = Dl[k];
@@ -308,13 +326,13 @@ __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, con
     if (df_lt(q2, q1)) { const df x = q1; q1 = q2; q2 = x; }
     if (df_lt(q1, q0)) { const df x = q0; q0 = q1; q1 = x; }
     const df dh = df_sqrt(df_add(df_add(q0, q1), q2));
-    const df v = link ? df_sub(dh, C.thr_link) : df_sub(C.thr_non, dh);
+    const df v = link ? df_sub(dh, C.thr_link[ti]) : df_sub(C.thr_non[ti], dh);
     if (!df_gt0(v)) return false;
     const double vd = df_to_d(v);
     lt = (int64_t)k > e ? vd * vd * C.inv_loss_unit : 0.0;   // in loss units
     // 2 v r / |r| (link) or -2 v r / |r| (non-link); coincident points use the original separation
     const df s = link ? df_add(v, v) : df_neg(df_add(v, v));
-    if (dh.hi > C.tau) {
+    if (dh.hi > C.tau[ti]) {
         const df c = df_div(s, dh);
 #pragma unroll
         for (int a = 0; a < 3; ++a) g[a] = df_mul(c, r[a]);
@@ -567,7 +585,7 @@ struct HeavyPlan {
 // its row within the group, so a warp maps an edge to its row without a search.
 struct LightPlan {
     const uint32_t *ptr;             // per row: first light edge (heavy rows own none)
-    const uint32_t *col;             // partner | link << 31
+    const uint32_t *col;             // partner | link << 31 (| threshold index << 29 with several)
     const uint8_t *slot;             // row - first row of its 32-row group
 };
 
@@ -586,7 +604,7 @@ struct WarpTab {
     float4 st[7][32];                // the rows' state for Adam, fetched while the edges are walked
     int64_t row[32];                 // the warp's rows: dense index
     uint32_t qk[96];                 // queued pairs: partner
-    uint8_t qs[96];                  // queued pairs: row slot | link << 7
+    uint8_t qs[96];                  // queued pairs: row slot | threshold index << 5 | link << 7
     float4 q[32];                    // the rows' rounded current positions
     unsigned own[32];                // per row slot: this batch's violated entries of that row
     float gt[6][32];                 // this batch's gradient terms (x hi, x lo, y hi, ...) by entry
@@ -606,8 +624,10 @@ struct WarpTab {
 // a heavy warp writes its chunk partial and k_pgd_heavy adds the partials of a heavy
 // row in chunk order.  MULTI = false is the single-block specialisation; with MULTI the
 // items come from the table of blocks still iterating, so a block that has stopped
-// costs nothing in later launches, and the rows of one item share a block.
-template <bool MULTI>
+// costs nothing in later launches, and the rows of one item share a block.  MT: the
+// problem has several linking lengths and each CSR entry carries the index of its pair's
+// (single block only); the screen and the evaluation use that length's thresholds.
+template <bool MULTI, bool MT>
 __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
     const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE,
     int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP, const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk,
@@ -745,7 +765,8 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
         }
         __syncwarp();
         const PgdConsts &Cl = CB[b];            // the item's block
-        const float sl_link = Cl.screen_link, sl_non = Cl.screen_non;
+        const float sl_link = Cl.screen_link[0], sl_non = Cl.screen_non[0];
+        constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;   // partner bits of a CSR entry
         const int per_l = Cl.periodic;
         const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
 
@@ -760,12 +781,13 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
             bool hit = false;
             if (valid) {
                 const uint32_t k = T.qk[lane];
-                s = T.qs[lane] & 0x7f;
+                s = T.qs[lane] & 0x1f;
+                const int ti = MT ? (T.qs[lane] >> 5) & 3 : 0;
                 const bool link = (T.qs[lane] >> 7) != 0;
                 const int64_t er = T.row[s];
                 const float4 *Dh = Bf.dh(tb & 1), *Dl = Bf.dl(tb & 1);
                 double lt = 0.0;
-                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, PE, Dh, Dl, Cl, gt, lt);
+                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, ti, PE, Dh, Dl, Cl, gt, lt);
                 if (hit) {
                     lfx += (unsigned long long)llrint(lt);
                     viol += (int64_t)k > er ? 1ull : 0ull;
@@ -797,12 +819,12 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
             __syncwarp();
         };
 
-        auto enqueue = [&](bool need, uint32_t k, int s, bool link) {
+        auto enqueue = [&](bool need, uint32_t cv, int s) {
             const unsigned bal = __ballot_sync(FULL, need);
             if (need) {
                 const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-                T.qk[pos] = k;
-                T.qs[pos] = (uint8_t)(s | (link ? 0x80 : 0));
+                T.qk[pos] = cv & PMASK;
+                T.qs[pos] = (uint8_t)(s | (MT ? ((cv >> 29) & 3u) << 5 : 0u) | ((cv >> 31) ? 0x80 : 0));
             }
             qn += __popc(bal);
         };
@@ -811,11 +833,15 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
         auto screen = [&](bool ok, int s, uint32_t cv) -> bool {
             if (!ok) return false;
             const float4 qr = T.q[s];
-            const uint32_t k = cv & 0x7fffffffu;
+            const uint32_t k = cv & PMASK;
             const float4 qk = Qc[k];
             const bool pp = per_l != 0;
             const float d2 =
                 cdist2(cdiff(qr.x, qk.x, pp, L0), cdiff(qr.y, qk.y, pp, L1), cdiff(qr.z, qk.z, pp, L2));
+            if (MT) {
+                const int ti = (cv >> 29) & 3;
+                return (cv >> 31) ? !(d2 < Cl.screen_link[ti]) : !(d2 > Cl.screen_non[ti]);
+            }
             return (cv >> 31) ? !(d2 < sl_link) : !(d2 > sl_non);
         };
         const uint32_t *ecol = heavy_warp ? col : LP.col;
@@ -829,8 +855,8 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
             const int s1 = (ok1 && !heavy_warp) ? (int)LP.slot[t1] : 0;
             const bool n0 = screen(ok0, s0, c0v);
             const bool n1 = screen(ok1, s1, c1v);
-            enqueue(n0, c0v & 0x7fffffffu, s0, (c0v >> 31) != 0u);
-            enqueue(n1, c1v & 0x7fffffffu, s1, (c1v >> 31) != 0u);
+            enqueue(n0, c0v, s0);
+            enqueue(n1, c1v, s1);
             __syncwarp();
             while (qn >= 32) {
                 batch(32);
@@ -1037,11 +1063,18 @@ PgdConsts pgd_consts(const Consts &c, const pc_params *p) {
     // exact offset by at most one ulp of the coordinates plus one ulp of |r| per axis
     const double R = c.b + 2.0 * std::sqrt(3.0) * c.xi + 4.0 * c.xi;
     const double B4 = 2.0 * std::sqrt(3.0) * (ulp32(c.M + 2.0 * c.xi) + ulp32(R));
-    K.screen_link = thrL - B4 > 0 ? f32_down((thrL - B4) * (thrL - B4) * (1.0 - std::ldexp(1.0, -20))) : -1.0f;
-    K.screen_non = f32_up((thrN + B4) * (thrN + B4) * (1.0 + std::ldexp(1.0, -20)));
-    K.tau = (float)std::ldexp(c.b, -30);
-    K.thr_link = df_split(thrL);
-    K.thr_non = df_split(thrN);
+    K.screen_link[0] = thrL - B4 > 0 ? f32_down((thrL - B4) * (thrL - B4) * (1.0 - std::ldexp(1.0, -20))) : -1.0f;
+    K.screen_non[0] = f32_up((thrN + B4) * (thrN + B4) * (1.0 + std::ldexp(1.0, -20)));
+    K.tau[0] = (float)std::ldexp(c.b, -30);
+    K.thr_link[0] = df_split(thrL);
+    K.thr_non[0] = df_split(thrN);
+    for (int k = 1; k < MAX_THR; ++k) {
+        K.screen_link[k] = K.screen_link[0];
+        K.screen_non[k] = K.screen_non[0];
+        K.tau[k] = K.tau[0];
+        K.thr_link[k] = K.thr_link[0];
+        K.thr_non[k] = K.thr_non[0];
+    }
     K.xi_box = df_split(c.xi_box_d);
     K.alpha = df_split(p->alpha_rel * c.xi);
     K.eps_adam = df_split(p->eps_rel * c.xi);
@@ -1058,6 +1091,18 @@ PgdConsts pgd_consts(const Consts &c, const pc_params *p) {
     K.inv_loss_unit = 1.0 / K.loss_unit;
     K.stall_patience = p->stall_patience;
     return K;
+}
+
+// The thresholds of several linking lengths (constants of each, same xi, m and data).
+void pgd_thresholds(PgdConsts &K, const std::vector<Consts> &ck, const pc_params *p) {
+    for (size_t k = 0; k < ck.size(); ++k) {
+        const PgdConsts one = pgd_consts(ck[k], p);
+        K.screen_link[k] = one.screen_link[0];
+        K.screen_non[k] = one.screen_non[0];
+        K.tau[k] = one.tau[0];
+        K.thr_link[k] = one.thr_link[0];
+        K.thr_non[k] = one.thr_non[0];
+    }
 }
 
 }  // namespace
@@ -1095,13 +1140,18 @@ struct PgdSolver::Impl {
     int graph_k = 0;
     int kernels_per_iter = 1;
 
+    bool mt = false;                         // several linking lengths (single block)
+
     void launch_iter() {
-        if (nb == 1)
-            k_pgd_iter<false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p,
-                                                           gs.p, wt, hist_loss, hist_viol);
+        if (mt)
+            k_pgd_iter<false, true><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb,
+                                                                 blk.p, gs.p, wt, hist_loss, hist_viol);
+        else if (nb == 1)
+            k_pgd_iter<false, false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb,
+                                                                  blk.p, gs.p, wt, hist_loss, hist_viol);
         else
-            k_pgd_iter<true><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p,
-                                                          gs.p, wt, nullptr, nullptr);
+            k_pgd_iter<true, false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb,
+                                                                 blk.p, gs.p, wt, nullptr, nullptr);
         PC_CHECK_LAUNCH();
         if (n_heavy > 0) {
             k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, rb.p, Bf, CB.p,
@@ -1119,12 +1169,15 @@ struct PgdSolver::Impl {
 
 PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
                      const float *recon, const unsigned long long *A, int64_t nA, cudaStream_t s, HostScratch &hs,
-                     double *hist_loss, unsigned long long *hist_viol)
+                     double *hist_loss, unsigned long long *hist_viol, const ThrSet *thr)
     : im(new Impl()) {
     Impl &I = *im;
     I.s = s;
     const int nb = S.nb;
     I.nb = nb;
+    I.mt = thr && thr->c.size() > 1;
+    if (I.mt && (nb != 1 || thr->c.size() > (size_t)MAX_THR || !thr->Athr))
+        fail(PC_EINVAL, "several linking lengths: one block and at most 4 lengths");
     I.hist_loss = hist_loss;
     I.hist_viol = hist_viol;
     const int64_t n = B.n;
@@ -1137,6 +1190,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     for (int b = 0; b < nb; ++b) {
         const pc_params *p = &S.prm[b];
         hK[b] = pgd_consts(cp[b], p);
+        if (I.mt) pgd_thresholds(hK[b], thr->c, p);
         PgdBlk &k = hB[b];
         memset(&k, 0, sizeof(k));
         k.b1p = p->beta1;
@@ -1172,20 +1226,25 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     scan_exclusive_u32(mark.p, dense.p, n, tot.p, s);
     const int64_t ne = *(uint32_t *)read_back(hs, tot.p, sizeof(uint32_t), s);
     I.ne = ne;
+    if (I.mt && ne >= ((int64_t)1 << 29)) fail(PC_EINVAL, "several linking lengths: at most 2^29 editable particles");
+    const int tb = I.mt ? 2 : 0;   // threshold-index bits of the directed keys
+    ThrB2 tb2;
+    for (int k = 0; k < MAX_THR; ++k) tb2.b2[k] = I.mt && k < (int)thr->c.size() ? thr->c[k].b2 : 0.f;
     DBuf<uint32_t> epos(ne, s);
     k_epos<<<grid_for(n), 256, 0, s>>>(mark.p, dense.p, n, epos.p);
     PC_CHECK_LAUNCH();
     mark.release();
     const int64_t m = 2 * nA;
     DBuf<unsigned long long> keys(m, s);
-    k_dir_keys<<<grid_for(nA), 256, 0, s>>>(A, nA, dense.p, nbits, keys.p);
+    k_dir_keys<<<grid_for(nA), 256, 0, s>>>(A, I.mt ? thr->Athr : nullptr, nA, dense.p, nbits, tb, keys.p);
     PC_CHECK_LAUNCH();
-    radix_sort_u64((uint64_t *)keys.p, nullptr, m, nbits + std::max(1, ceil_log2((uint64_t)ne)), s);
+    radix_sort_u64((uint64_t *)keys.p, nullptr, m, nbits + tb + std::max(1, ceil_log2((uint64_t)ne)), s);
     I.row_ptr.alloc(ne + 1, s);
     I.col.alloc(m, s);
-    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbits, ne, I.row_ptr.p);
+    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbits + tb, ne, I.row_ptr.p);
     PC_CHECK_LAUNCH();
-    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbits, dense.p, epos.p, B.P4.p, S.dev.p, S.doff.p, nb, I.col.p);
+    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbits, tb, tb2, dense.p, epos.p, B.P4.p, S.dev.p, S.doff.p, nb,
+                                       I.col.p);
     PC_CHECK_LAUNCH();
     keys.release();
     dense.release();
@@ -1443,7 +1502,8 @@ void PgdSolver::block_result(int b, PgdResult &r) const {
 
 PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
                const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
-               HostScratch &hs, double *delta_out, double *hist_loss, unsigned long long *hist_viol, int graph_k) {
+               HostScratch &hs, double *delta_out, double *hist_loss, unsigned long long *hist_viol, int graph_k,
+               const ThrSet *thr) {
     PgdRun run;
     const int64_t n = B.n;
     cudaEvent_t ev[4];
@@ -1458,7 +1518,7 @@ PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp
     k_copy_recon<<<grid_for(3 * n), 256, 0, s>>>(recon, corrected, 3 * n);
     PC_CHECK_LAUNCH();
     if (delta_out) PC_CUDA(cudaMemsetAsync(delta_out, 0, 3 * n * sizeof(double), s));
-    PgdSolver sol(B, S, cp, orig, recon, A, nA, s, hs, hist_loss, hist_viol);
+    PgdSolver sol(B, S, cp, orig, recon, A, nA, s, hs, hist_loss, hist_viol, thr);
     PC_CUDA(cudaEventRecord(ev[1], s));
     if (sol.empty()) {
         // nothing to enforce anywhere: reconstructions stand, zero iterations

@@ -120,6 +120,14 @@ struct PgdRun {
     double ms_csr = 0;    // CSR and state build
     int64_t launches = 0;
 };
+// Several linking lengths enforced together in one single-block problem (the union of
+// the pairs each selects, Sec. 1 and Sec. 5): the index of each active pair's linking
+// length and the constants of every length (at most 4, ascending).
+struct ThrSet {
+    const uint8_t *Athr = nullptr;   // device, one entry per active pair
+    std::vector<Consts> c;
+};
+
 // Resumable PGD over every block of a set (Algorithm 1, the loop).  The constructor
 // builds E, the CSR of A and the iteration state on stream s (it synchronises s a few
 // times); launch() enqueues iteration launches, replaying a captured CUDA graph when
@@ -130,7 +138,7 @@ class PgdSolver {
   public:
     PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
               const float *recon, const unsigned long long *A, int64_t nA, cudaStream_t s, HostScratch &hs,
-              double *hist_loss = nullptr, unsigned long long *hist_viol = nullptr);
+              double *hist_loss = nullptr, unsigned long long *hist_viol = nullptr, const ThrSet *thr = nullptr);
     ~PgdSolver();
     PgdSolver(const PgdSolver &) = delete;
     PgdSolver &operator=(const PgdSolver &) = delete;
@@ -161,7 +169,7 @@ class PgdSolver {
 PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
                const float *recon, const unsigned long long *A, int64_t nA, float *corrected, cudaStream_t s,
                HostScratch &hs, double *delta_out = nullptr, double *hist_loss = nullptr,
-               unsigned long long *hist_viol = nullptr, int graph_k = 0);
+               unsigned long long *hist_viol = nullptr, int graph_k = 0, const ThrSet *thr = nullptr);
 
 // ---------------------------------------------------------------- selection (api.cu)
 int ctx_device(const pc_ctx *ctx);
@@ -194,6 +202,13 @@ void select_count(HostScratch &hs, const float *orig, cudaStream_t s, Selection 
 int64_t select_more_bytes(const Selection &h);
 // Emission pass, halo forest, per-block statistics; releases the count-pass temporaries.
 void select_emit(HostScratch &hs, cudaStream_t s, Selection &h);
+
+// Several linking lengths (select.cu): inv[order[p]] = p for a binning, and the pairs of
+// another binning's selection (positions, key min << 32 | max) as positions of the binning
+// whose inverse is inv, each with the linking-length index t.
+void inverse_order(const Binned &B, uint32_t *inv, cudaStream_t s);
+void remap_pairs(const unsigned long long *A, int64_t m, const uint32_t *order_k, const uint32_t *inv, uint8_t t,
+                 unsigned long long *out, uint8_t *tout, cudaStream_t s);
 
 // Edit stream (edits.cu)
 size_t encode_edits(const float *recon, const float *corr, int64_t n, const pc_params *p, uint8_t *out, size_t cap,

@@ -223,4 +223,40 @@ void export_pairs(const Binned &B, const BlockSet &S, const unsigned long long *
     PC_CUDA(cudaStreamSynchronize(s));
 }
 
+// ---------------------------------------------------------------- several linking lengths
+namespace {
+
+__global__ void k_inverse_order(const uint32_t *__restrict__ order, int64_t n, uint32_t *__restrict__ inv) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        inv[order[p]] = (uint32_t)p;
+}
+
+__global__ void k_remap_pairs(const unsigned long long *__restrict__ A, int64_t m, const uint32_t *__restrict__ order_k,
+                              const uint32_t *__restrict__ inv, uint8_t t, unsigned long long *__restrict__ out,
+                              uint8_t *__restrict__ tout) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long pk = A[r];
+        const uint32_t a = inv[order_k[pk >> 32]], b = inv[order_k[pk & 0xffffffffull]];
+        out[r] = ((unsigned long long)min(a, b) << 32) | max(a, b);
+        tout[r] = t;
+    }
+}
+
+int remap_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), (int64_t)num_sms() * 16)); }
+
+}  // namespace
+
+void inverse_order(const Binned &B, uint32_t *inv, cudaStream_t s) {
+    if (B.n <= 0) return;
+    k_inverse_order<<<remap_grid(B.n), 256, 0, s>>>(B.order.p, B.n, inv);
+    PC_CHECK_LAUNCH();
+}
+
+void remap_pairs(const unsigned long long *A, int64_t m, const uint32_t *order_k, const uint32_t *inv, uint8_t t,
+                 unsigned long long *out, uint8_t *tout, cudaStream_t s) {
+    if (m <= 0) return;
+    k_remap_pairs<<<remap_grid(m), 256, 0, s>>>(A, m, order_k, inv, t, out, tout);
+    PC_CHECK_LAUNCH();
+}
+
 }  // namespace pc

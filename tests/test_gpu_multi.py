@@ -1,0 +1,138 @@
+"""Several linking lengths at once (Sec. 1 and Sec. 5: the union of the pairs each length
+selects), through pc_correct_multi: the union's pair counts equal the oracle's exactly,
+replayed offsets match the oracle's per-pair-threshold PGD within 1e-6 xi where the case
+is well conditioned, and converged runs keep the friends-of-friends labels of every
+length."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_18801_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+FACTORS = (0.8, 1.0, 1.25)
+
+
+def dev(a, d):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(d)
+
+
+_W = {}
+
+
+def W_(name):
+    if name not in _W:
+        _W[name] = {
+            "cosmo4096": lambda: synth.tiny_cosmo(seed=1, n=4096),
+            "hacc32k": lambda: synth.hacc_box(eps_over_b=0.5, n=32 ** 3, seed=4),
+            "fluid20k": lambda: synth.fluid_box(n=20000, eps_over_b=0.5, seed=3),
+            "md300": lambda: synth.md_box(n_clusters=300, eps_over_b=0.3, seed=5),
+            "hacc32k_morton": lambda: synth.with_base(synth.hacc_box(eps_over_b=0.5, n=32 ** 3, seed=4), "morton"),
+            # narrower vulnerable windows (xi = 0.1 b, 0.2 b) for offset parity
+            "hacc32k_e01": lambda: synth.hacc_box(eps_over_b=0.1, n=32 ** 3, seed=4),
+            "hacc32k_e02": lambda: synth.hacc_box(eps_over_b=0.2, n=32 ** 3, seed=4),
+            "fluid20k_e01": lambda: synth.fluid_box(n=20000, eps_over_b=0.1, seed=3),
+            "md300_e01": lambda: synth.md_box(n_clusters=300, eps_over_b=0.1, seed=5),
+            "hacc32k_e01_morton": lambda: synth.with_base(synth.hacc_box(eps_over_b=0.1, n=32 ** 3, seed=4),
+                                                          "morton"),
+        }[name]()
+    return _W[name]
+
+
+def _check_coords(gpu, w, delta, editable):
+    g = gpu.astype(np.float64)
+    assert np.array_equal(gpu[~editable], w.recon[~editable])
+    exact = w.orig[editable].astype(np.float64) + delta[editable]
+    half_ulp = 0.5 * np.spacing(np.abs(gpu[editable])).astype(np.float64)
+    err = np.abs(g[editable] - exact) - half_ulp
+    assert err.max() <= TOL * w.xi, f"max excess {err.max() / w.xi:.3e} xi"
+
+
+# At xi = 0.5 b the windows of 0.8 b, b and 1.25 b overlap widely: a pair held as a link
+# of the larger length and a non-link of the smaller gets opposing terms, and the
+# replayed offsets there move by more than 1e-7 xi under a 1e-13 change of the step
+# (they are checked through their invariants below).  Offsets are compared on cases
+# that pass both conditioning tests.
+@pytest.mark.parametrize("name,mode,R", [("cosmo4096", 0, 10), ("cosmo4096", 2, 5), ("hacc32k_e01", 0, 5),
+                                         ("hacc32k_e01", 1, 5), ("hacc32k_e01", 2, 5), ("hacc32k_e02", 0, 3),
+                                         ("fluid20k_e01", 1, 10), ("md300_e01", 2, 10),
+                                         ("hacc32k_e01_morton", 0, 5), ("hacc32k_e01_morton", 2, 5)])
+def test_replayed_union_parity(cuda, name, mode, R):
+    import paper_2604_18801_gb300 as pc
+    w = W_(name)
+    bl = [f * w.b for f in FACTORS]
+    prm = w.params(mode=mode, replay_iters=R)
+    corr, st, _ = pc.correct_multi(dev(w.orig, cuda), dev(w.recon, cuda), prm, bl)
+    assert st["iters"] == R
+    ai, aj, al, ab = oracle.select_multi(w.orig, bl, **prm)
+    assert st["n_active"] == len(ai)
+    _, delta, ed, ost = oracle.pgd_multi(w.orig, w.recon, ai, aj, al, ab, **prm)
+    assert st["viol0"] == ost["viol0"] and st["n_editable"] == ost["n_editable"]
+    # well conditioned at the GPU's precision: reversed pair order, and a 1e-13 change of the step
+    _, d_rev, _, _ = oracle.pgd_multi(w.orig, w.recon, ai[::-1], aj[::-1], al[::-1], ab[::-1], **prm)
+    _, d_eps, _, _ = oracle.pgd_multi(w.orig, w.recon, ai, aj, al, ab, **dict(prm, alpha_rel=0.2 * (1 + 1e-13)))
+    assert max(np.abs(delta - d_rev).max(), np.abs(delta - d_eps).max()) <= 1e-7 * w.xi
+    _check_coords(corr.cpu().numpy(), w, delta, ed)
+
+
+@pytest.mark.parametrize("name,mode", [("cosmo4096", 0), ("cosmo4096", 2), ("hacc32k", 0), ("hacc32k", 1),
+                                       ("hacc32k", 2), ("md300", 2), ("fluid20k", 1), ("hacc32k_morton", 2),
+                                       ("hacc32k_e01", 0), ("md300_e01", 2)])
+def test_converged_union_keeps_every_length(cuda, name, mode):
+    import paper_2604_18801_gb300 as pc
+    w = W_(name)
+    bl = [f * w.b for f in FACTORS]
+    prm = w.params(mode=mode)
+    o, r = dev(w.orig, cuda), dev(w.recon, cuda)
+    corr, st, code = pc.correct_multi(o, r, prm, bl)
+    assert code == 0 and st["converged"] == 1 and st["viol_final"] == 0
+    dec = pc.apply_edits(r, pc.huff_decode(pc.huff_encode(pc.encode_edits(r, corr, prm))))
+    d = dec.cpu().numpy()
+    assert np.abs(d.astype(np.float64) - w.orig).max() <= w.xi
+    ai, aj, al, ab = oracle.select_multi(w.orig, bl, **prm)
+    for b in bl:
+        kb = dict(prm, b=b)
+        l0, n0 = pc.fof_labels(o, kb)
+        l1, n1 = pc.fof_labels(dec, kb)
+        assert n0 == n1 and bool((l0 == l1).all()), f"labels at b = {b}"
+        m = ab == b
+        assert oracle.count_flips(d, ai[m], aj[m], al[m], **kb) == 0
+
+
+def test_overlapping_windows(cuda):
+    # lengths closer than the vulnerable window: some pairs are enforced at both
+    import paper_2604_18801_gb300 as pc
+    w = W_("cosmo4096")
+    bl = [w.b, 1.02 * w.b]
+    prm = w.params(mode=0)
+    o, r = dev(w.orig, cuda), dev(w.recon, cuda)
+    corr, st, code = pc.correct_multi(o, r, prm, bl)
+    assert code == 0
+    ai, aj, al, ab = oracle.select_multi(w.orig, bl, **prm)
+    assert st["n_active"] == len(ai)
+    for b in bl:
+        kb = dict(prm, b=b)
+        assert bool((pc.fof_labels(o, kb)[0] == pc.fof_labels(corr, kb)[0]).all())
+
+
+def test_one_length_is_the_plain_correction(cuda):
+    import paper_2604_18801_gb300 as pc
+    w = W_("hacc32k")
+    prm = w.params(mode=2)
+    o, r = dev(w.orig, cuda), dev(w.recon, cuda)
+    c1, s1, _ = pc.correct(o, r, prm)
+    c2, s2, _ = pc.correct_multi(o, r, prm, [w.b])
+    assert bool((c1 == c2).all()) and s1["iters"] == s2["iters"]
+
+
+def test_arguments_are_checked(cuda):
+    import paper_2604_18801_gb300 as pc
+    w = W_("cosmo4096")
+    o, r = dev(w.orig, cuda), dev(w.recon, cuda)
+    for bl in ([w.b, 0.5 * w.b], [w.b, w.b], [], [w.b] * 5, [-w.b, w.b], [w.b, float("nan")]):
+        with pytest.raises(pc.PcError) as e:
+            pc.correct_multi(o, r, w.params(), bl)
+        assert e.value.code == -1
