@@ -69,15 +69,17 @@ typedef struct {
     double alpha_rel;      /* Adam step size in units of xi: alpha = alpha_rel * xi         */
     double beta1, beta2;   /* Adam moments (0.9, 0.999)                                    */
     double eps_rel;        /* Adam epsilon in units of xi (1e-8)                           */
-    double loss_tol;       /* eps_L: stop when the tight loss <= loss_tol (default 0)     */
+    double loss_tol;       /* eps_L: stop when the tight loss <= loss_tol; 0 (default):
+                              stop when no active pair is violated by more than b 2^-40  */
     int32_t replay_iters;  /* >= 0: run exactly this many updates, ignore the loss (-1 off) */
     int32_t cell_cap_log2; /* tuning: at most 2^cell_cap_log2 grid cells (0: cell_factor)    */
     int32_t stall_patience;/* stall reset (not in the paper; 0 = off): after this many checks
                               without progress, the next check puts every editable endpoint
                               of a violated pair back at its original position with cleared
                               Adam moments.  Progress: the loss in units of xi^2 2^-24,
-                              summed per violated pair after rounding to an integer, is 0 or
-                              below best - floor(best / 1024).                            */
+                              summed per violated pair after rounding to an integer, is
+                              below best - floor(best / 1024), or not above best with fewer
+                              violated pairs than at best.                                */
     int32_t cell_factor;   /* tuning: at most cell_factor * n grid cells, within [2^16, 2^28]
                               (0 = 8); cells are never smaller than the pair reach.  Only
                               speed depends on it (pc_autotune_cells picks one).          */

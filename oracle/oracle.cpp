@@ -50,13 +50,21 @@
 //    positions P satisfy every constraint (Sec. 3.3, convergence analysis), so:
 //    the loss of each check is also measured in fixed point, as the sum over violated pairs of
 //    llrint(v^2 / (xi^2 2^-24)); a check makes progress when that value is
-//    zero or below best - floor(best / 1024), and its value then becomes best
-//    (best starts at check 0).  After stall_patience consecutive checks
+//    below best - floor(best / 1024), or not above best with fewer violated
+//    pairs than best_v (violations too small for the fixed-point unit still
+//    count), and its value and count then become best and best_v (both start
+//    at check 0).  After stall_patience consecutive checks
 //    without progress, the next check resets every editable particle that is
 //    an endpoint of a violated pair to its original position (delta = 0) and
 //    clears its Adam moments instead of taking its Adam step; the other
 //    particles take their step.  The check after a reset starts a new best.
 //    stall_patience = 0 turns this off.
+//  * Counting a violation.  A pair with violation v > 0 takes its loss term and
+//    gradient; it counts as violated (the count that stops the loop at eps_L = 0,
+//    and the stall rule's count) only when v > b * 2^-40.  Pairs held from both
+//    sides with an endpoint on the box can settle at v -> 0+, where whether v is
+//    above zero depends on the last bits of the arithmetic; b * 2^-40 is far below
+//    the b * 2^-20 slack of the margin dt, so the decoded guarantee is unchanged.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -397,12 +405,14 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             dp[3 * k + d] = (double)cdiff(orig[3 * A[k].i + d], orig[3 * A[k].j + d], p->periodic, c.L[d]);
     // Per pair: thresholds of Eq. 3 (b -/+ dt with the pair's b) and the coincidence radius.
     std::vector<double> thr_link(na, c.thr_link), thr_non(na, c.thr_non), tau(na, c.tau);
+    std::vector<double> vtol(na, std::ldexp(p->b, -40));   // smallest violation that counts
     if (ab)
         for (int64_t k = 0; k < na; ++k) {
             const double dt = 2.0 * std::sqrt(3.0) * (c.eps_q + c.u) + ab[k] * std::ldexp(1.0, -20);
             thr_link[k] = ab[k] - dt;
             thr_non[k] = ab[k] + dt;
             tau[k] = std::ldexp(ab[k], -30);
+            vtol[k] = std::ldexp(ab[k], -40);
         }
     // P_hat starts at the base reconstruction: delta0 = recon - orig (exact in float64).
     std::vector<double> delta(3 * ne), m(3 * ne, 0.0), v(3 * ne, 0.0), g(3 * ne);
@@ -427,7 +437,7 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             const double viol_amt = A[k].link ? dh - thr_link[k] : thr_non[k] - dh;
             if (!(viol_amt > 0.0)) continue;
             L += viol_amt * viol_amt;
-            nv += 1;
+            if (viol_amt > vtol[k]) nv += 1;
             fx += (int64_t)std::llrint(viol_amt * viol_amt * inv_unit);
             hit[a] = hit[b] = 1;
             if (!want_grad) continue;
@@ -458,6 +468,7 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
     double b1t = 1.0, b2t = 1.0;
     int64_t lfx = 0;          // fixed-point loss of the last check
     int64_t best = 0;         // lowest fixed-point loss that counted as progress
+    int64_t best_v = 0;       // violated pairs at that check
     int64_t since = 0;        // checks since then
     bool reset_now = false;   // this check resets the endpoints of violated pairs
     for (;;) {
@@ -470,7 +481,8 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             st->loss0 = L;
             st->viol0 = nv;
         }
-        if (!replay && L <= p->loss_tol) {
+        const bool conv_now = p->loss_tol > 0.0 ? (L <= p->loss_tol) : (nv == 0);
+        if (!replay && conv_now) {
             converged = true;
             break;
         }
@@ -497,18 +509,21 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
         if (reset_now) {
             reset_now = false;
             best = INT64_MAX;
+            best_v = INT64_MAX;
             since = 0;
         } else if (t == 1) {
             best = lfx;
-        } else if (lfx == 0 || lfx < best - best / 1024) {
+            best_v = nv;
+        } else if (lfx < best - best / 1024 || (lfx <= best && nv < best_v)) {
             best = lfx;
+            best_v = nv;
             since = 0;
         } else if (p->stall_patience > 0 && ++since >= p->stall_patience) {
             reset_now = true;
             since = 0;
         }
     }
-    if (p->replay_iters >= 0) converged = (L <= p->loss_tol);
+    if (p->replay_iters >= 0) converged = p->loss_tol > 0.0 ? (L <= p->loss_tol) : (nv == 0);
     st->iters = t;
     st->converged = converged ? 1 : 0;
     st->loss_final = L;

@@ -58,6 +58,7 @@ struct PgdConsts {
     float screen_non[MAX_THR];    // non-link pair certainly satisfied when float32 d2 > screen_non
     float tau[MAX_THR];           // coincidence radius b * 2^-30 for the gradient direction
     df thr_link[MAX_THR], thr_non[MAX_THR];   // b -/+ delta_t of Eq. 3
+    double vtol[MAX_THR];         // a violation counts (stop rule, stall rule) above b * 2^-40
     df xi_box, alpha, eps_adam;
     df beta1, one_m_beta1, beta2, one_m_beta2;
     int t_max;
@@ -86,6 +87,7 @@ struct PgdBlk {
     int32_t reset;      // this launch resets the endpoints of violated pairs (stall rule)
     int32_t upd_reset;  // the value of reset for the launch just finished (heavy rows)
     unsigned long long best;        // lowest fixed-point loss that counted as progress
+    unsigned long long best_v;      // violated pairs at that check
     int32_t since;                  // checks since then
     int32_t pad;
     unsigned long long lfx, vacc;   // launch accumulators: loss (fixed point), violations
@@ -310,7 +312,7 @@ __device__ __forceinline__ df exact_r(float dp, float eh, float el, float kh, fl
 // offsets, in double-float, and the gradient term d/d(delta_e) of max(0, v)^2.
 __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, const float4 del, int64_t e, uint32_t k,
                                           bool link, int ti, const float4 *__restrict__ PE, const float4 *Dh,
-                                          const float4 *Dl, const PgdConsts &C, df g[3], double &lt) {
+                                          const float4 *Dl, const PgdConsts &C, df g[3], double &lt, bool &counts) {
     const float4 pk = __ldg(PE + k);
     const float4 dkh = Dh[k], dkl = Dl[k];
     const float3 dp = canon_dp(pe, pk, C.periodic, C.L);
@@ -329,6 +331,7 @@ __device__ __forceinline__ bool eval_pair(const float4 pe, const float4 deh, con
     const df v = link ? df_sub(dh, C.thr_link[ti]) : df_sub(C.thr_non[ti], dh);
     if (!df_gt0(v)) return false;
     const double vd = df_to_d(v);
+    counts = vd > C.vtol[ti];
     lt = (int64_t)k > e ? vd * vd * C.inv_loss_unit : 0.0;   // in loss units
     // 2 v r / |r| (link) or -2 v r / |r| (non-link); coincident points use the original separation
     const df s = link ? df_add(v, v) : df_neg(df_add(v, v));
@@ -436,11 +439,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ------------------------------------------------------------------ stop decisions
 // The tight loss is accumulated in fixed point: each violated pair adds llrint(v^2 / unit)
 // with unit = xi^2 2^-24 (v <= 2 sqrt3 xi + delta_t, so a term is below 2^28 units and 2^35
-// terms fit in 63 bits), and the violated pairs are counted.  Integer sums do not depend
-// on the order in which warps finish, so the result is deterministic although work items
-// are handed out dynamically.  The block that finishes the launch last takes, for every
-// block still iterating, the stop decision of Algorithm 1 for its check t (at eps_L = 0
-// the count decides: the loss is zero exactly when no active pair is violated).
+// terms fit in 63 bits), and the violated pairs are counted: a pair counts when its
+// violation exceeds b * 2^-40 (pairs held from both sides with an endpoint on the box can
+// settle at v -> 0+, where the sign of v is decided by the last bits of the arithmetic;
+// the margin's b * 2^-20 slack is far larger).  Integer sums do not depend on the order
+// in which warps finish, so the result is deterministic although work items are handed
+// out dynamically.  The block that finishes the launch last takes, for every block still
+// iterating, the stop decision of Algorithm 1 for its check t (at eps_L = 0 the count
+// decides).
 __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs,
                               double *hist_loss, unsigned long long *hist_viol, const WorkTab *wt) {
     const int lane = threadIdx.x & 31;
@@ -489,17 +495,22 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
             y.lo = (float)(i2 - (double)y.hi);
             B.ibc1 = x;
             B.ibc2 = y;
-            // stall rule on the loss of check t: progress is a fixed-point loss of zero or
-            // below best - floor(best / 1024); stall_patience checks without progress make
-            // the next launch reset the endpoints of its violated pairs
+            // stall rule on the loss of check t: progress is a fixed-point loss below
+            // best - floor(best / 1024), or not above best with fewer violated pairs (a
+            // violation too small for the fixed-point unit still counts); stall_patience
+            // checks without progress make the next launch reset the endpoints of its
+            // violated pairs
             if (B.reset) {
                 B.reset = 0;
                 B.best = ~0ull;
+                B.best_v = ~0ull;
                 B.since = 0;
             } else if (t == 0) {
                 B.best = LF;
-            } else if (LF == 0 || LF < B.best - B.best / 1024) {
+                B.best_v = V;
+            } else if (LF < B.best - B.best / 1024 || (LF <= B.best && V < B.best_v)) {
                 B.best = LF;
+                B.best_v = V;
                 B.since = 0;
             } else if (C.stall_patience > 0 && ++B.since >= C.stall_patience) {
                 B.reset = 1;
@@ -787,10 +798,11 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
                 const int64_t er = T.row[s];
                 const float4 *Dh = Bf.dh(tb & 1), *Dl = Bf.dl(tb & 1);
                 double lt = 0.0;
-                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, ti, PE, Dh, Dl, Cl, gt, lt);
+                bool counts = false;
+                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, ti, PE, Dh, Dl, Cl, gt, lt, counts);
                 if (hit) {
                     lfx += (unsigned long long)llrint(lt);
-                    viol += (int64_t)k > er ? 1ull : 0ull;
+                    viol += ((int64_t)k > er && counts) ? 1ull : 0ull;
                 }
             }
             // Each row adds its violated pairs one by one in edge order (queue order is
@@ -1068,7 +1080,9 @@ PgdConsts pgd_consts(const Consts &c, const pc_params *p) {
     K.tau[0] = (float)std::ldexp(c.b, -30);
     K.thr_link[0] = df_split(thrL);
     K.thr_non[0] = df_split(thrN);
+    K.vtol[0] = std::ldexp(c.b, -40);
     for (int k = 1; k < MAX_THR; ++k) {
+        K.vtol[k] = K.vtol[0];
         K.screen_link[k] = K.screen_link[0];
         K.screen_non[k] = K.screen_non[0];
         K.tau[k] = K.tau[0];
@@ -1102,6 +1116,7 @@ void pgd_thresholds(PgdConsts &K, const std::vector<Consts> &ck, const pc_params
         K.tau[k] = one.tau[0];
         K.thr_link[k] = one.thr_link[0];
         K.thr_non[k] = one.thr_non[0];
+        K.vtol[k] = one.vtol[0];
     }
 }
 

@@ -211,7 +211,7 @@ def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps
     thr_l = torch.as_tensor(consts["thr_link"], dtype=torch.float64)
     thr_n = torch.as_tensor(consts["thr_non"], dtype=torch.float64)
     unit = xi * xi * 2.0 ** -24
-    best, since, reset_now, resets = None, 0, False, 0
+    best, best_v, since, reset_now, resets = None, None, 0, False, 0
     for _ in range(steps):
         opt.zero_grad()
         r = dp + delta[a] - delta[b]
@@ -239,10 +239,11 @@ def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps
                 st["exp_avg_sq"][hit] = 0.0
                 resets += int(hit.any())
             fx = int(np.rint((vv * vv * (1.0 / unit)).numpy()).sum())
+            nv = int((vv > 0).sum())
         if reset_now:
-            reset_now, best, since = False, None, 0
-        elif best is None or fx == 0 or fx < best - best // 1024:
-            best, since = fx, 0
+            reset_now, best, best_v, since = False, None, None, 0
+        elif best is None or fx < best - best // 1024 or (fx <= best and nv < best_v):
+            best, best_v, since = fx, nv, 0
         elif stall > 0:
             since += 1
             if since >= stall:
