@@ -74,12 +74,13 @@ typedef struct {
     int32_t replay_iters;  /* >= 0: run exactly this many updates, ignore the loss (-1 off) */
     int32_t cell_cap_log2; /* tuning: at most 2^cell_cap_log2 grid cells (0: cell_factor)    */
     int32_t stall_patience;/* stall reset (not in the paper; 0 = off): after this many checks
-                              without progress, the next check puts every editable endpoint
-                              of a violated pair back at its original position with cleared
+                              without progress (doubled after every reset), the next check
+                              puts every editable endpoint of a violated pair back at its
+                              original position (when the violated pairs' RMS violation
+                              exceeds xi / 1024) with cleared
                               Adam moments.  Progress: the loss in units of xi^2 2^-24,
                               summed per violated pair after rounding to an integer, is
-                              below best - floor(best / 1024), or not above best with fewer
-                              violated pairs than at best.                                */
+                              below best - floor(best / 1024) (best: the lowest so far).  */
     int32_t cell_factor;   /* tuning: at most cell_factor * n grid cells, within [2^16, 2^28]
                               (0 = 8); cells are never smaller than the pair reach.  Only
                               speed depends on it (pc_autotune_cells picks one).          */

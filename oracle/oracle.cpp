@@ -50,12 +50,15 @@
 //    positions P satisfy every constraint (Sec. 3.3, convergence analysis), so:
 //    the loss of each check is also measured in fixed point, as the sum over violated pairs of
 //    llrint(v^2 / (xi^2 2^-24)); a check makes progress when that value is
-//    below best - floor(best / 1024), or not above best with fewer violated
-//    pairs than best_v (violations too small for the fixed-point unit still
-//    count), and its value and count then become best and best_v (both start
-//    at check 0).  After stall_patience consecutive checks
-//    without progress, the next check resets every editable particle that is
-//    an endpoint of a violated pair to its original position (delta = 0) and
+//    below best - floor(best / 1024), and best is the lowest value since the
+//    last reset (it starts at check 0).  After `patience` consecutive checks
+//    without progress (stall_patience at first, doubled after every reset, so
+//    that a slow tail of tiny violations is disturbed less and less often), the
+//    next check resets every editable particle that is an endpoint of a
+//    violated pair to its original position (delta = 0), provided the RMS
+//    violation of the violated pairs exceeds xi / 1024 (the fixed-point loss is
+//    above 16 units per violated pair; a slow tail of tiny violations is left
+//    to Adam), and
 //    clears its Adam moments instead of taking its Adam step; the other
 //    particles take their step.  The check after a reset starts a new best.
 //    stall_patience = 0 turns this off.
@@ -468,8 +471,8 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
     double b1t = 1.0, b2t = 1.0;
     int64_t lfx = 0;          // fixed-point loss of the last check
     int64_t best = 0;         // lowest fixed-point loss that counted as progress
-    int64_t best_v = 0;       // violated pairs at that check
     int64_t since = 0;        // checks since then
+    int64_t patience = p->stall_patience;   // doubles after every reset
     bool reset_now = false;   // this check resets the endpoints of violated pairs
     for (;;) {
         const bool replay = p->replay_iters >= 0;
@@ -509,18 +512,16 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
         if (reset_now) {
             reset_now = false;
             best = INT64_MAX;
-            best_v = INT64_MAX;
             since = 0;
         } else if (t == 1) {
             best = lfx;
-            best_v = nv;
-        } else if (lfx < best - best / 1024 || (lfx <= best && nv < best_v)) {
+        } else if (lfx < best - best / 1024) {
             best = lfx;
-            best_v = nv;
             since = 0;
-        } else if (p->stall_patience > 0 && ++since >= p->stall_patience) {
+        } else if (p->stall_patience > 0 && ++since >= patience && lfx > 16 * nv) {
             reset_now = true;
             since = 0;
+            if (patience < (1 << 24)) patience *= 2;
         }
     }
     if (p->replay_iters >= 0) converged = p->loss_tol > 0.0 ? (L <= p->loss_tol) : (nv == 0);

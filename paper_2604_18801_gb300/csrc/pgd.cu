@@ -87,8 +87,8 @@ struct PgdBlk {
     int32_t reset;      // this launch resets the endpoints of violated pairs (stall rule)
     int32_t upd_reset;  // the value of reset for the launch just finished (heavy rows)
     unsigned long long best;        // lowest fixed-point loss that counted as progress
-    unsigned long long best_v;      // violated pairs at that check
     int32_t since;                  // checks since then
+    int32_t patience;               // checks without progress before the next reset (doubles per reset)
     int32_t pad;
     unsigned long long lfx, vacc;   // launch accumulators: loss (fixed point), violations
 };
@@ -496,25 +496,23 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
             B.ibc1 = x;
             B.ibc2 = y;
             // stall rule on the loss of check t: progress is a fixed-point loss below
-            // best - floor(best / 1024), or not above best with fewer violated pairs (a
-            // violation too small for the fixed-point unit still counts); stall_patience
-            // checks without progress make the next launch reset the endpoints of its
-            // violated pairs
+            // best - floor(best / 1024); `patience` checks without progress (stall_patience,
+            // doubled after every reset) make the next launch reset the endpoints of its
+            // violated pairs, provided their RMS violation exceeds xi / 1024 (LF > 16 V in
+            // loss units): a slow tail of tiny violations is left to Adam
             if (B.reset) {
                 B.reset = 0;
                 B.best = ~0ull;
-                B.best_v = ~0ull;
                 B.since = 0;
             } else if (t == 0) {
                 B.best = LF;
-                B.best_v = V;
-            } else if (LF < B.best - B.best / 1024 || (LF <= B.best && V < B.best_v)) {
+            } else if (LF < B.best - B.best / 1024) {
                 B.best = LF;
-                B.best_v = V;
                 B.since = 0;
-            } else if (C.stall_patience > 0 && ++B.since >= C.stall_patience) {
+            } else if (C.stall_patience > 0 && ++B.since >= B.patience && LF > 16ull * V) {
                 B.reset = 1;
                 B.since = 0;
+                B.patience = B.patience < (1 << 24) ? 2 * B.patience : B.patience;
             }
         }
         B.lfx = 0;
@@ -1212,6 +1210,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
         k.b2p = p->beta2;
         k.ibc1 = df_split(1.0 / (1.0 - p->beta1));
         k.ibc2 = df_split(1.0 / (1.0 - p->beta2));
+        k.patience = p->stall_patience;
         I.max_checks = std::max<int64_t>(I.max_checks, (p->replay_iters >= 0 ? p->replay_iters : p->t_max) + 1);
     }
     I.CB.alloc(nb, s);

@@ -211,7 +211,7 @@ def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps
     thr_l = torch.as_tensor(consts["thr_link"], dtype=torch.float64)
     thr_n = torch.as_tensor(consts["thr_non"], dtype=torch.float64)
     unit = xi * xi * 2.0 ** -24
-    best, best_v, since, reset_now, resets = None, None, 0, False, 0
+    best, since, reset_now, resets, patience = None, 0, False, 0, stall
     for _ in range(steps):
         opt.zero_grad()
         r = dp + delta[a] - delta[b]
@@ -239,15 +239,16 @@ def _torch_pgd(orig, recon, ai, aj, alink, consts, xi, alpha_rel, eps_rel, steps
                 st["exp_avg_sq"][hit] = 0.0
                 resets += int(hit.any())
             fx = int(np.rint((vv * vv * (1.0 / unit)).numpy()).sum())
-            nv = int((vv > 0).sum())
+            nv = int((vv > consts["tau"] * 2.0 ** -10).sum())   # counted above b 2^-40
         if reset_now:
-            reset_now, best, best_v, since = False, None, None, 0
-        elif best is None or fx < best - best // 1024 or (fx <= best and nv < best_v):
-            best, best_v, since = fx, nv, 0
+            reset_now, best, since = False, None, 0
+        elif best is None or fx < best - best // 1024:
+            best, since = fx, 0
         elif stall > 0:
             since += 1
-            if since >= stall:
+            if since >= patience and fx > 16 * nv:
                 reset_now, since = True, 0
+                patience = 2 * patience if patience < (1 << 24) else patience
     return E, delta.detach().numpy(), resets
 
 
