@@ -282,9 +282,9 @@ pc_status pc_apply_edits_static(const float *recon_dev, int64_t n, const uint8_t
  * lossless compression"): canonical Huffman coding of an edit stream v1.  The paper
  * follows the Huffman stage with ZSTD; that stage is not part of this container.
  * Container "PCH1", little endian:
- *   0  "PCH1" | 4 u32 version=1 | 8 u64 raw_bytes | 16 u32 n_lanes | 20 u32 chunk=4096
+ *   0  "PCH1" | 4 u32 version=1 | 8 u64 raw_bytes | 16 u32 n_lanes | 20 u32 chunk=1024
  *   24 u32 max_len=15 | 28 u32 0 | 32..95 the stream's 64-byte header, verbatim
- *   96 per lane: u64 n_syms | u64 bit_len | u64 n_chunks=ceil(n_syms/4096) |
+ *   96 per lane: u64 n_syms | u64 bit_len | u64 n_chunks=ceil(n_syms/1024) |
  *      256 x u8 code length (0 = unused symbol) | n_chunks x u64 bit offset of the chunk |
  *      ceil(bit_len/32) x u32 words
  * Lane 0 holds the flag bytes, lane 1 + k byte k of every code (k < ceil(m/8)).  Each

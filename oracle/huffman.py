@@ -28,7 +28,7 @@ import heapq
 import numpy as np
 
 MAX_LEN = 15
-CHUNK = 4096
+CHUNK = 1024
 HEADER = 64
 
 

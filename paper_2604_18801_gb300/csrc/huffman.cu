@@ -5,7 +5,7 @@
 //
 // The stream body is split into lanes (flag bytes; byte k of every code), each coded with
 // its own canonical code of at most 15 bits.  On the device: one 256-bin histogram per
-// lane, the bit length of every 4096-symbol chunk, a scan of the chunk lengths (the
+// lane, the bit length of every 1024-symbol chunk, a scan of the chunk lengths (the
 // chunks' bit offsets, kept in the container so that every chunk decodes on its own),
 // and the codes written with one 32-bit atomic OR per word they touch.  The code lengths
 // and canonical codes (256 symbols per lane) are built on the host.
@@ -21,7 +21,8 @@ namespace pc {
 namespace {
 
 constexpr int HMAX = 15;          // longest code
-constexpr int HCHUNK = 4096;      // symbols per independently decodable chunk
+constexpr int HCHUNK = 1024;      // symbols per independently decodable chunk
+constexpr int ENC_SPT = HCHUNK / 256;   // symbols per thread of k_encode (256 threads per chunk)
 constexpr int HHEAD = 64;         // bytes of the edit stream's own header
 constexpr int CONT_HEAD = 96;     // container header: 32 bytes + the stream header
 
@@ -64,7 +65,7 @@ __global__ void k_chunk_bits(const uint8_t *__restrict__ src, Lane L, const uint
     }
 }
 
-// Codes of one chunk per block: each thread takes 16 consecutive symbols, a block scan of
+// Codes of one chunk per block: each thread takes ENC_SPT consecutive symbols, a block scan of
 // their bit lengths places them, and every code is ORed into the (zeroed) words it spans.
 __global__ void k_encode(const uint8_t *__restrict__ src, Lane L, const uint8_t *__restrict__ lens,
                          const uint32_t *__restrict__ codes, const unsigned long long *__restrict__ chunk_off,
@@ -78,8 +79,8 @@ __global__ void k_encode(const uint8_t *__restrict__ src, Lane L, const uint8_t 
     }
     __syncthreads();
     const int64_t c = blockIdx.x;
-    const int64_t i0 = c * HCHUNK + (int64_t)threadIdx.x * 16;
-    const int64_t i1 = min(i0 + 16, min((int64_t)HCHUNK * (c + 1), L.n));
+    const int64_t i0 = c * HCHUNK + (int64_t)threadIdx.x * ENC_SPT;
+    const int64_t i1 = min(i0 + ENC_SPT, min((int64_t)HCHUNK * (c + 1), L.n));
     unsigned int mine = 0;
     for (int64_t i = i0; i < i1; ++i) mine += ln[src[L.off + i * L.stride]];
     scan[threadIdx.x] = mine;

@@ -96,8 +96,9 @@ def test_container_of_a_hacc_box(cuda):
 
 @pytest.mark.parametrize("n,m,density,skew", [
     (8, 16, 1.0, "fib"),                    # one chunk per lane, a handful of symbols
-    (4096 * 8, 16, 0.3, "fib"),             # the flag lane is exactly one chunk
-    (4096 * 8 + 8, 8, 0.3, "uniform"),      # one symbol past a chunk
+    (1024 * 8, 16, 0.3, "fib"),             # the flag lane is exactly one chunk
+    (1024 * 8 + 8, 8, 0.3, "uniform"),      # one symbol past a chunk
+    (4096 * 8 + 8, 8, 0.3, "uniform"),      # several chunks, one symbol past the last full one
     (1_000_003, 24, 0.05, "fib"),           # many chunks, ragged tails, 3 code lanes
     (50_000, 16, 0.0, "fib"),               # no edits: flag lane of one symbol, empty code lanes
     (50_001, 32, 1.0, "uniform"),           # every particle edited
