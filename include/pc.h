@@ -30,6 +30,10 @@
  *   - The library never allocates with the host heap on the data path; device
  *     temporaries come from the stream-ordered pool of the context's device.
  *   - Particle ids are the row indices 0..N-1; N < 2^31.
+ *   - A context keeps pinned host scratch that most calls share: issue calls on one
+ *     context from one thread at a time (use one context per thread).  The lossless
+ *     calls and pc_cluster_metrics use scratch of their own, and the pc_serve_* calls
+ *     are thread safe.
  */
 #ifndef PC_H_
 #define PC_H_
