@@ -173,6 +173,25 @@ def test_correct_replayed_iterations_parity(cuda, name, mode, R):
     _check_coords(corr.cpu().numpy(), w, delta, ed, R)
 
 
+@pytest.mark.parametrize("name,mode,R", [("cosmo4096", 0, 16), ("hacc32k", 2, 16), ("fluid20k", 1, 16),
+                                         ("hacc32k_morton", 2, 16)])
+def test_stall_resets_parity(cuda, name, mode, R):
+    # stall_patience = 1 makes the stall rule fire early (patience 1, 2, 4, ...): the GPU's
+    # reset path (light and heavy rows) against the oracle's, on cases where the resets
+    # move the offsets by a sizeable fraction of xi
+    import paper_2604_18801_gb300 as pc
+    w = W_(name)
+    prm = w.params(mode=mode, replay_iters=R, stall_patience=1)
+    corr, st, code = pc.correct(dev(w.orig, cuda), dev(w.recon, cuda), prm)
+    assert st["iters"] == R
+    ai, aj, al, _ = oracle.select(w.orig, **prm)
+    _, delta, ed, ost = oracle.pgd(w.orig, w.recon, ai, aj, al, **prm)
+    _, plain, _, _ = oracle.pgd(w.orig, w.recon, ai, aj, al, **dict(prm, stall_patience=0))
+    assert np.abs(delta - plain).max() > 0.1 * w.xi
+    assert _well_conditioned(w, prm, ai, aj, al, delta)
+    _check_coords(corr.cpu().numpy(), w, delta, ed, R)
+
+
 @pytest.mark.parametrize("name", ["md300", "md300_morton"])
 def test_ill_conditioned_converged_cases_are_detected(name):
     # converged HF on the MD clusters (about 100 Adam steps): a 1e-13 relative change of
