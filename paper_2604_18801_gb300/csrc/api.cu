@@ -108,6 +108,23 @@ Consts make_consts(const pc_params *p, const Inspect &ins, int64_t n, bool windo
     c.xi_box_d = xi - c.eps_q - c.u;
     c.dt = 2.0 * std::sqrt(3.0) * (c.eps_q + c.u) + b * std::ldexp(1.0, -20);
     c.xi_box = (float)c.xi_box_d;
+    // Interior of a periodic box.  An active pair's original minimum-image separation is at
+    // most sqrt(hi2) per axis and each offset at most xi, so for a particle at least
+    // m = sqrt(hi2) (1 + 2^-10) + 3 xi inside every face, with every original position in
+    // [box_lo, box_hi), the partner's stored position is the direct image and the raw
+    // difference of current positions stays below L / 2: the minimum image never wraps.
+    c.interior_ok = 0;
+    if (c.periodic && window) {
+        const double mg = std::sqrt((double)c.hi2) * (1.0 + std::ldexp(1.0, -10)) + 3.0 * xi;
+        bool ok = true;
+        for (int k = 0; k < 3; ++k) {
+            ok &= (double)ins.lo[k] >= p->box_lo[k] && (double)ins.hi[k] < p->box_hi[k];
+            ok &= 0.5 * (p->box_hi[k] - p->box_lo[k]) > 2.0 * mg;
+            c.in_lo[k] = p->box_lo[k] + mg;
+            c.in_hi[k] = p->box_hi[k] - mg;
+        }
+        c.interior_ok = ok ? 1 : 0;
+    }
     // grid: cells no smaller than the largest classified distance
     const double reach = std::sqrt((double)c.hi2) * (1.0 + 1e-5);
     double ext[3];

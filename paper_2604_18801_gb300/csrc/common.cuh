@@ -63,6 +63,10 @@ struct Consts {
     float alpha, beta1, beta2, eps_adam;
     // double copies kept for the host
     double xi, b, eps_q, u, dt, xi_box_d, M;
+    // periodic boxes: a particle whose position lies in [in_lo, in_hi] on every axis has
+    // no active pair that wraps (set only when every original position is inside the box)
+    int interior_ok;
+    double in_lo[3], in_hi[3];
 };
 
 // Canonical float32 difference with minimum image (exact: one add/sub of L when |d| > L/2).

@@ -59,6 +59,8 @@ struct PgdConsts {
     float tau[MAX_THR];           // coincidence radius b * 2^-30 for the gradient direction
     df thr_link[MAX_THR], thr_non[MAX_THR];   // b -/+ delta_t of Eq. 3
     double vtol[MAX_THR];         // a violation counts (stop rule, stall rule) above b * 2^-40
+    int interior_ok;              // periodic box whose interior rows never wrap (see ilo, ihi)
+    float ilo[3], ihi[3];         // current position of an interior row, per axis
     df xi_box, alpha, eps_adam;
     df beta1, one_m_beta1, beta2, one_m_beta2;
     int t_max;
@@ -776,7 +778,13 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
         const PgdConsts &Cl = CB[b];            // the item's block
         const float sl_link = Cl.screen_link[0], sl_non = Cl.screen_non[0];
         constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;   // partner bits of a CSR entry
-        const int per_l = Cl.periodic;
+        // a warp whose rows all sit in the box's interior screens without the minimum image
+        // (it never wraps there, so the screen's d2 is the same bit for bit)
+        const bool row_lane = heavy_warp || lane < cnt;
+        const bool in_ok = Cl.interior_ok != 0 &&
+                           (!row_lane || (qe.x >= Cl.ilo[0] && qe.x <= Cl.ihi[0] && qe.y >= Cl.ilo[1] &&
+                                          qe.y <= Cl.ihi[1] && qe.z >= Cl.ilo[2] && qe.z <= Cl.ihi[2]));
+        const int per_l = (Cl.periodic != 0 && !__all_sync(FULL, in_ok)) ? 1 : 0;
         const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
 
         df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of the lane's row
@@ -1079,6 +1087,11 @@ PgdConsts pgd_consts(const Consts &c, const pc_params *p) {
     K.thr_link[0] = df_split(thrL);
     K.thr_non[0] = df_split(thrN);
     K.vtol[0] = std::ldexp(c.b, -40);
+    K.interior_ok = c.interior_ok;
+    for (int a = 0; a < 3; ++a) {   // rounded toward the interior
+        K.ilo[a] = f32_up(c.in_lo[a]);
+        K.ihi[a] = f32_down(c.in_hi[a]);
+    }
     for (int k = 1; k < MAX_THR; ++k) {
         K.vtol[k] = K.vtol[0];
         K.screen_link[k] = K.screen_link[0];
