@@ -39,7 +39,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # DRAM bytes (read + write) per algorithmic byte of k_pgd_iter, from the ncu capture in
 # profiles/k_pgd_iter_hacc4194304_eps0.1b_VP.md (471.8 MB for 322.2 MB); the kernel's traffic
 # grows with |E| and |A|, so a full-size launch's traffic is this ratio times its bytes.
-PGD_TRAFFIC_RATIO = 470.2 / 322.2
+PGD_TRAFFIC_RATIO = 469.0 / 322.2
 PGD_TRAFFIC_SOURCE = "profiles/k_pgd_iter_hacc4194304_eps0.1b_VP.md (scaled by algorithmic bytes)"
 
 
