@@ -35,12 +35,52 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MODES = {"VP": 0, "SC": 1, "HF": 2}
+# full size of each generator: the 256^3 HACC-shaped box, the 4M-atom MD cube, the 8M fluid box
+FULL_N = {"hacc": 256 ** 3, "md": 4_000_000, "fluid": 8_000_000}
+
+
+def make_workload(gen: str, n: int, eps: float, seed: int, base: str = "quant"):
+    """The plain workload of one generator at n particles (eps in units of b)."""
+    from paper_2604_18801_gb300 import synth
+    if gen == "md":
+        w = synth.md_box(n_clusters=max(1, n // 100), eps_over_b=eps, mode="HF", seed=seed)
+    elif gen == "fluid":
+        w = synth.fluid_box(n=n, eps_over_b=eps, seed=seed, mode="HF")
+    else:
+        w = synth.hacc_box(eps_over_b=eps, mode="HF", seed=seed, n=n)
+    return synth.with_base(w, base)
+
+
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# DRAM bytes (read + write) per algorithmic byte of k_pgd_iter, from the ncu capture in
-# profiles/k_pgd_iter_hacc4194304_eps0.1b_VP.md (471.8 MB for 322.2 MB); the kernel's traffic
-# grows with |E| and |A|, so a full-size launch's traffic is this ratio times its bytes.
-PGD_TRAFFIC_RATIO = 469.0 / 322.2
-PGD_TRAFFIC_SOURCE = "profiles/k_pgd_iter_hacc4194304_eps0.1b_VP.md (scaled by algorithmic bytes)"
+# algorithmic bytes of one PGD check (the loss, gradient and update of Algorithm 1 for every
+# active pair and editable particle): 16 B each for the offset, m, v and position read and
+# 48 B written per editable particle; 4 B per directed edge, i.e. 8 B per active pair
+PGD_BYTES_PER_ROW, PGD_BYTES_PER_PAIR = 112, 8
+# stall rule (not in the paper) for the mixed batched and served workloads, where a few
+# blocks settle in a local minimum of the non-convex loss under plain Adam-PGD
+STALL_PATIENCE = 100
+PER_MODE_KEYS = ("iters", "loss_evals", "n_vulnerable", "n_active", "n_editable", "viol0", "resets", "row_updates",
+                 "pair_evals", "ms_setup", "ms_pgd", "ms_pgd_iter", "pgd_launches")
+
+
+def pgd_roofline(stats_by_mode: dict, peak: float, peak_kind: str) -> dict:
+    """Roofline of the PGD iteration kernel from pc_correct's own counters: the algorithmic
+    bytes of every check that ran (loss_evals per mode: the launches that did work) over the
+    device time of all iteration launches (CUDA events in the library around them, so the
+    few empty launches after the stop count as time, not as bytes)."""
+    checks = sum(st["loss_evals"] for st in stats_by_mode.values())
+    launches = sum(st["pgd_launches"] for st in stats_by_mode.values())
+    nbytes = sum((PGD_BYTES_PER_ROW * st["n_editable"] + PGD_BYTES_PER_PAIR * st["n_active"]) * st["loss_evals"]
+                 for st in stats_by_mode.values())
+    ms = sum(st["ms_pgd_iter"] for st in stats_by_mode.values())
+    achieved = nbytes / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"kernel": "k_pgd_iter", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "traffic_note": "DRAM bytes of this kernel come from an ncu capture outside the bench run",
+            "peak_kind": peak_kind, "checks_per_step": int(checks), "launches_per_step": int(launches),
+            "avg_check_us": round(1e3 * ms / max(1, checks), 2),
+            "bytes_per_check": int(nbytes / max(1, checks)),
+            "formula": "sum over modes of (112 B x n_editable + 8 B x n_active) x loss_evals / sum of ms_pgd_iter"}
 
 
 def parse():
@@ -53,8 +93,10 @@ def parse():
     ap.add_argument("--modes", default="VP,SC,HF")
     ap.add_argument("--base", default="quant", choices=["quant", "morton"],
                     help="base-compressor stand-in: global quantizer or the Morton-order baseline (Sec. 4.1)")
-    ap.add_argument("--n", type=int, default=256 ** 3)
-    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--gen", default="hacc", choices=["hacc", "md", "fluid"],
+                    help="generator: HACC-shaped periodic box, MD-like cluster cube, or the fluid box")
+    ap.add_argument("--n", type=int, default=0, help="particles (0 = the generator's full size)")
+    ap.add_argument("--seed", type=int, default=-1, help="generator seed (-1: 1 HACC, 2 MD, 5 fluid)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--cpu-side", type=float, default=0.25, help="side of the sub-cube the CPU baseline corrects")
@@ -126,28 +168,61 @@ class Clocks:
 
 
 def sub_cube(w, side: float):
-    """Particles of the box inside [0, side)^3, as a non-periodic problem (CPU baseline sample)."""
+    """Particles in the corner box lo + [0, side) * (hi - lo) of the workload's box, as a
+    non-periodic problem (CPU baseline sample)."""
     import numpy as np
     from paper_2604_18801_gb300 import synth
-    m = np.all(w.orig < side, axis=1) & np.all(w.recon < side + w.xi, axis=1)
+    lo = np.array(w.box_lo, np.float64)
+    while True:   # widen a corner that holds too few particles to time
+        hi = lo + side * (np.array(w.box_hi, np.float64) - lo)
+        m = np.all(w.orig < hi, axis=1) & np.all(w.orig >= lo, axis=1)
+        if m.sum() >= min(1000, w.n) or side >= 1.0:
+            break
+        side = min(1.0, 2.0 * side)
     o = np.ascontiguousarray(w.orig[m])
     r = np.ascontiguousarray(w.recon[m])
-    return synth.Workload(name=f"{w.name}_subcube{side:g}", orig=o, recon=r, b=w.b, xi=w.xi, periodic=False,
-                          box_lo=(0, 0, 0), box_hi=(side, side, side), mode=w.mode)
+    blo = tuple(float(v) for v in np.minimum(o.min(axis=0), r.min(axis=0)))
+    bhi = tuple(float(v) for v in np.maximum(o.max(axis=0), r.max(axis=0)))
+    sub = synth.Workload(name=f"{w.name}_subcube{side:g}", orig=o, recon=r, b=w.b, xi=w.xi, periodic=False,
+                         box_lo=blo, box_hi=bhi, mode=w.mode)
+    sub.aux["side"] = side
+    return sub
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo), or the platform's processor string."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip().lower() in ("model name", "cpu model", "processor name"):
+                return v.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def cpu_baseline(w, modes, side):
-    """The CPU oracle, as it stands, on a sub-cube of the same box (single thread)."""
+    """The CPU oracle, as it stands, on a sub-cube of the same box: once on one thread and
+    once on all of the host's cores (its OpenMP build gives the same bits at any thread
+    count).  value / cores: the all-cores run."""
     import oracle
     s = sub_cube(w, side)
     oracle.build()
-    t = time.perf_counter()
-    for m in modes:
-        oracle.correct(s.orig, s.recon, **s.params(mode=MODES[m]))
-    dt = time.perf_counter() - t
-    return {"value": round(s.n * len(modes) / dt / 1e6, 6), "unit": "Mparticles/s", "cores": 1, "kind": "oracle",
-            "sample": f"{s.n} particles of the sub-cube [0,{side:g})^3 of the same box, modes {','.join(modes)}, "
-                      f"{dt:.1f} s single-threaded"}
+    runs = {}
+    for th in (1, os.cpu_count() or 1):
+        used = oracle.threads(th)
+        t = time.perf_counter()
+        for m in modes:
+            oracle.correct(s.orig, s.recon, **s.params(mode=MODES[m]))
+        runs[used] = time.perf_counter() - t
+    cores = max(runs)
+    dt, dt1 = runs[cores], runs[min(runs)]
+    return {"value": round(s.n * len(modes) / dt / 1e6, 6), "unit": "Mparticles/s", "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
+            "single_thread": {"value": round(s.n * len(modes) / dt1 / 1e6, 6), "cores": 1, "s": round(dt1, 2)},
+            "sample": f"{s.n} particles of a corner sub-box (side {s.aux['side']:g} of the box) of the same workload, "
+                      f"non-periodic, modes {','.join(modes)}: {dt:.1f} s on {cores} threads, {dt1:.1f} s on 1"}
 
 
 def job_throughput(ms: float, units: int, device=None):
@@ -220,7 +295,9 @@ def run_batch(a):
     # autotuner (not timed): cell factor of the fastest selection on the largest block
     kbig = int(np.argmax(sizes))
     cell_factor, tune_ms = pc.autotune_cells(orig[offs[kbig]:offs[kbig + 1]], ws[kbig].params())
-    prms = [w.params(cell_factor=cell_factor) for w in ws]
+    # a few of the 512 blocks settle in a local minimum of the non-convex loss under plain
+    # Adam-PGD; the batch runs with the stall rule on (the line reports how many fired)
+    prms = [w.params(cell_factor=cell_factor, stall_patience=STALL_PATIENCE) for w in ws]
 
     def step():
         out, stats, code = pc.correct_batch(orig, recon, sizes, prms)
@@ -280,6 +357,8 @@ def run_batch(a):
                               "ms": round(seq_ms, 3)},
             "speedup_vs_one_at_a_time": round(seq_ms / ms, 3),
             "max_iters": max(st["iters"] for st in stats), "sum_iters": sum(st["iters"] for st in stats),
+            "stall_patience": STALL_PATIENCE, "resets": sum(st["resets"] for st in stats),
+            "blocks_with_resets": sum(1 for st in stats if st["resets"] > 0),
             "pgd_launches": stats[0]["pgd_launches"], "ms_setup": round(stats[0]["ms_setup"], 3),
             "ms_pgd": round(stats[0]["ms_pgd"], 3), "gpu_launches": int(launches // a.steps),
             "clocks": clocks, "generate_s": round(gen_s, 1)}
@@ -306,7 +385,7 @@ def run_serve(a):
     dat = [(torch.from_numpy(w.orig).to(dev), torch.from_numpy(w.recon).to(dev)) for w in ws]
     kbig = max(range(len(ws)), key=lambda k: ws[k].n)
     cell_factor, _ = pc.autotune_cells(dat[kbig][0], ws[kbig].params())
-    prms = [w.params(cell_factor=cell_factor) for w in ws]
+    prms = [w.params(cell_factor=cell_factor, stall_patience=STALL_PATIENCE) for w in ws]
     caps = [64 + (w.n + 7) // 8 + 12 * w.n for w in ws]
     n_tot = sum(w.n for w in ws)
     torch.cuda.synchronize(dev)
@@ -526,6 +605,10 @@ def run_multi(a):
 
 def main():
     a = parse()
+    if a.n <= 0:
+        a.n = FULL_N[a.gen]
+    if a.seed < 0:
+        a.seed = {"hacc": 1, "md": 2, "fluid": 5}[a.gen]
     if a.workload == "batch":
         return run_batch(a)
     if a.workload == "capped":
@@ -538,13 +621,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     modes = [m.strip() for m in a.modes.split(",") if m.strip()]
-    workload = f"hacc{a.n}_eps{a.eps:g}b_{'+'.join(modes)}" + ("" if a.base == "quant" else "_" + a.base)
+    workload = f"{a.gen}{a.n}_eps{a.eps:g}b_{'+'.join(modes)}" + ("" if a.base == "quant" else "_" + a.base)
 
     if a.impl == "reference":
         if rank != 0:
             return
         from paper_2604_18801_gb300 import synth
-        w = synth.with_base(synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n), a.base)
+        w = make_workload(a.gen, a.n, a.eps, a.seed, a.base)
         for _ in range(a.warmup):
             pass
         times = []
@@ -574,7 +657,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    w = synth.with_base(synth.hacc_box(eps_over_b=a.eps, mode="HF", seed=a.seed, n=a.n), a.base)
+    w = make_workload(a.gen, a.n, a.eps, a.seed, a.base)
     o = torch.from_numpy(w.orig).to(dev)
     r = torch.from_numpy(w.recon).to(dev)
     # autotuner (not timed): cells per particle of the fastest selection on this machine
@@ -653,21 +736,10 @@ def main():
                        "encode_gbs": round(s_.numel() / e_ms / 1e6, 2), "decode_gbs": round(s_.numel() / d_ms / 1e6, 2),
                        "roundtrip_exact": ok}
 
-    # roofline of the dominant kernel (the PGD iteration): algorithmic bytes per launch =
-    # 112 B per editable particle + 8 B per active pair; duration from the in-library events
+    # roofline of the dominant kernel (the PGD iteration), from the last step's counters
     last = stats[-1]
-    bytes_it = sum((112 * last[m]["n_editable"] + 8 * last[m]["n_active"]) * last[m]["pgd_launches"] for m in modes)
-    ms_it = sum(last[m]["ms_pgd_iter"] for m in modes)
-    launches_it = sum(last[m]["pgd_launches"] for m in modes)
     pk, pk_kind = peaks()
-    achieved = bytes_it / (ms_it / 1e3) / 1e9 if ms_it > 0 else 0.0
-    peak = float(pk["hbm_gbs"])
-    roofline = {"kernel": "k_pgd_iter", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": int(PGD_TRAFFIC_RATIO * bytes_it / max(1, launches_it)), "traffic_source": PGD_TRAFFIC_SOURCE,
-                "peak_kind": pk_kind, "avg_launch_us": round(1e3 * ms_it / max(1, launches_it), 2),
-                "launches_per_step": launches_it,
-                "bytes_per_launch": int(bytes_it / max(1, launches_it))}
+    roofline = pgd_roofline(last, float(pk["hbm_gbs"]), pk_kind)
 
     # end to end through the public API with host buffers: pinned H2D, correct, encode, stream D2H
     ho = torch.from_numpy(w.orig).pin_memory()
@@ -700,8 +772,7 @@ def main():
                    "cell_factor": cell_factor,
                    "parallelism": f"replicas{world}", "l2": "inputs (2 x 201 MB) and PGD state larger than L2"},
         "membership_exact": exact,
-        "per_mode": {m: {k: last[m][k] for k in ("iters", "n_vulnerable", "n_active", "n_editable", "viol0",
-                                                   "ms_setup", "ms_pgd")} for m in modes},
+        "per_mode": {m: {k: last[m][k] for k in PER_MODE_KEYS} for m in modes},
         "roofline": roofline,
         "lossless": lossless,
         "e2e": {"value": round(e2e_v, 3), "unit": "Mparticles/s",

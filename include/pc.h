@@ -91,7 +91,7 @@ typedef struct {
 } pc_params;
 
 /* Fills defaults: m=16, t_max=10000, alpha_rel=0.2, beta=(0.9,0.999), eps_rel=2e-6,
- * loss_tol=0, replay_iters=-1, cell_cap_log2=0, stall_patience=100, cell_factor=0,
+ * loss_tol=0, replay_iters=-1, cell_cap_log2=0, stall_patience=0 (Algorithm 1 as printed), cell_factor=0,
  * unit box, non-periodic, mode VP. */
 void pc_params_default(pc_params *p);
 
@@ -155,7 +155,15 @@ typedef struct {
     double ms_setup;       /* binning + pair search + selection + CSR build      */
     double ms_pgd;         /* PGD loop including the output kernels              */
     double ms_pgd_iter;    /* device time of the iteration launches alone        */
-    int64_t pgd_launches;  /* iteration kernels launched (>= loss_evals)         */
+    int64_t pgd_launches;  /* iteration kernels launched (>= loss_evals; launches
+                              after the stop return at once)                    */
+    int64_t resets;        /* stall resets that fired (0 when stall_patience = 0) */
+    int64_t row_updates;   /* Adam steps applied to editable particles, summed over
+                              the updates (rows with neither a gradient so far nor
+                              a projection to do are left as they are)          */
+    int64_t pair_evals;    /* active pairs the float32 screen could not certify,
+                              evaluated in double-float, summed over the checks
+                              (each pair once from each endpoint)               */
 } pc_correct_stats;
 
 /* The correction pass (Algorithm 1 up to Delta).  corrected_dev (N x 3) receives

@@ -42,7 +42,8 @@ class CorrectStats(C.Structure):
                 ("loss0", C.c_double), ("loss_final", C.c_double), ("n_vulnerable", C.c_int64),
                 ("n_active", C.c_int64), ("n_editable", C.c_int64), ("converged", C.c_int32), ("pad_", C.c_int32),
                 ("ms_setup", C.c_double), ("ms_pgd", C.c_double), ("ms_pgd_iter", C.c_double),
-                ("pgd_launches", C.c_int64)]
+                ("pgd_launches", C.c_int64), ("resets", C.c_int64), ("row_updates", C.c_int64),
+                ("pair_evals", C.c_int64)]
 
 
 class Block(C.Structure):

@@ -270,8 +270,8 @@ void select_count(HostScratch &hs, const float *orig, cudaStream_t s, Selection 
         uf_init(h.safe.p, n, s);
     }
     pair_pass_union(h.B, S, h.fof.p, h.safe.p, h.counts.p, h.err.p, s, nb > 1 ? h.bc.p : nullptr);
-    if (h.fof.p) uf_flatten(h.fof.p, n, s);
-    if (h.safe.p) uf_flatten(h.safe.p, n, s);
+    if (h.fof.p) uf_flatten(h.fof.p, n, h.err.p, s);
+    if (h.safe.p) uf_flatten(h.safe.p, n, h.err.p, s);
     memcpy(h.cnt, read_back(hs, h.counts.p, sizeof(h.cnt), s), sizeof(h.cnt));
     const uint32_t ev = *(uint32_t *)read_back(hs, h.err.p, sizeof(uint32_t), s);
     if (ev & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
@@ -428,6 +428,9 @@ void correct_blocks(pc_ctx *ctx, const float *orig, const float *recon, BlockSet
             st.n_active = h->stats[b].n_active;
             st.n_editable = pr.n_editable;
             st.converged = pr.converged ? 1 : 0;
+            st.resets = pr.resets;
+            st.row_updates = pr.row_updates;
+            st.pair_evals = pr.pair_evals;
             st.ms_setup = (given ? 0.0 : h->stats[b].ms) + r.ms_csr;
             st.ms_pgd = r.ms;
             st.ms_pgd_iter = r.ms_iter;
@@ -470,7 +473,7 @@ void pc_params_default(pc_params *p) {
     p->loss_tol = 0.0;
     p->replay_iters = -1;
     p->cell_cap_log2 = 0;
-    p->stall_patience = 100;
+    p->stall_patience = 0;   // Algorithm 1 as printed: no stall rule
     p->cell_factor = 0;
 }
 
@@ -525,7 +528,7 @@ pc_status pc_fof_labels(pc_ctx *ctx, const float *xyz, int64_t n, const pc_param
         uint32_t *par = (uint32_t *)labels;
         uf_init(par, n, s);
         pair_pass_union(B, S, par, nullptr, counts.p, err.p, s);
-        uf_flatten(par, n, s);
+        uf_flatten(par, n, err.p, s);
         const uint32_t ev = *(uint32_t *)read_back(ctx->hs, err.p, sizeof(uint32_t), s);
         if (ev & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
         if (n_comp) *n_comp = count_roots(par, n, s, ctx->hs);
@@ -676,6 +679,9 @@ pc_status pc_correct_multi(pc_ctx *ctx, const float *orig, const float *recon, i
             st.n_active = total;
             st.n_editable = pr.n_editable;
             st.converged = pr.converged ? 1 : 0;
+            st.resets = pr.resets;
+            st.row_updates = pr.row_updates;
+            st.pair_evals = pr.pair_evals;
             st.ms_setup = ms_sel + r.ms_csr;
             st.ms_pgd = r.ms;
             st.ms_pgd_iter = r.ms_iter;

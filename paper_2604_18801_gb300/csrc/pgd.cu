@@ -48,6 +48,11 @@ constexpr int PGD_BLOCKS_PER_SM = 4;   // resident CTAs of the persistent iterat
 // their active pairs, Sec. 1 and Sec. 5); a CSR entry then carries its pair's index.
 constexpr int MAX_THR = 4;
 
+// act[e]: bit 0 = the row has had a gradient (or needs its first projection), bit 1 = the
+// row is heavy (more than HEAVY partners: its edges are walked in chunks of HEAVY).
+constexpr uint8_t ACT_ON = 1, ACT_HEAVY = 2;
+constexpr uint32_t HEAVY = 256;
+
 // Per-block PGD constants (one entry per block of the problem set).  The threshold arrays
 // are indexed by the pair's linking length (entry 0 alone with one).
 struct PgdConsts {
@@ -91,8 +96,10 @@ struct PgdBlk {
     unsigned long long best;        // lowest fixed-point loss that counted as progress
     int32_t since;                  // checks since then
     int32_t patience;               // checks without progress before the next reset (doubles per reset)
-    int32_t pad;
-    unsigned long long lfx, vacc;   // launch accumulators: loss (fixed point), violations
+    int32_t resets;                 // checks that triggered a stall reset
+    unsigned long long lfx, vacc;   // launch accumulators: loss (fixed point), violations,
+    unsigned long long uacc, eacc;  // ... rows updated (Adam steps), pairs evaluated in double-float
+    unsigned long long n_upd, n_eval;   // totals of the last two over the run
 };
 
 struct PgdGlobal {
@@ -199,42 +206,17 @@ __global__ void k_dir_keys(const unsigned long long *__restrict__ A, const uint8
 }
 
 __global__ void k_row_bounds(const unsigned long long *__restrict__ keys, int64_t m, int nb, int64_t nrows,
-                             uint32_t *__restrict__ row_ptr) {
+                             unsigned long long *__restrict__ row_ptr) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= m; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t prev = t == 0 ? -1 : (int64_t)(keys[t - 1] >> nb);
         const int64_t cur = t == m ? nrows : (int64_t)(keys[t] >> nb);   // nb: all bits below the row
-        for (int64_t r = prev + 1; r <= cur; ++r) row_ptr[r] = (uint32_t)t;
+        for (int64_t r = prev + 1; r <= cur; ++r) row_ptr[r] = (unsigned long long)t;
     }
 }
 
 __device__ __forceinline__ float3 canon_dp(const float4 p, const float4 q, int periodic, const float *L) {
     const bool per = periodic != 0;
     return make_float3(cdiff(p.x, q.x, per, L[0]), cdiff(p.y, q.y, per, L[1]), cdiff(p.z, q.z, per, L[2]));
-}
-
-// Squared linking lengths of the thresholds of a multi-threshold problem (float32).
-struct ThrB2 {
-    float b2[MAX_THR];
-};
-
-__global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, int nb, int tb, ThrB2 tb2,
-                       const uint32_t *__restrict__ dense, const uint32_t *__restrict__ epos,
-                       const float4 *__restrict__ P4, const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
-                       int nblk, uint32_t *__restrict__ col) {
-    const unsigned long long mask = (1ull << nb) - 1ull;
-    GRID_STRIDE(t, m) {
-        const unsigned long long k = keys[t];
-        const uint32_t ti = (uint32_t)(k & ((1ull << tb) - 1ull));
-        const uint32_t row = (uint32_t)(k >> (nb + tb)), nbp = (uint32_t)((k >> tb) & mask);
-        const uint32_t pos = epos[row];
-        const BlockDev &B = bt[find_block(off, nblk, pos)];
-        const float4 p = P4[pos], q = P4[nbp];
-        const float3 d = canon_dp(p, q, B.periodic, B.L);
-        // the link flag at the pair's own linking length
-        const float b2 = tb ? (ti == 0 ? tb2.b2[0] : ti == 1 ? tb2.b2[1] : ti == 2 ? tb2.b2[2] : tb2.b2[3]) : B.b2;
-        const bool link = cdist2(d.x, d.y, d.z) <= b2;
-        col[t] = dense[nbp] | (ti << 29) | (link ? 0x80000000u : 0u);
-    }
 }
 
 __global__ void k_state_init(const uint32_t *__restrict__ epos, int64_t ne, const float4 *__restrict__ P4,
@@ -268,7 +250,7 @@ __global__ void k_state_init(const uint32_t *__restrict__ epos, int64_t ne, cons
         const df xb = CB[b].xi_box, nl = df_neg(xb);
         const bool out = df_lt(xb, dx) || df_lt(dx, nl) || df_lt(xb, dy) || df_lt(dy, nl) || df_lt(xb, dz) ||
                          df_lt(dz, nl);
-        act[e] = out ? 1 : 0;
+        act[e] = out ? ACT_ON : 0;
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         Mhi[e] = z;
         Mlo[e] = z;
@@ -288,8 +270,6 @@ __device__ __forceinline__ df df_clamp(df x, df lim) {
     if (df_lt(x, nl)) return nl;
     return x;
 }
-
-__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
 __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
 #pragma unroll
@@ -359,14 +339,14 @@ struct RowState {
     float4 dh, dl, pe, mh, ml, vh, vl;
 };
 
-__device__ __forceinline__ void adam_core(int64_t e, const df g[3], const RowState &S, bool was,
+__device__ __forceinline__ void adam_core(int64_t e, const df g[3], const RowState &S, bool was, uint8_t av,
                                           uint8_t *__restrict__ act, const df ibc1, const df ibc2, bool reset,
                                           const PgdConsts &C, float4 *Nh, float4 *Nl, float4 *__restrict__ Mhi,
                                           float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
                                           float4 *__restrict__ Vlo, float4 *Qn) {
     const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
     if (!was && gz && !reset) return;
-    if (!was) act[e] = 1;
+    if (!was) act[e] = (uint8_t)(av | ACT_ON);
     if (reset) {
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), pe = S.pe;
         Nh[e] = z4;
@@ -415,7 +395,8 @@ __device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 
                                          float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
                                          float4 *__restrict__ Vlo, float4 *Qn) {
     const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
-    const bool was = act[e] != 0;
+    const uint8_t av = act[e];
+    const bool was = (av & ACT_ON) != 0;
     if (!was && gz && !reset) return;
     RowState S;
     S.dh = Dh[e];
@@ -427,16 +408,8 @@ __device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 
         S.vh = Vhi[e];
         S.vl = Vlo[e];
     }
-    adam_core(e, g, S, was, act, ibc1, ibc2, reset, C, Nh, Nl, Mhi, Mlo, Vhi, Vlo, Qn);
+    adam_core(e, g, S, was, av, act, ibc1, ibc2, reset, C, Nh, Nl, Mhi, Mlo, Vhi, Vlo, Qn);
 }
-
-// 16-byte asynchronous copies from global to shared memory (not cached in L1).
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ stop decisions
 // The tight loss is accumulated in fixed point: each violated pair adds llrint(v^2 / unit)
@@ -513,12 +486,17 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
                 B.since = 0;
             } else if (C.stall_patience > 0 && ++B.since >= B.patience && LF > 16ull * V) {
                 B.reset = 1;
+                ++B.resets;
                 B.since = 0;
                 B.patience = B.patience < (1 << 24) ? 2 * B.patience : B.patience;
             }
         }
         B.lfx = 0;
         B.vacc = 0;
+        B.n_upd += B.uacc;
+        B.n_eval += B.eacc;
+        B.uacc = 0;
+        B.eacc = 0;
     }
     active = __reduce_add_sync(0xffffffffu, active);
     if (wt) {
@@ -536,7 +514,7 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
 }
 
 struct BlockRed {
-    unsigned long long lfx, viol;
+    unsigned long long lfx, viol, upd, ev;
     unsigned count;
 };
 
@@ -544,6 +522,7 @@ struct BlockRed {
 // the last block of the launch takes the decisions.
 template <bool MULTI>
 __device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long long lfx, unsigned long long viol,
+                                                 unsigned long long upd, unsigned long long ev,
                                                  const PgdConsts *CB, int nb, PgdBlk *blk, PgdGlobal *gs,
                                                  double *hist_loss, unsigned long long *hist_viol,
                                                  const WorkTab &wt) {
@@ -551,12 +530,16 @@ __device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long lon
     if (!MULTI) {
         lfx = warp_sum_u(lfx);
         viol = warp_sum_u(viol);
+        upd = warp_sum_u(upd);
+        ev = warp_sum_u(ev);
     }
     unsigned prev = 0;
     if (lane == 0) {
         if (!MULTI) {
             if (lfx) atomicAdd(&br.lfx, lfx);
             if (viol) atomicAdd(&br.viol, viol);
+            if (upd) atomicAdd(&br.upd, upd);
+            if (ev) atomicAdd(&br.ev, ev);
         }
         __threadfence_block();
         prev = atomicAdd(&br.count, 1u);
@@ -567,9 +550,12 @@ __device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long lon
     if (lane == 0) {
         __threadfence_block();
         if (!MULTI) {
-            const unsigned long long bl = atomicAdd(&br.lfx, 0ull), bv = atomicAdd(&br.viol, 0ull);
+            const unsigned long long bl = atomicAdd(&br.lfx, 0ull), bv = atomicAdd(&br.viol, 0ull),
+                                     bu = atomicAdd(&br.upd, 0ull), be = atomicAdd(&br.ev, 0ull);
             if (bl) atomicAdd(&blk[0].lfx, bl);
             if (bv) atomicAdd(&blk[0].vacc, bv);
+            if (bu) atomicAdd(&blk[0].uacc, bu);
+            if (be) atomicAdd(&blk[0].eacc, be);
         }
         __threadfence();
         gprev = atomicAdd(&gs->ticket, 1u);
@@ -581,23 +567,23 @@ __device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long lon
 }
 
 // ------------------------------------------------------------------ iteration kernel
-// Rows with more than HEAVY partners are split into chunks of HEAVY edges.
-constexpr uint32_t HEAVY = 256;
-
 struct HeavyPlan {
-    int64_t n_chunks;                // heavy chunks (one warp each)
-    const uint32_t *chunk_row;       // row of each chunk
-    const uint32_t *chunk_start;     // first edge of each chunk
-    float4 *chunk_g;                 // per chunk: gradient partial (hi at 2c, lo at 2c+1)
+    int64_t n_chunks;                          // heavy chunks (one warp each)
+    const uint32_t *chunk_row;                 // row of each chunk
+    const unsigned long long *chunk_start;     // first edge of each chunk in the edge array
+    const uint32_t *chunk_len;                 // edges of each chunk (at most HEAVY)
+    float4 *chunk_g;                           // per chunk: gradient partial (hi at 2c, lo at 2c+1)
 };
 
-// The light rows' edges, in row order, apart from the heavy rows': a group of 32 rows
-// owns the contiguous range [ptr[r0], ptr[r0 + 32]), and each edge carries the slot of
-// its row within the group, so a warp maps an edge to its row without a search.
+// One edge array holds the light rows' edges, in row order, then the heavy rows' edges
+// (chunks index into that second part).  A group of 32 light rows owns the contiguous
+// range [ptr[r0], ptr[r0 + 32]) (heavy rows own no light edge), and each light edge
+// carries the slot of its row within the group, so a warp maps an edge to its row with
+// one byte load.  Offsets are 64-bit: a problem may have more than 2^32 directed edges.
 struct LightPlan {
-    const uint32_t *ptr;             // per row: first light edge (heavy rows own none)
+    const unsigned long long *ptr;   // per row: first light edge (ne + 1 entries)
     const uint32_t *col;             // partner | link << 31 (| threshold index << 29 with several)
-    const uint8_t *slot;             // row - first row of its 32-row group
+    const uint8_t *slot;             // light edges: row - first row of its 32-row group
 };
 
 struct PgdBufs {
@@ -611,39 +597,56 @@ struct PgdBufs {
     __device__ __forceinline__ float4 *q(int i) const { return i ? Q[1] : Q[0]; }
 };
 
+// A row whose Adam step waits in its warp's queue: the row, its block and flags
+// (block | buffer parity << 31 | had a gradient before << 30 | stall reset << 29) and
+// its gradient as three double-floats.
+struct AdamEnt {
+    uint32_t e, meta;
+    float g[6];
+};
+
+#ifndef PC_PGD_EPL
+#define PC_PGD_EPL 4
+#endif
+constexpr int EPL = PC_PGD_EPL;   // edges per lane per trip of the edge walk
+constexpr int QCAP = 256;  // uncertain pairs waiting for evaluation (a ring per warp; < 32 + EPL x 32)
+constexpr int ACAP = 64;   // rows waiting for their Adam step (a ring per warp)
+
 struct WarpTab {
-    float4 st[7][32];                // the rows' state for Adam, fetched while the edges are walked
-    int64_t row[32];                 // the warp's rows: dense index
-    uint32_t qk[96];                 // queued pairs: partner
-    uint8_t qs[96];                  // queued pairs: row slot | threshold index << 5 | link << 7
+    uint32_t qk[QCAP];               // queued pairs: partner
+    uint8_t qs[QCAP];                // queued pairs: row slot | threshold index << 5 | link << 7
     float4 q[32];                    // the rows' rounded current positions
     unsigned own[32];                // per row slot: this batch's violated entries of that row
     float gt[6][32];                 // this batch's gradient terms (x hi, x lo, y hi, ...) by entry
+    AdamEnt aq[ACAP];                // rows whose gradient is complete, waiting for Adam
 };
 
 // One PGD iteration for every block still iterating: check t_b and, unless it is the
 // block's last check, the update t_b + 1.
 //
 // Work items are groups of 32 consecutive light rows (editable particles) or one chunk
-// of HEAVY edges of a heavy row, handed out from a counter.  A light warp walks the
-// flat range of its rows' CSR edges 32 at a time; the float32 screen on the rounded
-// current positions Q certifies most pairs as satisfied and the others are appended,
-// in edge order, to the warp queue.  Every 32 queued pairs are evaluated in
-// double-float by the 32 lanes together; each row then adds its violated pairs one by
-// one in edge order, so a row's gradient does not depend on how rows are grouped into
-// warps, batches or blocks of the problem set.  Light lane i applies Adam to its row;
-// a heavy warp writes its chunk partial and k_pgd_heavy adds the partials of a heavy
-// row in chunk order.  MULTI = false is the single-block specialisation; with MULTI the
+// of HEAVY edges of a heavy row, handed out from a counter.  A warp walks the flat edge
+// range of its item 128 edges at a time (4 per lane, strided by 32 so that loads stay
+// coalesced and edge order is lane order within each 32-edge slice).  The float32 screen
+// on the rounded current positions Q certifies most pairs as satisfied; one warp vote
+// skips the queue when a whole trip is certified.  The others enter, in edge order, the
+// warp's ring of uncertain pairs, which the 32 lanes evaluate 32 at a time in
+// double-float; each row then adds its violated pairs one by one in edge order, so a
+// row's gradient does not depend on how rows are grouped into warps, batches or blocks
+// of the problem set.  A light row whose gradient is complete enters the warp's Adam
+// ring; whenever 32 rows are waiting, the warp applies Adam to them with every lane
+// busy (rows that need no update never enter, so the update runs on full warps).  A
+// heavy warp writes its chunk partial and k_pgd_heavy adds the partials of a heavy row
+// in chunk order.  MULTI = false is the single-block specialisation; with MULTI the
 // items come from the table of blocks still iterating, so a block that has stopped
 // costs nothing in later launches, and the rows of one item share a block.  MT: the
 // problem has several linking lengths and each CSR entry carries the index of its pair's
 // (single block only); the screen and the evaluation use that length's thresholds.
 template <bool MULTI, bool MT>
 __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
-    const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col, const float4 *__restrict__ PE,
-    int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP, const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk,
-    PgdGlobal *gs,
-    const WorkTab wt, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
+    const float4 *__restrict__ PE, int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP,
+    const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs, const WorkTab wt,
+    double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
     __shared__ int s_stop, s_t, s_reset, s_nact;
     __shared__ unsigned long long s_items;
     __shared__ df s_ibc1, s_ibc2;
@@ -660,32 +663,71 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
         br.count = 0;
         br.lfx = 0;
         br.viol = 0;
+        br.upd = 0;
+        br.ev = 0;
     }
     __syncthreads();
     if (s_stop) return;
 
     const unsigned FULL = 0xffffffffu;
+    const unsigned lt_mask = (1u << (threadIdx.x & 31)) - 1u;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     WarpTab &T = tab[w];
-    unsigned long long lfx = 0;     // this lane's share of the tight loss (single block), fixed point
-    unsigned long long viol = 0;
+    // this lane's share of the tight loss (fixed point), violations, rows updated and
+    // pairs evaluated (single block: summed at the end of the launch)
+    unsigned long long lfx = 0;
+    unsigned viol = 0, nupd = 0, nev = 0;
     const int64_t n_light_warps = (ne + 31) / 32;
     const int64_t n_items = MULTI ? (int64_t)s_items : n_light_warps + H.n_chunks;
+    int ahead = 0, an = 0;   // Adam ring: first entry, entries waiting
 
+    // Adam on the first c rows of the ring (lane i takes row i).
+    auto adam_flush = [&](int c) {
+        if (lane < c) {
+            const AdamEnt &A = T.aq[(ahead + lane) & (ACAP - 1)];
+            const uint32_t e = A.e, meta = A.meta;
+            const int b = MULTI ? (int)(meta & 0x1fffffffu) : 0;
+            const int pa = (int)(meta >> 31);
+            const bool was = ((meta >> 30) & 1u) != 0, rs = ((meta >> 29) & 1u) != 0;
+            const df g[3] = {df_make(A.g[0], A.g[1]), df_make(A.g[2], A.g[3]), df_make(A.g[4], A.g[5])};
+            RowState S;
+            S.dh = Bf.dh(pa)[e];
+            S.dl = Bf.dl(pa)[e];
+            S.pe = PE[e];
+            if (was) {
+                S.mh = Bf.Mh[e];
+                S.ml = Bf.Ml[e];
+                S.vh = Bf.Vh[e];
+                S.vl = Bf.Vl[e];
+            }
+            const df i1 = MULTI ? blk[b].ibc1 : s_ibc1, i2 = MULTI ? blk[b].ibc2 : s_ibc2;
+            adam_core(e, g, S, was, was ? ACT_ON : (uint8_t)0, Bf.act, i1, i2, rs, CB[b], Bf.dh(pa ^ 1),
+                      Bf.dl(pa ^ 1), Bf.Mh, Bf.Ml, Bf.Vh, Bf.Vl, Bf.q(pa ^ 1));
+        }
+        ahead = (ahead + c) & (ACAP - 1);
+        an -= c;
+        __syncwarp();
+    };
+
+    // One loop, one place where Adam runs: a full warp's worth of waiting rows goes first;
+    // after the last item, whatever is left.
+    bool done = false;
+    // the next item is claimed one item ahead, so the claim's round trip overlaps a walk
+    unsigned long long nitm = 0;
+    if (lane == 0) nitm = atomicAdd(&gs->work, 1ull);
     for (;;) {
-        unsigned long long itm = 0;
-        if (lane == 0) itm = atomicAdd(&gs->work, 1ull);
-        const int64_t item = (int64_t)__shfl_sync(FULL, itm, 0);
-        if (item >= n_items) break;
+        if (an >= 32 || (done && an > 0)) {
+            adam_flush(min(an, 32));
+            continue;
+        }
+        if (done) break;
+        const int64_t item = (int64_t)__shfl_sync(FULL, nitm, 0);
+        if (lane == 0 && item < n_items) nitm = atomicAdd(&gs->work, 1ull);
+        if (item >= n_items) {
+            done = true;
+            continue;
+        }
 
-        // Edge range [ebase, ebase + VT): a light warp's rows' light edges (each with its
-        // row's slot), or one heavy chunk (slot 0).
-        int64_t e = -1;
-        bool own = false;            // this lane applies Adam to row e
-        bool upd = false, was = false;   // ... at this launch; the row had a gradient before
-        uint32_t VT = 0, ebase = 0;
-        int64_t chunk = -1;
-        float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
         // the item's block: iteration, buffers and screen constants (one block per item)
         int b = 0, tb = s_t;
         bool bstop = false;
@@ -727,52 +769,43 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
                 item_chunk = item - n_light_warps;
             }
         }
+        const int pa = tb & 1;
+
+        // Edge range [ebase, ebase + VT) of the edge array: the light edges of the item's
+        // rows (each with its row's slot), or one heavy chunk (slot 0).  rbase: the row of
+        // slot 0.
+        int64_t rbase = r0, chunk = -1;
+        bool upd = false, was = false;   // the lane's row takes an update at this launch; had a gradient
+        uint32_t VT = 0;
+        unsigned long long ebase = 0;
+        float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!heavy_warp) {
-            e = r0 + lane;
             const bool have = lane < cnt;
-            uint32_t deg = 0;
+            uint8_t av = 0;
             if (have) {
-                deg = row_ptr[e + 1] - row_ptr[e];
-                qe = Bf.q(tb & 1)[e];
-                T.row[lane] = e;
+                const int64_t e = r0 + lane;
+                av = Bf.act[e];
+                qe = Bf.q(pa)[e];
                 T.q[lane] = qe;
             }
-            own = have && !bstop && deg <= HEAVY;
-            // the row's Adam state travels to shared memory while the edges are walked
+            const bool own = have && !bstop && !(av & ACT_HEAVY);
             upd = own && !is_last(CB[b], tb);
-            if (upd) {
-                const int pa = tb & 1;
-                was = Bf.act[e] != 0;
-                cp_async16(&T.st[0][lane], Bf.dh(pa) + e);
-                cp_async16(&T.st[1][lane], Bf.dl(pa) + e);
-                cp_async16(&T.st[2][lane], PE + e);
-                if (was) {
-                    cp_async16(&T.st[3][lane], Bf.Mh + e);
-                    cp_async16(&T.st[4][lane], Bf.Ml + e);
-                    cp_async16(&T.st[5][lane], Bf.Vh + e);
-                    cp_async16(&T.st[6][lane], Bf.Vl + e);
-                }
-            }
-            cp_async_commit();
-            uint32_t lb = 0, le = 0;
+            was = (av & ACT_ON) != 0;
+            unsigned long long lb = 0, le = 0;
             if (lane == 0) {
                 lb = LP.ptr[r0];
                 le = LP.ptr[r0 + cnt];
             }
             ebase = __shfl_sync(FULL, lb, 0);
-            VT = bstop ? 0u : __shfl_sync(FULL, le, 0) - ebase;
+            VT = bstop ? 0u : (uint32_t)(__shfl_sync(FULL, le, 0) - ebase);
         } else {
             chunk = item_chunk;
             const uint32_t row = H.chunk_row[chunk];
             ebase = H.chunk_start[chunk];
-            const uint32_t rend = row_ptr[row + 1];
-            VT = bstop ? 0u : min(HEAVY, rend - ebase);
-            e = row;
-            qe = Bf.q(tb & 1)[row];
-            if (lane == 0) {
-                T.row[0] = row;
-                T.q[0] = qe;
-            }
+            VT = bstop ? 0u : H.chunk_len[chunk];
+            rbase = row;
+            qe = Bf.q(pa)[row];
+            if (lane == 0) T.q[0] = qe;
         }
         __syncwarp();
         const PgdConsts &Cl = CB[b];            // the item's block
@@ -784,32 +817,39 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
         const bool in_ok = Cl.interior_ok != 0 &&
                            (!row_lane || (qe.x >= Cl.ilo[0] && qe.x <= Cl.ihi[0] && qe.y >= Cl.ilo[1] &&
                                           qe.y <= Cl.ihi[1] && qe.z >= Cl.ilo[2] && qe.z <= Cl.ihi[2]));
-        const int per_l = (Cl.periodic != 0 && !__all_sync(FULL, in_ok)) ? 1 : 0;
+        const bool pp = Cl.periodic != 0 && !__all_sync(FULL, in_ok);
         const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
+        const float4 *Qc = Bf.q(pa);
+        const float4 *Dh = Bf.dh(pa), *Dl = Bf.dl(pa);
 
         df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of the lane's row
         bool rv = false;             // the lane's row has a violated pair
-        int qn = 0;
+        int qh = 0, qn = 0;          // uncertain-pair ring: first entry, entries waiting
 
-        auto batch = [&](int cnt) {
-            const bool valid = lane < cnt;
+        // Evaluates the first min(qn, 32) queued pairs and adds each violated pair's term
+        // to its row's gradient.
+        auto batch = [&]() {
+            const int c = min(qn, 32);
+            const bool valid = lane < c;
             int s = 32;
             df gt[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
             bool hit = false;
             if (valid) {
-                const uint32_t k = T.qk[lane];
-                s = T.qs[lane] & 0x1f;
-                const int ti = MT ? (T.qs[lane] >> 5) & 3 : 0;
-                const bool link = (T.qs[lane] >> 7) != 0;
-                const int64_t er = T.row[s];
-                const float4 *Dh = Bf.dh(tb & 1), *Dl = Bf.dl(tb & 1);
-                double lt = 0.0;
+                const int pos = (qh + lane) & (QCAP - 1);
+                const uint32_t k = T.qk[pos];
+                const uint32_t qsv = T.qs[pos];
+                s = (int)(qsv & 0x1fu);
+                const int ti = MT ? (int)((qsv >> 5) & 3u) : 0;
+                const bool link = (qsv >> 7) != 0;
+                const int64_t er = rbase + s;
+                double ltv = 0.0;
                 bool counts = false;
-                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, ti, PE, Dh, Dl, Cl, gt, lt, counts);
+                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, ti, PE, Dh, Dl, Cl, gt, ltv, counts);
                 if (hit) {
-                    lfx += (unsigned long long)llrint(lt);
-                    viol += ((int64_t)k > er && counts) ? 1ull : 0ull;
+                    lfx += (unsigned long long)llrint(ltv);
+                    viol += ((int64_t)k > er && counts) ? 1u : 0u;
                 }
+                ++nev;
             }
             // Each row adds its violated pairs one by one in edge order (queue order is
             // edge order).  The row's owner is lane `slot` (light) or lane 0 (heavy: slot 0):
@@ -834,26 +874,17 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
                 for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], df_make(T.gt[2 * a][i], T.gt[2 * a + 1][i]));
                 rv = true;
             }
+            qh = (qh + c) & (QCAP - 1);
+            qn -= c;
             __syncwarp();
         };
 
-        auto enqueue = [&](bool need, uint32_t cv, int s) {
-            const unsigned bal = __ballot_sync(FULL, need);
-            if (need) {
-                const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-                T.qk[pos] = cv & PMASK;
-                T.qs[pos] = (uint8_t)(s | (MT ? ((cv >> 29) & 3u) << 5 : 0u) | ((cv >> 31) ? 0x80 : 0));
-            }
-            qn += __popc(bal);
-        };
-        // float32 screen of one edge of row slot s against partner k
-        const float4 *Qc = Bf.q(tb & 1);
+        // float32 screen of one edge of row slot s against partner cv: true when the pair
+        // may be violated (the double-float evaluation decides)
         auto screen = [&](bool ok, int s, uint32_t cv) -> bool {
             if (!ok) return false;
             const float4 qr = T.q[s];
-            const uint32_t k = cv & PMASK;
-            const float4 qk = Qc[k];
-            const bool pp = per_l != 0;
+            const float4 qk = Qc[cv & PMASK];
             const float d2 =
                 cdist2(cdiff(qr.x, qk.x, pp, L0), cdiff(qr.y, qk.y, pp, L1), cdiff(qr.z, qk.z, pp, L2));
             if (MT) {
@@ -862,79 +893,99 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
             }
             return (cv >> 31) ? !(d2 < sl_link) : !(d2 > sl_non);
         };
-        const uint32_t *ecol = heavy_warp ? col : LP.col;
-        // two edges per lane per trip: both partner loads are in flight before either is used
-        for (uint32_t base = 0; base < VT; base += 64) {
-            const uint32_t v0 = base + lane, v1 = base + 32 + lane;
-            const bool ok0 = v0 < VT, ok1 = v1 < VT;
-            const uint32_t t0 = ebase + v0, t1 = ebase + v1;
-            const uint32_t c0v = ok0 ? ecol[t0] : 0u, c1v = ok1 ? ecol[t1] : 0u;
-            const int s0 = (ok0 && !heavy_warp) ? (int)LP.slot[t0] : 0;
-            const int s1 = (ok1 && !heavy_warp) ? (int)LP.slot[t1] : 0;
-            const bool n0 = screen(ok0, s0, c0v);
-            const bool n1 = screen(ok1, s1, c1v);
-            enqueue(n0, c0v, s0);
-            enqueue(n1, c1v, s1);
-            __syncwarp();
-            while (qn >= 32) {
-                batch(32);
-                uint32_t mk[2] = {0u, 0u};
-                uint8_t ms[2] = {0, 0};
+
+        const uint32_t *__restrict__ ecol = LP.col + ebase;
+        const uint8_t *__restrict__ eslot = LP.slot + ebase;
+        // software pipeline: the columns and slots of the next trip are loaded before this
+        // trip's partner positions are gathered, so each trip waits on one round trip
+        uint32_t cvn[EPL];
+        int sln[EPL];
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (lane + 32 * h < qn - 32) {
-                        mk[h] = T.qk[32 + lane + 32 * h];
-                        ms[h] = T.qs[32 + lane + 32 * h];
-                    }
-                __syncwarp();
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (lane + 32 * h < qn - 32) {
-                        T.qk[lane + 32 * h] = mk[h];
-                        T.qs[lane + 32 * h] = ms[h];
-                    }
-                qn -= 32;
-                __syncwarp();
-            }
+        for (int j = 0; j < EPL; ++j) {
+            const uint32_t v = 32u * j + lane;
+            cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
+            sln[j] = (v < VT && !heavy_warp) ? (int)__ldcs(eslot + v) : 0;
         }
-        if (qn > 0) batch(qn);
+        for (uint32_t base = 0; base < VT; base += 32 * EPL) {
+            uint32_t cv[EPL];
+            int sl[EPL];
+            bool nd[EPL];
+#pragma unroll
+            for (int j = 0; j < EPL; ++j) {
+                nd[j] = base + 32u * j + lane < VT;
+                cv[j] = cvn[j];
+                sl[j] = sln[j];
+                const uint32_t v = base + 32u * (EPL + j) + lane;
+                cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
+                sln[j] = (v < VT && !heavy_warp) ? (int)__ldcs(eslot + v) : 0;
+            }
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < EPL; ++j) {
+                nd[j] = screen(nd[j], sl[j], cv[j]);
+                any |= nd[j];
+            }
+            if (!__any_sync(FULL, any)) continue;
+#pragma unroll
+            for (int j = 0; j < EPL; ++j) {
+                const unsigned bal = __ballot_sync(FULL, nd[j]);
+                if (nd[j]) {
+                    const int pos = (qh + qn + __popc(bal & lt_mask)) & (QCAP - 1);
+                    T.qk[pos] = cv[j] & PMASK;
+                    T.qs[pos] = (uint8_t)(sl[j] | (MT ? ((cv[j] >> 29) & 3u) << 5 : 0u) | ((cv[j] >> 31) ? 0x80 : 0));
+                }
+                qn += __popc(bal);
+            }
+            __syncwarp();
+            while (qn >= 32) batch();
+        }
+        while (qn > 0) batch();
 
         if (!heavy_warp) {
-            cp_async_wait_all();
+            // rows whose update is due join the Adam ring; a full warp's worth is applied
+            bool need = false, rs = false;
             if (upd) {
-                const df i1 = MULTI ? blk[b].ibc1 : s_ibc1, i2 = MULTI ? blk[b].ibc2 : s_ibc2;
-                const bool rs = rv && (MULTI ? blk[b].reset != 0 : s_reset != 0);
-                const int pa = tb & 1;
-                RowState S;
-                S.dh = T.st[0][lane];
-                S.dl = T.st[1][lane];
-                S.pe = T.st[2][lane];
-                if (was) {
-                    S.mh = T.st[3][lane];
-                    S.ml = T.st[4][lane];
-                    S.vh = T.st[5][lane];
-                    S.vl = T.st[6][lane];
-                }
-                adam_core(e, g, S, was, Bf.act, i1, i2, rs, Cl, Bf.dh(pa ^ 1), Bf.dl(pa ^ 1), Bf.Mh, Bf.Ml, Bf.Vh,
-                          Bf.Vl, Bf.q(pa ^ 1));
+                rs = rv && (MULTI ? blk[b].reset != 0 : s_reset != 0);
+                const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
+                need = was || !gz || rs;
             }
+            const unsigned bal = __ballot_sync(FULL, need);
+            if (need) {
+                AdamEnt &A = T.aq[(ahead + an + __popc(bal & lt_mask)) & (ACAP - 1)];
+                A.e = (uint32_t)(r0 + lane);
+                A.meta = (MULTI ? (uint32_t)b : 0u) | ((uint32_t)pa << 31) | ((uint32_t)was << 30) |
+                         ((uint32_t)rs << 29);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    A.g[2 * a] = g[a].hi;
+                    A.g[2 * a + 1] = g[a].lo;
+                }
+            }
+            const int nn = __popc(bal);
+            an += nn;
+            if (!MULTI) nupd += (lane == 0) ? (unsigned)nn : 0u;
+            __syncwarp();
+            if (MULTI && lane == 0 && nn) atomicAdd(&blk[b].uacc, (unsigned long long)nn);
         } else if (lane == 0 && !bstop) {
             H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, rv ? 1.f : 0.f);
             H.chunk_g[2 * chunk + 1] = make_float4(g[0].lo, g[1].lo, g[2].lo, 0.f);
         }
         if (MULTI) {
-            // the item's loss and violations belong to its block
-            const unsigned long long il = warp_sum_u(lfx), iv = warp_sum_u(viol);
+            // the item's loss, violations and evaluations belong to its block
+            const unsigned long long il = warp_sum_u(lfx), iv = __reduce_add_sync(FULL, viol),
+                                     ie = __reduce_add_sync(FULL, nev);
             if (lane == 0 && !bstop) {
                 if (il) atomicAdd(&blk[b].lfx, il);
                 if (iv) atomicAdd(&blk[b].vacc, iv);
+                if (ie) atomicAdd(&blk[b].eacc, ie);
             }
             lfx = 0;
             viol = 0;
+            nev = 0;
         }
         __syncwarp();
     }   // work items
-    finish_iteration<MULTI>(br, lfx, viol, CB, nb, blk, gs, hist_loss, hist_viol, wt);
+    finish_iteration<MULTI>(br, lfx, viol, nupd, nev, CB, nb, blk, gs, hist_loss, hist_viol, wt);
 }
 
 // Heavy rows: sum the chunk partials in chunk order and apply Adam (same update as
@@ -942,11 +993,11 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
 __global__ void k_pgd_heavy(const uint32_t *__restrict__ hrow, const uint32_t *__restrict__ hc0, int64_t nh,
                             const float4 *__restrict__ chunk_g, const float4 *__restrict__ PE,
                             const uint32_t *__restrict__ rb, PgdBufs Bf, const PgdConsts *__restrict__ CB,
-                            const PgdBlk *__restrict__ blk) {
+                            PgdBlk *blk) {
     GRID_STRIDE(i, nh) {
         const uint32_t e = hrow[i];
         const int b = (int)rb[e];
-        const PgdBlk &B = blk[b];
+        PgdBlk &B = blk[b];
         if (!B.upd_on) continue;
         const int pa = B.upd_t & 1;
         df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
@@ -958,63 +1009,91 @@ __global__ void k_pgd_heavy(const uint32_t *__restrict__ hrow, const uint32_t *_
             g[1] = df_add(g[1], df_make(h.y, l.y));
             g[2] = df_add(g[2], df_make(h.z, l.z));
         }
-        adam_row(e, g, Bf.dh(pa), Bf.dl(pa), PE, Bf.act, B.upd_ibc1, B.upd_ibc2, rv && B.upd_reset != 0, CB[b],
-                 Bf.dh(pa ^ 1),
+        const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
+        const bool rs = rv && B.upd_reset != 0;
+        if ((Bf.act[e] & ACT_ON) || !gz || rs) atomicAdd(&B.n_upd, 1ull);
+        adam_row(e, g, Bf.dh(pa), Bf.dl(pa), PE, Bf.act, B.upd_ibc1, B.upd_ibc2, rs, CB[b], Bf.dh(pa ^ 1),
                  Bf.dl(pa ^ 1), Bf.Mh, Bf.Ml, Bf.Vh, Bf.Vl, Bf.q(pa ^ 1));
     }
 }
 
-// CSR-side plan of the heavy rows: chunk counts, row list, chunk list.
-__global__ void k_heavy_count(const uint32_t *__restrict__ row_ptr, int64_t ne, uint32_t *__restrict__ nchunk,
-                              uint32_t *__restrict__ isheavy) {
+// ------------------------------------------------------------------ edge plan
+// Degrees from the CSR offsets: light degree (0 for a heavy row), heavy degree, chunk
+// count and heavy flag of every row; the heavy bit also goes into act.
+__global__ void k_degrees(const unsigned long long *__restrict__ row_ptr, int64_t ne,
+                          unsigned long long *__restrict__ ldeg, unsigned long long *__restrict__ hdeg,
+                          uint32_t *__restrict__ nchunk, uint32_t *__restrict__ isheavy, uint8_t *__restrict__ act) {
     GRID_STRIDE(e, ne) {
-        const uint32_t d = row_ptr[e + 1] - row_ptr[e];
+        const unsigned long long d = row_ptr[e + 1] - row_ptr[e];
         const bool h = d > HEAVY;
-        nchunk[e] = h ? (d + HEAVY - 1) / HEAVY : 0u;
+        ldeg[e] = h ? 0ull : d;
+        hdeg[e] = h ? d : 0ull;
+        nchunk[e] = h ? (uint32_t)((d + HEAVY - 1) / HEAVY) : 0u;
         isheavy[e] = h ? 1u : 0u;
+        if (h) act[e] = (uint8_t)(act[e] | ACT_HEAVY);
     }
 }
 
-__global__ void k_heavy_fill(const uint32_t *__restrict__ row_ptr, int64_t ne, const uint32_t *__restrict__ nchunk,
+// Squared linking lengths of the thresholds of a multi-threshold problem (float32).
+struct ThrB2 {
+    float b2[MAX_THR];
+};
+
+// One CSR entry per directed edge t (sorted keys: row, partner position, threshold
+// index): partner's dense index, threshold index and the link flag at the pair's own
+// linking length, written to the row's place in the edge array (light rows: their
+// group's range, with the row's slot; heavy rows: after every light edge).
+__global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, int nb, int tb, ThrB2 tb2,
+                       const unsigned long long *__restrict__ row_ptr, const unsigned long long *__restrict__ lptr,
+                       const unsigned long long *__restrict__ hptr, unsigned long long n_light,
+                       const uint32_t *__restrict__ dense, const uint32_t *__restrict__ epos,
+                       const uint32_t *__restrict__ rb, const int64_t *__restrict__ roff,
+                       const float4 *__restrict__ P4, const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
+                       int nblk, uint32_t *__restrict__ ecol, uint8_t *__restrict__ eslot) {
+    const unsigned long long mask = (1ull << nb) - 1ull;
+    GRID_STRIDE(t, m) {
+        const unsigned long long k = keys[t];
+        const uint32_t ti = (uint32_t)(k & ((1ull << tb) - 1ull));
+        const uint32_t row = (uint32_t)(k >> (nb + tb)), nbp = (uint32_t)((k >> tb) & mask);
+        const uint32_t pos = epos[row];
+        const BlockDev &B = bt[find_block(off, nblk, pos)];
+        const float4 p = P4[pos], q = P4[nbp];
+        const float3 d = canon_dp(p, q, B.periodic, B.L);
+        // the link flag at the pair's own linking length
+        const float b2 = tb ? (ti == 0 ? tb2.b2[0] : ti == 1 ? tb2.b2[1] : ti == 2 ? tb2.b2[2] : tb2.b2[3]) : B.b2;
+        const bool link = cdist2(d.x, d.y, d.z) <= b2;
+        const uint32_t cv = dense[nbp] | (ti << 29) | (link ? 0x80000000u : 0u);
+        const unsigned long long r_lo = row_ptr[row], j = (unsigned long long)t - r_lo;
+        if (row_ptr[row + 1] - r_lo > HEAVY) {
+            ecol[n_light + hptr[row] + j] = cv;
+        } else {
+            const unsigned long long dst = lptr[row] + j;
+            const int64_t r0 = roff ? roff[rb[row]] : 0;
+            ecol[dst] = cv;
+            eslot[dst] = (uint8_t)(((int64_t)row - r0) & 31);
+        }
+    }
+}
+
+// Heavy rows: the chunks (row, first edge, length) and the per-row chunk ranges.
+__global__ void k_heavy_fill(const unsigned long long *__restrict__ hdeg, const unsigned long long *__restrict__ hptr,
+                             unsigned long long n_light, int64_t ne, const uint32_t *__restrict__ nchunk,
                              const uint32_t *__restrict__ c0, const uint32_t *__restrict__ isheavy,
                              const uint32_t *__restrict__ hpos, uint32_t *__restrict__ chunk_row,
-                             uint32_t *__restrict__ chunk_start, uint32_t *__restrict__ hrow,
-                             uint32_t *__restrict__ hc0) {
+                             unsigned long long *__restrict__ chunk_start, uint32_t *__restrict__ chunk_len,
+                             uint32_t *__restrict__ hrow, uint32_t *__restrict__ hc0) {
     GRID_STRIDE(e, ne) {
         if (!isheavy[e]) continue;
         const uint32_t c = c0[e];
+        const unsigned long long d = hdeg[e];
         for (uint32_t j = 0; j < nchunk[e]; ++j) {
+            const unsigned long long s0 = (unsigned long long)j * HEAVY;
             chunk_row[c + j] = (uint32_t)e;
-            chunk_start[c + j] = row_ptr[e] + j * HEAVY;
+            chunk_start[c + j] = n_light + hptr[e] + s0;
+            chunk_len[c + j] = (uint32_t)min((unsigned long long)HEAVY, d - s0);
         }
         hrow[hpos[e]] = (uint32_t)e;
         hc0[hpos[e]] = c;
-    }
-}
-
-// Light edge plan: degrees of the light rows, then their edges with each row's slot in its
-// 32-row group (groups start at the first row of their block).
-__global__ void k_light_deg(const uint32_t *__restrict__ row_ptr, int64_t ne, uint32_t *__restrict__ ldeg) {
-    GRID_STRIDE(e, ne) {
-        const uint32_t d = row_ptr[e + 1] - row_ptr[e];
-        ldeg[e] = d <= HEAVY ? d : 0u;
-    }
-}
-
-__global__ void k_light_fill(const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
-                             const uint32_t *__restrict__ lptr, int64_t ne, const uint32_t *__restrict__ rb,
-                             const int64_t *__restrict__ roff, uint32_t *__restrict__ lcol,
-                             uint8_t *__restrict__ lslot) {
-    GRID_STRIDE(e, ne) {
-        const uint32_t a = row_ptr[e], d = row_ptr[e + 1] - a;
-        if (d > HEAVY) continue;
-        const int64_t r0 = roff ? roff[rb[e]] : 0;
-        const uint8_t sl = (uint8_t)((e - r0) & 31);
-        const uint32_t o = lptr[e];
-        for (uint32_t k = 0; k < d; ++k) {
-            lcol[o + k] = col[a + k];
-            lslot[o + k] = sl;
-        }
     }
 }
 
@@ -1144,8 +1223,9 @@ struct PgdSolver::Impl {
     DBuf<PgdConsts> CB;
     DBuf<PgdBlk> blk;
     DBuf<PgdGlobal> gs;
-    DBuf<uint32_t> row_ptr, col, rb, chunk_row, chunk_start, hrow, hc0, lptr, lcol;
-    DBuf<uint8_t> lslot;
+    DBuf<uint32_t> rb, chunk_row, chunk_len, hrow, hc0, ecol;
+    DBuf<unsigned long long> lptr, chunk_start;
+    DBuf<uint8_t> eslot;
     LightPlan LP{};
     DBuf<float4> PE, Dh0, Dl0, Dh1, Dl1, Mh, Ml, Vh, Vl, Q0, Q1, chunk_g;
     DBuf<uint8_t> act;
@@ -1170,14 +1250,14 @@ struct PgdSolver::Impl {
 
     void launch_iter() {
         if (mt)
-            k_pgd_iter<false, true><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb,
-                                                                 blk.p, gs.p, wt, hist_loss, hist_viol);
+            k_pgd_iter<false, true><<<nblk, PGD_THREADS, 0, s>>>(PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p, gs.p, wt,
+                                                                 hist_loss, hist_viol);
         else if (nb == 1)
-            k_pgd_iter<false, false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb,
-                                                                  blk.p, gs.p, wt, hist_loss, hist_viol);
+            k_pgd_iter<false, false><<<nblk, PGD_THREADS, 0, s>>>(PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p, gs.p, wt,
+                                                                  hist_loss, hist_viol);
         else
-            k_pgd_iter<true, false><<<nblk, PGD_THREADS, 0, s>>>(row_ptr.p, col.p, PE.p, ne, Bf, HP, LP, CB.p, nb,
-                                                                 blk.p, gs.p, wt, nullptr, nullptr);
+            k_pgd_iter<true, false><<<nblk, PGD_THREADS, 0, s>>>(PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p, gs.p, wt,
+                                                                 nullptr, nullptr);
         PC_CHECK_LAUNCH();
         if (n_heavy > 0) {
             k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, rb.p, Bf, CB.p,
@@ -1261,20 +1341,17 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     k_epos<<<grid_for(n), 256, 0, s>>>(mark.p, dense.p, n, epos.p);
     PC_CHECK_LAUNCH();
     mark.release();
+    // directed edges sorted by (row, partner position, threshold index); 64-bit offsets
     const int64_t m = 2 * nA;
     DBuf<unsigned long long> keys(m, s);
     k_dir_keys<<<grid_for(nA), 256, 0, s>>>(A, I.mt ? thr->Athr : nullptr, nA, dense.p, nbits, tb, keys.p);
     PC_CHECK_LAUNCH();
     radix_sort_u64((uint64_t *)keys.p, nullptr, m, nbits + tb + std::max(1, ceil_log2((uint64_t)ne)), s);
-    I.row_ptr.alloc(ne + 1, s);
-    I.col.alloc(m, s);
-    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbits + tb, ne, I.row_ptr.p);
+    DBuf<unsigned long long> row_ptr(ne + 1, s);
+    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbits + tb, ne, row_ptr.p);
     PC_CHECK_LAUNCH();
-    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbits, tb, tb2, dense.p, epos.p, B.P4.p, S.dev.p, S.doff.p, nb,
-                                       I.col.p);
-    PC_CHECK_LAUNCH();
-    keys.release();
-    dense.release();
+
+    // ---- iteration state
     for (DBuf<float4> *d : {&I.PE, &I.Dh0, &I.Dl0, &I.Dh1, &I.Dl1, &I.Mh, &I.Ml, &I.Vh, &I.Vl, &I.Q0, &I.Q1})
         d->alloc(ne, s);
     I.act.alloc(ne, s);
@@ -1285,7 +1362,6 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
                                               I.Dh0.p, I.Dl0.p, I.Dh1.p, I.Dl1.p, I.Q0.p, I.Q1.p, I.Mh.p, I.Ml.p,
                                               I.Vh.p, I.Vl.p, I.act.p, rows_pb.p);
     PC_CHECK_LAUNCH();
-    epos.release();
     // rows per block -> row offsets (rows are in sorted-position order, blocks own contiguous ranges)
     const unsigned long long *rows =
         (const unsigned long long *)read_back(hs, rows_pb.p, nb * sizeof(unsigned long long), s);
@@ -1302,49 +1378,51 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     Bf.Vh = I.Vh.p;
     Bf.Vl = I.Vl.p;
     Bf.act = I.act.p;
-
-    // heavy rows (more than HEAVY partners) are split into chunks of HEAVY edges
-    DBuf<uint32_t> nchunk(ne, s), isheavy(ne, s), c0(ne, s), hpos(ne, s), tot2(2, s);
-    k_heavy_count<<<grid_for(ne), 256, 0, s>>>(I.row_ptr.p, ne, nchunk.p, isheavy.p);
-    PC_CHECK_LAUNCH();
-    scan_exclusive_u32(nchunk.p, c0.p, ne, tot2.p, s);
-    scan_exclusive_u32(isheavy.p, hpos.p, ne, tot2.p + 1, s);
-    uint32_t tots[2];
-    memcpy(tots, read_back(hs, tot2.p, 2 * sizeof(uint32_t), s), sizeof(tots));
-    const int64_t n_chunks = tots[0];
-    I.n_heavy = tots[1];
-    I.chunk_row.alloc(n_chunks, s);
-    I.chunk_start.alloc(n_chunks, s);
-    I.hrow.alloc(I.n_heavy, s);
-    I.hc0.alloc(I.n_heavy + 1, s);
-    I.chunk_g.alloc(2 * n_chunks, s);
-    if (I.n_heavy > 0) {
-        k_heavy_fill<<<grid_for(ne), 256, 0, s>>>(I.row_ptr.p, ne, nchunk.p, c0.p, isheavy.p, hpos.p, I.chunk_row.p,
-                                                  I.chunk_start.p, I.hrow.p, I.hc0.p);
-        PC_CHECK_LAUNCH();
-        PC_CUDA(cudaMemcpyAsync(I.hc0.p + I.n_heavy, tot2.p, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-    }
-    I.kernels_per_iter = I.n_heavy > 0 ? 2 : 1;
     DBuf<int64_t> roff;
     if (nb > 1) {
         roff.alloc(nb + 1, s);
         PC_CUDA(cudaMemcpyAsync(roff.p, I.row_off.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     }
-    // light edge plan
-    {
-        DBuf<uint32_t> ldeg(ne, s);
-        I.lptr.alloc(ne + 1, s);
-        k_light_deg<<<grid_for(ne), 256, 0, s>>>(I.row_ptr.p, ne, ldeg.p);
+
+    // ---- edge plan: light rows' edges in row order, then heavy rows' (chunks of HEAVY)
+    DBuf<unsigned long long> ldeg(ne, s), hdeg(ne, s), hptr(ne + 1, s), tot64(2, s);
+    DBuf<uint32_t> nchunk(ne, s), isheavy(ne, s), c0(ne, s), hpos(ne, s), tot2(2, s);
+    k_degrees<<<grid_for(ne), 256, 0, s>>>(row_ptr.p, ne, ldeg.p, hdeg.p, nchunk.p, isheavy.p, I.act.p);
+    PC_CHECK_LAUNCH();
+    I.lptr.alloc(ne + 1, s);
+    scan_exclusive_u64((const uint64_t *)ldeg.p, (uint64_t *)I.lptr.p, ne, (uint64_t *)(I.lptr.p + ne), s);
+    scan_exclusive_u64((const uint64_t *)hdeg.p, (uint64_t *)hptr.p, ne, (uint64_t *)tot64.p, s);
+    scan_exclusive_u32(nchunk.p, c0.p, ne, tot2.p, s);
+    scan_exclusive_u32(isheavy.p, hpos.p, ne, tot2.p + 1, s);
+    ldeg.release();
+    uint32_t tots[2];
+    memcpy(tots, read_back(hs, tot2.p, 2 * sizeof(uint32_t), s), sizeof(tots));
+    const unsigned long long n_light = *(const unsigned long long *)read_back(hs, I.lptr.p + ne, 8, s);
+    const int64_t n_chunks = tots[0];
+    I.n_heavy = tots[1];
+    I.ecol.alloc(std::max<int64_t>(1, m), s);
+    I.eslot.alloc(std::max<unsigned long long>(1, n_light), s);
+    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbits, tb, tb2, row_ptr.p, I.lptr.p, hptr.p, n_light, dense.p,
+                                       epos.p, I.rb.p, roff.p, B.P4.p, S.dev.p, S.doff.p, nb, I.ecol.p, I.eslot.p);
+    PC_CHECK_LAUNCH();
+    keys.release();
+    row_ptr.release();
+    dense.release();
+    epos.release();
+    I.chunk_row.alloc(n_chunks, s);
+    I.chunk_start.alloc(n_chunks, s);
+    I.chunk_len.alloc(n_chunks, s);
+    I.hrow.alloc(I.n_heavy, s);
+    I.hc0.alloc(I.n_heavy + 1, s);
+    I.chunk_g.alloc(2 * n_chunks, s);
+    if (I.n_heavy > 0) {
+        k_heavy_fill<<<grid_for(ne), 256, 0, s>>>(hdeg.p, hptr.p, n_light, ne, nchunk.p, c0.p, isheavy.p, hpos.p,
+                                                  I.chunk_row.p, I.chunk_start.p, I.chunk_len.p, I.hrow.p, I.hc0.p);
         PC_CHECK_LAUNCH();
-        scan_exclusive_u32(ldeg.p, I.lptr.p, ne, I.lptr.p + ne, s);
-        const uint32_t n_light = *(const uint32_t *)read_back(hs, I.lptr.p + ne, sizeof(uint32_t), s);
-        I.lcol.alloc(std::max<uint32_t>(1, n_light), s);
-        I.lslot.alloc(std::max<uint32_t>(1, n_light), s);
-        k_light_fill<<<grid_for(ne), 256, 0, s>>>(I.row_ptr.p, I.col.p, I.lptr.p, ne, I.rb.p, roff.p, I.lcol.p,
-                                                  I.lslot.p);
-        PC_CHECK_LAUNCH();
-        I.LP = LightPlan{I.lptr.p, I.lcol.p, I.lslot.p};
+        PC_CUDA(cudaMemcpyAsync(I.hc0.p + I.n_heavy, tot2.p, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     }
+    I.kernels_per_iter = I.n_heavy > 0 ? 2 : 1;
+    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.eslot.p};
     if (nb > 1) {
         // work table of the blocks still iterating (all of them before the first launch)
         I.bw.alloc(nb, s);
@@ -1355,11 +1433,12 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
         I.wt = WorkTab{I.bw.p, I.act_blk.p, I.act_pref.p};
         k_worktab_init<<<1, 32, 0, s>>>(nb, I.blk.p, I.wt, I.gs.p);
         PC_CHECK_LAUNCH();
-        PC_CUDA(cudaStreamSynchronize(s));   // roff is released on return
     }
+    PC_CUDA(cudaStreamSynchronize(s));   // roff and the plan temporaries are released on return
     I.HP.n_chunks = n_chunks;
     I.HP.chunk_row = I.chunk_row.p;
     I.HP.chunk_start = I.chunk_start.p;
+    I.HP.chunk_len = I.chunk_len.p;
     I.HP.chunk_g = I.chunk_g.p;
     const int64_t n_items = cdiv(ne, 32) + nb + n_chunks;
     I.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS), (int64_t)num_sms() * PGD_BLOCKS_PER_SM));
@@ -1505,6 +1584,9 @@ void PgdSolver::results(std::vector<PgdResult> &out) {
         r.loss_final = hb[b].loss;
         r.converged = hb[b].converged != 0;
         r.n_editable = I.row_off[b + 1] - I.row_off[b];
+        r.resets = hb[b].resets;
+        r.row_updates = (int64_t)hb[b].n_upd;
+        r.pair_evals = (int64_t)hb[b].n_eval;
     }
 }
 
@@ -1525,6 +1607,9 @@ void PgdSolver::block_result(int b, PgdResult &r) const {
     r.loss_final = B.loss;
     r.converged = B.converged != 0;
     r.n_editable = I.row_off[b + 1] - I.row_off[b];
+    r.resets = B.resets;
+    r.row_updates = (int64_t)B.n_upd;
+    r.pair_evals = (int64_t)B.n_eval;
 }
 
 PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp, const float *orig,
@@ -1566,7 +1651,9 @@ PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp
                 set_error("PGD loop did not reach its stop decision");
                 throw Fail{PC_ETIMEOUT};
             }
-            chunk = std::min(chunk * 2, 256);
+            // the next poll comes after at most 32 launches: launches past every block's stop
+            // return at once, so a bounded overshoot costs little
+            chunk = std::min(chunk * 2, 32);
         }
     }
     PC_CUDA(cudaEventRecord(ev[2], s));

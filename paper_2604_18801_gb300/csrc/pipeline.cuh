@@ -94,7 +94,9 @@ void pair_pass_emit(const Binned &B, const BlockSet &S, const uint32_t *fof_lab,
                     unsigned long long *counts, uint32_t *err, cudaStream_t s);
 // Union-find helpers (labels = smallest id of the set)
 void uf_init(uint32_t *par, int64_t n, cudaStream_t s);
-void uf_flatten(uint32_t *par, int64_t n, cudaStream_t s);
+// Rewrites par so every entry holds its root; a root walk that exceeds its bound sets
+// ERR_UF_RETRY in *err (device).
+void uf_flatten(uint32_t *par, int64_t n, uint32_t *err, cudaStream_t s);
 
 // ---------------------------------------------------------------- selection (select.cu)
 // HF spanning forest: Boruvka on safe-component supernodes over candidate links C
@@ -112,6 +114,9 @@ struct PgdResult {       // per block
     int64_t iters = 0, loss_evals = 0, viol0 = 0, viol_final = 0, n_editable = 0;
     double loss0 = 0, loss_final = 0;
     bool converged = false;
+    int64_t resets = 0;        // checks that triggered a stall reset
+    int64_t row_updates = 0;   // Adam steps applied, summed over the updates
+    int64_t pair_evals = 0;    // pairs evaluated in double-float (both directions), summed over the checks
 };
 struct PgdRun {
     std::vector<PgdResult> blocks;

@@ -134,8 +134,8 @@ constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_WARPS = RS_THREADS / 32;
 
-template <class K>
-__global__ void k_rs_hist(const K *__restrict__ keys, int64_t n, int shift, uint32_t *__restrict__ hist,
+template <class K, class O>
+__global__ void k_rs_hist(const K *__restrict__ keys, int64_t n, int shift, O *__restrict__ hist,
                           int64_t ntiles) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
@@ -150,12 +150,13 @@ __global__ void k_rs_hist(const K *__restrict__ keys, int64_t n, int shift, uint
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-template <class K, bool HAS_V>
+// O: type of the output positions (32-bit below 2^32 elements, else 64-bit).
+template <class K, bool HAS_V, class O>
 __global__ void k_rs_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
                              uint32_t *__restrict__ vout, int64_t n, int shift,
-                             const uint32_t *__restrict__ off, int64_t ntiles) {
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t wc[RS_WARPS][256];
+                             const O *__restrict__ off, int64_t ntiles) {
+    __shared__ O run[256];
+    __shared__ O wc[RS_WARPS][256];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     run[tid] = off[(int64_t)tid * ntiles + blockIdx.x];
 #pragma unroll
@@ -171,13 +172,13 @@ __global__ void k_rs_scatter(const K *__restrict__ kin, const uint32_t *__restri
         const uint32_t d = valid ? ((uint32_t)(k >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int rank = __popc(peers & lt);
-        if (valid && rank == 0) wc[w][d] = __popc(peers);
+        if (valid && rank == 0) wc[w][d] = (O)__popc(peers);
         __syncthreads();
         {
-            uint32_t s = run[tid];
+            O s = run[tid];
 #pragma unroll
             for (int q = 0; q < RS_WARPS; ++q) {
-                const uint32_t c = wc[q][tid];
+                const O c = wc[q][tid];
                 wc[q][tid] = s;
                 s += c;
             }
@@ -185,7 +186,7 @@ __global__ void k_rs_scatter(const K *__restrict__ kin, const uint32_t *__restri
         }
         __syncthreads();
         if (valid) {
-            const uint32_t pos = wc[w][d] + (uint32_t)rank;
+            const O pos = wc[w][d] + (O)rank;
             kout[pos] = k;
             if (HAS_V) vout[pos] = v;
         }
@@ -196,29 +197,25 @@ __global__ void k_rs_scatter(const K *__restrict__ kin, const uint32_t *__restri
     }
 }
 
-template <class K>
-void radix_impl(K *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s) {
-    if (n <= 1 || bits <= 0) return;
-    if (n >= (int64_t)0xffffffffll) {
-        set_error("radix sort: more than 2^32-1 elements");
-        throw Fail{PC_EINVAL};
-    }
+template <class K, class O>
+void radix_passes(K *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s) {
     const int64_t ntiles = cdiv(n, RS_TILE);
     DBuf<K> k2(n, s);
     DBuf<uint32_t> v2(vals ? n : 0, s);
-    DBuf<uint32_t> hist(256 * ntiles, s);
+    DBuf<O> hist(256 * ntiles, s);
     K *ka = keys, *kb = k2.p;
     uint32_t *va = vals, *vb = v2.p;
     int passes = 0;
     for (int shift = 0; shift < bits; shift += 8, ++passes) {
-        k_rs_hist<K><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, n, shift, hist.p, ntiles);
+        k_rs_hist<K, O><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, n, shift, hist.p, ntiles);
         PC_CHECK_LAUNCH();
-        scan_impl<uint32_t>(hist.p, hist.p, 256 * ntiles, nullptr, s);
+        scan_impl<O>(hist.p, hist.p, 256 * ntiles, nullptr, s);
         if (vals)
-            k_rs_scatter<K, true><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, hist.p, ntiles);
+            k_rs_scatter<K, true, O><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, hist.p,
+                                                                             ntiles);
         else
-            k_rs_scatter<K, false><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, nullptr, kb, nullptr, n, shift, hist.p,
-                                                                          ntiles);
+            k_rs_scatter<K, false, O><<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, nullptr, kb, nullptr, n, shift,
+                                                                              hist.p, ntiles);
         PC_CHECK_LAUNCH();
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -227,6 +224,14 @@ void radix_impl(K *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s) {
         PC_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, s));
         if (vals) PC_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     }
+}
+
+template <class K>
+void radix_impl(K *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s) {
+    if (n <= 1 || bits <= 0) return;
+    // positions (histogram offsets) are 32-bit below 2^32 elements and 64-bit above
+    if (n < (int64_t)0xffffffffll) radix_passes<K, uint32_t>(keys, vals, n, bits, s);
+    else radix_passes<K, unsigned long long>(keys, vals, n, bits, s);
 }
 
 __global__ void k_fill_u32(uint32_t *p, uint32_t v, int64_t n) {
@@ -244,7 +249,8 @@ void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *
     scan_impl<uint32_t>(in, out, n, total_dev, s);
 }
 void scan_exclusive_u64(const uint64_t *in, uint64_t *out, int64_t n, uint64_t *total_dev, cudaStream_t s) {
-    scan_impl<uint64_t>(in, out, n, total_dev, s);
+    scan_impl<unsigned long long>((const unsigned long long *)in, (unsigned long long *)out, n,
+                                  (unsigned long long *)total_dev, s);
 }
 void radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, cudaStream_t s) {
     radix_impl<uint32_t>(keys, vals, n, bits, s);

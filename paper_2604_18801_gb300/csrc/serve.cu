@@ -254,6 +254,9 @@ void finish_job(pc_server *srv, Cohort &c, int b) {
     st.n_editable = r.n_editable;
     st.converged = r.converged ? 1 : 0;
     st.pgd_launches = c.launched;
+    st.resets = r.resets;
+    st.row_updates = r.row_updates;
+    st.pair_evals = r.pair_evals;
     if (sp.stream_dev) {
         j->res.stream_bytes = encode_edits(sp.recon_dev, sp.corrected_dev, sp.n, &sp.params, sp.stream_dev,
                                            sp.stream_cap, c.s, srv->hs_run);

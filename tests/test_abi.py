@@ -44,7 +44,7 @@ def test_struct_sizes_match_the_header():
     # pc_params: 2+3+3 doubles, 4 ints, 5 doubles, 4 ints
     assert C.sizeof(_native.Params) == 8 * 8 + 4 * 4 + 5 * 8 + 4 * 4
     assert C.sizeof(_native.SelectStats) == 10 * 8 + 8
-    assert C.sizeof(_native.CorrectStats) == 4 * 8 + 2 * 8 + 3 * 8 + 8 + 3 * 8 + 8
+    assert C.sizeof(_native.CorrectStats) == 4 * 8 + 2 * 8 + 3 * 8 + 8 + 3 * 8 + 8 + 3 * 8
 
 
 def test_struct_layouts_match_a_c_compiler(tmp_path):
@@ -58,7 +58,7 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
     checks = [("pc_params", _native.Params, ["b", "xi", "periodic", "t_max", "alpha_rel", "loss_tol", "replay_iters",
                                               "stall_patience", "cell_factor"]),
               ("pc_select_stats", _native.SelectStats, ["n_links", "ms"]),
-              ("pc_correct_stats", _native.CorrectStats, ["converged", "ms_setup", "pgd_launches"]),
+              ("pc_correct_stats", _native.CorrectStats, ["converged", "ms_setup", "pgd_launches", "resets", "pair_evals"]),
               ("pc_block", _native.Block, ["n", "params"]),
               ("pc_job", _native.Job, ["n", "params", "corrected_dev", "stream_cap"]),
               ("pc_job_result", _native.JobResult, ["done_ns", "stream_bytes", "cohort_jobs", "stats", "error"]),
