@@ -292,8 +292,10 @@ void bin_particles(const float *orig, const BlockSet &S, Binned &B, cudaStream_t
 
 // ======================================================================= union-find
 // Parent arrays keep par[x] <= x; the root of a set is its smallest id.
-__device__ __forceinline__ uint32_t uf_root(uint32_t *par, uint32_t x) {
-    for (int it = 0; it < (1 << 26); ++it) {   // a walk is at most n steps; the cap only guards a broken invariant
+// A walk takes at most n steps; the cap only guards a broken invariant, and reaching it sets
+// ERR_UF_RETRY in *err (the caller then fails with PC_ETIMEOUT instead of using the label).
+__device__ __forceinline__ uint32_t uf_root(uint32_t *par, uint32_t x, uint32_t *err) {
+    for (int it = 0; it < (1 << 26); ++it) {
         const uint32_t p = __ldcg(par + x);
         if (p == x) return x;
         const uint32_t g = __ldcg(par + p);
@@ -301,6 +303,7 @@ __device__ __forceinline__ uint32_t uf_root(uint32_t *par, uint32_t x) {
         __stcg(par + x, g);   // path halving; g is an ancestor of x, so any interleaving is safe
         x = g;                // strictly decreasing: terminates
     }
+    atomicOr(err, ERR_UF_RETRY);
     return x;
 }
 
@@ -308,8 +311,8 @@ constexpr int UF_RETRY_CAP = 1 << 22;
 
 __device__ __forceinline__ void uf_union(uint32_t *par, uint32_t a, uint32_t b, uint32_t *err) {
     for (int it = 0; it < UF_RETRY_CAP; ++it) {
-        a = uf_root(par, a);
-        b = uf_root(par, b);
+        a = uf_root(par, a, err);
+        b = uf_root(par, b, err);
         if (a == b) return;
         if (a > b) {
             const uint32_t t = a;
@@ -322,25 +325,25 @@ __device__ __forceinline__ void uf_union(uint32_t *par, uint32_t a, uint32_t b, 
 }
 
 namespace {
-__global__ void k_uf_flatten(uint32_t *par, int64_t n) {
+__global__ void k_uf_flatten(uint32_t *par, int64_t n, uint32_t *err) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        (void)uf_root(par, (uint32_t)i);
+        (void)uf_root(par, (uint32_t)i, err);
 }
-__global__ void k_uf_labels(uint32_t *par, int64_t n, uint32_t *lab) {
+__global__ void k_uf_labels(uint32_t *par, int64_t n, uint32_t *lab, uint32_t *err) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        lab[i] = uf_root(par, (uint32_t)i);
+        lab[i] = uf_root(par, (uint32_t)i, err);
 }
 }  // namespace
 
 void uf_init(uint32_t *par, int64_t n, cudaStream_t s) { iota_u32(par, n, s); }
 
 // Rewrites par so every entry holds its root (two sweeps: path halving, then roots into a copy).
-void uf_flatten(uint32_t *par, int64_t n, cudaStream_t s) {
+void uf_flatten(uint32_t *par, int64_t n, uint32_t *err, cudaStream_t s) {
     if (n <= 0) return;
-    k_uf_flatten<<<grid_for(n), 256, 0, s>>>(par, n);
+    k_uf_flatten<<<grid_for(n), 256, 0, s>>>(par, n, err);
     PC_CHECK_LAUNCH();
     DBuf<uint32_t> lab(n, s);
-    k_uf_labels<<<grid_for(n), 256, 0, s>>>(par, n, lab.p);
+    k_uf_labels<<<grid_for(n), 256, 0, s>>>(par, n, lab.p, err);
     PC_CHECK_LAUNCH();
     PC_CUDA(cudaMemcpyAsync(par, lab.p, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
 }
