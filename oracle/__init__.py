@@ -25,10 +25,11 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.cpp`` into ``liboracle.so`` (no fused multiply-add)."""
+    """Compile ``oracle.cpp`` into ``liboracle.so`` (no fused multiply-add; OpenMP, whose
+    thread count changes the speed and never the results)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
                "-shared", "-o", tmp, _SRC]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
@@ -62,7 +63,7 @@ class PgdStats(C.Structure):
 
 DEFAULTS = dict(b=1.0, xi=0.1, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), periodic=0,
                 mode=0, m_bits=16, t_max=10000, alpha_rel=0.2, beta1=0.9, beta2=0.999,
-                eps_rel=2e-6, loss_tol=0.0, replay_iters=-1, stall_patience=100)
+                eps_rel=2e-6, loss_tol=0.0, replay_iters=-1, stall_patience=0)
 
 
 def make_params(**kw) -> Params:
@@ -86,6 +87,8 @@ def lib():
                                            C.POINTER(C.c_uint8), C.POINTER(C.c_int32),
                                            C.POINTER(C.c_double))
             P = C.POINTER(Params)
+            L.or_threads.argtypes = [C.c_int32]
+            L.or_threads.restype = C.c_int32
             L.or_constants.argtypes = [P, f32p, f32p, C.c_int64, C.POINTER(Consts)]
             L.or_dist2.argtypes = [f32p, C.c_int64, C.c_int64, P]
             L.or_dist2.restype = C.c_float
@@ -113,6 +116,11 @@ def lib():
             L.or_count_flips.restype = C.c_int64
             _lib = L
     return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Sets the oracle's OpenMP thread count (n > 0) and returns the count in use."""
+    return int(lib().or_threads(int(n)))
 
 
 def _f32(a):

@@ -62,6 +62,10 @@
 //    clears its Adam moments instead of taking its Adam step; the other
 //    particles take their step.  The check after a reset starts a new best.
 //    stall_patience = 0 turns this off.
+//  * Threads.  Built with OpenMP, the pair search splits the particles among
+//    threads and sorts the pairs afterwards, the PGD computes each pair's terms
+//    independently and then sums them in pair order, and the Adam update takes
+//    each coordinate on its own: results are the same bits for any thread count.
 //  * Counting a violation.  A pair with violation v > 0 takes its loss term and
 //    gradient; it counts as violated (the count that stops the loop at eps_L = 0,
 //    and the stall rule's count) only when v > b * 2^-40.  Pairs held from both
@@ -74,6 +78,10 @@
 #include <cstring>
 #include <numeric>
 #include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 extern "C" {
 
@@ -243,7 +251,20 @@ std::vector<Pair> grid_pairs(const float *P, int64_t n, const or_params *p, cons
     for (int64_t k = 0; k < ncell; ++k) start[k + 1] += start[k];
     std::vector<int64_t> fill(start.begin(), start.end() - 1), member(n);
     for (int64_t i = 0; i < n; ++i) member[fill[cell[i]]++] = i;
+    // particles are split among threads; every thread keeps its own list, and the
+    // lists are joined and sorted below, so the result does not depend on the split
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    std::vector<std::vector<Pair>> part(nthr);
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        std::vector<Pair> &mine = part[tid];
         for (int oz = -1; oz <= 1; ++oz)
             for (int oy = -1; oy <= 1; ++oy)
                 for (int ox = -1; ox <= 1; ++ox) {
@@ -261,10 +282,11 @@ std::vector<Pair> grid_pairs(const float *P, int64_t n, const or_params *p, cons
                         int64_t j = member[t];
                         if (j <= i) continue;
                         int cls = classify(cdist2(P, i, j, p->periodic, c.L), c);
-                        if (cls != CLS_FAR) out.push_back({(uint32_t)i, (uint32_t)j, (uint8_t)cls});
+                        if (cls != CLS_FAR) mine.push_back({(uint32_t)i, (uint32_t)j, (uint8_t)cls});
                     }
                 }
     }
+    for (const std::vector<Pair> &q : part) out.insert(out.end(), q.begin(), q.end());
     std::sort(out.begin(), out.end(), [](const Pair &a, const Pair &b) {
         return a.i != b.i ? a.i < b.i : a.j < b.j;
     });
@@ -423,14 +445,15 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
         for (int d = 0; d < 3; ++d)
             delta[3 * e + d] = (double)recon[3 * E[e] + d] - (double)orig[3 * E[e] + d];
 
-    // Tight loss of Eq. 3 and (optionally) its gradient with respect to delta.
+    // Tight loss of Eq. 3 and (optionally) its gradient with respect to delta.  Each
+    // pair's violated amount and direction are computed on their own (on several
+    // threads when built with OpenMP); the loss, the counts and the gradient then add
+    // them in pair order, so the sums do not depend on the number of threads.
     const double inv_unit = 1.0 / (p->xi * p->xi * std::ldexp(1.0, -24));
     std::vector<uint8_t> hit(ne);   // editable particle is an endpoint of a violated pair
+    std::vector<double> vamt(na), dir(3 * na);
     auto evaluate = [&](bool want_grad, double *loss, int64_t *viol, int64_t *lfx) {
-        double L = 0.0;
-        int64_t nv = 0, fx = 0;
-        std::fill(hit.begin(), hit.end(), 0);
-        if (want_grad) std::fill(g.begin(), g.end(), 0.0);
+#pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < na; ++k) {
             const int64_t a = idx[A[k].i], b = idx[A[k].j];
             double r[3];
@@ -438,12 +461,8 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
             const double dh = norm3(r);
             // link: penalise d_hat > b - dt;  non-link: penalise d_hat < b + dt
             const double viol_amt = A[k].link ? dh - thr_link[k] : thr_non[k] - dh;
-            if (!(viol_amt > 0.0)) continue;
-            L += viol_amt * viol_amt;
-            if (viol_amt > vtol[k]) nv += 1;
-            fx += (int64_t)std::llrint(viol_amt * viol_amt * inv_unit);
-            hit[a] = hit[b] = 1;
-            if (!want_grad) continue;
+            vamt[k] = viol_amt;
+            if (!(viol_amt > 0.0) || !want_grad) continue;
             double u[3];
             if (dh > tau[k]) {
                 for (int d = 0; d < 3; ++d) u[d] = r[d] / dh;
@@ -452,11 +471,26 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
                                             dp[3 * k + 2] * dp[3 * k + 2]);
                 for (int d = 0; d < 3; ++d) u[d] = n0 > 0.0 ? dp[3 * k + d] / n0 : 0.0;
             }
+            for (int d = 0; d < 3; ++d) dir[3 * k + d] = u[d];
+        }
+        double L = 0.0;
+        int64_t nv = 0, fx = 0;
+        std::fill(hit.begin(), hit.end(), 0);
+        if (want_grad) std::fill(g.begin(), g.end(), 0.0);
+        for (int64_t k = 0; k < na; ++k) {
+            const double viol_amt = vamt[k];
+            if (!(viol_amt > 0.0)) continue;
+            const int64_t a = idx[A[k].i], b = idx[A[k].j];
+            L += viol_amt * viol_amt;
+            if (viol_amt > vtol[k]) nv += 1;
+            fx += (int64_t)std::llrint(viol_amt * viol_amt * inv_unit);
+            hit[a] = hit[b] = 1;
+            if (!want_grad) continue;
             // d/d(delta_i) of (d_hat - thr)^2 is 2 (d_hat - thr) r/|r|; of (thr - d_hat)^2 it is the negative
             const double s = A[k].link ? 2.0 * viol_amt : -2.0 * viol_amt;
             for (int d = 0; d < 3; ++d) {
-                g[3 * a + d] += s * u[d];
-                g[3 * b + d] -= s * u[d];
+                g[3 * a + d] += s * dir[3 * k + d];
+                g[3 * b + d] -= s * dir[3 * k + d];
             }
         }
         *loss = L;
@@ -494,6 +528,7 @@ void pgd(const float *orig, const float *recon, int64_t n, const std::vector<Act
         t += 1;
         b1t *= p->beta1;
         b2t *= p->beta2;
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < 3 * ne; ++q) {
             if (reset_now && hit[q / 3]) {
                 delta[q] = 0.0;
@@ -562,6 +597,17 @@ const int HEADER = 64;
 }  // namespace
 
 extern "C" {
+
+// Threads of the OpenMP build (1 without OpenMP); n <= 0 leaves the count as it is.
+int32_t or_threads(int32_t n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return (int32_t)omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 void or_constants(const or_params *p, const float *orig, const float *recon, int64_t n, or_consts *out) {
     *out = make_consts(p, orig, recon, n);
