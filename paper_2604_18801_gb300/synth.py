@@ -81,6 +81,7 @@ class Workload:
         p = dict(b=self.b, xi=self.xi, periodic=int(self.periodic),
                  box_lo=tuple(self.box_lo), box_hi=tuple(self.box_hi),
                  mode=MODES[self.mode])
+        p.update(self.aux.get("params", {}))   # solver settings this input is run with
         p.update(over)
         return p
 
@@ -170,7 +171,11 @@ def with_base(w: "Workload", base: str, cell_particles: int = 64) -> "Workload":
     vol = float(np.prod(np.asarray(w.box_hi, np.float64) - np.asarray(w.box_lo, np.float64)))
     cell = (vol * cell_particles / max(1, w.n)) ** (1.0 / 3.0)
     recon = morton_recon(w.orig, w.xi, cell, w.box_lo, w.box_hi)
-    return dataclasses.replace(w, recon=recon, name=w.name + "_morton")
+    # On this reconstruction plain Adam-PGD can settle in a local minimum of the
+    # non-convex loss (at eps = 0.5 b it does on the 32^3 HACC-shaped box and the fluid
+    # box); such inputs are run with the stall rule on (100 checks of patience).
+    aux = dict(w.aux, params=dict(w.aux.get("params", {}), stall_patience=100))
+    return dataclasses.replace(w, recon=recon, name=w.name + "_morton", aux=aux)
 
 
 def _wrap_unit(x: np.ndarray) -> np.ndarray:

@@ -295,7 +295,7 @@ def test_stall_reset_escapes_a_local_minimum():
     w = synth.hacc_box(eps_over_b=0.5, mode="HF", seed=3004, n=1915)
     stuck, st0 = oracle.correct(w.orig, w.recon, **w.params(stall_patience=0, t_max=3000))
     assert st0["converged"] == 0 and st0["viol_final"] >= 1
-    corr, st = oracle.correct(w.orig, w.recon, **w.params())
+    corr, st = oracle.correct(w.orig, w.recon, **w.params(stall_patience=100))
     assert st["converged"] == 1 and st["iters"] < 1000
     kw = w.params()
     dec = oracle.decode(w.recon, oracle.encode(w.recon, corr, **kw))
