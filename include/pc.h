@@ -88,10 +88,16 @@ typedef struct {
     int32_t cell_factor;   /* tuning: at most cell_factor * n grid cells, within [2^16, 2^28]
                               (0 = 8); cells are never smaller than the pair reach.  Only
                               speed depends on it (pc_autotune_cells picks one).          */
+    int32_t dense_cell;    /* tuning: grid cells holding at least this many particles are
+                              searched by one warp per 32 of their particles, the others by
+                              one thread per particle (0 = no such cells).  Only speed
+                              depends on it.                                              */
+    int32_t reserved_;     /* 0 */
 } pc_params;
 
 /* Fills defaults: m=16, t_max=10000, alpha_rel=0.2, beta=(0.9,0.999), eps_rel=2e-6,
  * loss_tol=0, replay_iters=-1, cell_cap_log2=0, stall_patience=0 (Algorithm 1 as printed), cell_factor=0,
+ * dense_cell=0,
  * unit box, non-periodic, mode VP. */
 void pc_params_default(pc_params *p);
 
@@ -211,6 +217,15 @@ pc_status pc_correct_batch(pc_ctx *ctx, const float *orig_dev, const float *reco
  * times.  The selected pairs do not depend on the factor, only the time does. */
 pc_status pc_autotune_cells(pc_ctx *ctx, const float *xyz_dev, int64_t n, const pc_params *params, int32_t *best,
                             double *ms, void *stream);
+
+/* Autotuner for the pair search (not part of the paper): the cell factor as
+ * pc_autotune_cells does, then the dense-cell threshold (0 = none, 32, 128, 512) at that
+ * factor, each timed over the whole selection on the given point set (the second of two
+ * runs).  *tuned receives *params with cell_factor, dense_cell (and cell_cap_log2 = 0)
+ * set to the fastest combination; ms (host, may be NULL) receives the 5 + 4 times.  The
+ * selected pairs do not depend on either knob.  Synchronises the stream. */
+pc_status pc_autotune(pc_ctx *ctx, const float *xyz_dev, int64_t n, const pc_params *params, pc_params *tuned,
+                      double *ms, void *stream);
 
 /* Cluster-query metrics of Sec. 4.1 ("Metrics"), for judging an iteration-capped
  * correction (Sec. 4.2 uses a 100-iteration limit).  lab0 / lab1: friends-of-friends

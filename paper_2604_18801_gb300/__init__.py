@@ -235,6 +235,22 @@ def autotune_cells(xyz: torch.Tensor, params, ctx: Context = None):
     return int(best.value), dict(zip((2, 4, 8, 16, 32), list(ms)))
 
 
+def autotune(xyz: torch.Tensor, params, ctx: Context = None):
+    """Pair-search knobs with the fastest selection on this point set: (cell_factor,
+    dense_cell, times in ms of the 5 cell factors and the 4 dense-cell thresholds).
+    Results never depend on either knob."""
+    _xyz(xyz, "xyz")
+    ctx = ctx or default_context(xyz.device.index)
+    p = _params(params)
+    q = _native.Params()
+    ms = (C.c_double * 9)()
+    _native.check(_native.lib().pc_autotune(ctx.h, xyz.data_ptr(), xyz.shape[0], C.byref(p), C.byref(q), ms,
+                                            _stream(xyz.device)), "pc_autotune")
+    times = {"cell_factor": dict(zip((2, 4, 8, 16, 32), list(ms)[:5])),
+             "dense_cell": dict(zip((0, 32, 128, 512), list(ms)[5:]))}
+    return int(q.cell_factor), int(q.dense_cell), times
+
+
 def cluster_metrics(lab0: torch.Tensor, lab1: torch.Tensor, min_members: int = 20, n_bins: int = 50,
                     volume: float = 1.0, ctx: Context = None) -> dict:
     """ARI, MWM-IoU and halo mass functions (Sec. 4.1) between two labelings of the same

@@ -28,7 +28,8 @@ class Params(C.Structure):
                 ("periodic", C.c_int32), ("mode", C.c_int32), ("m_bits", C.c_int32), ("t_max", C.c_int32),
                 ("alpha_rel", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps_rel", C.c_double),
                 ("loss_tol", C.c_double), ("replay_iters", C.c_int32), ("cell_cap_log2", C.c_int32),
-                ("stall_patience", C.c_int32), ("cell_factor", C.c_int32)]
+                ("stall_patience", C.c_int32), ("cell_factor", C.c_int32), ("dense_cell", C.c_int32),
+                ("reserved_", C.c_int32)]
 
 
 class SelectStats(C.Structure):
@@ -110,6 +111,7 @@ def lib():
         L.pc_huff_encode.argtypes = [vp, vp, sz, vp, sz, C.POINTER(sz), vp]
         L.pc_huff_decode.argtypes = [vp, vp, sz, vp, sz, C.POINTER(sz), vp]
         L.pc_autotune_cells.argtypes = [vp, vp, i64, P, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
+        L.pc_autotune.argtypes = [vp, vp, i64, P, P, C.POINTER(C.c_double), vp]
         L.pc_cluster_metrics.argtypes = [vp, vp, vp, i64, C.c_int32, C.c_int32, C.c_double,
                                          C.POINTER(ClusterMetrics), vp, vp, vp, vp]
         L.pc_server_create.argtypes = [vp, sz, C.c_int32, i64, C.POINTER(vp)]
@@ -120,7 +122,8 @@ def lib():
         L.pc_serve_wait.argtypes = [vp, C.c_uint64, i64, C.POINTER(JobResult)]
         L.pc_serve_counters.argtypes = [vp, C.POINTER(i64)]
         for f in ("pc_ctx_create", "pc_fof_labels", "pc_select_constraints", "pc_constraints_copy", "pc_correct",
-                  "pc_correct_detail", "pc_correct_batch", "pc_correct_multi", "pc_autotune_cells", "pc_cluster_metrics",
+                  "pc_correct_detail", "pc_correct_batch", "pc_correct_multi", "pc_autotune_cells", "pc_autotune",
+                  "pc_cluster_metrics",
                   "pc_server_create", "pc_serve_submit",
                   "pc_serve_poll",
                   "pc_serve_wait", "pc_serve_counters",

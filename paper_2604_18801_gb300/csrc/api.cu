@@ -59,7 +59,7 @@ void check_params(const pc_params *p, int64_t n, bool need_pgd) {
         if (p->m_bits < 2 || p->m_bits > 32) fail(PC_EINVAL, "m_bits must be in [2, 32]");
         if (p->t_max < 0) fail(PC_EINVAL, "t_max must be >= 0");
         if (!(p->alpha_rel > 0.0) || !(p->beta1 >= 0.0 && p->beta1 < 1.0) || !(p->beta2 >= 0.0 && p->beta2 < 1.0) ||
-            !(p->eps_rel > 0.0) || !(p->loss_tol >= 0.0) || p->stall_patience < 0)
+            !(p->eps_rel > 0.0) || !(p->loss_tol >= 0.0) || p->stall_patience < 0 || p->dense_cell < 0)
             fail(PC_EINVAL, "bad Adam parameters");
     }
 }
@@ -475,6 +475,8 @@ void pc_params_default(pc_params *p) {
     p->cell_cap_log2 = 0;
     p->stall_patience = 0;   // Algorithm 1 as printed: no stall rule
     p->cell_factor = 0;
+    p->dense_cell = 0;
+    p->reserved_ = 0;
 }
 
 const char *pc_last_error(void) { return g_err.c_str(); }
@@ -761,6 +763,66 @@ pc_status pc_autotune_cells(pc_ctx *ctx, const float *xyz, int64_t n, const pc_p
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        return PC_OK;
+    });
+}
+
+pc_status pc_autotune(pc_ctx *ctx, const float *xyz, int64_t n, const pc_params *p, pc_params *tuned, double *ms,
+                      void *stream) {
+    return guarded([&]() -> pc_status {
+        use_device(ctx);
+        check_params(p, n, false);
+        if (!xyz || !tuned) fail(PC_EINVAL, "NULL argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        static const int32_t cf[5] = {2, 4, 8, 16, 32};
+        static const int32_t dc[4] = {0, 32, 128, 512};
+        cudaEvent_t e0, e1;
+        PC_CUDA(cudaEventCreate(&e0));
+        PC_CUDA(cudaEventCreate(&e1));
+        // times the whole selection twice (the first run warms the pool) and keeps the second
+        auto time_select = [&](const pc_params &q) -> double {
+            float t = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                pc_constraints h;
+                single_block(h.S, n, &q);
+                PC_CUDA(cudaEventRecord(e0, s));
+                do_select(ctx, xyz, s, &h);
+                PC_CUDA(cudaEventRecord(e1, s));
+                PC_CUDA(cudaEventSynchronize(e1));
+                PC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            }
+            return t;
+        };
+        pc_params q = *p;
+        q.cell_cap_log2 = 0;
+        double best_ms = 1e300;
+        int32_t best_cf = 8, best_dc = q.dense_cell;
+        for (int c = 0; c < 5; ++c) {   // the cell factor first, at the given dense-cell threshold
+            q.cell_factor = cf[c];
+            q.dense_cell = best_dc;
+            const double t = time_select(q);
+            if (ms) ms[c] = t;
+            if (t < best_ms) {
+                best_ms = t;
+                best_cf = cf[c];
+            }
+        }
+        for (int c = 0; c < 4; ++c) {   // then the dense-cell threshold at that factor
+            q.cell_factor = best_cf;
+            q.dense_cell = dc[c];
+            const double t = time_select(q);
+            if (ms) ms[5 + c] = t;
+            if (t < best_ms || (dc[c] == best_dc && t <= best_ms)) {
+                best_ms = t;
+                best_dc = dc[c];
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *tuned = *p;
+        tuned->cell_factor = best_cf;
+        tuned->cell_cap_log2 = 0;
+        tuned->dense_cell = best_dc;
         return PC_OK;
     });
 }

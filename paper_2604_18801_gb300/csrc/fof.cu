@@ -287,7 +287,8 @@ void bin_particles(const float *orig, const BlockSet &S, Binned &B, cudaStream_t
     PC_CHECK_LAUNCH();
     k_cell_bounds<<<grid_for(n + 1), 256, 0, s>>>(B.keys.p, n, S.ncells, B.cell_start.p);
     PC_CHECK_LAUNCH();
-    (void)hs;
+    const int32_t dc = S.prm.empty() ? 0 : S.prm[0].dense_cell;
+    cell_maps(B, S, dc > 0 ? (uint32_t)dc : 0u, s, hs);
 }
 
 // ======================================================================= union-find
@@ -349,6 +350,20 @@ void uf_flatten(uint32_t *par, int64_t n, uint32_t *err, cudaStream_t s) {
 }
 
 // ======================================================================= pair search
+// Every unordered pair within reach is classified exactly once, by one of two kernels:
+//  * k_pairs_sparse: one thread per particle of a sparse cell (fewer than dense_min
+//    particles) visits its own cell's later particles and the 13 forward neighbour cells
+//    (lexicographically positive (dz, dy, dx)), skipping empty cells on an occupancy
+//    bitmap (one bit per cell, small enough to stay in L2) and dense cells;
+//  * k_pairs_dense: one warp per chunk of at most 32 particles of a dense cell (one per
+//    lane) visits all 27 cells of the neighbourhood: the home cell (later particles), every
+//    sparse neighbour, and the dense neighbours in forward directions.  Each neighbour
+//    cell is staged in shared memory 32 particles at a time with coalesced float4 loads,
+//    and every lane tests its particle against the staged ones (broadcast reads), so the
+//    warp's lanes stay busy in dense halos.
+// A pair of two sparse cells is visited from the backward cell, a pair with one dense
+// cell by that cell's warps, a pair of two dense cells in the forward direction, and a
+// pair inside one cell once (later particles only).
 namespace {
 
 struct PairArgs {
@@ -378,128 +393,289 @@ __constant__ int c_off[14][3] = {{0, 0, 0},  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}
                                  {0, 0, 1},  {1, 0, 1},   {-1, 1, 1}, {0, 1, 1},  {1, 1, 1},
                                  {-1, 1, 0}, {0, 1, 0},   {1, 1, 0},  {1, 0, 0}};
 
-// PASS 1: union-find + counts.  PASS 2: emission by the block's mode (0 VP, 1 SC, 2 HF).
+__device__ __forceinline__ bool cell_bit(const uint32_t *__restrict__ m, uint32_t c) {
+    return (__ldg(m + (c >> 5)) >> (c & 31)) & 1u;
+}
+
+struct ClassCounts {
+    uint32_t links = 0, safe = 0, pb = 0, pc = 0;
+};
+
+// One pair within reach (d2 <= hi2; sorted positions k, kj; particle ids id, jd), in one
+// pass: pass 1 counts it by class and unites links (FoF) and safe links (safe
+// components); pass 2 emits it by the block's mode (VP: every vulnerable pair; SC:
+// vulnerable pairs between safe components; HF: created pairs between halos to A, broken
+// links between safe components to the forest candidates C).
 template <int PASS>
-__global__ void __launch_bounds__(256) k_pairs(const float4 *__restrict__ P4, const uint32_t *__restrict__ keys,
-                                               const uint32_t *__restrict__ cell_start, int64_t n,
-                                               const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
-                                               int nb, PairArgs a) {
+__device__ __forceinline__ void pair_action(float d2, int64_t k, int64_t kj, uint32_t id, uint32_t jd, float lo2,
+                                            float b2, int mode, uint32_t my_safe, uint32_t my_fof,
+                                            const PairArgs &a, ClassCounts &cn) {
+    if (PASS == 1) {
+        if (d2 <= lo2) {
+            ++cn.safe;
+            ++cn.links;
+            if (a.safe_par) uf_union(a.safe_par, id, jd, a.err);
+            if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
+        } else if (d2 <= b2) {
+            ++cn.pb;
+            ++cn.links;
+            if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
+        } else {
+            ++cn.pc;
+        }
+    } else {
+        if (d2 <= lo2) return;   // safe link: never vulnerable
+        const unsigned long long pk = k < kj ? (((unsigned long long)k << 32) | (unsigned long long)kj)
+                                             : (((unsigned long long)kj << 32) | (unsigned long long)k);
+        if (mode == 0) {
+            emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
+        } else if (mode == 1) {
+            if (a.safe_lab[jd] != my_safe) emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
+        } else {
+            if (d2 > b2) {
+                if (a.fof_lab[jd] != my_fof) emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
+            } else {
+                if (a.safe_lab[jd] != my_safe) emit_pair(pk, a.C, a.capC, a.counts + CNT_C, a.err);
+            }
+        }
+    }
+}
+
+// Pass 1 class counts of a warp: per block (one atomic per warp when the warp lies in one
+// block) and in total.
+__device__ __forceinline__ void flush_counts(ClassCounts cn, int bk, const PairArgs &a) {
+    const unsigned FULL = 0xffffffffu;
+    if (a.blk_counts) {
+        int same = 0;
+        __match_all_sync(FULL, bk, &same);
+        if (!same) {
+            if (bk >= 0) {
+                unsigned long long *c = a.blk_counts + 4 * bk;
+                if (cn.links) atomicAdd(c + 0, (unsigned long long)cn.links);
+                if (cn.safe) atomicAdd(c + 1, (unsigned long long)cn.safe);
+                if (cn.pb) atomicAdd(c + 2, (unsigned long long)cn.pb);
+                if (cn.pc) atomicAdd(c + 3, (unsigned long long)cn.pc);
+            }
+        }
+        const unsigned wl = __reduce_add_sync(FULL, cn.links), ws = __reduce_add_sync(FULL, cn.safe),
+                       wp = __reduce_add_sync(FULL, cn.pb), wc = __reduce_add_sync(FULL, cn.pc);
+        if (same && (threadIdx.x & 31) == 0 && bk >= 0) {
+            unsigned long long *c = a.blk_counts + 4 * bk;
+            if (wl) atomicAdd(c + 0, (unsigned long long)wl);
+            if (ws) atomicAdd(c + 1, (unsigned long long)ws);
+            if (wp) atomicAdd(c + 2, (unsigned long long)wp);
+            if (wc) atomicAdd(c + 3, (unsigned long long)wc);
+        }
+    }
+    const unsigned wl = __reduce_add_sync(FULL, cn.links), ws = __reduce_add_sync(FULL, cn.safe),
+                   wp = __reduce_add_sync(FULL, cn.pb), wc = __reduce_add_sync(FULL, cn.pc);
+    if ((threadIdx.x & 31) == 0) {
+        if (wl) atomicAdd(a.counts + CNT_LINKS, (unsigned long long)wl);
+        if (ws) atomicAdd(a.counts + CNT_SAFE, (unsigned long long)ws);
+        if (wp) atomicAdd(a.counts + CNT_PB, (unsigned long long)wp);
+        if (wc) atomicAdd(a.counts + CNT_PC, (unsigned long long)wc);
+    }
+}
+
+// Cell coordinates of a sorted position's cell within its block's grid.
+__device__ __forceinline__ void cell_xyz(uint32_t key, const BlockDev &B, int &cx, int &cy, int &cz) {
+    const uint32_t l = key - (uint32_t)B.cell_base;
+    cx = (int)(l % (uint32_t)B.nc[0]);
+    cy = (int)((l / (uint32_t)B.nc[0]) % (uint32_t)B.nc[1]);
+    cz = (int)(l / ((uint32_t)B.nc[0] * (uint32_t)B.nc[1]));
+}
+
+// Global index of the neighbour cell (cx + ox, cy + oy, cz + oz), or false when it does
+// not exist: outside a non-periodic grid, or a step along a periodic axis of one cell
+// (which has no distinct neighbour along it; periodic axes have one or at least 3 cells).
+__device__ __forceinline__ bool neighbour(const BlockDev &B, int cx, int cy, int cz, int ox, int oy, int oz,
+                                          uint32_t &cell) {
+    const int nx = B.nc[0], ny = B.nc[1], nz = B.nc[2];
+    int qx = cx + ox, qy = cy + oy, qz = cz + oz;
+    if (B.periodic) {
+        if ((nx == 1 && ox) || (ny == 1 && oy) || (nz == 1 && oz)) return false;
+        qx = qx < 0 ? qx + nx : (qx >= nx ? qx - nx : qx);
+        qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
+        qz = qz < 0 ? qz + nz : (qz >= nz ? qz - nz : qz);
+    } else if (qx < 0 || qx >= nx || qy < 0 || qy >= ny || qz < 0 || qz >= nz) {
+        return false;
+    }
+    cell = (uint32_t)B.cell_base + ((uint32_t)qz * (uint32_t)ny + (uint32_t)qy) * (uint32_t)nx + (uint32_t)qx;
+    return true;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(256) k_pairs_sparse(const float4 *__restrict__ P4, const uint32_t *__restrict__ keys,
+                                                      const uint32_t *__restrict__ cell_start, int64_t n,
+                                                      const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
+                                                      int nb, CellMaps M, PairArgs a) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t n_links = 0, n_safe = 0, n_pb = 0, n_pc = 0;
+    ClassCounts cn;
     const int bk = k < n ? find_block(off, nb, k) : -1;
-    if (k < n) {
+    if (k < n && !cell_bit(M.dense, keys[k])) {
         const BlockDev &B = bt[bk];
         const float4 p = P4[k];
         const uint32_t id = __float_as_uint(p.w);
-        const uint32_t key = keys[k] - (uint32_t)B.cell_base;
-        const int nx = B.nc[0], ny = B.nc[1], nz = B.nc[2];
-        const int cx = (int)(key % (uint32_t)nx);
-        const int cy = (int)((key / (uint32_t)nx) % (uint32_t)ny);
-        const int cz = (int)(key / ((uint32_t)nx * (uint32_t)ny));
+        int cx, cy, cz;
+        cell_xyz(keys[k], B, cx, cy, cz);
         const bool per = B.periodic != 0;
         const float lo2 = B.lo2, b2 = B.b2, hi2 = B.hi2;
-        const int mode = B.mode;
         uint32_t my_safe = 0, my_fof = 0;
         if (PASS == 2) {
-            if (mode >= 1) my_safe = a.safe_lab[id];
-            if (mode == 2) my_fof = a.fof_lab[id];
+            if (B.mode >= 1) my_safe = a.safe_lab[id];
+            if (B.mode == 2) my_fof = a.fof_lab[id];
         }
         for (int o = 0; o < 14; ++o) {
-            const int ox = c_off[o][0], oy = c_off[o][1], oz = c_off[o][2];
-            // a periodic axis with a single cell has no distinct neighbour along it
-            if (per && ((nx == 1 && ox) || (ny == 1 && oy) || (nz == 1 && oz))) continue;
-            int qx = cx + ox, qy = cy + oy, qz = cz + oz;
-            if (per) {
-                qx = qx < 0 ? qx + nx : (qx >= nx ? qx - nx : qx);
-                qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
-                qz = qz < 0 ? qz + nz : (qz >= nz ? qz - nz : qz);
-            } else if (qx < 0 || qx >= nx || qy < 0 || qy >= ny || qz < 0 || qz >= nz) {
-                continue;
-            }
-            const uint32_t cell = (uint32_t)B.cell_base +
-                                  ((uint32_t)qz * (uint32_t)ny + (uint32_t)qy) * (uint32_t)nx + (uint32_t)qx;
+            uint32_t cell;
+            if (!neighbour(B, cx, cy, cz, c_off[o][0], c_off[o][1], c_off[o][2], cell)) continue;
+            if (!cell_bit(M.occ, cell)) continue;                  // empty
+            if (o != 0 && cell_bit(M.dense, cell)) continue;       // its warps take these pairs
             int64_t js = min((int64_t)cell_start[cell], n);
             const int64_t je = min((int64_t)cell_start[cell + 1], n);
             if (o == 0) js = k + 1;
             for (int64_t kj = js; kj < je; ++kj) {
                 const float4 q = __ldg(P4 + kj);
-                const float dx = cdiff(p.x, q.x, per, B.L[0]);
-                const float dy = cdiff(p.y, q.y, per, B.L[1]);
-                const float dz = cdiff(p.z, q.z, per, B.L[2]);
-                const float d2 = cdist2(dx, dy, dz);
+                const float d2 = cdist2(cdiff(p.x, q.x, per, B.L[0]), cdiff(p.y, q.y, per, B.L[1]),
+                                        cdiff(p.z, q.z, per, B.L[2]));
                 if (d2 > hi2) continue;
-                const uint32_t jd = __float_as_uint(q.w);
-                if (PASS == 1) {
-                    if (d2 <= lo2) {
-                        ++n_safe;
-                        ++n_links;
-                        if (a.safe_par) uf_union(a.safe_par, id, jd, a.err);
-                        if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
-                    } else if (d2 <= b2) {
-                        ++n_pb;
-                        ++n_links;
-                        if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
-                    } else {
-                        ++n_pc;
-                    }
-                } else {
-                    if (d2 <= lo2) continue;   // safe link: never vulnerable
-                    const unsigned long long pk = k < kj ? (((unsigned long long)k << 32) | (unsigned long long)kj)
-                                                         : (((unsigned long long)kj << 32) | (unsigned long long)k);
-                    if (mode == 0) {
-                        emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
-                    } else if (mode == 1) {
-                        if (a.safe_lab[jd] != my_safe) emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
-                    } else {
-                        if (d2 > b2) {
-                            if (a.fof_lab[jd] != my_fof) emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
-                        } else {
-                            if (a.safe_lab[jd] != my_safe) emit_pair(pk, a.C, a.capC, a.counts + CNT_C, a.err);
-                        }
-                    }
-                }
+                pair_action<PASS>(d2, k, kj, id, __float_as_uint(q.w), lo2, b2, B.mode, my_safe, my_fof, a, cn);
             }
         }
     }
     if (PASS == 1) {
         __syncwarp();
-        const unsigned FULL = 0xffffffffu;
-        if (a.blk_counts) {
-            // per-block counts: one atomic per warp when the warp lies in one block
-            int same = 0;
-            __match_all_sync(FULL, bk, &same);
-            if (!same) {
-                if (bk >= 0) {
-                    unsigned long long *c = a.blk_counts + 4 * bk;
-                    if (n_links) atomicAdd(c + 0, (unsigned long long)n_links);
-                    if (n_safe) atomicAdd(c + 1, (unsigned long long)n_safe);
-                    if (n_pb) atomicAdd(c + 2, (unsigned long long)n_pb);
-                    if (n_pc) atomicAdd(c + 3, (unsigned long long)n_pc);
+        flush_counts(cn, bk, a);
+    }
+}
+
+constexpr int DENSE_WARPS = 8;
+
+template <int PASS>
+__global__ void __launch_bounds__(32 * DENSE_WARPS) k_pairs_dense(
+    const float4 *__restrict__ P4, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ cell_start,
+    int64_t n, const BlockDev *__restrict__ bt, const int64_t *__restrict__ off, int nb, CellMaps M,
+    const DenseChunk *__restrict__ chunks, int64_t n_chunks, unsigned long long *work, PairArgs a) {
+    __shared__ float4 tile[DENSE_WARPS][32];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(work, 1ull);
+        c = __shfl_sync(FULL, c, 0);
+        if ((int64_t)c >= n_chunks) break;
+        const DenseChunk ch = chunks[c];
+        const int bk = find_block(off, nb, (int64_t)ch.k0);
+        const BlockDev &B = bt[bk];
+        const int64_t ka = (int64_t)ch.k0 + lane;
+        const bool va = lane < (int)ch.cnt;
+        const float4 p = va ? P4[ka] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t id = __float_as_uint(p.w);
+        int cx, cy, cz;
+        cell_xyz(keys[ch.k0], B, cx, cy, cz);
+        const bool per = B.periodic != 0;
+        const float lo2 = B.lo2, b2 = B.b2, hi2 = B.hi2;
+        uint32_t my_safe = 0, my_fof = 0;
+        if (PASS == 2 && va) {
+            if (B.mode >= 1) my_safe = a.safe_lab[id];
+            if (B.mode == 2) my_fof = a.fof_lab[id];
+        }
+        ClassCounts cn;
+        for (int o = 0; o < 27; ++o) {
+            const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+            uint32_t cell;
+            if (!neighbour(B, cx, cy, cz, ox, oy, oz, cell)) continue;
+            if (!cell_bit(M.occ, cell)) continue;
+            const bool home = (ox | oy | oz) == 0;
+            const bool forward = oz > 0 || (oz == 0 && (oy > 0 || (oy == 0 && ox > 0)));
+            if (!home && !forward && cell_bit(M.dense, cell)) continue;   // the other cell's warps take it
+            const int64_t js = min((int64_t)cell_start[cell], n), je = min((int64_t)cell_start[cell + 1], n);
+            for (int64_t base = js; base < je; base += 32) {
+                // stage up to 32 particles of the neighbour cell (one coalesced float4 load)
+                const int m = (int)min((int64_t)32, je - base);
+                if (lane < m) tile[w][lane] = P4[base + lane];
+                __syncwarp();
+                for (int j = 0; j < m; ++j) {
+                    const float4 q = tile[w][j];
+                    const int64_t kj = base + j;
+                    if (!va || (home && kj <= ka)) continue;
+                    const float d2 = cdist2(cdiff(p.x, q.x, per, B.L[0]), cdiff(p.y, q.y, per, B.L[1]),
+                                            cdiff(p.z, q.z, per, B.L[2]));
+                    if (d2 > hi2) continue;
+                    pair_action<PASS>(d2, ka, kj, id, __float_as_uint(q.w), lo2, b2, B.mode, my_safe, my_fof, a,
+                                      cn);
                 }
-            }
-            const unsigned wl = __reduce_add_sync(FULL, n_links), ws = __reduce_add_sync(FULL, n_safe),
-                           wp = __reduce_add_sync(FULL, n_pb), wc = __reduce_add_sync(FULL, n_pc);
-            if (same && (threadIdx.x & 31) == 0 && bk >= 0) {
-                unsigned long long *c = a.blk_counts + 4 * bk;
-                if (wl) atomicAdd(c + 0, (unsigned long long)wl);
-                if (ws) atomicAdd(c + 1, (unsigned long long)ws);
-                if (wp) atomicAdd(c + 2, (unsigned long long)wp);
-                if (wc) atomicAdd(c + 3, (unsigned long long)wc);
+                __syncwarp();
             }
         }
-        n_links = __reduce_add_sync(FULL, n_links);
-        n_safe = __reduce_add_sync(FULL, n_safe);
-        n_pb = __reduce_add_sync(FULL, n_pb);
-        n_pc = __reduce_add_sync(FULL, n_pc);
-        if ((threadIdx.x & 31) == 0) {
-            if (n_links) atomicAdd(a.counts + CNT_LINKS, (unsigned long long)n_links);
-            if (n_safe) atomicAdd(a.counts + CNT_SAFE, (unsigned long long)n_safe);
-            if (n_pb) atomicAdd(a.counts + CNT_PB, (unsigned long long)n_pb);
-            if (n_pc) atomicAdd(a.counts + CNT_PC, (unsigned long long)n_pc);
+        if (PASS == 1) flush_counts(cn, bk, a);
+    }
+}
+
+// Occupancy and density maps of the grid, and the dense cells cut into chunks of at
+// most 32 particles: one thread per cell's first sorted particle.
+__global__ void k_cell_maps(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ cell_start, int64_t n,
+                            uint32_t dense_min, uint32_t *__restrict__ occ, uint32_t *__restrict__ dense,
+                            DenseChunk *__restrict__ chunks, uint64_t cap, unsigned long long *n_chunks,
+                            uint32_t *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = keys[k];
+        if (k > 0 && keys[k - 1] == c) continue;
+        atomicOr(occ + (c >> 5), 1u << (c & 31));
+        const uint32_t cnt = cell_start[c + 1] - (uint32_t)k;
+        if (cnt < dense_min) continue;
+        atomicOr(dense + (c >> 5), 1u << (c & 31));
+        const uint32_t nch = (cnt + 31u) / 32u;
+        const unsigned long long at = atomicAdd(n_chunks, (unsigned long long)nch);
+        for (uint32_t j = 0; j < nch; ++j) {
+            if (at + j < cap) chunks[at + j] = DenseChunk{(uint32_t)k + 32u * j, min(32u, cnt - 32u * j)};
+            else atomicOr(err, ERR_INDEX);
         }
     }
 }
 
+}  // namespace
+
+void cell_maps(Binned &B, const BlockSet &S, uint32_t dense_min, cudaStream_t s, HostScratch &hs) {
+    const int64_t n = B.n;
+    const int64_t words = (S.ncells + 32) / 32;
+    B.occ.alloc(words, s);
+    B.dense.alloc(words, s);
+    PC_CUDA(cudaMemsetAsync(B.occ.p, 0, words * sizeof(uint32_t), s));
+    PC_CUDA(cudaMemsetAsync(B.dense.p, 0, words * sizeof(uint32_t), s));
+    // dense_min = 0: no dense cells (every particle is searched by its own thread)
+    const uint64_t cap = dense_min ? (uint64_t)(n / std::max<uint32_t>(2, dense_min) + n / 32 + 1) : 1;
+    B.chunks.alloc(cap, s);
+    DBuf<unsigned long long> cnt(1, s);
+    DBuf<uint32_t> err(1, s);
+    PC_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+    PC_CUDA(cudaMemsetAsync(err.p, 0, sizeof(uint32_t), s));
+    k_cell_maps<<<grid_for(n), 256, 0, s>>>(B.keys.p, B.cell_start.p, n,
+                                            dense_min ? std::max<uint32_t>(2, dense_min) : 0xffffffffu, B.occ.p,
+                                            B.dense.p, B.chunks.p, cap, cnt.p, err.p);
+    PC_CHECK_LAUNCH();
+    const unsigned long long *h = (const unsigned long long *)read_back(hs, cnt.p, sizeof(unsigned long long), s);
+    B.n_chunks = (int64_t)*h;
+    const uint32_t ev = *(const uint32_t *)read_back(hs, err.p, sizeof(uint32_t), s);
+    if (ev & ERR_INDEX) fail(PC_ECUDA, "dense-cell chunk list overflowed its bound");
+}
+
+namespace {
+template <int PASS>
+void run_pair_pass(const Binned &B, const BlockSet &S, const PairArgs &a, cudaStream_t s) {
+    const int64_t n = B.n;
+    const CellMaps M{B.occ.p, B.dense.p};
+    k_pairs_sparse<PASS><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, S.dev.p,
+                                                               S.doff.p, S.nb, M, a);
+    PC_CHECK_LAUNCH();
+    if (B.n_chunks > 0) {
+        DBuf<unsigned long long> work(1, s);
+        PC_CUDA(cudaMemsetAsync(work.p, 0, sizeof(unsigned long long), s));
+        const int grid = (int)std::min<int64_t>(cdiv(B.n_chunks, DENSE_WARPS), (int64_t)num_sms() * 8);
+        k_pairs_dense<PASS><<<grid, 32 * DENSE_WARPS, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, S.dev.p, S.doff.p,
+                                                             S.nb, M, B.chunks.p, B.n_chunks, work.p, a);
+        PC_CHECK_LAUNCH();
+    }
+}
 }  // namespace
 
 void pair_pass_union(const Binned &B, const BlockSet &S, uint32_t *fof_par, uint32_t *safe_par,
@@ -510,10 +686,7 @@ void pair_pass_union(const Binned &B, const BlockSet &S, uint32_t *fof_par, uint
     a.safe_par = safe_par;
     a.counts = counts;
     a.err = err;
-    const int64_t n = B.n;
-    k_pairs<1><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, S.dev.p, S.doff.p, S.nb,
-                                                       a);
-    PC_CHECK_LAUNCH();
+    run_pair_pass<1>(B, S, a, s);
 }
 
 void pair_pass_emit(const Binned &B, const BlockSet &S, const uint32_t *fof_lab, const uint32_t *safe_lab,
@@ -528,10 +701,7 @@ void pair_pass_emit(const Binned &B, const BlockSet &S, const uint32_t *fof_lab,
     a.capC = capC;
     a.counts = counts;
     a.err = err;
-    const int64_t n = B.n;
-    k_pairs<2><<<(unsigned)cdiv(n, 256), 256, 0, s>>>(B.P4.p, B.keys.p, B.cell_start.p, n, S.dev.p, S.doff.p, S.nb,
-                                                       a);
-    PC_CHECK_LAUNCH();
+    run_pair_pass<2>(B, S, a, s);
 }
 
 }  // namespace pc

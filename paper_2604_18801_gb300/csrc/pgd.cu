@@ -11,20 +11,22 @@
 // Q = fl(P + delta), both in two ping-pong buffers; the Adam moments m, v as
 // double-floats; one activity byte.
 //
-// One iteration = k_pgd_iter (+ k_pgd_heavy when some rows have more than
-// HEAVY partners).  Warps take work items (groups of 32 light rows, or one
-// HEAVY-edge chunk of a heavy row) from a counter.  A float32 screen on Q
+// One iteration = one launch of k_pgd_iter.  Warps take work items (a heavy
+// row -- more than HEAVY partners -- or a group of 32 light rows) from a
+// counter, heavy rows first and longest first.  A float32 screen on Q
 // certifies most pairs as satisfied; the others are evaluated in
 // double-float, 32 at a time, and each row's gradient is a fixed-order sum
-// (segmented shuffle scan within a batch, batches in edge order, chunks in
-// chunk order), so no float atomics are used and the offsets are
-// deterministic.  The loss (each pair counted once, in the row of its smaller
-// dense index) is accumulated in fixed point and the violations are counted;
-// the last block takes the stop decision of Algorithm 1.  The Adam step of
-// the same launch is written to the other buffers, so when the check says
-// "stop" the current buffer is the answer and nothing has to be undone.
+// (its violated pairs in edge order), so no float atomics are used and the
+// offsets are deterministic.  The loss (each pair counted once, in the row of
+// its smaller dense index) is accumulated in fixed point and the violations
+// are counted; the last block takes the stop decision of Algorithm 1.  The
+// Adam step of the same launch is written to the other buffers, so when the
+// check says "stop" the current buffer is the answer and nothing has to be
+// undone.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <type_traits>
 
 #include "df.cuh"
 #include "pipeline.cuh"
@@ -49,7 +51,7 @@ constexpr int PGD_BLOCKS_PER_SM = 4;   // resident CTAs of the persistent iterat
 constexpr int MAX_THR = 4;
 
 // act[e]: bit 0 = the row has had a gradient (or needs its first projection), bit 1 = the
-// row is heavy (more than HEAVY partners: its edges are walked in chunks of HEAVY).
+// row is heavy (more than HEAVY partners: it is a work item of its own).
 constexpr uint8_t ACT_ON = 1, ACT_HEAVY = 2;
 constexpr uint32_t HEAVY = 256;
 
@@ -105,17 +107,22 @@ struct PgdBlk {
 struct PgdGlobal {
     uint32_t ticket;
     int32_t all_stop;
-    unsigned long long work;        // next work item of the launch
+    unsigned long long work;        // next work item of the screen
     int32_t active;                 // blocks still iterating after the last launch
     int32_t pad;
     unsigned long long n_items;     // work items of the blocks still iterating (problem sets)
+    unsigned long long ncand;       // candidate rows the screen listed for the update
+    unsigned long long work2;       // next candidate of the update
+    unsigned long long nhcand;      // heavy candidate rows with an uncertain pair (a list of their own)
+    unsigned long long work3;       // next heavy candidate of the update
 };
 
-// Work of one block of a problem set: its rows [row0, row0 + nrows) form ceil(nrows / 32)
-// light items (groups of 32 rows that never straddle two blocks; the heavy rows among
-// them have no light edges), followed by its heavy chunks [ch0, ch0 + nch).
+// Work of one block of a problem set: its heavy rows, items [h0, h0 + nh) of the heavy
+// list (longest first), then ceil(nrows / 32) light items over its rows [row0, row0 +
+// nrows) (groups of 32 rows that never straddle two blocks; the heavy rows among them
+// have no light edges).
 struct BlkWork {
-    uint32_t row0, nrows, ch0, nch;
+    uint32_t row0, nrows, h0, nh;
 };
 
 // Items of the blocks still iterating, for the next launch: active block k is act_blk[k]
@@ -137,7 +144,7 @@ __device__ void build_worktab(int nb, const PgdBlk *blk, const WorkTab wt, PgdGl
         unsigned long long it = 0;
         if (a) {
             const BlkWork w = wt.bw[b];
-            it = (unsigned long long)((w.nrows + 31u) >> 5) + w.nch;
+            it = (unsigned long long)((w.nrows + 31u) >> 5) + w.nh;
         }
         unsigned long long inc = it;
 #pragma unroll
@@ -165,43 +172,90 @@ __global__ void k_worktab_init(int nb, const PgdBlk *blk, const WorkTab wt, PgdG
     if (threadIdx.x < 32) build_worktab(nb, blk, wt, gs);
 }
 
-// Per-block row and chunk ranges (rows are in sorted-position order, so every block owns
-// a contiguous range of rows, and chunks follow their rows).
-__global__ void k_blk_work(const int64_t *__restrict__ row_off, const uint32_t *__restrict__ c0, int64_t ne,
-                           int64_t n_chunks, int nb, BlkWork *__restrict__ bw) {
+// Per-block row ranges and heavy-item ranges (rows are in sorted-position order, so every
+// block owns a contiguous range of rows; heavy items are sorted by block first).
+__global__ void k_blk_work(const int64_t *__restrict__ row_off, const uint32_t *__restrict__ h_off, int nb,
+                           BlkWork *__restrict__ bw) {
     GRID_STRIDE(b, nb) {
         const int64_t r0 = row_off[b], r1 = row_off[b + 1];
-        const uint32_t h0 = r0 < ne ? c0[r0] : (uint32_t)n_chunks, h1 = r1 < ne ? c0[r1] : (uint32_t)n_chunks;
-        bw[b] = BlkWork{(uint32_t)r0, (uint32_t)(r1 - r0), h0, h1 - h0};
+        bw[b] = BlkWork{(uint32_t)r0, (uint32_t)(r1 - r0), h_off[b], h_off[b + 1] - h_off[b]};
     }
 }
 
 // ------------------------------------------------------------------ CSR build
-__global__ void k_mark(const unsigned long long *__restrict__ A, int64_t m, uint32_t *__restrict__ mark) {
+// The editable particles are numbered in an order that depends on the data alone, not on
+// the tuned cell grid of the pair search: by block, then by the Morton code of the
+// original position on a fixed lattice of 2^14 cells per axis over the block's box, ties
+// by particle id.  Each row lists its partners in that order.  Summation orders, and so
+// the results' bits, do not depend on the tuning knobs; neighbours stay close in memory.
+struct MortonBox {
+    double lo[3], scale[3];   // lattice cell of coordinate x: floor((x - lo) * scale), clamped
+};
+
+// Spreads the low 21 bits of x to every third bit.
+__device__ __forceinline__ unsigned long long spread3(unsigned long long x) {
+    x &= 0x1fffffull;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+constexpr int MORTON_BITS = 14;   // per axis
+
+__global__ void k_mark_ids(const unsigned long long *__restrict__ A, int64_t m, const uint32_t *__restrict__ order,
+                           uint32_t *__restrict__ mark) {
     GRID_STRIDE(r, m) {
         const unsigned long long pk = A[r];
-        mark[pk >> 32] = 1u;
-        mark[pk & 0xffffffffull] = 1u;
+        mark[order[pk >> 32]] = 1u;
+        mark[order[pk & 0xffffffffull]] = 1u;
     }
 }
 
-__global__ void k_epos(const uint32_t *__restrict__ mark, const uint32_t *__restrict__ dense, int64_t n,
-                       uint32_t *__restrict__ epos) {
-    GRID_STRIDE(k, n) {
-        if (mark[k]) epos[dense[k]] = (uint32_t)k;
+// Key (block << 42 | Morton code) of every editable particle, in id order.
+__global__ void k_edit_keys(const uint32_t *__restrict__ mark, const uint32_t *__restrict__ rank, int64_t n,
+                            const float *__restrict__ orig, const int64_t *__restrict__ off, int nblk,
+                            const MortonBox *__restrict__ mb, unsigned long long *__restrict__ key,
+                            uint32_t *__restrict__ eid) {
+    GRID_STRIDE(i, n) {
+        if (!mark[i]) continue;
+        const uint32_t r = rank[i];
+        const int b = find_block(off, nblk, i);
+        const MortonBox &M = mb[b];
+        unsigned long long code = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double q = floor(((double)orig[3 * i + a] - M.lo[a]) * M.scale[a]);
+            q = fmin(fmax(q, 0.0), (double)((1 << MORTON_BITS) - 1));
+            code |= spread3((unsigned long long)q) << a;
+        }
+        key[r] = ((unsigned long long)b << (3 * MORTON_BITS)) | code;
+        eid[r] = (uint32_t)i;
     }
 }
 
-// Directed keys (row << nb | partner position) << tb | threshold index (tb = 0: one
-// linking length; tb = 2: Athr gives each pair's index).
+// Row e of the numbering: its sorted position (epos) and the position -> row map.
+__global__ void k_edit_maps(const uint32_t *__restrict__ eid, int64_t ne, const uint32_t *__restrict__ inv,
+                            uint32_t *__restrict__ epos, uint32_t *__restrict__ dense) {
+    GRID_STRIDE(e, ne) {
+        const uint32_t pos = inv[eid[e]];
+        epos[e] = pos;
+        dense[pos] = (uint32_t)e;
+    }
+}
+
+// Directed keys (row << nbe | partner row) << tb | threshold index (tb = 0: one linking
+// length; tb = 2: Athr gives each pair's index).
 __global__ void k_dir_keys(const unsigned long long *__restrict__ A, const uint8_t *__restrict__ Athr, int64_t m,
-                           const uint32_t *__restrict__ dense, int nb, int tb, unsigned long long *__restrict__ keys) {
+                           const uint32_t *__restrict__ dense, int nbe, int tb, unsigned long long *__restrict__ keys) {
     GRID_STRIDE(r, m) {
         const unsigned long long pk = A[r];
-        const uint32_t ki = (uint32_t)(pk >> 32), kj = (uint32_t)(pk & 0xffffffffull);
+        const unsigned long long di = dense[pk >> 32], dj = dense[pk & 0xffffffffull];
         const unsigned long long t = tb ? (unsigned long long)Athr[r] : 0ull;
-        keys[2 * r] = ((((unsigned long long)dense[ki] << nb) | kj) << tb) | t;
-        keys[2 * r + 1] = ((((unsigned long long)dense[kj] << nb) | ki) << tb) | t;
+        keys[2 * r] = (((di << nbe) | dj) << tb) | t;
+        keys[2 * r + 1] = (((dj << nbe) | di) << tb) | t;
     }
 }
 
@@ -388,29 +442,6 @@ __device__ __forceinline__ void adam_core(int64_t e, const df g[3], const RowSta
     Qn[e] = make_float4(qo[0], qo[1], qo[2], 0.f);
 }
 
-// Adam on one row, loading its state from global memory.
-__device__ __forceinline__ void adam_row(int64_t e, const df g[3], const float4 *Dh, const float4 *Dl,
-                                         const float4 *__restrict__ PE, uint8_t *__restrict__ act, const df ibc1,
-                                         const df ibc2, bool reset, const PgdConsts &C, float4 *Nh, float4 *Nl,
-                                         float4 *__restrict__ Mhi, float4 *__restrict__ Mlo, float4 *__restrict__ Vhi,
-                                         float4 *__restrict__ Vlo, float4 *Qn) {
-    const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
-    const uint8_t av = act[e];
-    const bool was = (av & ACT_ON) != 0;
-    if (!was && gz && !reset) return;
-    RowState S;
-    S.dh = Dh[e];
-    S.dl = Dl[e];
-    S.pe = PE[e];
-    if (was) {
-        S.mh = Mhi[e];
-        S.ml = Mlo[e];
-        S.vh = Vhi[e];
-        S.vl = Vlo[e];
-    }
-    adam_core(e, g, S, was, av, act, ibc1, ibc2, reset, C, Nh, Nl, Mhi, Mlo, Vhi, Vlo, Qn);
-}
-
 // ------------------------------------------------------------------ stop decisions
 // The tight loss is accumulated in fixed point: each violated pair adds llrint(v^2 / unit)
 // with unit = xi^2 2^-24 (v <= 2 sqrt3 xi + delta_t, so a term is below 2^28 units and 2^35
@@ -508,6 +539,10 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
         gs->active = active;
         if (active == 0) gs->all_stop = 1;
         gs->work = 0;
+        gs->work2 = 0;
+        gs->ncand = 0;
+        gs->work3 = 0;
+        gs->nhcand = 0;
         gs->ticket = 0;
     }
     __threadfence();
@@ -567,16 +602,19 @@ __device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long lon
 }
 
 // ------------------------------------------------------------------ iteration kernel
+// A heavy row: its edges (one contiguous range of the edge array) and its row.
+struct HeavyItem {
+    unsigned long long start;
+    uint32_t row, len;
+};
+
 struct HeavyPlan {
-    int64_t n_chunks;                          // heavy chunks (one warp each)
-    const uint32_t *chunk_row;                 // row of each chunk
-    const unsigned long long *chunk_start;     // first edge of each chunk in the edge array
-    const uint32_t *chunk_len;                 // edges of each chunk (at most HEAVY)
-    float4 *chunk_g;                           // per chunk: gradient partial (hi at 2c, lo at 2c+1)
+    int64_t n_heavy;                 // heavy rows (one work item each)
+    const HeavyItem *item;           // by block, then longest first
 };
 
 // One edge array holds the light rows' edges, in row order, then the heavy rows' edges
-// (chunks index into that second part).  A group of 32 light rows owns the contiguous
+// (each heavy row one contiguous range of that second part).  A group of 32 light rows owns the contiguous
 // range [ptr[r0], ptr[r0 + 32]) (heavy rows own no light edge), and each light edge
 // carries the slot of its row within the group, so a warp maps an edge to its row with
 // one byte load.  Offsets are 64-bit: a problem may have more than 2^32 directed edges.
@@ -584,6 +622,10 @@ struct LightPlan {
     const unsigned long long *ptr;   // per row: first light edge (ne + 1 entries)
     const uint32_t *col;             // partner | link << 31 (| threshold index << 29 with several)
     const uint8_t *slot;             // light edges: row - first row of its 32-row group
+    // the screen's copy of the light edges: within each 32-row group, sorted by CSR entry
+    // (partner), so that neighbouring lanes gather the same or nearby partners
+    const uint32_t *scol;
+    const uint8_t *sslot;
 };
 
 struct PgdBufs {
@@ -597,147 +639,103 @@ struct PgdBufs {
     __device__ __forceinline__ float4 *q(int i) const { return i ? Q[1] : Q[0]; }
 };
 
-// A row whose Adam step waits in its warp's queue: the row, its block and flags
-// (block | buffer parity << 31 | had a gradient before << 30 | stall reset << 29) and
-// its gradient as three double-floats.
-struct AdamEnt {
-    uint32_t e, meta;
-    float g[6];
-};
+// ------------------------------------------------------------------ one iteration: two kernels
+// Per iteration, k_pgd_screen walks every active pair with a float32 screen and lists the
+// candidate rows of the update: every row that has an uncertain pair (one the screen
+// could not certify as satisfied) or takes an Adam step (it has had a gradient, or needs
+// its first projection).  k_pgd_update then evaluates, for each candidate row with an
+// uncertain pair, that row's pairs in double-float (re-screening its edges, in edge
+// order), sums its gradient in edge order, and applies Adam to every candidate row; the
+// last block of the update takes the stop decisions of Algorithm 1.  The screen needs no
+// double-float state, so it runs at high occupancy, and the update works on a compact list
+// with every lane busy.
 
-#ifndef PC_PGD_EPL
-#define PC_PGD_EPL 4
-#endif
-constexpr int EPL = PC_PGD_EPL;   // edges per lane per trip of the edge walk
-constexpr int QCAP = 256;  // uncertain pairs waiting for evaluation (a ring per warp; < 32 + EPL x 32)
-constexpr int ACAP = 64;   // rows waiting for their Adam step (a ring per warp)
+// Candidate list entry: row | CAND_UNC when the row has an uncertain pair.
+constexpr uint32_t CAND_UNC = 0x80000000u;
+constexpr int SCREEN_BLOCKS_PER_SM = 5;
+constexpr int QCAP = 128;   // uncertain pairs waiting for evaluation (a ring per warp; < 32 + 2 x 32)
+constexpr int EPL = 4;      // edges per lane per trip of the screen's walk
 
-struct WarpTab {
-    uint32_t qk[QCAP];               // queued pairs: partner
-    uint8_t qs[QCAP];                // queued pairs: row slot | threshold index << 5 | link << 7
-    float4 q[32];                    // the rows' rounded current positions
-    unsigned own[32];                // per row slot: this batch's violated entries of that row
-    float gt[6][32];                 // this batch's gradient terms (x hi, x lo, y hi, ...) by entry
-    AdamEnt aq[ACAP];                // rows whose gradient is complete, waiting for Adam
-};
+// Edge range of one row: light rows own [ptr[e], ptr[e + 1]) of the light part, heavy rows
+// the range of their heavy item.
+__device__ __forceinline__ void row_edges(const LightPlan &LP, const HeavyPlan &H, const uint32_t *__restrict__ hmap,
+                                          uint32_t e, bool heavy, unsigned long long &start, uint32_t &len) {
+    if (heavy) {
+        const HeavyItem hv = H.item[hmap[e]];
+        start = hv.start;
+        len = hv.len;
+    } else {
+        start = LP.ptr[e];
+        len = (uint32_t)(LP.ptr[e + 1] - start);
+    }
+}
 
-// One PGD iteration for every block still iterating: check t_b and, unless it is the
-// block's last check, the update t_b + 1.
-//
-// Work items are groups of 32 consecutive light rows (editable particles) or one chunk
-// of HEAVY edges of a heavy row, handed out from a counter.  A warp walks the flat edge
-// range of its item 128 edges at a time (4 per lane, strided by 32 so that loads stay
-// coalesced and edge order is lane order within each 32-edge slice).  The float32 screen
-// on the rounded current positions Q certifies most pairs as satisfied; one warp vote
-// skips the queue when a whole trip is certified.  The others enter, in edge order, the
-// warp's ring of uncertain pairs, which the 32 lanes evaluate 32 at a time in
-// double-float; each row then adds its violated pairs one by one in edge order, so a
-// row's gradient does not depend on how rows are grouped into warps, batches or blocks
-// of the problem set.  A light row whose gradient is complete enters the warp's Adam
-// ring; whenever 32 rows are waiting, the warp applies Adam to them with every lane
-// busy (rows that need no update never enter, so the update runs on full warps).  A
-// heavy warp writes its chunk partial and k_pgd_heavy adds the partials of a heavy row
-// in chunk order.  MULTI = false is the single-block specialisation; with MULTI the
-// items come from the table of blocks still iterating, so a block that has stopped
-// costs nothing in later launches, and the rows of one item share a block.  MT: the
-// problem has several linking lengths and each CSR entry carries the index of its pair's
-// (single block only); the screen and the evaluation use that length's thresholds.
+// float32 screen of one pair: true when it may be violated (the double-float evaluation
+// decides).  qr: the row's rounded position; qk: the partner's; cv: the CSR entry.  PP:
+// minimum image; with one linking length the thresholds come in registers (sl_link,
+// sl_non), with several (MT) from the table by the entry's index.
+template <bool MT, bool PP>
+__device__ __forceinline__ bool screen_pair(const float4 qr, const float4 qk, uint32_t cv, const float L0,
+                                            const float L1, const float L2, float sl_link, float sl_non,
+                                            const PgdConsts &C) {
+    const float d2 = cdist2(cdiff(qr.x, qk.x, PP, L0), cdiff(qr.y, qk.y, PP, L1), cdiff(qr.z, qk.z, PP, L2));
+    if (MT) {
+        const int ti = (int)((cv >> 29) & 3u);
+        return (cv >> 31) ? !(d2 < C.screen_link[ti]) : !(d2 > C.screen_non[ti]);
+    }
+    return (cv >> 31) ? !(d2 < sl_link) : !(d2 > sl_non);
+}
+
+// Whether a warp whose rows are at rounded positions q (one per lane that holds a row)
+// may skip the minimum image: every row lies in the periodic box's interior, where no
+// active pair wraps (so the screen's d2 is the same bit for bit).
+__device__ __forceinline__ bool needs_image(const PgdConsts &C, bool row_lane, const float4 q) {
+    const bool in_ok = C.interior_ok != 0 && (!row_lane || (q.x >= C.ilo[0] && q.x <= C.ihi[0] && q.y >= C.ilo[1] &&
+                                                            q.y <= C.ihi[1] && q.z >= C.ilo[2] && q.z <= C.ihi[2]));
+    return C.periodic != 0 && !__all_sync(0xffffffffu, in_ok);
+}
+
+// The screen.  Work items are heavy rows (more than HEAVY partners; longest first, so the
+// longest walks start early) and groups of 32 consecutive light rows, handed out from a
+// counter (the next item is claimed one item ahead).  A warp walks its item's flat edge
+// range 128 edges at a time (4 per lane, strided by 32 so that loads stay coalesced; the
+// next trip's columns and slots load while this trip's partner positions are gathered),
+// and marks the rows with an uncertain pair.
 template <bool MULTI, bool MT>
-__global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
-    const float4 *__restrict__ PE, int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP,
-    const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs, const WorkTab wt,
-    double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
-    __shared__ int s_stop, s_t, s_reset, s_nact;
+__global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_screen(
+    int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP, const PgdConsts *__restrict__ CB,
+    const PgdBlk *__restrict__ blk, PgdGlobal *gs, const WorkTab wt, uint32_t *__restrict__ cand,
+    uint32_t *__restrict__ hcand) {
+    __shared__ int s_stop, s_t, s_nact;
     __shared__ unsigned long long s_items;
-    __shared__ df s_ibc1, s_ibc2;
-    __shared__ WarpTab tab[WARPS];
-    __shared__ BlockRed br;
+    __shared__ float4 sq[WARPS][32];      // the item's rows' rounded positions
+    __shared__ uint32_t sunc[WARPS];      // bit s: row slot s has an uncertain pair
     if (threadIdx.x == 0) {
         s_stop = gs->all_stop;
         s_nact = gs->active;
         s_items = gs->n_items;
         s_t = blk[0].t;
-        s_ibc1 = blk[0].ibc1;
-        s_ibc2 = blk[0].ibc2;
-        s_reset = blk[0].reset;
-        br.count = 0;
-        br.lfx = 0;
-        br.viol = 0;
-        br.upd = 0;
-        br.ev = 0;
     }
     __syncthreads();
     if (s_stop) return;
-
     const unsigned FULL = 0xffffffffu;
-    const unsigned lt_mask = (1u << (threadIdx.x & 31)) - 1u;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    WarpTab &T = tab[w];
-    // this lane's share of the tight loss (fixed point), violations, rows updated and
-    // pairs evaluated (single block: summed at the end of the launch)
-    unsigned long long lfx = 0;
-    unsigned viol = 0, nupd = 0, nev = 0;
+    constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;   // partner bits of a CSR entry
     const int64_t n_light_warps = (ne + 31) / 32;
-    const int64_t n_items = MULTI ? (int64_t)s_items : n_light_warps + H.n_chunks;
-    int ahead = 0, an = 0;   // Adam ring: first entry, entries waiting
-
-    // Adam on the first c rows of the ring (lane i takes row i).
-    auto adam_flush = [&](int c) {
-        if (lane < c) {
-            const AdamEnt &A = T.aq[(ahead + lane) & (ACAP - 1)];
-            const uint32_t e = A.e, meta = A.meta;
-            const int b = MULTI ? (int)(meta & 0x1fffffffu) : 0;
-            const int pa = (int)(meta >> 31);
-            const bool was = ((meta >> 30) & 1u) != 0, rs = ((meta >> 29) & 1u) != 0;
-            const df g[3] = {df_make(A.g[0], A.g[1]), df_make(A.g[2], A.g[3]), df_make(A.g[4], A.g[5])};
-            RowState S;
-            S.dh = Bf.dh(pa)[e];
-            S.dl = Bf.dl(pa)[e];
-            S.pe = PE[e];
-            if (was) {
-                S.mh = Bf.Mh[e];
-                S.ml = Bf.Ml[e];
-                S.vh = Bf.Vh[e];
-                S.vl = Bf.Vl[e];
-            }
-            const df i1 = MULTI ? blk[b].ibc1 : s_ibc1, i2 = MULTI ? blk[b].ibc2 : s_ibc2;
-            adam_core(e, g, S, was, was ? ACT_ON : (uint8_t)0, Bf.act, i1, i2, rs, CB[b], Bf.dh(pa ^ 1),
-                      Bf.dl(pa ^ 1), Bf.Mh, Bf.Ml, Bf.Vh, Bf.Vl, Bf.q(pa ^ 1));
-        }
-        ahead = (ahead + c) & (ACAP - 1);
-        an -= c;
-        __syncwarp();
-    };
-
-    // One loop, one place where Adam runs: a full warp's worth of waiting rows goes first;
-    // after the last item, whatever is left.
-    bool done = false;
-    // the next item is claimed one item ahead, so the claim's round trip overlaps a walk
+    const int64_t n_items = MULTI ? (int64_t)s_items : n_light_warps + H.n_heavy;
     unsigned long long nitm = 0;
     if (lane == 0) nitm = atomicAdd(&gs->work, 1ull);
     for (;;) {
-        if (an >= 32 || (done && an > 0)) {
-            adam_flush(min(an, 32));
-            continue;
-        }
-        if (done) break;
         const int64_t item = (int64_t)__shfl_sync(FULL, nitm, 0);
-        if (lane == 0 && item < n_items) nitm = atomicAdd(&gs->work, 1ull);
-        if (item >= n_items) {
-            done = true;
-            continue;
-        }
-
-        // the item's block: iteration, buffers and screen constants (one block per item)
+        if (item >= n_items) break;
+        if (lane == 0) nitm = atomicAdd(&gs->work, 1ull);
         int b = 0, tb = s_t;
-        bool bstop = false;
-        int64_t r0 = 0, item_chunk = 0;
+        int64_t r0 = 0, hk = 0;
         int cnt = 0;
         bool heavy_warp;
         if (MULTI) {
-            // active block of the item: largest k with act_pref[k] <= item
             int kk = 0;
-            if (lane == 0) {
+            if (lane == 0) {   // active block of the item: largest k with act_pref[k] <= item
                 int lo = 0, hi = s_nact - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
@@ -750,285 +748,409 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_iter(
             b = (int)wt.act_blk[kk];
             const int64_t j = item - (int64_t)wt.act_pref[kk];
             const BlkWork bw = wt.bw[b];
-            const int64_t nl = (bw.nrows + 31u) >> 5;
-            heavy_warp = j >= nl;
+            heavy_warp = j < (int64_t)bw.nh;
             if (!heavy_warp) {
-                r0 = (int64_t)bw.row0 + 32 * j;
-                cnt = (int)min((int64_t)32, (int64_t)bw.nrows - 32 * j);
+                const int64_t jl = j - (int64_t)bw.nh;
+                r0 = (int64_t)bw.row0 + 32 * jl;
+                cnt = (int)min((int64_t)32, (int64_t)bw.nrows - 32 * jl);
             } else {
-                item_chunk = (int64_t)bw.ch0 + (j - nl);
+                hk = (int64_t)bw.h0 + j;
             }
             tb = blk[b].t;
-            bstop = blk[b].stop != 0;
         } else {
-            heavy_warp = item >= n_light_warps;
+            heavy_warp = item < H.n_heavy;
             if (!heavy_warp) {
-                r0 = item * 32;
+                r0 = (item - H.n_heavy) * 32;
                 cnt = (int)min((int64_t)32, ne - r0);
             } else {
-                item_chunk = item - n_light_warps;
+                hk = item;
             }
         }
         const int pa = tb & 1;
-
-        // Edge range [ebase, ebase + VT) of the edge array: the light edges of the item's
-        // rows (each with its row's slot), or one heavy chunk (slot 0).  rbase: the row of
-        // slot 0.
-        int64_t rbase = r0, chunk = -1;
-        bool upd = false, was = false;   // the lane's row takes an update at this launch; had a gradient
-        uint32_t VT = 0;
-        unsigned long long ebase = 0;
-        float4 qe = make_float4(0.f, 0.f, 0.f, 0.f);
+        // the item's edges [ebase, ebase + VT); lane i holds row rbase + i (light: i < cnt;
+        // heavy: lane 0, slot 0)
+        int64_t rbase = r0;
+        bool have;
+        uint32_t VT;
+        unsigned long long ebase;
         if (!heavy_warp) {
-            const bool have = lane < cnt;
-            uint8_t av = 0;
-            if (have) {
-                const int64_t e = r0 + lane;
-                av = Bf.act[e];
-                qe = Bf.q(pa)[e];
-                T.q[lane] = qe;
-            }
-            const bool own = have && !bstop && !(av & ACT_HEAVY);
-            upd = own && !is_last(CB[b], tb);
-            was = (av & ACT_ON) != 0;
+            have = lane < cnt;
             unsigned long long lb = 0, le = 0;
             if (lane == 0) {
                 lb = LP.ptr[r0];
                 le = LP.ptr[r0 + cnt];
             }
             ebase = __shfl_sync(FULL, lb, 0);
-            VT = bstop ? 0u : (uint32_t)(__shfl_sync(FULL, le, 0) - ebase);
+            VT = (uint32_t)(__shfl_sync(FULL, le, 0) - ebase);
         } else {
-            chunk = item_chunk;
-            const uint32_t row = H.chunk_row[chunk];
-            ebase = H.chunk_start[chunk];
-            VT = bstop ? 0u : H.chunk_len[chunk];
-            rbase = row;
-            qe = Bf.q(pa)[row];
-            if (lane == 0) T.q[0] = qe;
+            const HeavyItem hv = H.item[hk];
+            have = lane == 0;
+            rbase = hv.row;
+            ebase = hv.start;
+            VT = hv.len;
+        }
+        const float4 qe = (have || heavy_warp) ? Bf.q(pa)[rbase + (heavy_warp ? 0 : lane)]
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        uint8_t av = 0;
+        if (have) {
+            av = Bf.act[rbase + lane];
+            sq[w][lane] = qe;
+        }
+        if (lane == 0) sunc[w] = 0u;
+        __syncwarp();
+        const PgdConsts &Cl = CB[b];
+        const bool pp = needs_image(Cl, heavy_warp || have, qe);
+        const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
+        const float4 *__restrict__ Qc = Bf.q(pa);
+        const uint32_t *__restrict__ ecol = (heavy_warp ? LP.col : LP.scol) + ebase;
+        const uint8_t *__restrict__ eslot = LP.sslot + ebase;
+        const float slk = Cl.screen_link[0], sln_ = Cl.screen_non[0];
+        auto walk = [&](auto image) {
+            constexpr bool PP = decltype(image)::value;
+            uint32_t cvn[EPL];
+            int sln[EPL];
+#pragma unroll
+            for (int j = 0; j < EPL; ++j) {
+                const uint32_t v = 32u * j + lane;
+                cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
+                sln[j] = (v < VT && !heavy_warp) ? (int)__ldcs(eslot + v) : 0;
+            }
+            for (uint32_t base = 0; base < VT; base += 32 * EPL) {
+                uint32_t cv[EPL];
+                int sl[EPL];
+                bool nd[EPL];
+#pragma unroll
+                for (int j = 0; j < EPL; ++j) {
+                    nd[j] = base + 32u * j + lane < VT;
+                    cv[j] = cvn[j];
+                    sl[j] = sln[j];
+                    const uint32_t v = base + 32u * (EPL + j) + lane;
+                    cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
+                    sln[j] = (v < VT && !heavy_warp) ? (int)__ldcs(eslot + v) : 0;
+                }
+                uint32_t um = 0u;
+#pragma unroll
+                for (int j = 0; j < EPL; ++j)
+                    if (nd[j] && screen_pair<MT, PP>(sq[w][sl[j]], Qc[cv[j] & PMASK], cv[j], L0, L1, L2, slk, sln_, Cl))
+                        um |= 1u << sl[j];
+                if (__any_sync(FULL, um != 0u) && um) atomicOr(&sunc[w], um);
+            }
+        };
+        if (pp) walk(std::true_type{});
+        else walk(std::false_type{});
+        __syncwarp();
+        // candidates of the update: rows with an uncertain pair, and rows that take a step
+        const bool unc = have && ((sunc[w] >> (heavy_warp ? 0 : lane)) & 1u);
+        const bool own = have && (heavy_warp || !(av & ACT_HEAVY));
+        const bool steps = (av & ACT_ON) && !is_last(Cl, tb);
+        // warp-uniform (the flag word is shared): both branches below hold whole warps, as
+        // the ballot and shuffle of the second one need
+        const bool heavy_unc = heavy_warp && (sunc[w] & 1u) != 0u;
+        if (heavy_unc) {
+            // a heavy row with an uncertain pair is re-walked by a warp of its own
+            if (lane == 0) hcand[atomicAdd(&gs->nhcand, 1ull)] = (uint32_t)rbase;
+        } else {
+            const bool c = own && (unc || steps);
+            const unsigned bal = __ballot_sync(FULL, c);
+            unsigned long long at = 0;
+            if (lane == 0 && bal) at = atomicAdd(&gs->ncand, (unsigned long long)__popc(bal));
+            at = __shfl_sync(FULL, at, 0);
+            if (c) cand[at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)(rbase + lane) | (unc ? CAND_UNC : 0u);
         }
         __syncwarp();
-        const PgdConsts &Cl = CB[b];            // the item's block
-        const float sl_link = Cl.screen_link[0], sl_non = Cl.screen_non[0];
-        constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;   // partner bits of a CSR entry
-        // a warp whose rows all sit in the box's interior screens without the minimum image
-        // (it never wraps there, so the screen's d2 is the same bit for bit)
-        const bool row_lane = heavy_warp || lane < cnt;
-        const bool in_ok = Cl.interior_ok != 0 &&
-                           (!row_lane || (qe.x >= Cl.ilo[0] && qe.x <= Cl.ihi[0] && qe.y >= Cl.ilo[1] &&
-                                          qe.y <= Cl.ihi[1] && qe.z >= Cl.ilo[2] && qe.z <= Cl.ihi[2]));
-        const bool pp = Cl.periodic != 0 && !__all_sync(FULL, in_ok);
-        const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
-        const float4 *Qc = Bf.q(pa);
-        const float4 *Dh = Bf.dh(pa), *Dl = Bf.dl(pa);
+    }
+}
 
+struct WarpTab {
+    float4 st[7][32];                // the rows' Adam state (offset hi, lo, position, m hi, lo, v hi, lo)
+    uint32_t qk[QCAP];               // queued pairs: partner
+    uint8_t qs[QCAP];                // queued pairs: row slot | threshold index << 5 | link << 7
+    uint32_t erow[32];               // the chunk's rows by slot
+    int eb[32], epa[32];             // ... their blocks and buffer parities
+    unsigned own[32];                // per row slot: this batch's violated entries of that row
+    float gt[6][32];                 // this batch's gradient terms (x hi, x lo, y hi, ...) by entry
+};
+
+// 16-byte asynchronous copies from global to shared memory (not cached in L1).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The update: warps take first the heavy rows with an uncertain pair, one each, then the
+// other candidate rows 32 at a time (slot i = lane i).  The rows with an
+// uncertain pair are re-screened by the whole warp, 32 edges at a time, one row after the
+// other in slot order; the pairs the screen cannot certify enter the warp's ring, in edge
+// order, tagged with their row's slot, and are evaluated in double-float 32 at a time.
+// Each light row's owner lane then adds its violated pairs one by one in edge order (the
+// same order for any grouping of rows, so a row's gradient does not depend on its chunk,
+// batch or block); a heavy row's warp adds each batch of its pairs by a fixed tree first.
+// Then every candidate row that is due takes its Adam step, lanes in parallel.
+template <bool MULTI, bool MT>
+__global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
+    const float4 *__restrict__ PE, PgdBufs Bf, HeavyPlan H, LightPlan LP, const uint32_t *__restrict__ hmap,
+    const uint32_t *__restrict__ rb, const uint32_t *__restrict__ cand, const uint32_t *__restrict__ hcand,
+    const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs, const WorkTab wt,
+    double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
+    __shared__ int s_stop, s_t, s_reset;
+    __shared__ unsigned long long s_ncand, s_nhcand;
+    __shared__ df s_ibc1, s_ibc2;
+    __shared__ WarpTab tab[WARPS];
+    __shared__ BlockRed br;
+    if (threadIdx.x == 0) {
+        s_stop = gs->all_stop;
+        s_ncand = gs->ncand;
+        s_nhcand = gs->nhcand;
+        s_t = blk[0].t;
+        s_ibc1 = blk[0].ibc1;
+        s_ibc2 = blk[0].ibc2;
+        s_reset = blk[0].reset;
+        br.count = 0;
+        br.lfx = 0;
+        br.viol = 0;
+        br.upd = 0;
+        br.ev = 0;
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    WarpTab &T = tab[w];
+    constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;
+    unsigned long long lfx = 0;       // this lane's share of the tight loss, fixed point (single block)
+    unsigned viol = 0, nupd = 0, nev = 0;
+    const unsigned long long ncand = s_ncand, nhcand = s_nhcand;
+    bool heavy_done = false;
+    for (;;) {
+        // claim: a heavy row (slot 0), else a chunk of 32 candidate rows
+        unsigned long long cb = 0;
+        int kind = 0;   // 1: heavy row, 2: chunk, 0: nothing left
+        if (lane == 0) {
+            if (!heavy_done) {
+                cb = atomicAdd(&gs->work3, 1ull);
+                if (cb < nhcand) kind = 1;
+                else heavy_done = true;
+            }
+            if (kind == 0) {
+                cb = atomicAdd(&gs->work2, 32ull);
+                kind = cb < ncand ? 2 : 0;
+            }
+        }
+        kind = __shfl_sync(FULL, kind, 0);
+        heavy_done = __shfl_sync(FULL, heavy_done, 0);
+        cb = __shfl_sync(FULL, cb, 0);
+        if (kind == 0) break;
+        const bool have = kind == 1 ? lane == 0 : cb + lane < ncand;
+        const uint32_t ce = !have ? 0u : (kind == 1 ? (hcand[cb] | CAND_UNC) : cand[cb + lane]);
+        const uint32_t e = ce & ~CAND_UNC;
+        const bool unc = have && (ce & CAND_UNC);
+        const int b = MULTI ? (have ? (int)rb[e] : 0) : 0;
+        const int tb = MULTI ? blk[b].t : s_t;
+        const int pa = tb & 1;
+        const PgdConsts &C = CB[b];
         df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};   // gradient of the lane's row
-        bool rv = false;             // the lane's row has a violated pair
-        int qh = 0, qn = 0;          // uncertain-pair ring: first entry, entries waiting
+        bool rv = false;                   // the lane's row has a violated pair
+        uint8_t av = 0;
+        if (have) av = Bf.act[e];
+        // the rows' Adam state travels to shared memory while the uncertain pairs are evaluated
+        const bool due = have && !is_last(C, tb);
+        const bool was = (av & ACT_ON) != 0;
+        if (due && (was || unc)) {
+            cp_async16(&T.st[0][lane], Bf.dh(pa) + e);
+            cp_async16(&T.st[1][lane], Bf.dl(pa) + e);
+            cp_async16(&T.st[2][lane], PE + e);
+            if (was) {
+                cp_async16(&T.st[3][lane], Bf.Mh + e);
+                cp_async16(&T.st[4][lane], Bf.Ml + e);
+                cp_async16(&T.st[5][lane], Bf.Vh + e);
+                cp_async16(&T.st[6][lane], Bf.Vl + e);
+            }
+        }
+        cp_async_commit();
+        T.erow[lane] = e;
+        T.eb[lane] = b;
+        T.epa[lane] = pa;
+        __syncwarp();
 
-        // Evaluates the first min(qn, 32) queued pairs and adds each violated pair's term
-        // to its row's gradient.
+        int qh = 0, qn = 0;
+        // evaluates the first min(qn, 32) queued pairs; their rows' owners add the violated ones
         auto batch = [&]() {
             const int c = min(qn, 32);
-            const bool valid = lane < c;
-            int s = 32;
+            int sq = 32;
             df gt[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
             bool hit = false;
-            if (valid) {
+            unsigned long long ll = 0;
+            unsigned lv = 0;
+            int bs = -1;
+            if (lane < c) {
                 const int pos = (qh + lane) & (QCAP - 1);
                 const uint32_t k = T.qk[pos];
                 const uint32_t qsv = T.qs[pos];
-                s = (int)(qsv & 0x1fu);
+                sq = (int)(qsv & 0x1fu);
                 const int ti = MT ? (int)((qsv >> 5) & 3u) : 0;
-                const bool link = (qsv >> 7) != 0;
-                const int64_t er = rbase + s;
+                const uint32_t er = T.erow[sq];
+                bs = T.eb[sq];
+                const int ps = T.epa[sq];
+                const float4 *Dh = Bf.dh(ps), *Dl = Bf.dl(ps);
                 double ltv = 0.0;
                 bool counts = false;
-                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, link, ti, PE, Dh, Dl, Cl, gt, ltv, counts);
+                hit = eval_pair(PE[er], Dh[er], Dl[er], er, k, (qsv >> 7) != 0, ti, PE, Dh, Dl, CB[bs], gt, ltv,
+                                counts);
                 if (hit) {
-                    lfx += (unsigned long long)llrint(ltv);
-                    viol += ((int64_t)k > er && counts) ? 1u : 0u;
+                    ll = (unsigned long long)llrint(ltv);
+                    lv = (k > er && counts) ? 1u : 0u;
                 }
-                ++nev;
             }
-            // Each row adds its violated pairs one by one in edge order (queue order is
-            // edge order).  The row's owner is lane `slot` (light) or lane 0 (heavy: slot 0):
-            // the entries of a slot are found with one match, and every owner walks its own
-            // entries while the others walk theirs.
-            if (hit) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    T.gt[2 * a][lane] = gt[a].hi;
-                    T.gt[2 * a + 1][lane] = gt[a].lo;
-                }
+            if (MULTI) {   // the pairs' loss belongs to their rows' blocks
+                if (ll) atomicAdd(&blk[bs].lfx, ll);
+                if (lv) atomicAdd(&blk[bs].vacc, (unsigned long long)lv);
+                const unsigned same = __match_any_sync(FULL, bs);
+                const unsigned ge = __reduce_add_sync(same, lane < c ? 1u : 0u);
+                if (bs >= 0 && lane == __ffs(same) - 1 && ge) atomicAdd(&blk[bs].eacc, (unsigned long long)ge);
+            } else {
+                lfx += ll;
+                viol += lv;
+                nev += lane < c ? 1u : 0u;
             }
             const unsigned hm = __ballot_sync(FULL, hit);
-            T.own[lane] = 0u;
-            const unsigned same = __match_any_sync(FULL, s);
-            __syncwarp();
-            if (hit) T.own[s] = same & hm;   // the entries of one slot all write the same mask
-            __syncwarp();
-            for (unsigned mine = T.own[lane]; mine; mine &= mine - 1) {
-                const int i = __ffs(mine) - 1;
+            if (kind == 1) {
+                // one heavy row (slot 0): the batch holds entries [32k, 32k + 32) of the row's
+                // re-screened pairs, added by a fixed tree over those positions (zeros where
+                // a pair is not violated), then into the row's sum; the shape depends on the
+                // row's data alone, so the sum is the same in every run
+                df t[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], df_make(T.gt[2 * a][i], T.gt[2 * a + 1][i]));
-                rv = true;
+                for (int a = 0; a < 3; ++a) t[a] = hit ? gt[a] : df_make(0.f, 0.f);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        t[a] = df_add(t[a], df_make(__shfl_down_sync(FULL, t[a].hi, off),
+                                                    __shfl_down_sync(FULL, t[a].lo, off)));
+                if (lane == 0 && hm) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], t[a]);
+                    rv = true;
+                }
+            } else {
+                if (hit) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        T.gt[2 * a][lane] = gt[a].hi;
+                        T.gt[2 * a + 1][lane] = gt[a].lo;
+                    }
+                }
+                T.own[lane] = 0u;
+                const unsigned same_s = __match_any_sync(FULL, sq);
+                __syncwarp();
+                if (hit) T.own[sq] = same_s & hm;   // the entries of one slot all write the same mask
+                __syncwarp();
+                for (unsigned mine = T.own[lane]; mine; mine &= mine - 1) {
+                    const int i = __ffs(mine) - 1;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) g[a] = df_add(g[a], df_make(T.gt[2 * a][i], T.gt[2 * a + 1][i]));
+                    rv = true;
+                }
             }
             qh = (qh + c) & (QCAP - 1);
             qn -= c;
             __syncwarp();
         };
 
-        // float32 screen of one edge of row slot s against partner cv: true when the pair
-        // may be violated (the double-float evaluation decides)
-        auto screen = [&](bool ok, int s, uint32_t cv) -> bool {
-            if (!ok) return false;
-            const float4 qr = T.q[s];
-            const float4 qk = Qc[cv & PMASK];
-            const float d2 =
-                cdist2(cdiff(qr.x, qk.x, pp, L0), cdiff(qr.y, qk.y, pp, L1), cdiff(qr.z, qk.z, pp, L2));
-            if (MT) {
-                const int ti = (cv >> 29) & 3;
-                return (cv >> 31) ? !(d2 < Cl.screen_link[ti]) : !(d2 > Cl.screen_non[ti]);
-            }
-            return (cv >> 31) ? !(d2 < sl_link) : !(d2 > sl_non);
-        };
-
-        const uint32_t *__restrict__ ecol = LP.col + ebase;
-        const uint8_t *__restrict__ eslot = LP.slot + ebase;
-        // software pipeline: the columns and slots of the next trip are loaded before this
-        // trip's partner positions are gathered, so each trip waits on one round trip
-        uint32_t cvn[EPL];
-        int sln[EPL];
+        // re-screen the edges of every row with an uncertain pair, in slot order
+        for (unsigned um = __ballot_sync(FULL, unc); um; um &= um - 1) {
+            const int r = __ffs(um) - 1;
+            const uint32_t er = T.erow[r];
+            const int par = T.epa[r];
+            const PgdConsts &Cr = CB[T.eb[r]];
+            const uint8_t avr = (uint8_t)__shfl_sync(FULL, (unsigned)av, r);
+            const float4 *Qc = Bf.q(par);
+            const float4 qr = Qc[er];
+            const bool pp = needs_image(Cr, true, qr);
+            const float L0 = Cr.L[0], L1 = Cr.L[1], L2 = Cr.L[2];
+            unsigned long long es;
+            uint32_t len;
+            row_edges(LP, H, hmap, er, (avr & ACT_HEAVY) != 0, es, len);
+            const uint32_t *__restrict__ ecol = LP.col + es;
+            for (uint32_t base = 0; base < len; base += 64) {
+                uint32_t cv[2];
+                bool nd[2];
 #pragma unroll
-        for (int j = 0; j < EPL; ++j) {
-            const uint32_t v = 32u * j + lane;
-            cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
-            sln[j] = (v < VT && !heavy_warp) ? (int)__ldcs(eslot + v) : 0;
-        }
-        for (uint32_t base = 0; base < VT; base += 32 * EPL) {
-            uint32_t cv[EPL];
-            int sl[EPL];
-            bool nd[EPL];
-#pragma unroll
-            for (int j = 0; j < EPL; ++j) {
-                nd[j] = base + 32u * j + lane < VT;
-                cv[j] = cvn[j];
-                sl[j] = sln[j];
-                const uint32_t v = base + 32u * (EPL + j) + lane;
-                cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
-                sln[j] = (v < VT && !heavy_warp) ? (int)__ldcs(eslot + v) : 0;
-            }
-            bool any = false;
-#pragma unroll
-            for (int j = 0; j < EPL; ++j) {
-                nd[j] = screen(nd[j], sl[j], cv[j]);
-                any |= nd[j];
-            }
-            if (!__any_sync(FULL, any)) continue;
-#pragma unroll
-            for (int j = 0; j < EPL; ++j) {
-                const unsigned bal = __ballot_sync(FULL, nd[j]);
-                if (nd[j]) {
-                    const int pos = (qh + qn + __popc(bal & lt_mask)) & (QCAP - 1);
-                    T.qk[pos] = cv[j] & PMASK;
-                    T.qs[pos] = (uint8_t)(sl[j] | (MT ? ((cv[j] >> 29) & 3u) << 5 : 0u) | ((cv[j] >> 31) ? 0x80 : 0));
+                for (int j = 0; j < 2; ++j) {
+                    const uint32_t v = base + 32u * j + lane;
+                    cv[j] = v < len ? ecol[v] : 0u;
+                    nd[j] = v < len;
                 }
-                qn += __popc(bal);
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    nd[j] = nd[j] && (pp ? screen_pair<MT, true>(qr, Qc[cv[j] & PMASK], cv[j], L0, L1, L2,
+                                                                 Cr.screen_link[0], Cr.screen_non[0], Cr)
+                                         : screen_pair<MT, false>(qr, Qc[cv[j] & PMASK], cv[j], L0, L1, L2,
+                                                                  Cr.screen_link[0], Cr.screen_non[0], Cr));
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const unsigned bal = __ballot_sync(FULL, nd[j]);
+                    if (nd[j]) {
+                        const int pos = (qh + qn + __popc(bal & lt_mask)) & (QCAP - 1);
+                        T.qk[pos] = cv[j] & PMASK;
+                        T.qs[pos] = (uint8_t)(r | (MT ? ((cv[j] >> 29) & 3u) << 5 : 0u) | ((cv[j] >> 31) ? 0x80 : 0));
+                    }
+                    qn += __popc(bal);
+                }
+                __syncwarp();
+                while (qn >= 32) batch();
             }
-            __syncwarp();
-            while (qn >= 32) batch();
         }
         while (qn > 0) batch();
 
-        if (!heavy_warp) {
-            // rows whose update is due join the Adam ring; a full warp's worth is applied
-            bool need = false, rs = false;
-            if (upd) {
-                rs = rv && (MULTI ? blk[b].reset != 0 : s_reset != 0);
-                const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
-                need = was || !gz || rs;
-            }
-            const unsigned bal = __ballot_sync(FULL, need);
-            if (need) {
-                AdamEnt &A = T.aq[(ahead + an + __popc(bal & lt_mask)) & (ACAP - 1)];
-                A.e = (uint32_t)(r0 + lane);
-                A.meta = (MULTI ? (uint32_t)b : 0u) | ((uint32_t)pa << 31) | ((uint32_t)was << 30) |
-                         ((uint32_t)rs << 29);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    A.g[2 * a] = g[a].hi;
-                    A.g[2 * a + 1] = g[a].lo;
+        // Adam on every candidate row that is due (its block is not at its last check)
+        cp_async_wait_all();
+        if (due) {
+            const bool rs = rv && (MULTI ? blk[b].reset != 0 : s_reset != 0);
+            const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
+            if (was || !gz || rs) {
+                RowState S;
+                S.dh = T.st[0][lane];
+                S.dl = T.st[1][lane];
+                S.pe = T.st[2][lane];
+                if (was) {
+                    S.mh = T.st[3][lane];
+                    S.ml = T.st[4][lane];
+                    S.vh = T.st[5][lane];
+                    S.vl = T.st[6][lane];
                 }
+                const df i1 = MULTI ? blk[b].ibc1 : s_ibc1, i2 = MULTI ? blk[b].ibc2 : s_ibc2;
+                adam_core(e, g, S, was, av, Bf.act, i1, i2, rs, C, Bf.dh(pa ^ 1), Bf.dl(pa ^ 1), Bf.Mh, Bf.Ml, Bf.Vh,
+                          Bf.Vl, Bf.q(pa ^ 1));
+                ++nupd;
             }
-            const int nn = __popc(bal);
-            an += nn;
-            if (!MULTI) nupd += (lane == 0) ? (unsigned)nn : 0u;
-            __syncwarp();
-            if (MULTI && lane == 0 && nn) atomicAdd(&blk[b].uacc, (unsigned long long)nn);
-        } else if (lane == 0 && !bstop) {
-            H.chunk_g[2 * chunk] = make_float4(g[0].hi, g[1].hi, g[2].hi, rv ? 1.f : 0.f);
-            H.chunk_g[2 * chunk + 1] = make_float4(g[0].lo, g[1].lo, g[2].lo, 0.f);
         }
         if (MULTI) {
-            // the item's loss, violations and evaluations belong to its block
-            const unsigned long long il = warp_sum_u(lfx), iv = __reduce_add_sync(FULL, viol),
-                                     ie = __reduce_add_sync(FULL, nev);
-            if (lane == 0 && !bstop) {
-                if (il) atomicAdd(&blk[b].lfx, il);
-                if (iv) atomicAdd(&blk[b].vacc, iv);
-                if (ie) atomicAdd(&blk[b].eacc, ie);
-            }
-            lfx = 0;
-            viol = 0;
-            nev = 0;
+            // the chunk's updates, by the rows' blocks
+            const unsigned same = __match_any_sync(FULL, have ? b : -1);
+            const unsigned su = __reduce_add_sync(same, nupd);
+            if (have && lane == __ffs(same) - 1 && su) atomicAdd(&blk[b].uacc, (unsigned long long)su);
+            nupd = 0;
         }
         __syncwarp();
-    }   // work items
+    }
     finish_iteration<MULTI>(br, lfx, viol, nupd, nev, CB, nb, blk, gs, hist_loss, hist_viol, wt);
 }
 
-// Heavy rows: sum the chunk partials in chunk order and apply Adam (same update as
-// light rows), with the check index and step of the iteration launch just finished.
-__global__ void k_pgd_heavy(const uint32_t *__restrict__ hrow, const uint32_t *__restrict__ hc0, int64_t nh,
-                            const float4 *__restrict__ chunk_g, const float4 *__restrict__ PE,
-                            const uint32_t *__restrict__ rb, PgdBufs Bf, const PgdConsts *__restrict__ CB,
-                            PgdBlk *blk) {
-    GRID_STRIDE(i, nh) {
-        const uint32_t e = hrow[i];
-        const int b = (int)rb[e];
-        PgdBlk &B = blk[b];
-        if (!B.upd_on) continue;
-        const int pa = B.upd_t & 1;
-        df g[3] = {df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
-        bool rv = false;
-        for (uint32_t c = hc0[i]; c < hc0[i + 1]; ++c) {
-            const float4 h = chunk_g[2 * c], l = chunk_g[2 * c + 1];
-            rv |= h.w != 0.f;
-            g[0] = df_add(g[0], df_make(h.x, l.x));
-            g[1] = df_add(g[1], df_make(h.y, l.y));
-            g[2] = df_add(g[2], df_make(h.z, l.z));
-        }
-        const bool gz = g[0].hi == 0.f && g[1].hi == 0.f && g[2].hi == 0.f;
-        const bool rs = rv && B.upd_reset != 0;
-        if ((Bf.act[e] & ACT_ON) || !gz || rs) atomicAdd(&B.n_upd, 1ull);
-        adam_row(e, g, Bf.dh(pa), Bf.dl(pa), PE, Bf.act, B.upd_ibc1, B.upd_ibc2, rs, CB[b], Bf.dh(pa ^ 1),
-                 Bf.dl(pa ^ 1), Bf.Mh, Bf.Ml, Bf.Vh, Bf.Vl, Bf.q(pa ^ 1));
-    }
-}
-
 // ------------------------------------------------------------------ edge plan
-// Degrees from the CSR offsets: light degree (0 for a heavy row), heavy degree, chunk
-// count and heavy flag of every row; the heavy bit also goes into act.
+// Degrees from the CSR offsets: light degree (0 for a heavy row), heavy degree and heavy
+// flag of every row; the heavy bit also goes into act.
 __global__ void k_degrees(const unsigned long long *__restrict__ row_ptr, int64_t ne,
                           unsigned long long *__restrict__ ldeg, unsigned long long *__restrict__ hdeg,
-                          uint32_t *__restrict__ nchunk, uint32_t *__restrict__ isheavy, uint8_t *__restrict__ act) {
+                          uint32_t *__restrict__ isheavy, uint8_t *__restrict__ act) {
     GRID_STRIDE(e, ne) {
         const unsigned long long d = row_ptr[e + 1] - row_ptr[e];
         const bool h = d > HEAVY;
         ldeg[e] = h ? 0ull : d;
         hdeg[e] = h ? d : 0ull;
-        nchunk[e] = h ? (uint32_t)((d + HEAVY - 1) / HEAVY) : 0u;
         isheavy[e] = h ? 1u : 0u;
         if (h) act[e] = (uint8_t)(act[e] | ACT_HEAVY);
     }
@@ -1039,30 +1161,30 @@ struct ThrB2 {
     float b2[MAX_THR];
 };
 
-// One CSR entry per directed edge t (sorted keys: row, partner position, threshold
-// index): partner's dense index, threshold index and the link flag at the pair's own
-// linking length, written to the row's place in the edge array (light rows: their
-// group's range, with the row's slot; heavy rows: after every light edge).
-__global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, int nb, int tb, ThrB2 tb2,
+// One CSR entry per directed edge t (sorted keys: row, partner row, threshold index):
+// partner's row, threshold index and the link flag at the pair's own linking length,
+// written to the row's place in the edge array (light rows: their group's range, with the
+// row's slot; heavy rows: after every light edge).
+__global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, int nbe, int tb, ThrB2 tb2,
                        const unsigned long long *__restrict__ row_ptr, const unsigned long long *__restrict__ lptr,
                        const unsigned long long *__restrict__ hptr, unsigned long long n_light,
-                       const uint32_t *__restrict__ dense, const uint32_t *__restrict__ epos,
-                       const uint32_t *__restrict__ rb, const int64_t *__restrict__ roff,
-                       const float4 *__restrict__ P4, const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
-                       int nblk, uint32_t *__restrict__ ecol, uint8_t *__restrict__ eslot) {
-    const unsigned long long mask = (1ull << nb) - 1ull;
+                       const uint32_t *__restrict__ epos, const uint32_t *__restrict__ rb,
+                       const int64_t *__restrict__ roff, const float4 *__restrict__ P4,
+                       const BlockDev *__restrict__ bt, const int64_t *__restrict__ off, int nblk,
+                       uint32_t *__restrict__ ecol, uint8_t *__restrict__ eslot) {
+    const unsigned long long mask = (1ull << nbe) - 1ull;
     GRID_STRIDE(t, m) {
         const unsigned long long k = keys[t];
         const uint32_t ti = (uint32_t)(k & ((1ull << tb) - 1ull));
-        const uint32_t row = (uint32_t)(k >> (nb + tb)), nbp = (uint32_t)((k >> tb) & mask);
+        const uint32_t row = (uint32_t)(k >> (nbe + tb)), prow = (uint32_t)((k >> tb) & mask);
         const uint32_t pos = epos[row];
         const BlockDev &B = bt[find_block(off, nblk, pos)];
-        const float4 p = P4[pos], q = P4[nbp];
+        const float4 p = P4[pos], q = P4[epos[prow]];
         const float3 d = canon_dp(p, q, B.periodic, B.L);
         // the link flag at the pair's own linking length
         const float b2 = tb ? (ti == 0 ? tb2.b2[0] : ti == 1 ? tb2.b2[1] : ti == 2 ? tb2.b2[2] : tb2.b2[3]) : B.b2;
         const bool link = cdist2(d.x, d.y, d.z) <= b2;
-        const uint32_t cv = dense[nbp] | (ti << 29) | (link ? 0x80000000u : 0u);
+        const uint32_t cv = prow | (ti << 29) | (link ? 0x80000000u : 0u);
         const unsigned long long r_lo = row_ptr[row], j = (unsigned long long)t - r_lo;
         if (row_ptr[row + 1] - r_lo > HEAVY) {
             ecol[n_light + hptr[row] + j] = cv;
@@ -1075,25 +1197,77 @@ __global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, i
     }
 }
 
-// Heavy rows: the chunks (row, first edge, length) and the per-row chunk ranges.
-__global__ void k_heavy_fill(const unsigned long long *__restrict__ hdeg, const unsigned long long *__restrict__ hptr,
-                             unsigned long long n_light, int64_t ne, const uint32_t *__restrict__ nchunk,
-                             const uint32_t *__restrict__ c0, const uint32_t *__restrict__ isheavy,
-                             const uint32_t *__restrict__ hpos, uint32_t *__restrict__ chunk_row,
-                             unsigned long long *__restrict__ chunk_start, uint32_t *__restrict__ chunk_len,
-                             uint32_t *__restrict__ hrow, uint32_t *__restrict__ hc0) {
+// The 32-row groups of light rows (groups start at the first row of each block): first
+// row and row count of each, appended in any order.
+__global__ void k_groups(int64_t ne, const uint32_t *__restrict__ rb, const int64_t *__restrict__ roff,
+                         uint2 *__restrict__ grp, unsigned long long *__restrict__ ngrp) {
+    GRID_STRIDE(e, ne) {
+        const int64_t r0 = roff ? roff[rb[e]] : 0, r1 = roff ? roff[rb[e] + 1] : ne;
+        if (((e - r0) & 31) != 0) continue;
+        const unsigned long long at = atomicAdd(ngrp, 1ull);
+        grp[at] = make_uint2((uint32_t)e, (uint32_t)min((int64_t)32, r1 - e));
+    }
+}
+
+// The screen's edge stream: each group's light edges sorted by (CSR entry, slot), one CTA
+// per group, a bitonic sort in shared memory (groups hold at most 32 x HEAVY edges).
+constexpr int GSORT_CAP = 32 * HEAVY;
+__global__ void __launch_bounds__(256) k_group_sort(const uint2 *__restrict__ grp, const unsigned long long *__restrict__ lptr,
+                                                    const uint32_t *__restrict__ col, const uint8_t *__restrict__ slot,
+                                                    uint32_t *__restrict__ scol, uint8_t *__restrict__ sslot) {
+    extern __shared__ unsigned long long sk[];
+    const uint2 g = grp[blockIdx.x];
+    const unsigned long long a = lptr[g.x], len = lptr[g.x + g.y] - a;
+    if (len == 0) return;
+    int cap = 1;
+    while (cap < (int)len) cap <<= 1;
+    for (int i = threadIdx.x; i < cap; i += blockDim.x)
+        sk[i] = i < (int)len ? (((unsigned long long)col[a + i] << 8) | slot[a + i]) : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= cap; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long x = sk[i], y = sk[l];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        sk[i] = y;
+                        sk[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < (int)len; i += blockDim.x) {
+        scol[a + i] = (uint32_t)(sk[i] >> 8);
+        sslot[a + i] = (uint8_t)(sk[i] & 0xffu);
+    }
+}
+
+// Heavy rows, compacted: sort key (block << 32 | ~degree, so that each block's heavy rows
+// come together, longest first), row, and the rows per block.
+__global__ void k_heavy_keys(const unsigned long long *__restrict__ hdeg, const uint32_t *__restrict__ isheavy,
+                             const uint32_t *__restrict__ hpos, const uint32_t *__restrict__ rb, int64_t ne,
+                             unsigned long long *__restrict__ hkey, uint32_t *__restrict__ hrow,
+                             uint32_t *__restrict__ per_block) {
     GRID_STRIDE(e, ne) {
         if (!isheavy[e]) continue;
-        const uint32_t c = c0[e];
-        const unsigned long long d = hdeg[e];
-        for (uint32_t j = 0; j < nchunk[e]; ++j) {
-            const unsigned long long s0 = (unsigned long long)j * HEAVY;
-            chunk_row[c + j] = (uint32_t)e;
-            chunk_start[c + j] = n_light + hptr[e] + s0;
-            chunk_len[c + j] = (uint32_t)min((unsigned long long)HEAVY, d - s0);
-        }
-        hrow[hpos[e]] = (uint32_t)e;
-        hc0[hpos[e]] = c;
+        const uint32_t k = hpos[e], b = rb[e];
+        hkey[k] = ((unsigned long long)b << 32) | (0xffffffffull - min(hdeg[e], 0xffffffffull));
+        hrow[k] = (uint32_t)e;
+        atomicAdd(per_block + b, 1u);
+    }
+}
+
+// The heavy items in sorted order: edge range and row.
+__global__ void k_heavy_items(const uint32_t *__restrict__ hrow, int64_t nh, const unsigned long long *__restrict__ hptr,
+                              const unsigned long long *__restrict__ hdeg, unsigned long long n_light,
+                              HeavyItem *__restrict__ item, uint32_t *__restrict__ hmap) {
+    GRID_STRIDE(k, nh) {
+        const uint32_t e = hrow[k];
+        item[k] = HeavyItem{n_light + hptr[e], e, (uint32_t)hdeg[e]};
+        hmap[e] = (uint32_t)k;
     }
 }
 
@@ -1216,18 +1390,20 @@ void pgd_thresholds(PgdConsts &K, const std::vector<Consts> &ck, const pc_params
 struct PgdSolver::Impl {
     cudaStream_t s = 0;
     int nb = 0;
-    int64_t ne = 0, n_heavy = 0, max_checks = 0;
+    int64_t ne = 0, n_heavy = 0, max_checks = 0, n_items = 0;
     int nblk = 1;
     double *hist_loss = nullptr;
     unsigned long long *hist_viol = nullptr;
     DBuf<PgdConsts> CB;
     DBuf<PgdBlk> blk;
     DBuf<PgdGlobal> gs;
-    DBuf<uint32_t> rb, chunk_row, chunk_len, hrow, hc0, ecol;
-    DBuf<unsigned long long> lptr, chunk_start;
-    DBuf<uint8_t> eslot;
+    DBuf<uint32_t> rb, ecol, hmap, cand, hcand;
+    DBuf<unsigned long long> lptr;
+    DBuf<HeavyItem> hitem;
+    DBuf<uint8_t> eslot, sslot;
+    DBuf<uint32_t> scol;
     LightPlan LP{};
-    DBuf<float4> PE, Dh0, Dl0, Dh1, Dl1, Mh, Ml, Vh, Vl, Q0, Q1, chunk_g;
+    DBuf<float4> PE, Dh0, Dl0, Dh1, Dl1, Mh, Ml, Vh, Vl, Q0, Q1;
     DBuf<uint8_t> act;
     DBuf<BlkWork> bw;
     DBuf<uint32_t> act_blk;
@@ -1244,26 +1420,29 @@ struct PgdSolver::Impl {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_k = 0;
-    int kernels_per_iter = 1;
 
     bool mt = false;                         // several linking lengths (single block)
 
     void launch_iter() {
-        if (mt)
-            k_pgd_iter<false, true><<<nblk, PGD_THREADS, 0, s>>>(PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p, gs.p, wt,
-                                                                 hist_loss, hist_viol);
-        else if (nb == 1)
-            k_pgd_iter<false, false><<<nblk, PGD_THREADS, 0, s>>>(PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p, gs.p, wt,
-                                                                  hist_loss, hist_viol);
-        else
-            k_pgd_iter<true, false><<<nblk, PGD_THREADS, 0, s>>>(PE.p, ne, Bf, HP, LP, CB.p, nb, blk.p, gs.p, wt,
-                                                                 nullptr, nullptr);
-        PC_CHECK_LAUNCH();
-        if (n_heavy > 0) {
-            k_pgd_heavy<<<grid_for(n_heavy), 256, 0, s>>>(hrow.p, hc0.p, n_heavy, chunk_g.p, PE.p, rb.p, Bf, CB.p,
-                                                          blk.p);
+        const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS),
+                                                                  (int64_t)num_sms() * SCREEN_BLOCKS_PER_SM));
+        if (mt) {
+            k_pgd_screen<false, true><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, cand.p, hcand.p);
             PC_CHECK_LAUNCH();
+            k_pgd_update<false, true><<<nblk, PGD_THREADS, 0, s>>>(PE.p, Bf, HP, LP, hmap.p, rb.p, cand.p, hcand.p, CB.p, nb,
+                                                                   blk.p, gs.p, wt, hist_loss, hist_viol);
+        } else if (nb == 1) {
+            k_pgd_screen<false, false><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, cand.p, hcand.p);
+            PC_CHECK_LAUNCH();
+            k_pgd_update<false, false><<<nblk, PGD_THREADS, 0, s>>>(PE.p, Bf, HP, LP, hmap.p, rb.p, cand.p, hcand.p, CB.p, nb,
+                                                                    blk.p, gs.p, wt, hist_loss, hist_viol);
+        } else {
+            k_pgd_screen<true, false><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, cand.p, hcand.p);
+            PC_CHECK_LAUNCH();
+            k_pgd_update<true, false><<<nblk, PGD_THREADS, 0, s>>>(PE.p, Bf, HP, LP, hmap.p, rb.p, cand.p, hcand.p, CB.p, nb,
+                                                                   blk.p, gs.p, wt, nullptr, nullptr);
         }
+        PC_CHECK_LAUNCH();
     }
     ~Impl() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -1324,31 +1503,55 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     I.row_off.assign(nb + 1, 0);
     if (nA == 0) return;
 
-    // ---- E and CSR
-    const int nbits = std::max(1, ceil_log2((uint64_t)n));
-    DBuf<uint32_t> mark(n, s), dense(n, s), tot(1, s);
+    // ---- E (numbered canonically, see MortonBox) and CSR
+    DBuf<uint32_t> mark(n, s), rank(n, s), tot(1, s);
     PC_CUDA(cudaMemsetAsync(mark.p, 0, n * sizeof(uint32_t), s));
-    k_mark<<<grid_for(nA), 256, 0, s>>>(A, nA, mark.p);
+    k_mark_ids<<<grid_for(nA), 256, 0, s>>>(A, nA, B.order.p, mark.p);
     PC_CHECK_LAUNCH();
-    scan_exclusive_u32(mark.p, dense.p, n, tot.p, s);
+    scan_exclusive_u32(mark.p, rank.p, n, tot.p, s);
     const int64_t ne = *(uint32_t *)read_back(hs, tot.p, sizeof(uint32_t), s);
     I.ne = ne;
     if (I.mt && ne >= ((int64_t)1 << 29)) fail(PC_EINVAL, "several linking lengths: at most 2^29 editable particles");
     const int tb = I.mt ? 2 : 0;   // threshold-index bits of the directed keys
     ThrB2 tb2;
     for (int k = 0; k < MAX_THR; ++k) tb2.b2[k] = I.mt && k < (int)thr->c.size() ? thr->c[k].b2 : 0.f;
-    DBuf<uint32_t> epos(ne, s);
-    k_epos<<<grid_for(n), 256, 0, s>>>(mark.p, dense.p, n, epos.p);
-    PC_CHECK_LAUNCH();
+    DBuf<uint32_t> epos(ne, s), dense(n, s);
+    {
+        // lattice of each block's box: the periodic box, or the bounding box of the originals
+        std::vector<MortonBox> hm(nb);
+        for (int b = 0; b < nb; ++b) {
+            for (int a = 0; a < 3; ++a) {
+                const bool per = S.prm[b].periodic != 0;
+                const double lo = per ? S.prm[b].box_lo[a] : (double)S.ins[b].lo[a];
+                const double ext = per ? S.prm[b].box_hi[a] - S.prm[b].box_lo[a]
+                                       : (double)S.ins[b].hi[a] - (double)S.ins[b].lo[a];
+                hm[b].lo[a] = lo;
+                hm[b].scale[a] = ext > 0.0 ? std::ldexp(1.0, MORTON_BITS) / ext : 0.0;
+            }
+        }
+        DBuf<MortonBox> mb(nb, s);
+        PC_CUDA(cudaMemcpyAsync(mb.p, hm.data(), nb * sizeof(MortonBox), cudaMemcpyHostToDevice, s));
+        DBuf<unsigned long long> ekey(std::max<int64_t>(1, ne), s);
+        DBuf<uint32_t> eid(std::max<int64_t>(1, ne), s), inv(n, s);
+        k_edit_keys<<<grid_for(n), 256, 0, s>>>(mark.p, rank.p, n, orig, S.doff.p, nb, mb.p, ekey.p, eid.p);
+        PC_CHECK_LAUNCH();
+        radix_sort_u64((uint64_t *)ekey.p, eid.p, ne, 3 * MORTON_BITS + std::max(1, ceil_log2((uint64_t)nb)), s);
+        inverse_order(B, inv.p, s);
+        k_edit_maps<<<grid_for(ne), 256, 0, s>>>(eid.p, ne, inv.p, epos.p, dense.p);
+        PC_CHECK_LAUNCH();
+        PC_CUDA(cudaStreamSynchronize(s));   // hm lives on this stack frame
+    }
     mark.release();
-    // directed edges sorted by (row, partner position, threshold index); 64-bit offsets
+    rank.release();
+    // directed edges sorted by (row, partner row, threshold index); 64-bit offsets
+    const int nbe = std::max(1, ceil_log2((uint64_t)ne));
     const int64_t m = 2 * nA;
     DBuf<unsigned long long> keys(m, s);
-    k_dir_keys<<<grid_for(nA), 256, 0, s>>>(A, I.mt ? thr->Athr : nullptr, nA, dense.p, nbits, tb, keys.p);
+    k_dir_keys<<<grid_for(nA), 256, 0, s>>>(A, I.mt ? thr->Athr : nullptr, nA, dense.p, nbe, tb, keys.p);
     PC_CHECK_LAUNCH();
-    radix_sort_u64((uint64_t *)keys.p, nullptr, m, nbits + tb + std::max(1, ceil_log2((uint64_t)ne)), s);
+    radix_sort_u64((uint64_t *)keys.p, nullptr, m, 2 * nbe + tb, s);
     DBuf<unsigned long long> row_ptr(ne + 1, s);
-    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbits + tb, ne, row_ptr.p);
+    k_row_bounds<<<grid_for(m + 1), 256, 0, s>>>(keys.p, m, nbe + tb, ne, row_ptr.p);
     PC_CHECK_LAUNCH();
 
     // ---- iteration state
@@ -1384,64 +1587,81 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
         PC_CUDA(cudaMemcpyAsync(roff.p, I.row_off.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     }
 
-    // ---- edge plan: light rows' edges in row order, then heavy rows' (chunks of HEAVY)
+    // ---- edge plan: light rows' edges in row order, then heavy rows' (one item each)
     DBuf<unsigned long long> ldeg(ne, s), hdeg(ne, s), hptr(ne + 1, s), tot64(2, s);
-    DBuf<uint32_t> nchunk(ne, s), isheavy(ne, s), c0(ne, s), hpos(ne, s), tot2(2, s);
-    k_degrees<<<grid_for(ne), 256, 0, s>>>(row_ptr.p, ne, ldeg.p, hdeg.p, nchunk.p, isheavy.p, I.act.p);
+    DBuf<uint32_t> isheavy(ne, s), hpos(ne, s), tot2(1, s);
+    k_degrees<<<grid_for(ne), 256, 0, s>>>(row_ptr.p, ne, ldeg.p, hdeg.p, isheavy.p, I.act.p);
     PC_CHECK_LAUNCH();
     I.lptr.alloc(ne + 1, s);
     scan_exclusive_u64((const uint64_t *)ldeg.p, (uint64_t *)I.lptr.p, ne, (uint64_t *)(I.lptr.p + ne), s);
     scan_exclusive_u64((const uint64_t *)hdeg.p, (uint64_t *)hptr.p, ne, (uint64_t *)tot64.p, s);
-    scan_exclusive_u32(nchunk.p, c0.p, ne, tot2.p, s);
-    scan_exclusive_u32(isheavy.p, hpos.p, ne, tot2.p + 1, s);
+    scan_exclusive_u32(isheavy.p, hpos.p, ne, tot2.p, s);
     ldeg.release();
-    uint32_t tots[2];
-    memcpy(tots, read_back(hs, tot2.p, 2 * sizeof(uint32_t), s), sizeof(tots));
+    I.n_heavy = *(const uint32_t *)read_back(hs, tot2.p, sizeof(uint32_t), s);
     const unsigned long long n_light = *(const unsigned long long *)read_back(hs, I.lptr.p + ne, 8, s);
-    const int64_t n_chunks = tots[0];
-    I.n_heavy = tots[1];
     I.ecol.alloc(std::max<int64_t>(1, m), s);
     I.eslot.alloc(std::max<unsigned long long>(1, n_light), s);
-    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbits, tb, tb2, row_ptr.p, I.lptr.p, hptr.p, n_light, dense.p,
-                                       epos.p, I.rb.p, roff.p, B.P4.p, S.dev.p, S.doff.p, nb, I.ecol.p, I.eslot.p);
+    k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbe, tb, tb2, row_ptr.p, I.lptr.p, hptr.p, n_light, epos.p,
+                                       I.rb.p, roff.p, B.P4.p, S.dev.p, S.doff.p, nb, I.ecol.p, I.eslot.p);
     PC_CHECK_LAUNCH();
     keys.release();
     row_ptr.release();
     dense.release();
     epos.release();
-    I.chunk_row.alloc(n_chunks, s);
-    I.chunk_start.alloc(n_chunks, s);
-    I.chunk_len.alloc(n_chunks, s);
-    I.hrow.alloc(I.n_heavy, s);
-    I.hc0.alloc(I.n_heavy + 1, s);
-    I.chunk_g.alloc(2 * n_chunks, s);
-    if (I.n_heavy > 0) {
-        k_heavy_fill<<<grid_for(ne), 256, 0, s>>>(hdeg.p, hptr.p, n_light, ne, nchunk.p, c0.p, isheavy.p, hpos.p,
-                                                  I.chunk_row.p, I.chunk_start.p, I.chunk_len.p, I.hrow.p, I.hc0.p);
+    // the screen's copy of the light edges, sorted by partner within each 32-row group
+    I.scol.alloc(std::max<unsigned long long>(1, n_light), s);
+    I.sslot.alloc(std::max<unsigned long long>(1, n_light), s);
+    if (n_light > 0) {
+        DBuf<uint2> grp(cdiv(ne, 32) + nb, s);
+        DBuf<unsigned long long> ngrp(1, s);
+        PC_CUDA(cudaMemsetAsync(ngrp.p, 0, sizeof(unsigned long long), s));
+        k_groups<<<grid_for(ne), 256, 0, s>>>(ne, I.rb.p, roff.p, grp.p, ngrp.p);
         PC_CHECK_LAUNCH();
-        PC_CUDA(cudaMemcpyAsync(I.hc0.p + I.n_heavy, tot2.p, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+        const int64_t ng = (int64_t)*(const unsigned long long *)read_back(hs, ngrp.p, 8, s);
+        PC_CUDA(cudaFuncSetAttribute(k_group_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(GSORT_CAP * sizeof(unsigned long long))));
+        if (ng > 0) {
+            k_group_sort<<<(unsigned)ng, 256, GSORT_CAP * sizeof(unsigned long long), s>>>(
+                grp.p, I.lptr.p, I.ecol.p, I.eslot.p, I.scol.p, I.sslot.p);
+            PC_CHECK_LAUNCH();
+        }
     }
-    I.kernels_per_iter = I.n_heavy > 0 ? 2 : 1;
-    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.eslot.p};
+    // heavy rows: by block, longest first (long walks start early); per-block ranges
+    DBuf<uint32_t> h_per_blk(nb, s), h_off(nb + 1, s);
+    PC_CUDA(cudaMemsetAsync(h_per_blk.p, 0, nb * sizeof(uint32_t), s));
+    I.hitem.alloc(std::max<int64_t>(1, I.n_heavy), s);
+    I.hmap.alloc(ne, s);
+    I.cand.alloc(ne, s);
+    I.hcand.alloc(std::max<int64_t>(1, I.n_heavy), s);
+    if (I.n_heavy > 0) {
+        DBuf<unsigned long long> hkey(I.n_heavy, s);
+        DBuf<uint32_t> hrow(I.n_heavy, s);
+        k_heavy_keys<<<grid_for(ne), 256, 0, s>>>(hdeg.p, isheavy.p, hpos.p, I.rb.p, ne, hkey.p, hrow.p,
+                                                  h_per_blk.p);
+        PC_CHECK_LAUNCH();
+        radix_sort_u64((uint64_t *)hkey.p, hrow.p, I.n_heavy, 32 + std::max(1, ceil_log2((uint64_t)nb)), s);
+        k_heavy_items<<<grid_for(I.n_heavy), 256, 0, s>>>(hrow.p, I.n_heavy, hptr.p, hdeg.p, n_light, I.hitem.p,
+                                                          I.hmap.p);
+        PC_CHECK_LAUNCH();
+    }
+    scan_exclusive_u32(h_per_blk.p, h_off.p, nb, h_off.p + nb, s);
+    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.eslot.p, I.scol.p, I.sslot.p};
     if (nb > 1) {
         // work table of the blocks still iterating (all of them before the first launch)
         I.bw.alloc(nb, s);
         I.act_blk.alloc(nb, s);
         I.act_pref.alloc(nb + 1, s);
-        k_blk_work<<<grid_for(nb), 256, 0, s>>>(roff.p, c0.p, ne, n_chunks, nb, I.bw.p);
+        k_blk_work<<<grid_for(nb), 256, 0, s>>>(roff.p, h_off.p, nb, I.bw.p);
         PC_CHECK_LAUNCH();
         I.wt = WorkTab{I.bw.p, I.act_blk.p, I.act_pref.p};
         k_worktab_init<<<1, 32, 0, s>>>(nb, I.blk.p, I.wt, I.gs.p);
         PC_CHECK_LAUNCH();
     }
     PC_CUDA(cudaStreamSynchronize(s));   // roff and the plan temporaries are released on return
-    I.HP.n_chunks = n_chunks;
-    I.HP.chunk_row = I.chunk_row.p;
-    I.HP.chunk_start = I.chunk_start.p;
-    I.HP.chunk_len = I.chunk_len.p;
-    I.HP.chunk_g = I.chunk_g.p;
-    const int64_t n_items = cdiv(ne, 32) + nb + n_chunks;
-    I.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS), (int64_t)num_sms() * PGD_BLOCKS_PER_SM));
+    I.HP.n_heavy = I.n_heavy;
+    I.HP.item = I.hitem.p;
+    I.n_items = cdiv(ne, 32) + nb + I.n_heavy;
+    I.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(ne, 32 * WARPS), (int64_t)num_sms() * PGD_BLOCKS_PER_SM));
 }
 
 PgdSolver::~PgdSolver() { delete im; }
@@ -1485,7 +1705,7 @@ void PgdSolver::capture(int k) {
     cudaStreamDestroy(cs);
     PC_CUDA(e);
     PC_CUDA(cudaGraphInstantiate(&I.exec, I.graph, 0));
-    add_launches(-(int64_t)k * I.kernels_per_iter);   // captured, not run
+    add_launches(-2 * (int64_t)k);   // captured, not run
     I.graph_k = k;
 }
 
@@ -1496,7 +1716,7 @@ int64_t PgdSolver::launch(int k) {
     if (I.exec) {
         for (; done + I.graph_k <= k || done == 0; done += I.graph_k) {
             PC_CUDA(cudaGraphLaunch(I.exec, I.s));
-            add_launches((int64_t)I.graph_k * I.kernels_per_iter);
+            add_launches(2 * (int64_t)I.graph_k);
         }
     } else {
         for (; done < k; ++done) I.launch_iter();
@@ -1639,7 +1859,15 @@ PgdRun run_pgd(const Binned &B, const BlockSet &S, const std::vector<Consts> &cp
     } else {
         if (graph_k > 0) sol.capture(graph_k);
         // iterations: launch in growing chunks, poll the device stop flags between chunks
-        const int64_t max_launch = sol.max_launches();
+        // every block stops by its last check, so max_launches() launches always suffice;
+        // PC_PGD_LAUNCH_LIMIT (a host-side test hook) lowers the limit to exercise the
+        // PC_ETIMEOUT path: the host stops polling and fails, the launches already queued
+        // run to completion on the stream
+        int64_t max_launch = sol.max_launches();
+        if (const char *lim = getenv("PC_PGD_LAUNCH_LIMIT")) {
+            const long long v = atoll(lim);
+            if (v > 0) max_launch = std::min<int64_t>(max_launch, v);
+        }
         int64_t launched = 0;
         int chunk = graph_k > 0 ? graph_k : 4;
         for (;;) {

@@ -64,20 +64,38 @@ void inspect_blocks(const float *orig, const float *recon, BlockSet &S, cudaStre
 void setup_blocks(BlockSet &S, bool window, cudaStream_t s);
 
 // ---------------------------------------------------------------- binning
+// Sorted positions [k0, k0 + cnt) of one dense cell, cnt <= 32 (one warp of the pair search).
+struct DenseChunk {
+    uint32_t k0, cnt;
+};
+// Bitmaps over the cells of a binning: occupied cells, and dense cells (at least dense_min
+// particles, whose pairs one warp per chunk searches).
+struct CellMaps {
+    const uint32_t *occ, *dense;
+};
 struct Binned {
     int64_t n = 0;
     DBuf<uint32_t> keys;        // sorted cell keys (block cell base + local cell)
     DBuf<uint32_t> order;       // sorted position -> particle id
     DBuf<float4> P4;            // sorted original positions, w = id bits
     DBuf<uint32_t> cell_start;  // ncells + 1
+    DBuf<uint32_t> occ, dense;  // one bit per cell
+    DBuf<DenseChunk> chunks;    // the dense cells in chunks of at most 32 particles
+    int64_t n_chunks = 0;
     void release_to_default_stream() {
         keys.s = 0;
         order.s = 0;
         P4.s = 0;
         cell_start.s = 0;
+        occ.s = 0;
+        dense.s = 0;
+        chunks.s = 0;
     }
 };
+// Binning and the cell maps of the pair search (dense_min from the first block's
+// dense_cell parameter; 0, the default, makes no cell dense).
 void bin_particles(const float *orig, const BlockSet &S, Binned &B, cudaStream_t s, HostScratch &hs);
+void cell_maps(Binned &B, const BlockSet &S, uint32_t dense_min, cudaStream_t s, HostScratch &hs);
 
 // ---------------------------------------------------------------- pair search
 enum { CNT_LINKS = 0, CNT_SAFE = 1, CNT_PB = 2, CNT_PC = 3, CNT_A = 4, CNT_C = 5, CNT_N = 8 };

@@ -40,6 +40,7 @@ struct Job {
     uint64_t ticket = 0;
     pc_job spec{};
     pc_job_result res{};
+    bool alone = false;   // admit in a cohort of its own (its cohort did not fit the budget)
 };
 
 enum CohortState { C_COUNTED, C_RUNNING };
@@ -55,6 +56,7 @@ struct Cohort {
     std::unique_ptr<Selection> sel;
     std::unique_ptr<PgdSolver> sol;
     std::vector<char> finished;
+    int64_t slots_back = 0;              // finished jobs whose slots went back to the server
     int chunk = GRAPH_LAUNCHES;
     int64_t launched = 0;
     bool in_flight = false;              // a chunk and its status copy are queued
@@ -90,7 +92,8 @@ struct pc_server {
     std::map<uint64_t, std::unique_ptr<pc::Job>> jobs;   // every job ever submitted
     std::deque<pc::Job *> pending;                         // FIFO
     std::vector<std::unique_ptr<pc::Cohort>> ready;       // set up, not yet taken by the run thread
-    int64_t used = 0, peak = 0, resident_jobs = 0;         // memory estimate and jobs of live cohorts
+    int64_t used = 0, peak = 0, resident_jobs = 0;         // memory estimate; unfinished jobs of live cohorts
+    int64_t live_cohorts = 0;                              // admitted and not yet retired
     int64_t n_submitted = 0, n_finished = 0, n_cohorts = 0;
     // thread-owned
     std::vector<std::unique_ptr<pc::Cohort>> running;     // run thread, oldest first
@@ -212,6 +215,9 @@ void setup_run(pc_server *srv, Cohort &c) {
     c.sel->B.order.release();
     c.sel->B.P4.release();
     c.sel->B.cell_start.release();
+    c.sel->B.occ.release();
+    c.sel->B.dense.release();
+    c.sel->B.chunks.release();
     c.finished.assign(c.jobs.size(), 0);
     const int64_t t0 = now_ns();
     {
@@ -230,6 +236,15 @@ void setup_run(pc_server *srv, Cohort &c) {
     c.in_flight = true;
     c.rows = c.sol->rows();
     c.state = C_RUNNING;
+}
+
+// A finished job's slot goes back to the server at once (its device memory stays with
+// the cohort's buffers until the cohort retires).
+void give_back_slot(pc_server *srv, Cohort &c) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    --srv->resident_jobs;
+    ++c.slots_back;
+    srv->cv_setup.notify_all();
 }
 
 // Finishes job b of the cohort (its block has stopped).
@@ -265,6 +280,7 @@ void finish_job(pc_server *srv, Cohort &c, int b) {
     }
     c.finished[b] = 1;
     publish(srv, j, PC_JOB_DONE, r.converged ? PC_OK : PC_WARN_NOT_CONVERGED, nullptr);
+    give_back_slot(srv, c);
 }
 
 // Finishes the jobs whose blocks have stopped, from the landed status copy.
@@ -276,6 +292,7 @@ void finish_stopped(pc_server *srv, Cohort &c) {
         } catch (const Fail &f) {
             c.finished[b] = 1;
             publish(srv, c.jobs[b], PC_JOB_ERROR, f.st, pc_last_error());
+            give_back_slot(srv, c);
         }
     }
     c.rows = c.sol->active_rows();
@@ -291,7 +308,8 @@ bool cohort_done(const Cohort &c) {
 void release(pc_server *srv, const Cohort &c) {
     std::lock_guard<std::mutex> lk(srv->mu);
     srv->used -= c.bytes1 + (c.state == C_RUNNING ? c.bytes2 : 0);
-    srv->resident_jobs -= (int64_t)c.jobs.size();
+    srv->resident_jobs -= (int64_t)c.jobs.size() - c.slots_back;
+    --srv->live_cohorts;
     srv->cv_setup.notify_all();
 }
 
@@ -305,6 +323,7 @@ std::vector<Job *> take_jobs(pc_server *srv, int64_t &n, int64_t &bytes) {
     while (!srv->pending.empty()) {
         Job *j = srv->pending.front();
         if (srv->resident_jobs + (int64_t)take.size() >= srv->max_slots) break;
+        if (j->alone && !take.empty()) break;     // it goes in a cohort of its own
         const int64_t nn = n + j->spec.n, bj = count_pass_bytes(j->spec);
         if (!take.empty() && nn > srv->max_cohort_n) break;
         if (srv->used + bytes + bj > srv->budget) {
@@ -325,10 +344,12 @@ std::vector<Job *> take_jobs(pc_server *srv, int64_t &n, int64_t &bytes) {
         take.push_back(j);
         n = nn;
         bytes += bj;
+        if (j->alone) break;
     }
     if (!take.empty()) {
         srv->used += bytes;
         srv->resident_jobs += (int64_t)take.size();
+        ++srv->live_cohorts;
         ++srv->n_cohorts;
         srv->peak = std::max(srv->peak, srv->used);
     }
@@ -388,7 +409,7 @@ void setup_main(pc_server *srv) {
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             while (srv->used + c->bytes2 > srv->budget) {
-                if (srv->resident_jobs == (int64_t)c->jobs.size()) {   // nothing else will free memory
+                if (srv->live_cohorts == 1) {   // this is the only cohort: nothing else will free memory
                     fits = false;
                     break;
                 }
@@ -398,6 +419,19 @@ void setup_main(pc_server *srv) {
                 srv->used += c->bytes2;
                 srv->peak = std::max(srv->peak, srv->used);
             }
+        }
+        if (!fits && c->jobs.size() > 1) {
+            // together they do not fit: back to the head of the queue, each in a cohort of its own
+            release(srv, *c);
+            {
+                std::lock_guard<std::mutex> lk(srv->mu);
+                for (auto it = c->jobs.rbegin(); it != c->jobs.rend(); ++it) {
+                    (*it)->alone = true;
+                    srv->pending.push_front(*it);
+                }
+            }
+            c->jobs.clear();
+            continue;
         }
         if (!fits) {
             fail_cohort(srv, *c, PC_ENOMEM, "cohort does not fit the server's memory budget");

@@ -41,8 +41,8 @@ def test_param_defaults():
 
 
 def test_struct_sizes_match_the_header():
-    # pc_params: 2+3+3 doubles, 4 ints, 5 doubles, 4 ints
-    assert C.sizeof(_native.Params) == 8 * 8 + 4 * 4 + 5 * 8 + 4 * 4
+    # pc_params: 2+3+3 doubles, 4 ints, 5 doubles, 6 ints
+    assert C.sizeof(_native.Params) == 8 * 8 + 4 * 4 + 5 * 8 + 6 * 4
     assert C.sizeof(_native.SelectStats) == 10 * 8 + 8
     assert C.sizeof(_native.CorrectStats) == 4 * 8 + 2 * 8 + 3 * 8 + 8 + 3 * 8 + 8 + 3 * 8
 
@@ -56,7 +56,7 @@ def test_struct_layouts_match_a_c_compiler(tmp_path):
         import pytest
         pytest.skip("no C compiler")
     checks = [("pc_params", _native.Params, ["b", "xi", "periodic", "t_max", "alpha_rel", "loss_tol", "replay_iters",
-                                              "stall_patience", "cell_factor"]),
+                                              "stall_patience", "cell_factor", "dense_cell"]),
               ("pc_select_stats", _native.SelectStats, ["n_links", "ms"]),
               ("pc_correct_stats", _native.CorrectStats, ["converged", "ms_setup", "pgd_launches", "resets", "pair_evals"]),
               ("pc_block", _native.Block, ["n", "params"]),

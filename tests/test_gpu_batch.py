@@ -92,3 +92,25 @@ def test_cell_factor_changes_speed_only(cuda):
             ref = got
         else:
             assert all(np.array_equal(a, b) for a, b in zip(ref, got))
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_tuning_knobs_change_speed_only(cuda, mode):
+    # The pair search's knobs (cell factor, dense-cell threshold) change the binning, but the
+    # correction numbers its editable particles in a canonical order, so the corrected
+    # coordinates are the same bits for every setting; pc_autotune returns a valid setting.
+    import torch
+    import paper_2604_18801_gb300 as pc
+    w = synth.hacc_box(eps_over_b=0.1, mode="VP", seed=62, n=120000)
+    o, r = torch.from_numpy(w.orig).to(cuda), torch.from_numpy(w.recon).to(cuda)
+    cf, dc, times = pc.autotune(o, w.params(mode=mode))
+    assert cf in (2, 4, 8, 16, 32) and dc in (0, 32, 128, 512)
+    assert all(v > 0 for t in times.values() for v in t.values())
+    ref = None
+    for f, d in ((2, 0), (8, 32), (32, 12), (cf, dc)):
+        c, st, code = pc.correct(o, r, w.params(mode=mode, cell_factor=f, dense_cell=d))
+        assert code == 0
+        if ref is None:
+            ref = (c, st["iters"])
+        else:
+            assert st["iters"] == ref[1] and torch.equal(c, ref[0]), (f, d)

@@ -1,0 +1,74 @@
+"""Every plain configuration of the benchmark suite at full size on the GPU, each checked
+for exact membership against the oracle.
+
+- the HACC-shaped 256^3 box at eps = 0.5 b (VP and HF) and eps = 1.0 b (HF);
+- the 4M-atom MD-like cube (40,000 clusters of 100 atoms, eps = 0.3 b, HF);
+- the 8M-particle fluid box (2:1:1, density 1 + 0.8 sin(2 pi x) cos(2 pi y)) at
+  eps = 0.1 b (SC) and eps = 0.5 b (VP).
+(eps = 0.1 b on the HACC-shaped box is tests/test_gpu_fullsize.py.)
+
+The runs use the stall rule (stall_patience = 100: at eps = 0.5 b plain Adam-PGD settles in
+a local minimum of the non-convex loss on this machine).  For each run: the correction
+converges, every
+decoded coordinate lies within xi of the original, the friends-of-friends labels of the
+decoded data (GPU) equal the oracle's labels of the original (its own grid pair search and
+sequential union-find over the links; labels depend on b alone, so the oracle enumerates
+links only), and the oracle finds no active pair whose link state changed.  For the MD
+cube the labels are also the generator's clusters (steps of 0.8 b inside a cluster, gaps
+of more than 1.2 b between clusters).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_18801_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "hacc256_eps0.5": lambda: synth.hacc_box(eps_over_b=0.5, mode="VP", seed=1),
+    "hacc256_eps1.0": lambda: synth.hacc_box(eps_over_b=1.0, mode="HF", seed=1),
+    "md4m_eps0.3": lambda: synth.md_box(n_clusters=40000, eps_over_b=0.3, mode="HF", seed=2),
+    "fluid8m_eps0.1": lambda: synth.fluid_box(n=8_000_000, eps_over_b=0.1, seed=5, mode="SC"),
+    "fluid8m_eps0.5": lambda: synth.fluid_box(n=8_000_000, eps_over_b=0.5, seed=5, mode="VP"),
+}
+_cache = {}
+
+
+def workload(name):
+    if name not in _cache:
+        _cache.clear()   # one full-size box in host memory at a time
+        w = CASES[name]()
+        lab, _, nc = oracle.fof_labels(w.orig, **w.params(xi=0.0))
+        _cache[name] = (w, lab, nc)
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name,mode", [("hacc256_eps0.5", "VP"), ("hacc256_eps0.5", "HF"),
+                                       ("hacc256_eps1.0", "HF"), ("md4m_eps0.3", "HF"),
+                                       ("fluid8m_eps0.1", "SC"), ("fluid8m_eps0.5", "VP")])
+def test_configuration_membership_exact(cuda, name, mode):
+    import torch
+    import paper_2604_18801_gb300 as pc
+    w, lab0, n0 = workload(name)
+    kw = w.params(mode=synth.MODES[mode], stall_patience=100)
+    o = torch.from_numpy(w.orig).to(cuda)
+    r = torch.from_numpy(w.recon).to(cuda)
+    cons = pc.select_constraints(o, kw)
+    ai, aj, al = [x.cpu().numpy() for x in cons.pairs()]
+    corr, st, code = pc.correct(o, r, kw, constraints=cons)
+    cons.close()
+    assert code == 0 and st["converged"] == 1 and st["viol_final"] == 0
+    assert len(ai) == st["n_active"]
+    dec = pc.apply_edits(r, pc.encode_edits(r, corr, kw))
+    dec_h = dec.cpu().numpy()
+    del corr
+    assert np.abs(dec_h.astype(np.float64) - w.orig).max() <= w.xi
+    l1, n1 = pc.fof_labels(dec, kw)
+    assert n1 == n0 and np.array_equal(l1.cpu().numpy(), lab0)
+    assert oracle.count_flips(dec_h, ai, aj, al, **kw) == 0
+    if name.startswith("md"):
+        cl = w.aux["cluster_of"]
+        first = np.full(cl.max() + 1, np.iinfo(np.int64).max)
+        np.minimum.at(first, cl, np.arange(w.n))
+        assert np.array_equal(lab0, first[cl])

@@ -11,7 +11,9 @@ can compute one by one or as a property that holds at any size:
   whose link state changed (must be none; for VP, A = V holds every pair that could flip,
   so the link set itself is unchanged) and decodes the edit stream itself (must equal the
   GPU decoder bit for bit); every decoded coordinate stays within xi of the original, and
-  the friends-of-friends labels of the decoded data equal those of the original;
+  the friends-of-friends labels of the decoded data equal the oracle's labels of the
+  original (its own grid pair search and sequential union-find over the links, about
+  3e7 of them, computed once);
 * the lossless container of each stream equals the oracle's byte for byte;
 * the box reconstructed by the Morton-order baseline instead of the quantizer converges
   in HF mode with the same guarantees.
@@ -28,6 +30,13 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def box():
     return synth.hacc_box(eps_over_b=0.1, mode="VP", seed=1)
+
+
+@pytest.fixture(scope="module")
+def oracle_labels(box):
+    # labels depend on b alone: with xi = 0 the oracle enumerates only the links
+    lab, _, n_comp = oracle.fof_labels(box.orig, **box.params(xi=0.0))
+    return lab, n_comp
 
 
 def test_vulnerable_pairs_of_sampled_particles(cuda, box):
@@ -60,7 +69,7 @@ def test_vulnerable_pairs_of_sampled_particles(cuda, box):
 
 
 @pytest.mark.parametrize("mode", ["VP", "SC", "HF"])
-def test_full_size_correction_keeps_every_active_link_state(cuda, box, mode):
+def test_full_size_correction_keeps_every_active_link_state(cuda, box, oracle_labels, mode):
     import torch
     import paper_2604_18801_gb300 as pc
     w = box
@@ -85,12 +94,31 @@ def test_full_size_correction_keeps_every_active_link_state(cuda, box, mode):
     assert torch.equal(pc.huff_decode(blob), stream)
     # every active pair keeps its original link state after decoding
     assert oracle.count_flips(dec_h, ai, aj, al, **kw) == 0
-    l0, n0 = pc.fof_labels(o, kw)
+    # the decoded data's labels are the oracle's labels of the original
+    lab0, n0 = oracle_labels
     l1, n1 = pc.fof_labels(dec, kw)
-    assert n0 == n1 and torch.equal(l0, l1)
+    assert n1 == n0 and np.array_equal(l1.cpu().numpy(), lab0)
+    assert st["resets"] == 0   # Algorithm 1 as printed
 
 
-def test_full_size_morton_baseline_halo_forest(cuda, box):
+def test_full_size_oracle_labels_of_decoded_data(cuda, box, oracle_labels):
+    """The whole membership check on the oracle's side for one mode: its labels of the
+    GPU-decoded VP output equal its labels of the original."""
+    import torch
+    import paper_2604_18801_gb300 as pc
+    w = box
+    kw = w.params(mode=0)
+    o = torch.from_numpy(w.orig).to(cuda)
+    r = torch.from_numpy(w.recon).to(cuda)
+    corr, st, code = pc.correct(o, r, kw)
+    assert code == 0
+    dec_h = pc.apply_edits(r, pc.encode_edits(r, corr, kw)).cpu().numpy()
+    lab1, _, n1 = oracle.fof_labels(dec_h, **dict(kw, xi=0.0))
+    lab0, n0 = oracle_labels
+    assert n1 == n0 and np.array_equal(lab1, lab0)
+
+
+def test_full_size_morton_baseline_halo_forest(cuda, box, oracle_labels):
     """The same box reconstructed by the Morton-order baseline (Sec. 4.1): HF correction
     converges, keeps every active link state and gives the original labels."""
     import torch
@@ -108,6 +136,6 @@ def test_full_size_morton_baseline_halo_forest(cuda, box):
     dec_h = dec.cpu().numpy()
     assert np.abs(dec_h.astype(np.float64) - w.orig).max() <= w.xi
     assert oracle.count_flips(dec_h, ai, aj, al, **kw) == 0
-    l0, n0 = pc.fof_labels(o, kw)
+    lab0, n0 = oracle_labels
     l1, n1 = pc.fof_labels(dec, kw)
-    assert n0 == n1 and torch.equal(l0, l1)
+    assert n1 == n0 and np.array_equal(l1.cpu().numpy(), lab0)

@@ -82,10 +82,12 @@ def test_replayed_union_parity(cuda, name, mode, R):
                                        ("hacc32k", 2), ("md300", 2), ("fluid20k", 1), ("hacc32k_morton", 2),
                                        ("hacc32k_e01", 0), ("md300_e01", 2)])
 def test_converged_union_keeps_every_length(cuda, name, mode):
+    # The union of several lengths holds some pairs from both sides; at eps = 0.5 b plain
+    # Adam-PGD can settle in a local minimum of that loss, so these runs use the stall rule.
     import paper_2604_18801_gb300 as pc
     w = W_(name)
     bl = [f * w.b for f in FACTORS]
-    prm = w.params(mode=mode)
+    prm = w.params(mode=mode, stall_patience=100)
     o, r = dev(w.orig, cuda), dev(w.recon, cuda)
     corr, st, code = pc.correct_multi(o, r, prm, bl)
     assert code == 0 and st["converged"] == 1 and st["viol_final"] == 0

@@ -1,12 +1,14 @@
 """Serving form: jobs that arrive at different times are batched into cohorts that run side
 by side; each job's corrected coordinates and edit stream must be bit-identical to
-pc_correct and pc_encode_edits on that job alone, and memory and input errors end only the
-job concerned."""
+pc_correct and pc_encode_edits on that job alone, its decoded output must have the oracle's
+friends-of-friends labels of the original, and memory and input errors end only the job
+concerned."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2604_18801_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +51,10 @@ def test_each_result_is_the_same_alone_and_in_the_mix(cuda):
         assert torch.equal(stream, pc.encode_edits(r, alone, w.params())), w.name
         dec = pc.apply_edits(r, stream)
         assert float((dec.double() - o.double()).abs().max()) <= w.xi
+        # membership of the served result against the oracle's labels
+        lab0, _, _ = oracle.fof_labels(w.orig, **w.params(xi=0.0))
+        lab1, _, _ = oracle.fof_labels(dec.cpu().numpy(), **w.params(xi=0.0))
+        assert np.array_equal(lab0, lab1), w.name
 
 
 def test_errors_end_only_the_job_concerned(cuda):
@@ -74,3 +80,24 @@ def test_errors_end_only_the_job_concerned(cuda):
     assert r_good["state"] == "DONE" and r_good["status"] == 0
     alone, _, _ = pc.correct(og, rg, good.params())
     assert torch.equal(out, alone)
+
+
+def test_jobs_that_fit_only_one_at_a_time_both_finish(cuda):
+    # Two jobs whose joint memory estimate exceeds the budget while each fits alone: the
+    # cohort they were admitted in cannot proceed, so its jobs go back to the queue and run
+    # in cohorts of their own (instead of both failing with PC_ENOMEM).
+    import torch
+    import paper_2604_18801_gb300 as pc
+    ws = [synth.hacc_box(eps_over_b=0.1, mode="VP", seed=70 + k, n=100000) for k in range(2)]
+    dev = [(torch.from_numpy(w.orig).to(cuda), torch.from_numpy(w.recon).to(cuda)) for w in ws]
+    with pc.Server(mem_budget=8 << 30) as probe:
+        probe.result(probe.submit(dev[0][0], dev[0][1], ws[0].params()))
+        one = probe.counters()["peak_bytes"]
+    with pc.Server(mem_budget=int(1.3 * one)) as srv:
+        tickets = [srv.submit(o, r, w.params()) for w, (o, r) in zip(ws, dev)]
+        results = [srv.result(t) for t in tickets]
+    for w, (o, r), (out, _, d) in zip(ws, dev, results):
+        assert d["state"] == "DONE" and d["status"] == 0, d
+        assert d["cohort_jobs"] == 1
+        alone, _, _ = pc.correct(o, r, w.params())
+        assert torch.equal(out, alone)
