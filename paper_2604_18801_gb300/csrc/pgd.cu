@@ -111,10 +111,8 @@ struct PgdGlobal {
     int32_t active;                 // blocks still iterating after the last launch
     int32_t pad;
     unsigned long long n_items;     // work items of the blocks still iterating (problem sets)
-    unsigned long long ncand;       // candidate rows the screen listed for the update
-    unsigned long long work2;       // next candidate of the update
-    unsigned long long nhcand;      // heavy candidate rows with an uncertain pair (a list of their own)
-    unsigned long long work3;       // next heavy candidate of the update
+    unsigned long long work2;       // next light item of the update
+    unsigned long long work3;       // next heavy row of the update
 };
 
 // Work of one block of a problem set: its heavy rows, items [h0, h0 + nh) of the heavy
@@ -123,6 +121,7 @@ struct PgdGlobal {
 // have no light edges).
 struct BlkWork {
     uint32_t row0, nrows, h0, nh;
+    uint32_t g0;   // the light group index of the block's first 32 rows
 };
 
 // Items of the blocks still iterating, for the next launch: active block k is act_blk[k]
@@ -174,11 +173,11 @@ __global__ void k_worktab_init(int nb, const PgdBlk *blk, const WorkTab wt, PgdG
 
 // Per-block row ranges and heavy-item ranges (rows are in sorted-position order, so every
 // block owns a contiguous range of rows; heavy items are sorted by block first).
-__global__ void k_blk_work(const int64_t *__restrict__ row_off, const uint32_t *__restrict__ h_off, int nb,
-                           BlkWork *__restrict__ bw) {
+__global__ void k_blk_work(const int64_t *__restrict__ row_off, const uint32_t *__restrict__ h_off,
+                           const uint32_t *__restrict__ gbase, int nb, BlkWork *__restrict__ bw) {
     GRID_STRIDE(b, nb) {
         const int64_t r0 = row_off[b], r1 = row_off[b + 1];
-        bw[b] = BlkWork{(uint32_t)r0, (uint32_t)(r1 - r0), h_off[b], h_off[b + 1] - h_off[b]};
+        bw[b] = BlkWork{(uint32_t)r0, (uint32_t)(r1 - r0), h_off[b], h_off[b + 1] - h_off[b], gbase[b]};
     }
 }
 
@@ -540,9 +539,7 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
         if (active == 0) gs->all_stop = 1;
         gs->work = 0;
         gs->work2 = 0;
-        gs->ncand = 0;
         gs->work3 = 0;
-        gs->nhcand = 0;
         gs->ticket = 0;
     }
     __threadfence();
@@ -606,6 +603,8 @@ __device__ __forceinline__ void finish_iteration(BlockRed &br, unsigned long lon
 struct HeavyItem {
     unsigned long long start;
     uint32_t row, len;
+    uint32_t ulo;   // rank of the first partner after the row (the screen walks [ulo, len))
+    uint32_t pad;
 };
 
 struct HeavyPlan {
@@ -621,11 +620,16 @@ struct HeavyPlan {
 struct LightPlan {
     const unsigned long long *ptr;   // per row: first light edge (ne + 1 entries)
     const uint32_t *col;             // partner | link << 31 (| threshold index << 29 with several)
-    const uint8_t *slot;             // light edges: row - first row of its 32-row group
-    // the screen's copy of the light edges: within each 32-row group, sorted by CSR entry
-    // (partner), so that neighbouring lanes gather the same or nearby partners
-    const uint32_t *scol;
-    const uint8_t *sslot;
+    // The screen's stream: each pair once, from the row that comes first.  Group g (32
+    // light rows) owns [gup[g], gup[g + 1]): its rows' edges to later partners, sorted by
+    // partner so that neighbouring lanes gather the same or nearby partners; scol is the
+    // CSR entry, saux the edge's place in the group's range of the edge array << 5 | the
+    // row's slot.
+    const unsigned long long *gup;
+    const uint32_t *scol, *saux;
+    // per edge to a later partner (by position in the edge array): the position of the
+    // reverse edge in the partner's row
+    const unsigned long long *erev;
 };
 
 struct PgdBufs {
@@ -653,6 +657,7 @@ struct PgdBufs {
 // Candidate list entry: row | CAND_UNC when the row has an uncertain pair.
 constexpr uint32_t CAND_UNC = 0x80000000u;
 constexpr int SCREEN_BLOCKS_PER_SM = 5;
+constexpr int KERNELS_PER_ITER = 2;   // screen, update
 constexpr int QCAP = 128;   // uncertain pairs waiting for evaluation (a ring per warp; < 32 + 2 x 32)
 constexpr int EPL = 4;      // edges per lane per trip of the screen's walk
 
@@ -695,21 +700,71 @@ __device__ __forceinline__ bool needs_image(const PgdConsts &C, bool row_lane, c
     return C.periodic != 0 && !__all_sync(0xffffffffu, in_ok);
 }
 
+// Work item `item` of the screen's item space: a heavy row (H.item[hk]) or a group of 32
+// light rows (group g, rows [r0, r0 + cnt)) of block b.  A problem set's items are those of
+// its blocks still iterating (the work table), each block's heavy rows first; a single
+// problem's items are every heavy row, then every group.  Called by all lanes of a warp.
+template <bool MULTI>
+__device__ __forceinline__ void map_item(int64_t item, int64_t ne, const HeavyPlan &H, const WorkTab &wt, int nact,
+                                         int &b, bool &heavy, int64_t &r0, int &cnt, int64_t &hk, int64_t &g) {
+    const unsigned FULL = 0xffffffffu;
+    b = 0;
+    r0 = 0;
+    cnt = 0;
+    hk = 0;
+    g = 0;
+    if (MULTI) {
+        int kk = 0;
+        if ((threadIdx.x & 31) == 0) {   // active block of the item: largest k with act_pref[k] <= item
+            int lo = 0, hi = nact - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (wt.act_pref[mid] <= (unsigned long long)item) lo = mid;
+                else hi = mid - 1;
+            }
+            kk = lo;
+        }
+        kk = __shfl_sync(FULL, kk, 0);
+        b = (int)wt.act_blk[kk];
+        const int64_t j = item - (int64_t)wt.act_pref[kk];
+        const BlkWork bw = wt.bw[b];
+        heavy = j < (int64_t)bw.nh;
+        if (!heavy) {
+            const int64_t jl = j - (int64_t)bw.nh;
+            r0 = (int64_t)bw.row0 + 32 * jl;
+            cnt = (int)min((int64_t)32, (int64_t)bw.nrows - 32 * jl);
+            g = (int64_t)bw.g0 + jl;
+        } else {
+            hk = (int64_t)bw.h0 + j;
+        }
+    } else {
+        heavy = item < H.n_heavy;
+        if (!heavy) {
+            g = item - H.n_heavy;
+            r0 = g * 32;
+            cnt = (int)min((int64_t)32, ne - r0);
+        } else {
+            hk = item;
+        }
+    }
+}
+
 // The screen.  Work items are heavy rows (more than HEAVY partners; longest first, so the
 // longest walks start early) and groups of 32 consecutive light rows, handed out from a
-// counter (the next item is claimed one item ahead).  A warp walks its item's flat edge
-// range 128 edges at a time (4 per lane, strided by 32 so that loads stay coalesced; the
-// next trip's columns and slots load while this trip's partner positions are gathered),
-// and marks the rows with an uncertain pair.
+// counter (the next item is claimed one item ahead).  Every pair is screened once, from
+// the row that comes first: a warp walks its item's stream of edges to later partners
+// 128 at a time (4 per lane, strided by 32 so that loads stay coalesced; the next trip's
+// entries load while this trip's partner positions are gathered).  A pair the float32
+// screen cannot certify sets the bits of both its directed edges in the bit mask of the
+// edge array and the flags of both rows; the list kernel and the update read them.
 template <bool MULTI, bool MT>
 __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_screen(
     int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP, const PgdConsts *__restrict__ CB,
-    const PgdBlk *__restrict__ blk, PgdGlobal *gs, const WorkTab wt, uint32_t *__restrict__ cand,
-    uint32_t *__restrict__ hcand) {
+    const PgdBlk *__restrict__ blk, PgdGlobal *gs, const WorkTab wt, uint32_t *__restrict__ ubits,
+    uint8_t *__restrict__ uflag) {
     __shared__ int s_stop, s_t, s_nact;
     __shared__ unsigned long long s_items;
     __shared__ float4 sq[WARPS][32];      // the item's rows' rounded positions
-    __shared__ uint32_t sunc[WARPS];      // bit s: row slot s has an uncertain pair
     if (threadIdx.x == 0) {
         s_stop = gs->all_stop;
         s_nact = gs->active;
@@ -729,134 +784,96 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
         const int64_t item = (int64_t)__shfl_sync(FULL, nitm, 0);
         if (item >= n_items) break;
         if (lane == 0) nitm = atomicAdd(&gs->work, 1ull);
-        int b = 0, tb = s_t;
-        int64_t r0 = 0, hk = 0;
-        int cnt = 0;
+        int b, cnt;
+        int64_t r0, hk, g;
         bool heavy_warp;
-        if (MULTI) {
-            int kk = 0;
-            if (lane == 0) {   // active block of the item: largest k with act_pref[k] <= item
-                int lo = 0, hi = s_nact - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (wt.act_pref[mid] <= (unsigned long long)item) lo = mid;
-                    else hi = mid - 1;
-                }
-                kk = lo;
-            }
-            kk = __shfl_sync(FULL, kk, 0);
-            b = (int)wt.act_blk[kk];
-            const int64_t j = item - (int64_t)wt.act_pref[kk];
-            const BlkWork bw = wt.bw[b];
-            heavy_warp = j < (int64_t)bw.nh;
-            if (!heavy_warp) {
-                const int64_t jl = j - (int64_t)bw.nh;
-                r0 = (int64_t)bw.row0 + 32 * jl;
-                cnt = (int)min((int64_t)32, (int64_t)bw.nrows - 32 * jl);
-            } else {
-                hk = (int64_t)bw.h0 + j;
-            }
-            tb = blk[b].t;
-        } else {
-            heavy_warp = item < H.n_heavy;
-            if (!heavy_warp) {
-                r0 = (item - H.n_heavy) * 32;
-                cnt = (int)min((int64_t)32, ne - r0);
-            } else {
-                hk = item;
-            }
-        }
+        map_item<MULTI>(item, ne, H, wt, s_nact, b, heavy_warp, r0, cnt, hk, g);
+        const int tb = MULTI ? blk[b].t : s_t;
         const int pa = tb & 1;
-        // the item's edges [ebase, ebase + VT); lane i holds row rbase + i (light: i < cnt;
-        // heavy: lane 0, slot 0)
+        // the item's stream [ebase, ebase + VT); lane i holds row rbase + i (light: i < cnt;
+        // heavy: lane 0, slot 0); fbase + (aux >> 5) is a light edge's place in the edge array
         int64_t rbase = r0;
         bool have;
         uint32_t VT;
-        unsigned long long ebase;
+        unsigned long long ebase, fbase = 0;
         if (!heavy_warp) {
             have = lane < cnt;
-            unsigned long long lb = 0, le = 0;
+            unsigned long long ub = 0, ue = 0, lb = 0;
             if (lane == 0) {
+                ub = LP.gup[g];
+                ue = LP.gup[g + 1];
                 lb = LP.ptr[r0];
-                le = LP.ptr[r0 + cnt];
             }
-            ebase = __shfl_sync(FULL, lb, 0);
-            VT = (uint32_t)(__shfl_sync(FULL, le, 0) - ebase);
+            ebase = __shfl_sync(FULL, ub, 0);
+            VT = (uint32_t)(__shfl_sync(FULL, ue, 0) - ebase);
+            fbase = __shfl_sync(FULL, lb, 0);
         } else {
             const HeavyItem hv = H.item[hk];
             have = lane == 0;
             rbase = hv.row;
-            ebase = hv.start;
-            VT = hv.len;
+            ebase = hv.start + hv.ulo;
+            VT = hv.len - hv.ulo;
         }
         const float4 qe = (have || heavy_warp) ? Bf.q(pa)[rbase + (heavy_warp ? 0 : lane)]
                                               : make_float4(0.f, 0.f, 0.f, 0.f);
-        uint8_t av = 0;
-        if (have) {
-            av = Bf.act[rbase + lane];
-            sq[w][lane] = qe;
-        }
-        if (lane == 0) sunc[w] = 0u;
+        if (have) sq[w][lane] = qe;
         __syncwarp();
         const PgdConsts &Cl = CB[b];
         const bool pp = needs_image(Cl, heavy_warp || have, qe);
         const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
         const float4 *__restrict__ Qc = Bf.q(pa);
         const uint32_t *__restrict__ ecol = (heavy_warp ? LP.col : LP.scol) + ebase;
-        const uint8_t *__restrict__ eslot = LP.sslot + ebase;
+        const uint32_t *__restrict__ eaux = LP.saux + ebase;
         const float slk = Cl.screen_link[0], sln_ = Cl.screen_non[0];
         auto walk = [&](auto image) {
             constexpr bool PP = decltype(image)::value;
-            uint32_t cvn[EPL];
-            int sln[EPL];
+            uint32_t cvn[EPL], axn[EPL];
 #pragma unroll
             for (int j = 0; j < EPL; ++j) {
                 const uint32_t v = 32u * j + lane;
                 cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
-                sln[j] = (v < VT && !heavy_warp) ? (int)__ldcs(eslot + v) : 0;
+                axn[j] = (v < VT && !heavy_warp) ? __ldcs(eaux + v) : 0u;
             }
             for (uint32_t base = 0; base < VT; base += 32 * EPL) {
-                uint32_t cv[EPL];
-                int sl[EPL];
+                uint32_t cv[EPL], ax[EPL];
                 bool nd[EPL];
 #pragma unroll
                 for (int j = 0; j < EPL; ++j) {
                     nd[j] = base + 32u * j + lane < VT;
                     cv[j] = cvn[j];
-                    sl[j] = sln[j];
+                    ax[j] = axn[j];
                     const uint32_t v = base + 32u * (EPL + j) + lane;
                     cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
-                    sln[j] = (v < VT && !heavy_warp) ? (int)__ldcs(eslot + v) : 0;
+                    axn[j] = (v < VT && !heavy_warp) ? __ldcs(eaux + v) : 0u;
                 }
-                uint32_t um = 0u;
+                unsigned um = 0u;
 #pragma unroll
                 for (int j = 0; j < EPL; ++j)
-                    if (nd[j] && screen_pair<MT, PP>(sq[w][sl[j]], Qc[cv[j] & PMASK], cv[j], L0, L1, L2, slk, sln_, Cl))
-                        um |= 1u << sl[j];
-                if (__any_sync(FULL, um != 0u) && um) atomicOr(&sunc[w], um);
+                    if (nd[j] && screen_pair<MT, PP>(sq[w][ax[j] & 31u], Qc[cv[j] & PMASK], cv[j], L0, L1, L2, slk,
+                                                     sln_, Cl))
+                        um |= 1u << j;
+                if (um) {
+                    // the trip's uncertain pairs: every reverse-edge load first, then both
+                    // directed edges' bits and both rows' flags
+                    unsigned long long f[EPL], r[EPL];
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j) {
+                        f[j] = heavy_warp ? ebase + base + 32u * j + lane : fbase + (ax[j] >> 5);
+                        r[j] = (um >> j) & 1u ? LP.erev[f[j]] : 0ull;
+                    }
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j)
+                        if ((um >> j) & 1u) {
+                            atomicOr(ubits + (f[j] >> 5), 1u << (f[j] & 31));
+                            atomicOr(ubits + (r[j] >> 5), 1u << (r[j] & 31));
+                            uflag[rbase + (ax[j] & 31u)] = 1;
+                            uflag[cv[j] & PMASK] = 1;
+                        }
+                }
             }
         };
         if (pp) walk(std::true_type{});
         else walk(std::false_type{});
-        __syncwarp();
-        // candidates of the update: rows with an uncertain pair, and rows that take a step
-        const bool unc = have && ((sunc[w] >> (heavy_warp ? 0 : lane)) & 1u);
-        const bool own = have && (heavy_warp || !(av & ACT_HEAVY));
-        const bool steps = (av & ACT_ON) && !is_last(Cl, tb);
-        // warp-uniform (the flag word is shared): both branches below hold whole warps, as
-        // the ballot and shuffle of the second one need
-        const bool heavy_unc = heavy_warp && (sunc[w] & 1u) != 0u;
-        if (heavy_unc) {
-            // a heavy row with an uncertain pair is re-walked by a warp of its own
-            if (lane == 0) hcand[atomicAdd(&gs->nhcand, 1ull)] = (uint32_t)rbase;
-        } else {
-            const bool c = own && (unc || steps);
-            const unsigned bal = __ballot_sync(FULL, c);
-            unsigned long long at = 0;
-            if (lane == 0 && bal) at = atomicAdd(&gs->ncand, (unsigned long long)__popc(bal));
-            at = __shfl_sync(FULL, at, 0);
-            if (c) cand[at + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)(rbase + lane) | (unc ? CAND_UNC : 0u);
-        }
         __syncwarp();
     }
 }
@@ -869,6 +886,7 @@ struct WarpTab {
     int eb[32], epa[32];             // ... their blocks and buffer parities
     unsigned own[32];                // per row slot: this batch's violated entries of that row
     float gt[6][32];                 // this batch's gradient terms (x hi, x lo, y hi, ...) by entry
+    uint32_t cb[64];                 // candidate rows waiting for a chunk (row | CAND_UNC), a ring
 };
 
 // 16-byte asynchronous copies from global to shared memory (not cached in L1).
@@ -880,29 +898,30 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // The update: warps take first the heavy rows with an uncertain pair, one each, then the
-// other candidate rows 32 at a time (slot i = lane i).  The rows with an
-// uncertain pair are re-screened by the whole warp, 32 edges at a time, one row after the
-// other in slot order; the pairs the screen cannot certify enter the warp's ring, in edge
-// order, tagged with their row's slot, and are evaluated in double-float 32 at a time.
+// other candidate rows 32 at a time (slot i = lane i).  A row's uncertain pairs are the set
+// bits of its edge range in the screen's bit mask: a heavy row's warp reads its words 32
+// at a time, and each lane of a chunk reads its own row's words, one pair per round.  The
+// pairs enter the warp's ring, in edge order within each row, tagged with their row's
+// slot, and are evaluated in double-float 32 at a time; their bits are cleared as read.
 // Each light row's owner lane then adds its violated pairs one by one in edge order (the
 // same order for any grouping of rows, so a row's gradient does not depend on its chunk,
 // batch or block); a heavy row's warp adds each batch of its pairs by a fixed tree first.
 // Then every candidate row that is due takes its Adam step, lanes in parallel.
 template <bool MULTI, bool MT>
 __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
-    const float4 *__restrict__ PE, PgdBufs Bf, HeavyPlan H, LightPlan LP, const uint32_t *__restrict__ hmap,
-    const uint32_t *__restrict__ rb, const uint32_t *__restrict__ cand, const uint32_t *__restrict__ hcand,
-    const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs, const WorkTab wt,
-    double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
-    __shared__ int s_stop, s_t, s_reset;
-    __shared__ unsigned long long s_ncand, s_nhcand;
+    int64_t ne, const float4 *__restrict__ PE, PgdBufs Bf, HeavyPlan H, LightPlan LP,
+    const uint32_t *__restrict__ hmap, const uint32_t *__restrict__ rb, uint32_t *__restrict__ ubits,
+    uint8_t *__restrict__ uflag, const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs,
+    const WorkTab wt, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
+    __shared__ int s_stop, s_t, s_reset, s_nact;
+    __shared__ unsigned long long s_items;
     __shared__ df s_ibc1, s_ibc2;
     __shared__ WarpTab tab[WARPS];
     __shared__ BlockRed br;
     if (threadIdx.x == 0) {
         s_stop = gs->all_stop;
-        s_ncand = gs->ncand;
-        s_nhcand = gs->nhcand;
+        s_nact = gs->active;
+        s_items = gs->n_items;
         s_t = blk[0].t;
         s_ibc1 = blk[0].ibc1;
         s_ibc2 = blk[0].ibc2;
@@ -922,29 +941,99 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
     constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;
     unsigned long long lfx = 0;       // this lane's share of the tight loss, fixed point (single block)
     unsigned viol = 0, nupd = 0, nev = 0;
-    const unsigned long long ncand = s_ncand, nhcand = s_nhcand;
-    bool heavy_done = false;
+    // Work comes in two phases.  First the heavy rows, one at a time: a row with an uncertain
+    // pair is taken by the warp at once (kind 1: the warp reads its pairs); a row that only
+    // steps joins the warp's ring of candidates.  Then groups of 32 light rows: each lane
+    // looks at its row's flag and Adam state, and the candidates join the ring.  Whenever the
+    // ring holds 32 (or nothing is left to claim), 32 of them are processed as a chunk
+    // (kind 2: each lane one row).  The flags are cleared as read.
+    const int64_t n_light_items = MULTI ? (int64_t)s_items : (ne + 31) / 32;
+    bool heavy_done = false, light_done = false;
+    int nc = 0, ch = 0;   // candidates in the ring and its head (warp-uniform)
     for (;;) {
-        // claim: a heavy row (slot 0), else a chunk of 32 candidate rows
-        unsigned long long cb = 0;
         int kind = 0;   // 1: heavy row, 2: chunk, 0: nothing left
-        if (lane == 0) {
+        bool have = false;
+        uint32_t ce = 0u;
+        for (;;) {
+            if (nc >= 32 || (heavy_done && light_done && nc > 0)) {
+                const int take = min(nc, 32);
+                have = lane < take;
+                ce = have ? T.cb[(ch + lane) & 63] : 0u;
+                __syncwarp();
+                ch = (ch + take) & 63;
+                nc -= take;
+                kind = 2;
+                break;
+            }
+            if (heavy_done && light_done) break;
+            unsigned long long k = 0;
             if (!heavy_done) {
-                cb = atomicAdd(&gs->work3, 1ull);
-                if (cb < nhcand) kind = 1;
-                else heavy_done = true;
+                if (lane == 0) k = atomicAdd(&gs->work3, 1ull);
+                k = __shfl_sync(FULL, k, 0);
+                if ((int64_t)k >= H.n_heavy) {
+                    heavy_done = true;
+                    continue;
+                }
+                int dec = 0;
+                uint32_t r = 0;
+                if (lane == 0) {
+                    r = H.item[k].row;
+                    const int rbk = MULTI ? (int)rb[r] : 0;
+                    if (!MULTI || blk[rbk].stop == 0) {
+                        const bool f = uflag[r] != 0;
+                        if (f) uflag[r] = 0;
+                        const bool steps = (Bf.act[r] & ACT_ON) && !is_last(CB[rbk], MULTI ? blk[rbk].t : s_t);
+                        dec = f ? 1 : (steps ? 2 : 0);
+                    }
+                }
+                dec = __shfl_sync(FULL, dec, 0);
+                r = __shfl_sync(FULL, r, 0);
+                if (dec == 1) {
+                    have = lane == 0;
+                    ce = have ? (r | CAND_UNC) : 0u;
+                    kind = 1;
+                    break;
+                }
+                if (dec == 2) {
+                    if (lane == 0) T.cb[(ch + nc) & 63] = r;
+                    __syncwarp();
+                    ++nc;
+                }
+                continue;
             }
-            if (kind == 0) {
-                cb = atomicAdd(&gs->work2, 32ull);
-                kind = cb < ncand ? 2 : 0;
+            if (lane == 0) k = atomicAdd(&gs->work2, 1ull);
+            k = __shfl_sync(FULL, k, 0);
+            if ((int64_t)k >= n_light_items) {
+                light_done = true;
+                continue;
             }
+            int ib, icnt;
+            int64_t ir0, ihk, ig;
+            bool ih;
+            if (MULTI) {
+                map_item<true>((int64_t)k, ne, H, wt, s_nact, ib, ih, ir0, icnt, ihk, ig);
+                if (ih) continue;   // heavy rows come in the first phase
+            } else {
+                ib = 0;
+                ir0 = (int64_t)k * 32;
+                icnt = (int)min((int64_t)32, ne - ir0);
+            }
+            bool c = false, f = false;
+            const int64_t r = ir0 + lane;
+            if (lane < icnt) {
+                const uint8_t av = Bf.act[r];
+                if (!(av & ACT_HEAVY)) {
+                    f = uflag[r] != 0;
+                    if (f) uflag[r] = 0;
+                    c = f || ((av & ACT_ON) && !is_last(CB[ib], MULTI ? blk[ib].t : s_t));
+                }
+            }
+            const unsigned bal = __ballot_sync(FULL, c);
+            if (c) T.cb[(ch + nc + __popc(bal & lt_mask)) & 63] = (uint32_t)r | (f ? CAND_UNC : 0u);
+            __syncwarp();
+            nc += __popc(bal);
         }
-        kind = __shfl_sync(FULL, kind, 0);
-        heavy_done = __shfl_sync(FULL, heavy_done, 0);
-        cb = __shfl_sync(FULL, cb, 0);
         if (kind == 0) break;
-        const bool have = kind == 1 ? lane == 0 : cb + lane < ncand;
-        const uint32_t ce = !have ? 0u : (kind == 1 ? (hcand[cb] | CAND_UNC) : cand[cb + lane]);
         const uint32_t e = ce & ~CAND_UNC;
         const bool unc = have && (ce & CAND_UNC);
         const int b = MULTI ? (have ? (int)rb[e] : 0) : 0;
@@ -1060,48 +1149,80 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
             __syncwarp();
         };
 
-        // re-screen the edges of every row with an uncertain pair, in slot order
-        for (unsigned um = __ballot_sync(FULL, unc); um; um &= um - 1) {
-            const int r = __ffs(um) - 1;
-            const uint32_t er = T.erow[r];
-            const int par = T.epa[r];
-            const PgdConsts &Cr = CB[T.eb[r]];
-            const uint8_t avr = (uint8_t)__shfl_sync(FULL, (unsigned)av, r);
-            const float4 *Qc = Bf.q(par);
-            const float4 qr = Qc[er];
-            const bool pp = needs_image(Cr, true, qr);
-            const float L0 = Cr.L[0], L1 = Cr.L[1], L2 = Cr.L[2];
+        // queue one entry per lane that has one (edge order within each row)
+        auto push = [&](bool has, uint32_t cv, int slot) {
+            const unsigned bal = __ballot_sync(FULL, has);
+            if (has) {
+                const int pos = (qh + qn + __popc(bal & lt_mask)) & (QCAP - 1);
+                T.qk[pos] = cv & PMASK;
+                T.qs[pos] = (uint8_t)(slot | (MT ? ((cv >> 29) & 3u) << 5 : 0u) | ((cv >> 31) ? 0x80 : 0));
+            }
+            qn += __popc(bal);
+            __syncwarp();
+            while (qn >= 32) batch();
+        };
+        // the bits of edge-array word wi that belong to the edge range [es, es + len), read
+        // and cleared (whole words of one row with a plain store; a word shared with the
+        // neighbouring rows' edges clears only this row's bits)
+        auto take_word = [&](unsigned long long wi, unsigned long long es, unsigned long long ee) -> uint32_t {
+            uint32_t m = 0xffffffffu;
+            if (wi == (es >> 5)) m &= 0xffffffffu << (es & 31);
+            if (wi == ((ee - 1) >> 5)) m &= 0xffffffffu >> (31 - ((ee - 1) & 31));
+            const uint32_t v = ubits[wi] & m;
+            if (v) {
+                if (m == 0xffffffffu) ubits[wi] = 0u;
+                else atomicAnd(ubits + wi, ~m);
+            }
+            return v;
+        };
+        if (kind == 1) {
+            // a heavy row: the warp reads its words 32 at a time; the set bits of each word,
+            // in order, are its uncertain pairs in edge order
+            const uint32_t er = __shfl_sync(FULL, e, 0);
             unsigned long long es;
             uint32_t len;
-            row_edges(LP, H, hmap, er, (avr & ACT_HEAVY) != 0, es, len);
-            const uint32_t *__restrict__ ecol = LP.col + es;
-            for (uint32_t base = 0; base < len; base += 64) {
-                uint32_t cv[2];
-                bool nd[2];
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const uint32_t v = base + 32u * j + lane;
-                    cv[j] = v < len ? ecol[v] : 0u;
-                    nd[j] = v < len;
+            row_edges(LP, H, hmap, er, true, es, len);
+            const unsigned long long ee = es + len, w0 = es >> 5, w1 = (ee - 1) >> 5;
+            for (unsigned long long wb = w0; wb <= w1; wb += 32) {
+                const unsigned long long wi = wb + lane;
+                const uint32_t word = wi <= w1 ? take_word(wi, es, ee) : 0u;
+                for (unsigned nz = __ballot_sync(FULL, word != 0u); nz; nz &= nz - 1) {
+                    const int j = __ffs(nz) - 1;
+                    const uint32_t bits = __shfl_sync(FULL, word, j);
+                    const bool has = (bits >> lane) & 1u;
+                    push(has, has ? LP.col[(wb + j) * 32 + lane] : 0u, 0);
                 }
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    nd[j] = nd[j] && (pp ? screen_pair<MT, true>(qr, Qc[cv[j] & PMASK], cv[j], L0, L1, L2,
-                                                                 Cr.screen_link[0], Cr.screen_non[0], Cr)
-                                         : screen_pair<MT, false>(qr, Qc[cv[j] & PMASK], cv[j], L0, L1, L2,
-                                                                  Cr.screen_link[0], Cr.screen_non[0], Cr));
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const unsigned bal = __ballot_sync(FULL, nd[j]);
-                    if (nd[j]) {
-                        const int pos = (qh + qn + __popc(bal & lt_mask)) & (QCAP - 1);
-                        T.qk[pos] = cv[j] & PMASK;
-                        T.qs[pos] = (uint8_t)(r | (MT ? ((cv[j] >> 29) & 3u) << 5 : 0u) | ((cv[j] >> 31) ? 0x80 : 0));
+            }
+        } else {
+            // light rows with an uncertain pair: each lane reads its own row's words and
+            // queues one pair per round
+            unsigned long long wcur = 0, wend = 0, es = 0, ee = 0;
+            uint32_t cur = 0;
+            bool pend = false;
+            if (unc) {
+                es = LP.ptr[e];
+                ee = LP.ptr[e + 1];
+                pend = ee > es;   // a flagged row always has an edge
+            }
+            if (pend) {
+                wcur = es >> 5;
+                wend = (ee - 1) >> 5;
+                cur = take_word(wcur, es, ee);
+            }
+            while (__any_sync(FULL, pend)) {
+                bool has = false;
+                uint32_t cv = 0u;
+                if (pend) {
+                    while (cur == 0u && wcur < wend) cur = take_word(++wcur, es, ee);
+                    if (cur) {
+                        const int bit = __ffs(cur) - 1;
+                        cur &= cur - 1u;
+                        cv = LP.col[wcur * 32 + bit];
+                        has = true;
                     }
-                    qn += __popc(bal);
+                    pend = cur != 0u || wcur < wend;
                 }
-                __syncwarp();
-                while (qn >= 32) batch();
+                push(has, cv, lane);
             }
         }
         while (qn > 0) batch();
@@ -1161,17 +1282,28 @@ struct ThrB2 {
     float b2[MAX_THR];
 };
 
+// Place in the edge array of the j-th edge of a row (light rows: their own range in row
+// order; heavy rows: after every light edge).
+__device__ __forceinline__ unsigned long long edge_place(const unsigned long long *__restrict__ row_ptr,
+                                                         const unsigned long long *__restrict__ lptr,
+                                                         const unsigned long long *__restrict__ hptr,
+                                                         unsigned long long n_light, uint32_t row,
+                                                         unsigned long long j) {
+    return row_ptr[row + 1] - row_ptr[row] > HEAVY ? n_light + hptr[row] + j : lptr[row] + j;
+}
+
 // One CSR entry per directed edge t (sorted keys: row, partner row, threshold index):
 // partner's row, threshold index and the link flag at the pair's own linking length,
-// written to the row's place in the edge array (light rows: their group's range, with the
-// row's slot; heavy rows: after every light edge).
+// written to the row's place in the edge array (light rows with the row's slot in its
+// group).  An edge to a later partner also records where its reverse edge lies (found by
+// binary search in the partner's sorted keys).
 __global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, int nbe, int tb, ThrB2 tb2,
                        const unsigned long long *__restrict__ row_ptr, const unsigned long long *__restrict__ lptr,
                        const unsigned long long *__restrict__ hptr, unsigned long long n_light,
                        const uint32_t *__restrict__ epos, const uint32_t *__restrict__ rb,
                        const int64_t *__restrict__ roff, const float4 *__restrict__ P4,
                        const BlockDev *__restrict__ bt, const int64_t *__restrict__ off, int nblk,
-                       uint32_t *__restrict__ ecol, uint8_t *__restrict__ eslot) {
+                       uint32_t *__restrict__ ecol, uint8_t *__restrict__ eslot, unsigned long long *__restrict__ erev) {
     const unsigned long long mask = (1ull << nbe) - 1ull;
     GRID_STRIDE(t, m) {
         const unsigned long long k = keys[t];
@@ -1186,43 +1318,80 @@ __global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, i
         const bool link = cdist2(d.x, d.y, d.z) <= b2;
         const uint32_t cv = prow | (ti << 29) | (link ? 0x80000000u : 0u);
         const unsigned long long r_lo = row_ptr[row], j = (unsigned long long)t - r_lo;
-        if (row_ptr[row + 1] - r_lo > HEAVY) {
-            ecol[n_light + hptr[row] + j] = cv;
-        } else {
-            const unsigned long long dst = lptr[row] + j;
+        const unsigned long long dst = edge_place(row_ptr, lptr, hptr, n_light, row, j);
+        ecol[dst] = cv;
+        if (row_ptr[row + 1] - r_lo <= HEAVY) {
             const int64_t r0 = roff ? roff[rb[row]] : 0;
-            ecol[dst] = cv;
             eslot[dst] = (uint8_t)(((int64_t)row - r0) & 31);
+        }
+        if (prow > row) {
+            const unsigned long long want = ((((unsigned long long)prow << nbe) | row) << tb) | ti;
+            unsigned long long lo = row_ptr[prow], hi = row_ptr[prow + 1];
+            while (lo < hi) {   // first key >= want in the partner's row (the reverse edge)
+                const unsigned long long mid = (lo + hi) >> 1;
+                if (keys[mid] < want) lo = mid + 1;
+                else hi = mid;
+            }
+            // both directions of every pair are keys, so the search always finds it; were it
+            // ever missing, the edge would name itself (every bit index stays in range)
+            erev[dst] = lo < row_ptr[prow + 1] && keys[lo] == want
+                            ? edge_place(row_ptr, lptr, hptr, n_light, prow, lo - row_ptr[prow])
+                            : dst;
         }
     }
 }
 
-// The 32-row groups of light rows (groups start at the first row of each block): first
-// row and row count of each, appended in any order.
+// The 32-row groups of light rows (groups start at the first row of each block; group g
+// of block b is gbase[b] + its index in the block): first row and row count of each, and
+// the number of edges of its rows to later partners (partners are sorted, so those form
+// the end of each row's range).
+template <uint32_t PMASK>
 __global__ void k_groups(int64_t ne, const uint32_t *__restrict__ rb, const int64_t *__restrict__ roff,
-                         uint2 *__restrict__ grp, unsigned long long *__restrict__ ngrp) {
+                         const uint32_t *__restrict__ gbase, const unsigned long long *__restrict__ lptr,
+                         const uint32_t *__restrict__ col, uint2 *__restrict__ grp,
+                         unsigned long long *__restrict__ nup) {
     GRID_STRIDE(e, ne) {
         const int64_t r0 = roff ? roff[rb[e]] : 0, r1 = roff ? roff[rb[e] + 1] : ne;
-        if (((e - r0) & 31) != 0) continue;
-        const unsigned long long at = atomicAdd(ngrp, 1ull);
-        grp[at] = make_uint2((uint32_t)e, (uint32_t)min((int64_t)32, r1 - e));
+        const int64_t g = (roff ? (int64_t)gbase[rb[e]] : 0) + (e - r0) / 32;
+        if (((e - r0) & 31) == 0) grp[g] = make_uint2((uint32_t)e, (uint32_t)min((int64_t)32, r1 - e));
+        unsigned long long lo = lptr[e], hi = lptr[e + 1];
+        const unsigned long long end = hi;
+        while (lo < hi) {   // first partner after row e
+            const unsigned long long mid = (lo + hi) >> 1;
+            if ((col[mid] & PMASK) <= (uint32_t)e) lo = mid + 1;
+            else hi = mid;
+        }
+        if (end > lo) atomicAdd(nup + g, end - lo);
     }
 }
 
-// The screen's edge stream: each group's light edges sorted by (CSR entry, slot), one CTA
-// per group, a bitonic sort in shared memory (groups hold at most 32 x HEAVY edges).
+// The screen's stream of each group: its rows' edges to later partners sorted by partner
+// (then by place), one CTA per group, a bitonic sort in shared memory (a group holds at
+// most 32 x HEAVY light edges, so a place fits 13 bits).
 constexpr int GSORT_CAP = 32 * HEAVY;
+template <uint32_t PMASK>
 __global__ void __launch_bounds__(256) k_group_sort(const uint2 *__restrict__ grp, const unsigned long long *__restrict__ lptr,
                                                     const uint32_t *__restrict__ col, const uint8_t *__restrict__ slot,
-                                                    uint32_t *__restrict__ scol, uint8_t *__restrict__ sslot) {
+                                                    const unsigned long long *__restrict__ gup,
+                                                    uint32_t *__restrict__ scol, uint32_t *__restrict__ saux) {
     extern __shared__ unsigned long long sk[];
-    const uint2 g = grp[blockIdx.x];
-    const unsigned long long a = lptr[g.x], len = lptr[g.x + g.y] - a;
-    if (len == 0) return;
+    __shared__ int s_n;
+    const int64_t g = blockIdx.x;
+    const unsigned long long u0 = gup[g], nu = gup[g + 1] - u0;
+    if (nu == 0) return;
+    const uint2 gr = grp[g];
+    const unsigned long long a = lptr[gr.x], len = lptr[gr.x + gr.y] - a;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < (int)len; i += blockDim.x) {
+        const uint32_t p = col[a + i] & PMASK, row = gr.x + slot[a + i];
+        if (p > row) sk[atomicAdd(&s_n, 1)] = ((unsigned long long)p << 13) | (unsigned long long)i;
+    }
+    __syncthreads();
+    const int n = min(s_n, (int)nu);   // equal: both count the partners after each row
     int cap = 1;
-    while (cap < (int)len) cap <<= 1;
-    for (int i = threadIdx.x; i < cap; i += blockDim.x)
-        sk[i] = i < (int)len ? (((unsigned long long)col[a + i] << 8) | slot[a + i]) : ~0ull;
+    while (cap < n) cap <<= 1;
+    for (int i = n + threadIdx.x; i < cap; i += blockDim.x) sk[i] = ~0ull;
     __syncthreads();
     for (int k = 2; k <= cap; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -1239,9 +1408,10 @@ __global__ void __launch_bounds__(256) k_group_sort(const uint2 *__restrict__ gr
             }
             __syncthreads();
         }
-    for (int i = threadIdx.x; i < (int)len; i += blockDim.x) {
-        scol[a + i] = (uint32_t)(sk[i] >> 8);
-        sslot[a + i] = (uint8_t)(sk[i] & 0xffu);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const uint32_t i = (uint32_t)(sk[j] & 8191ull);
+        scol[u0 + j] = col[a + i];
+        saux[u0 + j] = (i << 5) | slot[a + i];
     }
 }
 
@@ -1261,12 +1431,21 @@ __global__ void k_heavy_keys(const unsigned long long *__restrict__ hdeg, const 
 }
 
 // The heavy items in sorted order: edge range and row.
+template <uint32_t PMASK>
 __global__ void k_heavy_items(const uint32_t *__restrict__ hrow, int64_t nh, const unsigned long long *__restrict__ hptr,
                               const unsigned long long *__restrict__ hdeg, unsigned long long n_light,
-                              HeavyItem *__restrict__ item, uint32_t *__restrict__ hmap) {
+                              const uint32_t *__restrict__ col, HeavyItem *__restrict__ item,
+                              uint32_t *__restrict__ hmap) {
     GRID_STRIDE(k, nh) {
         const uint32_t e = hrow[k];
-        item[k] = HeavyItem{n_light + hptr[e], e, (uint32_t)hdeg[e]};
+        const unsigned long long st = n_light + hptr[e];
+        uint32_t lo = 0, hi = (uint32_t)hdeg[e];
+        while (lo < hi) {   // first partner after row e
+            const uint32_t mid = (lo + hi) >> 1;
+            if ((col[st + mid] & PMASK) <= e) lo = mid + 1;
+            else hi = mid;
+        }
+        item[k] = HeavyItem{st, e, (uint32_t)hdeg[e], lo, 0u};
         hmap[e] = (uint32_t)k;
     }
 }
@@ -1397,11 +1576,12 @@ struct PgdSolver::Impl {
     DBuf<PgdConsts> CB;
     DBuf<PgdBlk> blk;
     DBuf<PgdGlobal> gs;
-    DBuf<uint32_t> rb, ecol, hmap, cand, hcand;
+    DBuf<uint32_t> rb, ecol, hmap;
     DBuf<unsigned long long> lptr;
     DBuf<HeavyItem> hitem;
-    DBuf<uint8_t> eslot, sslot;
-    DBuf<uint32_t> scol;
+    DBuf<uint32_t> scol, saux, ubits;
+    DBuf<unsigned long long> gup, erev;
+    DBuf<uint8_t> uflag;
     LightPlan LP{};
     DBuf<float4> PE, Dh0, Dl0, Dh1, Dl1, Mh, Ml, Vh, Vl, Q0, Q1;
     DBuf<uint8_t> act;
@@ -1427,20 +1607,26 @@ struct PgdSolver::Impl {
         const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS),
                                                                   (int64_t)num_sms() * SCREEN_BLOCKS_PER_SM));
         if (mt) {
-            k_pgd_screen<false, true><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, cand.p, hcand.p);
+            k_pgd_screen<false, true><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, ubits.p,
+                                                                 uflag.p);
             PC_CHECK_LAUNCH();
-            k_pgd_update<false, true><<<nblk, PGD_THREADS, 0, s>>>(PE.p, Bf, HP, LP, hmap.p, rb.p, cand.p, hcand.p, CB.p, nb,
-                                                                   blk.p, gs.p, wt, hist_loss, hist_viol);
+            k_pgd_update<false, true><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, rb.p, ubits.p,
+                                                                   uflag.p, CB.p, nb, blk.p, gs.p, wt, hist_loss,
+                                                                   hist_viol);
         } else if (nb == 1) {
-            k_pgd_screen<false, false><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, cand.p, hcand.p);
+            k_pgd_screen<false, false><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, ubits.p,
+                                                                  uflag.p);
             PC_CHECK_LAUNCH();
-            k_pgd_update<false, false><<<nblk, PGD_THREADS, 0, s>>>(PE.p, Bf, HP, LP, hmap.p, rb.p, cand.p, hcand.p, CB.p, nb,
-                                                                    blk.p, gs.p, wt, hist_loss, hist_viol);
+            k_pgd_update<false, false><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, rb.p, ubits.p,
+                                                                    uflag.p, CB.p, nb, blk.p, gs.p, wt, hist_loss,
+                                                                    hist_viol);
         } else {
-            k_pgd_screen<true, false><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, cand.p, hcand.p);
+            k_pgd_screen<true, false><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, ubits.p,
+                                                                 uflag.p);
             PC_CHECK_LAUNCH();
-            k_pgd_update<true, false><<<nblk, PGD_THREADS, 0, s>>>(PE.p, Bf, HP, LP, hmap.p, rb.p, cand.p, hcand.p, CB.p, nb,
-                                                                   blk.p, gs.p, wt, nullptr, nullptr);
+            k_pgd_update<true, false><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, rb.p, ubits.p,
+                                                                   uflag.p, CB.p, nb, blk.p, gs.p, wt, nullptr,
+                                                                   nullptr);
         }
         PC_CHECK_LAUNCH();
     }
@@ -1600,39 +1786,61 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     I.n_heavy = *(const uint32_t *)read_back(hs, tot2.p, sizeof(uint32_t), s);
     const unsigned long long n_light = *(const unsigned long long *)read_back(hs, I.lptr.p + ne, 8, s);
     I.ecol.alloc(std::max<int64_t>(1, m), s);
-    I.eslot.alloc(std::max<unsigned long long>(1, n_light), s);
+    I.erev.alloc(std::max<int64_t>(1, m), s);
+    DBuf<uint8_t> eslot(std::max<unsigned long long>(1, n_light), s);
     k_cols<<<grid_for(m), 256, 0, s>>>(keys.p, m, nbe, tb, tb2, row_ptr.p, I.lptr.p, hptr.p, n_light, epos.p,
-                                       I.rb.p, roff.p, B.P4.p, S.dev.p, S.doff.p, nb, I.ecol.p, I.eslot.p);
+                                       I.rb.p, roff.p, B.P4.p, S.dev.p, S.doff.p, nb, I.ecol.p, eslot.p, I.erev.p);
     PC_CHECK_LAUNCH();
     keys.release();
     row_ptr.release();
     dense.release();
     epos.release();
-    // the screen's copy of the light edges, sorted by partner within each 32-row group
-    I.scol.alloc(std::max<unsigned long long>(1, n_light), s);
-    I.sslot.alloc(std::max<unsigned long long>(1, n_light), s);
-    if (n_light > 0) {
-        DBuf<uint2> grp(cdiv(ne, 32) + nb, s);
-        DBuf<unsigned long long> ngrp(1, s);
-        PC_CUDA(cudaMemsetAsync(ngrp.p, 0, sizeof(unsigned long long), s));
-        k_groups<<<grid_for(ne), 256, 0, s>>>(ne, I.rb.p, roff.p, grp.p, ngrp.p);
-        PC_CHECK_LAUNCH();
-        const int64_t ng = (int64_t)*(const unsigned long long *)read_back(hs, ngrp.p, 8, s);
-        PC_CUDA(cudaFuncSetAttribute(k_group_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(GSORT_CAP * sizeof(unsigned long long))));
-        if (ng > 0) {
-            k_group_sort<<<(unsigned)ng, 256, GSORT_CAP * sizeof(unsigned long long), s>>>(
-                grp.p, I.lptr.p, I.ecol.p, I.eslot.p, I.scol.p, I.sslot.p);
-            PC_CHECK_LAUNCH();
+    // light groups, numbered by block, and the screen's stream of each: its rows' edges to
+    // later partners, sorted by partner
+    std::vector<uint32_t> hgb(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) hgb[b + 1] = hgb[b] + (uint32_t)cdiv(I.row_off[b + 1] - I.row_off[b], 32);
+    const int64_t ng = hgb[nb];
+    DBuf<uint32_t> gbase(nb + 1, s);
+    PC_CUDA(cudaMemcpyAsync(gbase.p, hgb.data(), (nb + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    DBuf<uint2> grp(std::max<int64_t>(1, ng), s);
+    DBuf<unsigned long long> nup(std::max<int64_t>(1, ng), s);
+    I.gup.alloc(ng + 1, s);
+    PC_CUDA(cudaMemsetAsync(nup.p, 0, std::max<int64_t>(1, ng) * sizeof(unsigned long long), s));
+    if (I.mt)
+        k_groups<0x1fffffffu><<<grid_for(ne), 256, 0, s>>>(ne, I.rb.p, roff.p, gbase.p, I.lptr.p, I.ecol.p, grp.p,
+                                                           nup.p);
+    else
+        k_groups<0x7fffffffu><<<grid_for(ne), 256, 0, s>>>(ne, I.rb.p, roff.p, gbase.p, I.lptr.p, I.ecol.p, grp.p,
+                                                           nup.p);
+    PC_CHECK_LAUNCH();
+    scan_exclusive_u64((const uint64_t *)nup.p, (uint64_t *)I.gup.p, ng, (uint64_t *)(I.gup.p + ng), s);
+    const unsigned long long n_up = *(const unsigned long long *)read_back(hs, I.gup.p + ng, 8, s);
+    I.scol.alloc(std::max<unsigned long long>(1, n_up), s);
+    I.saux.alloc(std::max<unsigned long long>(1, n_up), s);
+    if (n_up > 0) {
+        const int smem = (int)(GSORT_CAP * sizeof(unsigned long long));
+        if (I.mt) {
+            PC_CUDA(cudaFuncSetAttribute(k_group_sort<0x1fffffffu>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            k_group_sort<0x1fffffffu><<<(unsigned)ng, 256, smem, s>>>(grp.p, I.lptr.p, I.ecol.p, eslot.p, I.gup.p,
+                                                                      I.scol.p, I.saux.p);
+        } else {
+            PC_CUDA(cudaFuncSetAttribute(k_group_sort<0x7fffffffu>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            k_group_sort<0x7fffffffu><<<(unsigned)ng, 256, smem, s>>>(grp.p, I.lptr.p, I.ecol.p, eslot.p, I.gup.p,
+                                                                      I.scol.p, I.saux.p);
         }
+        PC_CHECK_LAUNCH();
     }
+    eslot.release();
+    // the screen's bit mask over the edge array and the rows' flags (both cleared as read)
+    I.ubits.alloc(std::max<int64_t>(1, cdiv(m, 32)), s);
+    PC_CUDA(cudaMemsetAsync(I.ubits.p, 0, std::max<int64_t>(1, cdiv(m, 32)) * sizeof(uint32_t), s));
+    I.uflag.alloc(ne, s);
+    PC_CUDA(cudaMemsetAsync(I.uflag.p, 0, ne, s));
     // heavy rows: by block, longest first (long walks start early); per-block ranges
     DBuf<uint32_t> h_per_blk(nb, s), h_off(nb + 1, s);
     PC_CUDA(cudaMemsetAsync(h_per_blk.p, 0, nb * sizeof(uint32_t), s));
     I.hitem.alloc(std::max<int64_t>(1, I.n_heavy), s);
     I.hmap.alloc(ne, s);
-    I.cand.alloc(ne, s);
-    I.hcand.alloc(std::max<int64_t>(1, I.n_heavy), s);
     if (I.n_heavy > 0) {
         DBuf<unsigned long long> hkey(I.n_heavy, s);
         DBuf<uint32_t> hrow(I.n_heavy, s);
@@ -1640,18 +1848,22 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
                                                   h_per_blk.p);
         PC_CHECK_LAUNCH();
         radix_sort_u64((uint64_t *)hkey.p, hrow.p, I.n_heavy, 32 + std::max(1, ceil_log2((uint64_t)nb)), s);
-        k_heavy_items<<<grid_for(I.n_heavy), 256, 0, s>>>(hrow.p, I.n_heavy, hptr.p, hdeg.p, n_light, I.hitem.p,
-                                                          I.hmap.p);
+        if (I.mt)
+            k_heavy_items<0x1fffffffu><<<grid_for(I.n_heavy), 256, 0, s>>>(hrow.p, I.n_heavy, hptr.p, hdeg.p, n_light,
+                                                                           I.ecol.p, I.hitem.p, I.hmap.p);
+        else
+            k_heavy_items<0x7fffffffu><<<grid_for(I.n_heavy), 256, 0, s>>>(hrow.p, I.n_heavy, hptr.p, hdeg.p, n_light,
+                                                                           I.ecol.p, I.hitem.p, I.hmap.p);
         PC_CHECK_LAUNCH();
     }
     scan_exclusive_u32(h_per_blk.p, h_off.p, nb, h_off.p + nb, s);
-    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.eslot.p, I.scol.p, I.sslot.p};
+    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.gup.p, I.scol.p, I.saux.p, I.erev.p};
     if (nb > 1) {
         // work table of the blocks still iterating (all of them before the first launch)
         I.bw.alloc(nb, s);
         I.act_blk.alloc(nb, s);
         I.act_pref.alloc(nb + 1, s);
-        k_blk_work<<<grid_for(nb), 256, 0, s>>>(roff.p, h_off.p, nb, I.bw.p);
+        k_blk_work<<<grid_for(nb), 256, 0, s>>>(roff.p, h_off.p, gbase.p, nb, I.bw.p);
         PC_CHECK_LAUNCH();
         I.wt = WorkTab{I.bw.p, I.act_blk.p, I.act_pref.p};
         k_worktab_init<<<1, 32, 0, s>>>(nb, I.blk.p, I.wt, I.gs.p);
@@ -1705,7 +1917,7 @@ void PgdSolver::capture(int k) {
     cudaStreamDestroy(cs);
     PC_CUDA(e);
     PC_CUDA(cudaGraphInstantiate(&I.exec, I.graph, 0));
-    add_launches(-2 * (int64_t)k);   // captured, not run
+    add_launches(-KERNELS_PER_ITER * (int64_t)k);   // captured, not run
     I.graph_k = k;
 }
 
@@ -1716,7 +1928,7 @@ int64_t PgdSolver::launch(int k) {
     if (I.exec) {
         for (; done + I.graph_k <= k || done == 0; done += I.graph_k) {
             PC_CUDA(cudaGraphLaunch(I.exec, I.s));
-            add_launches(2 * (int64_t)I.graph_k);
+            add_launches(KERNELS_PER_ITER * (int64_t)I.graph_k);
         }
     } else {
         for (; done < k; ++done) I.launch_iter();
