@@ -3,6 +3,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -269,12 +270,22 @@ void select_count(HostScratch &hs, const float *orig, cudaStream_t s, Selection 
         h.safe.alloc(n, s);
         uf_init(h.safe.p, n, s);
     }
-    pair_pass_union(h.B, S, h.fof.p, h.safe.p, h.counts.p, h.err.p, s, nb > 1 ? h.bc.p : nullptr);
+    // pass 1 also keeps every vulnerable pair, so that the selection needs no second search;
+    // PC_VULN_CAP (a host-side test hook) lowers the buffer to exercise the emission pass
+    int64_t capV = vulnerable_guess(n);
+    if (const char *c = getenv("PC_VULN_CAP")) {
+        const long long v = atoll(c);
+        if (v > 0) capV = std::min<int64_t>(capV, v);
+    }
+    h.V.alloc(capV, s);
+    pair_pass_union(h.B, S, h.fof.p, h.safe.p, h.counts.p, h.err.p, s, nb > 1 ? h.bc.p : nullptr, h.V.p,
+                    (uint64_t)capV);
     if (h.fof.p) uf_flatten(h.fof.p, n, h.err.p, s);
     if (h.safe.p) uf_flatten(h.safe.p, n, h.err.p, s);
     memcpy(h.cnt, read_back(hs, h.counts.p, sizeof(h.cnt), s), sizeof(h.cnt));
     const uint32_t ev = *(uint32_t *)read_back(hs, h.err.p, sizeof(uint32_t), s);
     if (ev & ERR_UF_RETRY) fail(PC_ETIMEOUT, "union-find retry bound exceeded");
+    if (ev & ERR_VFULL) h.V.release();   // too many: the emission pass searches again
 }
 
 // Device bytes the emission, the spanning forest and the PGD state will take on top of
@@ -295,13 +306,25 @@ void select_emit(HostScratch &hs, cudaStream_t s, Selection &h) {
     const int nb = S.nb;
     const int64_t n = S.n;
     const unsigned long long *cnt = h.cnt;
-    const uint64_t capA = std::max<uint64_t>(1, cnt[CNT_PB] + cnt[CNT_PC]);
+    const uint64_t nV = cnt[CNT_PB] + cnt[CNT_PC];
+    const uint64_t capA = std::max<uint64_t>(1, nV);
     const uint64_t capC = h.any_fof ? std::max<uint64_t>(1, cnt[CNT_PB]) : 0;
-    h.A.alloc(capA, s);
     DBuf<unsigned long long> C(capC, s);
-    pair_pass_emit(h.B, S, h.fof.p, h.safe.p, h.A.p, capA, C.p, capC, h.counts.p, h.err.p, s);
     unsigned long long cnt2[CNT_N];
-    memcpy(cnt2, read_back(hs, h.counts.p, sizeof(cnt2), s), sizeof(cnt2));
+    if (h.V.p && !h.any_safe) {
+        // every block selects by VP: A is the vulnerable set itself
+        h.A = std::move(h.V);
+        memcpy(cnt2, cnt, sizeof(cnt2));
+        cnt2[CNT_A] = nV;
+    } else {
+        h.A.alloc(capA, s);
+        if (h.V.p)
+            filter_vulnerable(h.B, S, h.fof.p, h.safe.p, h.V.p, nV, h.A.p, capA, C.p, capC, h.counts.p, h.err.p, s);
+        else
+            pair_pass_emit(h.B, S, h.fof.p, h.safe.p, h.A.p, capA, C.p, capC, h.counts.p, h.err.p, s);
+        h.V.release();
+        memcpy(cnt2, read_back(hs, h.counts.p, sizeof(cnt2), s), sizeof(cnt2));
+    }
     const uint32_t e2v = *(uint32_t *)read_back(hs, h.err.p, sizeof(uint32_t), s);
     if (e2v & ERR_INDEX) fail(PC_ECUDA, "pair emission overflowed its count");
     int64_t nA = (int64_t)cnt2[CNT_A];

@@ -41,6 +41,7 @@ enum : uint32_t {
     ERR_OUTSIDE_BOX = 4u,
     ERR_UF_RETRY = 8u,      // a union-find retry loop exceeded its bound
     ERR_INDEX = 16u,        // an index check failed (should never happen)
+    ERR_VFULL = 32u,        // the count pass's buffer of vulnerable pairs is full (the emission pass runs)
 };
 
 // ---------------------------------------------------------------------------

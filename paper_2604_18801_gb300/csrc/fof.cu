@@ -368,6 +368,8 @@ namespace {
 
 struct PairArgs {
     unsigned long long *blk_counts;   // pass 1: per block links, safe, pb, pc (may be null)
+    unsigned long long *V;            // pass 1: every vulnerable pair (may be null)
+    uint64_t capV;
     uint32_t *fof_par, *safe_par;
     const uint32_t *fof_lab, *safe_lab;
     unsigned long long *A, *C;
@@ -377,7 +379,7 @@ struct PairArgs {
 };
 
 __device__ __forceinline__ void emit_pair(unsigned long long key, unsigned long long *out, uint64_t cap,
-                                          unsigned long long *cnt, uint32_t *err) {
+                                          unsigned long long *cnt, uint32_t *err, uint32_t full = ERR_INDEX) {
     // warp-aggregated reservation: one atomic per group of converged emitting lanes
     cg::coalesced_group g = cg::coalesced_threads();
     unsigned long long base = 0;
@@ -385,7 +387,12 @@ __device__ __forceinline__ void emit_pair(unsigned long long key, unsigned long 
     base = g.shfl(base, 0);
     const unsigned long long pos = base + g.thread_rank();
     if (pos < cap) out[pos] = key;
-    else atomicOr(err, ERR_INDEX);
+    else atomicOr(err, full);
+}
+
+__device__ __forceinline__ unsigned long long pair_key(int64_t k, int64_t kj) {
+    return k < kj ? (((unsigned long long)k << 32) | (unsigned long long)kj)
+                  : (((unsigned long long)kj << 32) | (unsigned long long)k);
 }
 
 // Home cell first, then the 13 forward neighbours (lexicographically positive (dz, dy, dx)).
@@ -416,17 +423,19 @@ __device__ __forceinline__ void pair_action(float d2, int64_t k, int64_t kj, uin
             ++cn.links;
             if (a.safe_par) uf_union(a.safe_par, id, jd, a.err);
             if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
-        } else if (d2 <= b2) {
-            ++cn.pb;
-            ++cn.links;
-            if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
         } else {
-            ++cn.pc;
+            if (d2 <= b2) {
+                ++cn.pb;
+                ++cn.links;
+                if (a.fof_par) uf_union(a.fof_par, id, jd, a.err);
+            } else {
+                ++cn.pc;
+            }
+            if (a.V) emit_pair(pair_key(k, kj), a.V, a.capV, a.counts + CNT_V, a.err, ERR_VFULL);
         }
     } else {
         if (d2 <= lo2) return;   // safe link: never vulnerable
-        const unsigned long long pk = k < kj ? (((unsigned long long)k << 32) | (unsigned long long)kj)
-                                             : (((unsigned long long)kj << 32) | (unsigned long long)k);
+        const unsigned long long pk = pair_key(k, kj);
         if (mode == 0) {
             emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
         } else if (mode == 1) {
@@ -660,6 +669,37 @@ void cell_maps(Binned &B, const BlockSet &S, uint32_t dense_min, cudaStream_t s,
 }
 
 namespace {
+// One vulnerable pair of pass 1 (key: sorted positions min << 32 | max) sent where pass 2
+// would send it, by its block's mode; the squared distance is recomputed from the same
+// rounded positions by the same expression (the difference is antisymmetric bit for bit).
+__global__ void k_filter_v(const float4 *__restrict__ P4, const unsigned long long *__restrict__ V, uint64_t nV,
+                           const BlockDev *__restrict__ bt, const int64_t *__restrict__ off, int nb,
+                           const uint32_t *__restrict__ fof_lab, const uint32_t *__restrict__ safe_lab, PairArgs a) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nV;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long pk = V[t];
+        const int64_t k = (int64_t)(pk >> 32), kj = (int64_t)(pk & 0xffffffffull);
+        const BlockDev &B = bt[find_block(off, nb, k)];
+        if (B.mode == 0) {
+            emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
+            continue;
+        }
+        const float4 p = P4[k], q = P4[kj];
+        const uint32_t id = __float_as_uint(p.w), jd = __float_as_uint(q.w);
+        if (B.mode == 1) {
+            if (safe_lab[id] != safe_lab[jd]) emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
+            continue;
+        }
+        const bool per = B.periodic != 0;
+        const float d2 = cdist2(cdiff(p.x, q.x, per, B.L[0]), cdiff(p.y, q.y, per, B.L[1]), cdiff(p.z, q.z, per, B.L[2]));
+        if (d2 > B.b2) {
+            if (fof_lab[id] != fof_lab[jd]) emit_pair(pk, a.A, a.capA, a.counts + CNT_A, a.err);
+        } else {
+            if (safe_lab[id] != safe_lab[jd]) emit_pair(pk, a.C, a.capC, a.counts + CNT_C, a.err);
+        }
+    }
+}
+
 template <int PASS>
 void run_pair_pass(const Binned &B, const BlockSet &S, const PairArgs &a, cudaStream_t s) {
     const int64_t n = B.n;
@@ -679,9 +719,12 @@ void run_pair_pass(const Binned &B, const BlockSet &S, const PairArgs &a, cudaSt
 }  // namespace
 
 void pair_pass_union(const Binned &B, const BlockSet &S, uint32_t *fof_par, uint32_t *safe_par,
-                     unsigned long long *counts, uint32_t *err, cudaStream_t s, unsigned long long *blk_counts) {
+                     unsigned long long *counts, uint32_t *err, cudaStream_t s, unsigned long long *blk_counts,
+                     unsigned long long *V, uint64_t capV) {
     PairArgs a = {};
     a.blk_counts = blk_counts;
+    a.V = V;
+    a.capV = capV;
     a.fof_par = fof_par;
     a.safe_par = safe_par;
     a.counts = counts;
@@ -702,6 +745,22 @@ void pair_pass_emit(const Binned &B, const BlockSet &S, const uint32_t *fof_lab,
     a.counts = counts;
     a.err = err;
     run_pair_pass<2>(B, S, a, s);
+}
+
+void filter_vulnerable(const Binned &B, const BlockSet &S, const uint32_t *fof_lab, const uint32_t *safe_lab,
+                       const unsigned long long *V, uint64_t nV, unsigned long long *A, uint64_t capA,
+                       unsigned long long *C, uint64_t capC, unsigned long long *counts, uint32_t *err,
+                       cudaStream_t s) {
+    if (nV == 0) return;
+    PairArgs a = {};
+    a.A = A;
+    a.C = C;
+    a.capA = capA;
+    a.capC = capC;
+    a.counts = counts;
+    a.err = err;
+    k_filter_v<<<grid_for((int64_t)nV), 256, 0, s>>>(B.P4.p, V, nV, S.dev.p, S.doff.p, S.nb, fof_lab, safe_lab, a);
+    PC_CHECK_LAUNCH();
 }
 
 }  // namespace pc

@@ -98,11 +98,24 @@ void bin_particles(const float *orig, const BlockSet &S, Binned &B, cudaStream_t
 void cell_maps(Binned &B, const BlockSet &S, uint32_t dense_min, cudaStream_t s, HostScratch &hs);
 
 // ---------------------------------------------------------------- pair search
-enum { CNT_LINKS = 0, CNT_SAFE = 1, CNT_PB = 2, CNT_PC = 3, CNT_A = 4, CNT_C = 5, CNT_N = 8 };
-// Pass 1: union-find over links (fof_par) and safe links (safe_par), class counts.
+enum { CNT_LINKS = 0, CNT_SAFE = 1, CNT_PB = 2, CNT_PC = 3, CNT_A = 4, CNT_C = 5, CNT_V = 6, CNT_N = 8 };
+
+// Capacity of the count pass's buffer of vulnerable pairs: 16 per particle covers the
+// workloads at xi <= 0.5 b; a denser problem overflows it and runs the emission pass.
+inline int64_t vulnerable_guess(int64_t n) { return std::max<int64_t>(1 << 16, 16 * n); }
+// Pass 1: union-find over links (fof_par) and safe links (safe_par), class counts; with V,
+// every vulnerable pair is also written to V (counted in CNT_V; ERR_VFULL when capV is
+// too small, and the emission pass must run).
 void pair_pass_union(const Binned &B, const BlockSet &S, uint32_t *fof_par, uint32_t *safe_par,
                      unsigned long long *counts, uint32_t *err, cudaStream_t s,
-                     unsigned long long *blk_counts = nullptr);
+                     unsigned long long *blk_counts = nullptr, unsigned long long *V = nullptr,
+                     uint64_t capV = 0);
+// The selection of pass 2 taken from the vulnerable pairs V of pass 1 instead of a second
+// search: the same pairs to A and C, by each block's mode.
+void filter_vulnerable(const Binned &B, const BlockSet &S, const uint32_t *fof_lab, const uint32_t *safe_lab,
+                       const unsigned long long *V, uint64_t nV, unsigned long long *A, uint64_t capA,
+                       unsigned long long *C, uint64_t capC, unsigned long long *counts, uint32_t *err,
+                       cudaStream_t s);
 // Pass 2: emission of selected pairs as (min_pos << 32 | max_pos), by each block's mode:
 //   VP: all vulnerable pairs -> A;  SC: vulnerable pairs joining different safe components -> A;
 //   HF: potentially created pairs joining different halos -> A, potentially broken links
@@ -212,6 +225,7 @@ struct Selection {
     // between the count and the emission passes
     DBuf<unsigned long long> counts, bc;
     DBuf<uint32_t> err, fof, safe;
+    DBuf<unsigned long long> V;           // the vulnerable pairs of pass 1 (empty when they overflowed)
     unsigned long long cnt[CNT_N] = {};
     bool any_fof = false, any_safe = false;
     cudaEvent_t ev0 = nullptr;

@@ -119,13 +119,13 @@ void publish(pc_server *srv, Job *j, int32_t state, int32_t status, const char *
     srv->cv_done.notify_all();
 }
 
-// Device bytes of a job's count pass: gathered inputs, binning, labels, and the cell table
-// (4 B per cell, at most cell_factor cells per particle).
+// Device bytes of a job's count pass: gathered inputs, binning, labels, the cell table
+// (4 B per cell, at most cell_factor cells per particle) and the vulnerable-pair buffer.
 int64_t count_pass_bytes(const pc_job &sp) {
     const int64_t f = sp.params.cell_factor > 0 ? sp.params.cell_factor : 8;
     const int64_t cells = sp.params.cell_cap_log2 > 0 ? ((int64_t)1 << std::min(sp.params.cell_cap_log2, 30))
                                                       : std::min<int64_t>((int64_t)1 << 28, f * sp.n);
-    return 176 * sp.n + 4 * std::max<int64_t>(cells, 1 << 16) + (int64_t)(1 << 20);
+    return 176 * sp.n + 4 * std::max<int64_t>(cells, 1 << 16) + 8 * vulnerable_guess(sp.n) + (int64_t)(1 << 20);
 }
 
 // Validates one job alone (finiteness, |recon - orig| <= xi, periodic box); throws Fail.
