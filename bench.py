@@ -66,19 +66,20 @@ PER_MODE_KEYS = ("iters", "loss_evals", "n_vulnerable", "n_active", "n_editable"
 
 
 def pgd_roofline(stats_by_mode: dict, peak: float, peak_kind: str) -> dict:
-    """Roofline of the PGD iteration kernel from pc_correct's own counters: the algorithmic
-    bytes of every check that ran (loss_evals per mode: the launches that did work) over the
-    device time of all iteration launches (CUDA events in the library around them, so the
-    few empty launches after the stop count as time, not as bytes)."""
+    """Roofline of one PGD iteration (k_pgd_screen then k_pgd_update) from pc_correct's own
+    counters: the algorithmic bytes of every check that ran (loss_evals per mode: the
+    iterations that did work) over the device time of all iteration launches (CUDA events in
+    the library around them, on the launching stream, so the few empty launches after the
+    stop count as time, not as bytes)."""
     checks = sum(st["loss_evals"] for st in stats_by_mode.values())
     launches = sum(st["pgd_launches"] for st in stats_by_mode.values())
     nbytes = sum((PGD_BYTES_PER_ROW * st["n_editable"] + PGD_BYTES_PER_PAIR * st["n_active"]) * st["loss_evals"]
                  for st in stats_by_mode.values())
     ms = sum(st["ms_pgd_iter"] for st in stats_by_mode.values())
     achieved = nbytes / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-    return {"kernel": "k_pgd_iter", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+    return {"kernel": "k_pgd_screen+k_pgd_update", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None,
-            "traffic_note": "DRAM bytes of this kernel come from an ncu capture outside the bench run",
+            "traffic_note": "DRAM bytes of these kernels come from an ncu capture outside the bench run",
             "peak_kind": peak_kind, "checks_per_step": int(checks), "launches_per_step": int(launches),
             "avg_check_us": round(1e3 * ms / max(1, checks), 2),
             "bytes_per_check": int(nbytes / max(1, checks)),

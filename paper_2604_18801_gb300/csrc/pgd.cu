@@ -54,6 +54,10 @@ constexpr int MAX_THR = 4;
 // row is heavy (more than HEAVY partners: it is a work item of its own).
 constexpr uint8_t ACT_ON = 1, ACT_HEAVY = 2;
 constexpr uint32_t HEAVY = 256;
+// A light work item is ITEM_GROUPS consecutive groups of 32 rows (of one block): its
+// stream ranges and row positions load together, so their latency is paid once.
+constexpr int ITEM_GROUPS = 4;
+constexpr int ITEM_ROWS = 32 * ITEM_GROUPS;
 
 // Per-block PGD constants (one entry per block of the problem set).  The threshold arrays
 // are indexed by the pair's linking length (entry 0 alone with one).
@@ -143,7 +147,7 @@ __device__ void build_worktab(int nb, const PgdBlk *blk, const WorkTab wt, PgdGl
         unsigned long long it = 0;
         if (a) {
             const BlkWork w = wt.bw[b];
-            it = (unsigned long long)((w.nrows + 31u) >> 5) + w.nh;
+            it = (unsigned long long)((w.nrows + (uint32_t)ITEM_ROWS - 1u) / (uint32_t)ITEM_ROWS) + w.nh;
         }
         unsigned long long inc = it;
 #pragma unroll
@@ -700,10 +704,11 @@ __device__ __forceinline__ bool needs_image(const PgdConsts &C, bool row_lane, c
     return C.periodic != 0 && !__all_sync(0xffffffffu, in_ok);
 }
 
-// Work item `item` of the screen's item space: a heavy row (H.item[hk]) or a group of 32
-// light rows (group g, rows [r0, r0 + cnt)) of block b.  A problem set's items are those of
-// its blocks still iterating (the work table), each block's heavy rows first; a single
-// problem's items are every heavy row, then every group.  Called by all lanes of a warp.
+// Work item `item` of the screen's item space: a heavy row (H.item[hk]) or up to
+// ITEM_GROUPS consecutive groups of 32 light rows (first group g, rows [r0, r0 + cnt)) of
+// block b.  A problem set's items are those of its blocks still iterating (the work
+// table), each block's heavy rows first; a single problem's items are every heavy row,
+// then the light items.  Called by all lanes of a warp.
 template <bool MULTI>
 __device__ __forceinline__ void map_item(int64_t item, int64_t ne, const HeavyPlan &H, const WorkTab &wt, int nact,
                                          int &b, bool &heavy, int64_t &r0, int &cnt, int64_t &hk, int64_t &g) {
@@ -731,18 +736,19 @@ __device__ __forceinline__ void map_item(int64_t item, int64_t ne, const HeavyPl
         heavy = j < (int64_t)bw.nh;
         if (!heavy) {
             const int64_t jl = j - (int64_t)bw.nh;
-            r0 = (int64_t)bw.row0 + 32 * jl;
-            cnt = (int)min((int64_t)32, (int64_t)bw.nrows - 32 * jl);
-            g = (int64_t)bw.g0 + jl;
+            r0 = (int64_t)bw.row0 + ITEM_ROWS * jl;
+            cnt = (int)min((int64_t)ITEM_ROWS, (int64_t)bw.nrows - ITEM_ROWS * jl);
+            g = (int64_t)bw.g0 + ITEM_GROUPS * jl;
         } else {
             hk = (int64_t)bw.h0 + j;
         }
     } else {
         heavy = item < H.n_heavy;
         if (!heavy) {
-            g = item - H.n_heavy;
-            r0 = g * 32;
-            cnt = (int)min((int64_t)32, ne - r0);
+            const int64_t jl = item - H.n_heavy;
+            g = ITEM_GROUPS * jl;
+            r0 = ITEM_ROWS * jl;
+            cnt = (int)min((int64_t)ITEM_ROWS, ne - r0);
         } else {
             hk = item;
         }
@@ -764,7 +770,7 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
     uint8_t *__restrict__ uflag) {
     __shared__ int s_stop, s_t, s_nact;
     __shared__ unsigned long long s_items;
-    __shared__ float4 sq[WARPS][32];      // the item's rows' rounded positions
+    __shared__ float4 sq[WARPS][ITEM_ROWS];   // the item's rows' rounded positions
     if (threadIdx.x == 0) {
         s_stop = gs->all_stop;
         s_nact = gs->active;
@@ -776,8 +782,7 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;   // partner bits of a CSR entry
-    const int64_t n_light_warps = (ne + 31) / 32;
-    const int64_t n_items = MULTI ? (int64_t)s_items : n_light_warps + H.n_heavy;
+    const int64_t n_items = MULTI ? (int64_t)s_items : (ne + ITEM_ROWS - 1) / ITEM_ROWS + H.n_heavy;
     unsigned long long nitm = 0;
     if (lane == 0) nitm = atomicAdd(&gs->work, 1ull);
     for (;;) {
@@ -790,43 +795,18 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
         map_item<MULTI>(item, ne, H, wt, s_nact, b, heavy_warp, r0, cnt, hk, g);
         const int tb = MULTI ? blk[b].t : s_t;
         const int pa = tb & 1;
-        // the item's stream [ebase, ebase + VT); lane i holds row rbase + i (light: i < cnt;
-        // heavy: lane 0, slot 0); fbase + (aux >> 5) is a light edge's place in the edge array
-        int64_t rbase = r0;
-        bool have;
-        uint32_t VT;
-        unsigned long long ebase, fbase = 0;
-        if (!heavy_warp) {
-            have = lane < cnt;
-            unsigned long long ub = 0, ue = 0, lb = 0;
-            if (lane == 0) {
-                ub = LP.gup[g];
-                ue = LP.gup[g + 1];
-                lb = LP.ptr[r0];
-            }
-            ebase = __shfl_sync(FULL, ub, 0);
-            VT = (uint32_t)(__shfl_sync(FULL, ue, 0) - ebase);
-            fbase = __shfl_sync(FULL, lb, 0);
-        } else {
-            const HeavyItem hv = H.item[hk];
-            have = lane == 0;
-            rbase = hv.row;
-            ebase = hv.start + hv.ulo;
-            VT = hv.len - hv.ulo;
-        }
-        const float4 qe = (have || heavy_warp) ? Bf.q(pa)[rbase + (heavy_warp ? 0 : lane)]
-                                              : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (have) sq[w][lane] = qe;
-        __syncwarp();
         const PgdConsts &Cl = CB[b];
-        const bool pp = needs_image(Cl, heavy_warp || have, qe);
         const float L0 = Cl.L[0], L1 = Cl.L[1], L2 = Cl.L[2];
         const float4 *__restrict__ Qc = Bf.q(pa);
-        const uint32_t *__restrict__ ecol = (heavy_warp ? LP.col : LP.scol) + ebase;
-        const uint32_t *__restrict__ eaux = LP.saux + ebase;
         const float slk = Cl.screen_link[0], sln_ = Cl.screen_non[0];
-        auto walk = [&](auto image) {
+        // one stream [ebase, ebase + VT): a heavy row's edges to later partners (row rbase,
+        // position at sqg[0]), or a group's (rows rbase + slot, positions sqg[slot]); fbase +
+        // (aux >> 5) is a light edge's place in the edge array
+        auto walk = [&](auto image, unsigned long long ebase, uint32_t VT, unsigned long long fbase, int64_t rbase,
+                        const float4 *sqg) {
             constexpr bool PP = decltype(image)::value;
+            const uint32_t *__restrict__ ecol = (heavy_warp ? LP.col : LP.scol) + ebase;
+            const uint32_t *__restrict__ eaux = LP.saux + ebase;
             uint32_t cvn[EPL], axn[EPL];
 #pragma unroll
             for (int j = 0; j < EPL; ++j) {
@@ -849,8 +829,8 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
                 unsigned um = 0u;
 #pragma unroll
                 for (int j = 0; j < EPL; ++j)
-                    if (nd[j] && screen_pair<MT, PP>(sq[w][ax[j] & 31u], Qc[cv[j] & PMASK], cv[j], L0, L1, L2, slk,
-                                                     sln_, Cl))
+                    if (nd[j] && screen_pair<MT, PP>(sqg[ax[j] & 31u], Qc[cv[j] & PMASK], cv[j], L0, L1, L2, slk, sln_,
+                                                     Cl))
                         um |= 1u << j;
                 if (um) {
                     // the trip's uncertain pairs: every reverse-edge load first, then both
@@ -872,8 +852,33 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
                 }
             }
         };
-        if (pp) walk(std::true_type{});
-        else walk(std::false_type{});
+        if (heavy_warp) {
+            const HeavyItem hv = H.item[hk];
+            const float4 qe = Qc[hv.row];
+            if (lane == 0) sq[w][0] = qe;
+            __syncwarp();
+            if (needs_image(Cl, true, qe)) walk(std::true_type{}, hv.start + hv.ulo, hv.len - hv.ulo, 0ull, hv.row, sq[w]);
+            else walk(std::false_type{}, hv.start + hv.ulo, hv.len - hv.ulo, 0ull, hv.row, sq[w]);
+        } else {
+            // every group's stream range, edge-array base and row positions, loaded together
+            const int ngr = (cnt + 31) >> 5;
+            unsigned long long gu = 0, fb = 0;
+            if (lane <= ngr) gu = LP.gup[g + lane];
+            if (lane < ngr) fb = LP.ptr[r0 + 32 * lane];
+#pragma unroll
+            for (int j = 0; j < ITEM_GROUPS; ++j)
+                if (32 * j + lane < cnt) sq[w][32 * j + lane] = Qc[r0 + 32 * j + lane];
+            __syncwarp();
+            for (int j = 0; j < ngr; ++j) {
+                const unsigned long long eb = __shfl_sync(FULL, gu, j);
+                const uint32_t vt = (uint32_t)(__shfl_sync(FULL, gu, j + 1) - eb);
+                const unsigned long long fbj = __shfl_sync(FULL, fb, j);
+                const bool have = 32 * j + lane < cnt;
+                const float4 qe = have ? sq[w][32 * j + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (needs_image(Cl, have, qe)) walk(std::true_type{}, eb, vt, fbj, r0 + 32 * j, sq[w] + 32 * j);
+                else walk(std::false_type{}, eb, vt, fbj, r0 + 32 * j, sq[w] + 32 * j);
+            }
+        }
         __syncwarp();
     }
 }
@@ -887,6 +892,7 @@ struct WarpTab {
     unsigned own[32];                // per row slot: this batch's violated entries of that row
     float gt[6][32];                 // this batch's gradient terms (x hi, x lo, y hi, ...) by entry
     uint32_t cb[64];                 // candidate rows waiting for a chunk (row | CAND_UNC), a ring
+    unsigned pm[2][ITEM_GROUPS];     // the current light item's groups: candidate and flag masks
 };
 
 // 16-byte asynchronous copies from global to shared memory (not cached in L1).
@@ -941,21 +947,26 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
     constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;
     unsigned long long lfx = 0;       // this lane's share of the tight loss, fixed point (single block)
     unsigned viol = 0, nupd = 0, nev = 0;
-    // Work comes in two phases.  First the heavy rows, one at a time: a row with an uncertain
-    // pair is taken by the warp at once (kind 1: the warp reads its pairs); a row that only
-    // steps joins the warp's ring of candidates.  Then groups of 32 light rows: each lane
-    // looks at its row's flag and Adam state, and the candidates join the ring.  Whenever the
-    // ring holds 32 (or nothing is left to claim), 32 of them are processed as a chunk
+    // Work comes in two phases.  First the heavy rows, 32 per claim (one per lane): a row
+    // with an uncertain pair is taken by the warp (kind 1: the warp reads its pairs); a row
+    // that only steps joins the warp's ring of candidates.  Then the light items (up to
+    // ITEM_ROWS rows): each lane looks at its rows' flags and Adam state, all loaded
+    // together, and the candidates join the ring one group of 32 rows at a time.  Whenever
+    // the ring holds 32 (or nothing is left to claim), 32 of them are processed as a chunk
     // (kind 2: each lane one row).  The flags are cleared as read.
-    const int64_t n_light_items = MULTI ? (int64_t)s_items : (ne + 31) / 32;
+    const int64_t n_light_items = MULTI ? (int64_t)s_items : (ne + ITEM_ROWS - 1) / ITEM_ROWS;
     bool heavy_done = false, light_done = false;
-    int nc = 0, ch = 0;   // candidates in the ring and its head (warp-uniform)
+    int nc = 0, ch = 0;          // candidates in the ring and its head (warp-uniform)
+    unsigned hmask = 0u;         // lanes whose heavy row (hrow) has an uncertain pair, not yet taken
+    uint32_t hrow = 0u;
+    int lpend = 0, lnum = 0;     // groups of the current light item not yet in the ring: [lpend, lnum)
+    int64_t lr0 = 0;             // first row of the current light item
     for (;;) {
         int kind = 0;   // 1: heavy row, 2: chunk, 0: nothing left
         bool have = false;
         uint32_t ce = 0u;
         for (;;) {
-            if (nc >= 32 || (heavy_done && light_done && nc > 0)) {
+            if (nc >= 32 || (heavy_done && hmask == 0u && light_done && lpend >= lnum && nc > 0)) {
                 const int take = min(nc, 32);
                 have = lane < take;
                 ce = have ? T.cb[(ch + lane) & 63] : 0u;
@@ -965,40 +976,51 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
                 kind = 2;
                 break;
             }
+            if (hmask) {
+                const int j = __ffs(hmask) - 1;
+                hmask &= hmask - 1u;
+                const uint32_t r = __shfl_sync(FULL, hrow, j);
+                have = lane == 0;
+                ce = have ? (r | CAND_UNC) : 0u;
+                kind = 1;
+                break;
+            }
+            if (lpend < lnum) {   // the next group of the current light item joins the ring
+                const unsigned cm = T.pm[0][lpend], fm = T.pm[1][lpend];
+                if ((cm >> lane) & 1u)
+                    T.cb[(ch + nc + __popc(cm & lt_mask)) & 63] =
+                        (uint32_t)(lr0 + 32 * lpend + lane) | (((fm >> lane) & 1u) ? CAND_UNC : 0u);
+                __syncwarp();
+                nc += __popc(cm);
+                ++lpend;
+                continue;
+            }
             if (heavy_done && light_done) break;
             unsigned long long k = 0;
             if (!heavy_done) {
-                if (lane == 0) k = atomicAdd(&gs->work3, 1ull);
+                if (lane == 0) k = atomicAdd(&gs->work3, 32ull);
                 k = __shfl_sync(FULL, k, 0);
                 if ((int64_t)k >= H.n_heavy) {
                     heavy_done = true;
                     continue;
                 }
-                int dec = 0;
-                uint32_t r = 0;
-                if (lane == 0) {
-                    r = H.item[k].row;
-                    const int rbk = MULTI ? (int)rb[r] : 0;
+                const int64_t hk = (int64_t)k + lane;
+                bool f = false, steps = false;
+                hrow = 0u;
+                if (hk < H.n_heavy) {
+                    hrow = H.item[hk].row;
+                    const int rbk = MULTI ? (int)rb[hrow] : 0;
                     if (!MULTI || blk[rbk].stop == 0) {
-                        const bool f = uflag[r] != 0;
-                        if (f) uflag[r] = 0;
-                        const bool steps = (Bf.act[r] & ACT_ON) && !is_last(CB[rbk], MULTI ? blk[rbk].t : s_t);
-                        dec = f ? 1 : (steps ? 2 : 0);
+                        f = uflag[hrow] != 0;
+                        if (f) uflag[hrow] = 0;
+                        steps = (Bf.act[hrow] & ACT_ON) && !is_last(CB[rbk], MULTI ? blk[rbk].t : s_t);
                     }
                 }
-                dec = __shfl_sync(FULL, dec, 0);
-                r = __shfl_sync(FULL, r, 0);
-                if (dec == 1) {
-                    have = lane == 0;
-                    ce = have ? (r | CAND_UNC) : 0u;
-                    kind = 1;
-                    break;
-                }
-                if (dec == 2) {
-                    if (lane == 0) T.cb[(ch + nc) & 63] = r;
-                    __syncwarp();
-                    ++nc;
-                }
+                hmask = __ballot_sync(FULL, f);
+                const unsigned sm = __ballot_sync(FULL, !f && steps);
+                if (!f && steps) T.cb[(ch + nc + __popc(sm & lt_mask)) & 63] = hrow;
+                __syncwarp();
+                nc += __popc(sm);
                 continue;
             }
             if (lane == 0) k = atomicAdd(&gs->work2, 1ull);
@@ -1015,23 +1037,34 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
                 if (ih) continue;   // heavy rows come in the first phase
             } else {
                 ib = 0;
-                ir0 = (int64_t)k * 32;
-                icnt = (int)min((int64_t)32, ne - ir0);
+                ir0 = (int64_t)k * ITEM_ROWS;
+                icnt = (int)min((int64_t)ITEM_ROWS, ne - ir0);
             }
-            bool c = false, f = false;
-            const int64_t r = ir0 + lane;
-            if (lane < icnt) {
-                const uint8_t av = Bf.act[r];
-                if (!(av & ACT_HEAVY)) {
-                    f = uflag[r] != 0;
-                    if (f) uflag[r] = 0;
-                    c = f || ((av & ACT_ON) && !is_last(CB[ib], MULTI ? blk[ib].t : s_t));
+            const int tlast = is_last(CB[ib], MULTI ? blk[ib].t : s_t);
+            uint8_t av[ITEM_GROUPS], fl[ITEM_GROUPS];
+#pragma unroll
+            for (int j = 0; j < ITEM_GROUPS; ++j) {
+                const int64_t r = ir0 + 32 * j + lane;
+                const bool in = 32 * j + lane < icnt;
+                av[j] = in ? Bf.act[r] : (uint8_t)ACT_HEAVY;
+                fl[j] = in ? uflag[r] : (uint8_t)0;
+            }
+#pragma unroll
+            for (int j = 0; j < ITEM_GROUPS; ++j) {
+                const bool light = !(av[j] & ACT_HEAVY);
+                const bool f = light && fl[j] != 0;
+                if (f) uflag[ir0 + 32 * j + lane] = 0;
+                const bool c = f || (light && (av[j] & ACT_ON) && !tlast);
+                const unsigned cm = __ballot_sync(FULL, c), fm = __ballot_sync(FULL, f);
+                if (lane == 0) {
+                    T.pm[0][j] = cm;
+                    T.pm[1][j] = fm;
                 }
             }
-            const unsigned bal = __ballot_sync(FULL, c);
-            if (c) T.cb[(ch + nc + __popc(bal & lt_mask)) & 63] = (uint32_t)r | (f ? CAND_UNC : 0u);
             __syncwarp();
-            nc += __popc(bal);
+            lr0 = ir0;
+            lpend = 0;
+            lnum = (icnt + 31) >> 5;
         }
         if (kind == 0) break;
         const uint32_t e = ce & ~CAND_UNC;
@@ -1872,7 +1905,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     PC_CUDA(cudaStreamSynchronize(s));   // roff and the plan temporaries are released on return
     I.HP.n_heavy = I.n_heavy;
     I.HP.item = I.hitem.p;
-    I.n_items = cdiv(ne, 32) + nb + I.n_heavy;
+    I.n_items = cdiv(ne, ITEM_ROWS) + nb + I.n_heavy;
     I.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(ne, 32 * WARPS), (int64_t)num_sms() * PGD_BLOCKS_PER_SM));
 }
 
