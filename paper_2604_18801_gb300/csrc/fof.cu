@@ -395,6 +395,42 @@ __device__ __forceinline__ unsigned long long pair_key(int64_t k, int64_t kj) {
                   : (((unsigned long long)kj << 32) | (unsigned long long)k);
 }
 
+// Pass 1 keeps the vulnerable pairs through a buffer per warp in shared memory: a lane
+// appends with a shared-memory atomic (no global contention however divergent the lanes
+// are), and the warp moves the buffer to V with one global reservation whenever it is
+// converged and the buffer is at least half full (and at its end).  A pair that finds the
+// buffer full goes to V directly.
+constexpr unsigned VBUF = 256;
+struct WarpVBuf {
+    unsigned long long *key;   // VBUF entries
+    unsigned *cnt;
+};
+
+__device__ __forceinline__ void vbuf_push(const WarpVBuf &wb, unsigned long long key, const PairArgs &a) {
+    const unsigned pos = atomicAdd(wb.cnt, 1u);
+    if (pos < VBUF) wb.key[pos] = key;
+    else emit_pair(key, a.V, a.capV, a.counts + CNT_V, a.err, ERR_VFULL);
+}
+
+// Called by all lanes of a converged warp.
+__device__ __forceinline__ void vbuf_flush(const WarpVBuf &wb, bool force, const PairArgs &a) {
+    const unsigned FULL = 0xffffffffu;
+    __syncwarp();
+    const unsigned c = *(volatile unsigned *)wb.cnt;
+    if (c == 0 || (!force && c < VBUF / 2)) return;
+    const unsigned m = min(c, VBUF);
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 0) base = atomicAdd(a.counts + CNT_V, (unsigned long long)m);
+    base = __shfl_sync(FULL, base, 0);
+    for (unsigned i = threadIdx.x & 31; i < m; i += 32) {
+        if (base + i < a.capV) a.V[base + i] = wb.key[i];
+        else atomicOr(a.err, ERR_VFULL);
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) *wb.cnt = 0u;
+    __syncwarp();
+}
+
 // Home cell first, then the 13 forward neighbours (lexicographically positive (dz, dy, dx)).
 __constant__ int c_off[14][3] = {{0, 0, 0},  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}, {-1, 0, 1},
                                  {0, 0, 1},  {1, 0, 1},   {-1, 1, 1}, {0, 1, 1},  {1, 1, 1},
@@ -416,7 +452,7 @@ struct ClassCounts {
 template <int PASS>
 __device__ __forceinline__ void pair_action(float d2, int64_t k, int64_t kj, uint32_t id, uint32_t jd, float lo2,
                                             float b2, int mode, uint32_t my_safe, uint32_t my_fof,
-                                            const PairArgs &a, ClassCounts &cn) {
+                                            const PairArgs &a, ClassCounts &cn, const WarpVBuf &wb) {
     if (PASS == 1) {
         if (d2 <= lo2) {
             ++cn.safe;
@@ -431,7 +467,7 @@ __device__ __forceinline__ void pair_action(float d2, int64_t k, int64_t kj, uin
             } else {
                 ++cn.pc;
             }
-            if (a.V) emit_pair(pair_key(k, kj), a.V, a.capV, a.counts + CNT_V, a.err, ERR_VFULL);
+            if (a.V) vbuf_push(wb, pair_key(k, kj), a);
         }
     } else {
         if (d2 <= lo2) return;   // safe link: never vulnerable
@@ -514,31 +550,41 @@ __device__ __forceinline__ bool neighbour(const BlockDev &B, int cx, int cy, int
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(256) k_pairs_sparse(const float4 *__restrict__ P4, const uint32_t *__restrict__ keys,
+__global__ void __launch_bounds__(256, 6) k_pairs_sparse(const float4 *__restrict__ P4, const uint32_t *__restrict__ keys,
                                                       const uint32_t *__restrict__ cell_start, int64_t n,
                                                       const BlockDev *__restrict__ bt, const int64_t *__restrict__ off,
                                                       int nb, CellMaps M, PairArgs a) {
+    __shared__ unsigned long long vkey[PASS == 1 ? 8 : 1][PASS == 1 ? VBUF : 1];
+    __shared__ unsigned vcnt[8];
+    const int w = threadIdx.x >> 5;
+    const WarpVBuf wb{vkey[PASS == 1 ? w : 0], vcnt + w};
+    const bool keep = PASS == 1 && a.V != nullptr;
+    if (keep && (threadIdx.x & 31) == 0) vcnt[w] = 0u;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     ClassCounts cn;
     const int bk = k < n ? find_block(off, nb, k) : -1;
-    if (k < n && !cell_bit(M.dense, keys[k])) {
-        const BlockDev &B = bt[bk];
-        const float4 p = P4[k];
-        const uint32_t id = __float_as_uint(p.w);
-        int cx, cy, cz;
+    const bool act = k < n && !cell_bit(M.dense, keys[k]);
+    const BlockDev &B = bt[act ? bk : 0];
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t id = 0, my_safe = 0, my_fof = 0;
+    int cx = 0, cy = 0, cz = 0;
+    if (act) {
+        p = P4[k];
+        id = __float_as_uint(p.w);
         cell_xyz(keys[k], B, cx, cy, cz);
-        const bool per = B.periodic != 0;
-        const float lo2 = B.lo2, b2 = B.b2, hi2 = B.hi2;
-        uint32_t my_safe = 0, my_fof = 0;
         if (PASS == 2) {
             if (B.mode >= 1) my_safe = a.safe_lab[id];
             if (B.mode == 2) my_fof = a.fof_lab[id];
         }
-        for (int o = 0; o < 14; ++o) {
-            uint32_t cell;
-            if (!neighbour(B, cx, cy, cz, c_off[o][0], c_off[o][1], c_off[o][2], cell)) continue;
-            if (!cell_bit(M.occ, cell)) continue;                  // empty
-            if (o != 0 && cell_bit(M.dense, cell)) continue;       // its warps take these pairs
+    }
+    const bool per = B.periodic != 0;
+    const float lo2 = B.lo2, b2 = B.b2, hi2 = B.hi2;
+    // every lane runs the 14 neighbour steps (a lane without a particle does nothing in
+    // them), so the warp is converged after each step and may move its buffer of kept pairs
+    for (int o = 0; o < 14; ++o) {
+        uint32_t cell;
+        if (act && neighbour(B, cx, cy, cz, c_off[o][0], c_off[o][1], c_off[o][2], cell) && cell_bit(M.occ, cell) &&
+            (o == 0 || !cell_bit(M.dense, cell))) {   // a dense neighbour's warps take these pairs
             int64_t js = min((int64_t)cell_start[cell], n);
             const int64_t je = min((int64_t)cell_start[cell + 1], n);
             if (o == 0) js = k + 1;
@@ -547,10 +593,12 @@ __global__ void __launch_bounds__(256) k_pairs_sparse(const float4 *__restrict__
                 const float d2 = cdist2(cdiff(p.x, q.x, per, B.L[0]), cdiff(p.y, q.y, per, B.L[1]),
                                         cdiff(p.z, q.z, per, B.L[2]));
                 if (d2 > hi2) continue;
-                pair_action<PASS>(d2, k, kj, id, __float_as_uint(q.w), lo2, b2, B.mode, my_safe, my_fof, a, cn);
+                pair_action<PASS>(d2, k, kj, id, __float_as_uint(q.w), lo2, b2, B.mode, my_safe, my_fof, a, cn, wb);
             }
         }
+        if (keep) vbuf_flush(wb, false, a);
     }
+    if (keep) vbuf_flush(wb, true, a);
     if (PASS == 1) {
         __syncwarp();
         flush_counts(cn, bk, a);
@@ -565,8 +613,13 @@ __global__ void __launch_bounds__(32 * DENSE_WARPS) k_pairs_dense(
     int64_t n, const BlockDev *__restrict__ bt, const int64_t *__restrict__ off, int nb, CellMaps M,
     const DenseChunk *__restrict__ chunks, int64_t n_chunks, unsigned long long *work, PairArgs a) {
     __shared__ float4 tile[DENSE_WARPS][32];
+    __shared__ unsigned long long vkey[PASS == 1 ? DENSE_WARPS : 1][PASS == 1 ? VBUF : 1];
+    __shared__ unsigned vcnt[DENSE_WARPS];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const WarpVBuf wb{vkey[PASS == 1 ? w : 0], vcnt + w};
+    const bool keep = PASS == 1 && a.V != nullptr;
+    if (keep && lane == 0) vcnt[w] = 0u;
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(work, 1ull);
@@ -611,13 +664,15 @@ __global__ void __launch_bounds__(32 * DENSE_WARPS) k_pairs_dense(
                                             cdiff(p.z, q.z, per, B.L[2]));
                     if (d2 > hi2) continue;
                     pair_action<PASS>(d2, ka, kj, id, __float_as_uint(q.w), lo2, b2, B.mode, my_safe, my_fof, a,
-                                      cn);
+                                      cn, wb);
                 }
                 __syncwarp();
+                if (keep) vbuf_flush(wb, false, a);
             }
         }
         if (PASS == 1) flush_counts(cn, bk, a);
     }
+    if (keep) vbuf_flush(wb, true, a);
 }
 
 // Occupancy and density maps of the grid, and the dense cells cut into chunks of at

@@ -947,7 +947,7 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
     constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;
     unsigned long long lfx = 0;       // this lane's share of the tight loss, fixed point (single block)
     unsigned viol = 0, nupd = 0, nev = 0;
-    // Work comes in two phases.  First the heavy rows, 32 per claim (one per lane): a row
+    // Work comes in two phases.  First the heavy rows, 32 per claim (one per lane, strided): a row
     // with an uncertain pair is taken by the warp (kind 1: the warp reads its pairs); a row
     // that only steps joins the warp's ring of candidates.  Then the light items (up to
     // ITEM_ROWS rows): each lane looks at its rows' flags and Adam state, all loaded
@@ -998,13 +998,16 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
             if (heavy_done && light_done) break;
             unsigned long long k = 0;
             if (!heavy_done) {
-                if (lane == 0) k = atomicAdd(&gs->work3, 32ull);
+                // claim c holds the heavy items c + j * stride (heavy rows are longest first,
+                // so every claim gets a like share of long and short rows)
+                const int64_t stride = (H.n_heavy + 31) / 32;
+                if (lane == 0) k = atomicAdd(&gs->work3, 1ull);
                 k = __shfl_sync(FULL, k, 0);
-                if ((int64_t)k >= H.n_heavy) {
+                if ((int64_t)k >= stride) {
                     heavy_done = true;
                     continue;
                 }
-                const int64_t hk = (int64_t)k + lane;
+                const int64_t hk = (int64_t)k + stride * lane;
                 bool f = false, steps = false;
                 hrow = 0u;
                 if (hk < H.n_heavy) {
