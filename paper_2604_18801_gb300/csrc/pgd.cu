@@ -44,7 +44,7 @@ inline int grid_for(int64_t n, int threads = 256) {
 
 constexpr int PGD_THREADS = 256;
 constexpr int WARPS = PGD_THREADS / 32;
-constexpr int PGD_BLOCKS_PER_SM = 4;   // resident CTAs of the persistent iteration grid
+constexpr int PGD_BLOCKS_PER_SM = 3;   // resident CTAs of the persistent iteration grid
 
 // Linking lengths of one problem: one, or up to MAX_THR enforced together (the union of
 // their active pairs, Sec. 1 and Sec. 5); a CSR entry then carries its pair's index.
@@ -108,16 +108,41 @@ struct PgdBlk {
     unsigned long long n_upd, n_eval;   // totals of the last two over the run
 };
 
+// Work items are claimed from NQ counters, each owning a contiguous slice of the item
+// space and each on a line of its own, so that claims do not queue on one address.
+constexpr int NQ = 16;
+struct alignas(128) QCounter {
+    unsigned long long v;
+    unsigned long long pad[15];
+};
+
 struct PgdGlobal {
     uint32_t ticket;
     int32_t all_stop;
-    unsigned long long work;        // next work item of the screen
     int32_t active;                 // blocks still iterating after the last launch
     int32_t pad;
     unsigned long long n_items;     // work items of the blocks still iterating (problem sets)
-    unsigned long long work2;       // next light item of the update
-    unsigned long long work3;       // next heavy row of the update
+    unsigned long long work3;       // next claim of heavy rows of the update
+    QCounter q1[NQ];                // the screen's items
+    QCounter q2[NQ];                // the update's light items
 };
+
+// The next item of [0, n) for a warp (called by one lane): a warp starts on slice
+// `slice` (its global warp index mod NQ) and moves on to the next slice when its own is
+// used up; n when every slice is used up.
+__device__ __forceinline__ int64_t claim_item(QCounter *q, int64_t n, int &slice, int &tried) {
+    const int64_t R = (n + NQ - 1) / NQ;
+    while (tried < NQ) {
+        const int64_t lo = (int64_t)slice * R, hi = min(n, lo + R);
+        if (lo < hi) {
+            const unsigned long long v = atomicAdd(&q[slice].v, 1ull);
+            if ((int64_t)v < hi - lo) return lo + (int64_t)v;
+        }
+        slice = slice + 1 == NQ ? 0 : slice + 1;
+        ++tried;
+    }
+    return n;
+}
 
 // Work of one block of a problem set: its heavy rows, items [h0, h0 + nh) of the heavy
 // list (longest first), then ceil(nrows / 32) light items over its rows [row0, row0 +
@@ -541,10 +566,12 @@ __device__ void decide_blocks(const PgdConsts *__restrict__ CB, int nb, PgdBlk *
     if (lane == 0) {
         gs->active = active;
         if (active == 0) gs->all_stop = 1;
-        gs->work = 0;
-        gs->work2 = 0;
         gs->work3 = 0;
         gs->ticket = 0;
+    }
+    if (lane < NQ) {
+        gs->q1[lane].v = 0;
+        gs->q2[lane].v = 0;
     }
     __threadfence();
 }
@@ -626,11 +653,12 @@ struct LightPlan {
     const uint32_t *col;             // partner | link << 31 (| threshold index << 29 with several)
     // The screen's stream: each pair once, from the row that comes first.  Group g (32
     // light rows) owns [gup[g], gup[g + 1]): its rows' edges to later partners, sorted by
-    // partner so that neighbouring lanes gather the same or nearby partners; scol is the
-    // CSR entry, saux the edge's place in the group's range of the edge array << 5 | the
-    // row's slot.
+    // partner so that neighbouring lanes gather the same or nearby partners; the groups of
+    // a work item are consecutive, so an item's stream is one range.  An entry is the CSR
+    // entry (x) and the edge's place relative to the item's first light edge << 7 | the row
+    // within the item (y), loaded together.
     const unsigned long long *gup;
-    const uint32_t *scol, *saux;
+    const uint2 *sst;
     // per edge to a later partner (by position in the edge array): the position of the
     // reverse edge in the partner's row
     const unsigned long long *erev;
@@ -658,9 +686,10 @@ struct PgdBufs {
 // double-float state, so it runs at high occupancy, and the update works on a compact list
 // with every lane busy.
 
-// Candidate list entry: row | CAND_UNC when the row has an uncertain pair.
-constexpr uint32_t CAND_UNC = 0x80000000u;
-constexpr int SCREEN_BLOCKS_PER_SM = 5;
+// Candidate entry: row | CAND_UNC when the row has an uncertain pair | CAND_HG when it is
+// a heavy row whose gradient a warp has already summed (kept in the heavy-gradient table).
+constexpr uint32_t CAND_UNC = 0x80000000u, CAND_HG = 0x40000000u;
+constexpr int SCREEN_BLOCKS_PER_SM = 4;
 constexpr int KERNELS_PER_ITER = 2;   // screen, update
 constexpr int QCAP = 128;   // uncertain pairs waiting for evaluation (a ring per warp; < 32 + 2 x 32)
 constexpr int EPL = 4;      // edges per lane per trip of the screen's walk
@@ -698,9 +727,11 @@ __device__ __forceinline__ bool screen_pair(const float4 qr, const float4 qk, ui
 // Whether a warp whose rows are at rounded positions q (one per lane that holds a row)
 // may skip the minimum image: every row lies in the periodic box's interior, where no
 // active pair wraps (so the screen's d2 is the same bit for bit).
+__device__ __forceinline__ bool interior(const PgdConsts &C, const float4 q) {
+    return q.x >= C.ilo[0] && q.x <= C.ihi[0] && q.y >= C.ilo[1] && q.y <= C.ihi[1] && q.z >= C.ilo[2] && q.z <= C.ihi[2];
+}
 __device__ __forceinline__ bool needs_image(const PgdConsts &C, bool row_lane, const float4 q) {
-    const bool in_ok = C.interior_ok != 0 && (!row_lane || (q.x >= C.ilo[0] && q.x <= C.ihi[0] && q.y >= C.ilo[1] &&
-                                                            q.y <= C.ihi[1] && q.z >= C.ilo[2] && q.z <= C.ihi[2]));
+    const bool in_ok = C.interior_ok != 0 && (!row_lane || interior(C, q));
     return C.periodic != 0 && !__all_sync(0xffffffffu, in_ok);
 }
 
@@ -783,12 +814,13 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;   // partner bits of a CSR entry
     const int64_t n_items = MULTI ? (int64_t)s_items : (ne + ITEM_ROWS - 1) / ITEM_ROWS + H.n_heavy;
-    unsigned long long nitm = 0;
-    if (lane == 0) nitm = atomicAdd(&gs->work, 1ull);
+    int qslice = (int)((blockIdx.x * WARPS + w) % NQ), qtried = 0;
+    long long nitm = 0;
+    if (lane == 0) nitm = claim_item(gs->q1, n_items, qslice, qtried);
     for (;;) {
         const int64_t item = (int64_t)__shfl_sync(FULL, nitm, 0);
         if (item >= n_items) break;
-        if (lane == 0) nitm = atomicAdd(&gs->work, 1ull);
+        if (lane == 0) nitm = claim_item(gs->q1, n_items, qslice, qtried);
         int b, cnt;
         int64_t r0, hk, g;
         bool heavy_warp;
@@ -800,19 +832,25 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
         const float4 *__restrict__ Qc = Bf.q(pa);
         const float slk = Cl.screen_link[0], sln_ = Cl.screen_non[0];
         // one stream [ebase, ebase + VT): a heavy row's edges to later partners (row rbase,
-        // position at sqg[0]), or a group's (rows rbase + slot, positions sqg[slot]); fbase +
-        // (aux >> 5) is a light edge's place in the edge array
-        auto walk = [&](auto image, unsigned long long ebase, uint32_t VT, unsigned long long fbase, int64_t rbase,
-                        const float4 *sqg) {
-            constexpr bool PP = decltype(image)::value;
-            const uint32_t *__restrict__ ecol = (heavy_warp ? LP.col : LP.scol) + ebase;
-            const uint32_t *__restrict__ eaux = LP.saux + ebase;
+        // position at sqg[0]), or a light item's (rows rbase + (aux & 127), positions
+        // sqg[aux & 127]); fbase + (aux >> 7) is a light edge's place in the edge array
+        auto walk = [&](auto image, auto heavy, unsigned long long ebase, uint32_t VT, unsigned long long fbase,
+                        int64_t rbase, const float4 *sqg) {
+            constexpr bool PP = decltype(image)::value, HV = decltype(heavy)::value;
+            const uint32_t *__restrict__ hcol = LP.col + ebase;   // heavy rows: the CSR entries
+            const uint2 *__restrict__ lst = LP.sst + ebase;       // light items: entry and aux
             uint32_t cvn[EPL], axn[EPL];
 #pragma unroll
             for (int j = 0; j < EPL; ++j) {
                 const uint32_t v = 32u * j + lane;
-                cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
-                axn[j] = (v < VT && !heavy_warp) ? __ldcs(eaux + v) : 0u;
+                if (HV) {
+                    cvn[j] = v < VT ? __ldcs(hcol + v) : 0u;
+                    axn[j] = 0u;
+                } else {
+                    const uint2 x = v < VT ? __ldcs(lst + v) : make_uint2(0u, 0u);
+                    cvn[j] = x.x;
+                    axn[j] = x.y;
+                }
             }
             for (uint32_t base = 0; base < VT; base += 32 * EPL) {
                 uint32_t cv[EPL], ax[EPL];
@@ -823,30 +861,36 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
                     cv[j] = cvn[j];
                     ax[j] = axn[j];
                     const uint32_t v = base + 32u * (EPL + j) + lane;
-                    cvn[j] = v < VT ? __ldcs(ecol + v) : 0u;
-                    axn[j] = (v < VT && !heavy_warp) ? __ldcs(eaux + v) : 0u;
+                    if (HV) {
+                        cvn[j] = v < VT ? __ldcs(hcol + v) : 0u;
+                    } else {
+                        const uint2 x = v < VT ? __ldcs(lst + v) : make_uint2(0u, 0u);
+                        cvn[j] = x.x;
+                        axn[j] = x.y;
+                    }
                 }
                 unsigned um = 0u;
 #pragma unroll
                 for (int j = 0; j < EPL; ++j)
-                    if (nd[j] && screen_pair<MT, PP>(sqg[ax[j] & 31u], Qc[cv[j] & PMASK], cv[j], L0, L1, L2, slk, sln_,
+                    if (nd[j] && screen_pair<MT, PP>(sqg[ax[j] & 127u], Qc[cv[j] & PMASK], cv[j], L0, L1, L2, slk, sln_,
                                                      Cl))
                         um |= 1u << j;
                 if (um) {
                     // the trip's uncertain pairs: every reverse-edge load first, then both
                     // directed edges' bits and both rows' flags
-                    unsigned long long f[EPL], r[EPL];
+                    auto fwd = [&](int j) -> unsigned long long {
+                        return HV ? ebase + base + 32u * j + lane : fbase + (ax[j] >> 7);
+                    };
+                    unsigned long long r[EPL];
 #pragma unroll
-                    for (int j = 0; j < EPL; ++j) {
-                        f[j] = heavy_warp ? ebase + base + 32u * j + lane : fbase + (ax[j] >> 5);
-                        r[j] = (um >> j) & 1u ? LP.erev[f[j]] : 0ull;
-                    }
+                    for (int j = 0; j < EPL; ++j) r[j] = (um >> j) & 1u ? LP.erev[fwd(j)] : 0ull;
 #pragma unroll
                     for (int j = 0; j < EPL; ++j)
                         if ((um >> j) & 1u) {
-                            atomicOr(ubits + (f[j] >> 5), 1u << (f[j] & 31));
+                            const unsigned long long f = fwd(j);
+                            atomicOr(ubits + (f >> 5), 1u << (f & 31));
                             atomicOr(ubits + (r[j] >> 5), 1u << (r[j] & 31));
-                            uflag[rbase + (ax[j] & 31u)] = 1;
+                            uflag[rbase + (ax[j] & 127u)] = 1;
                             uflag[cv[j] & PMASK] = 1;
                         }
                 }
@@ -857,27 +901,35 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
             const float4 qe = Qc[hv.row];
             if (lane == 0) sq[w][0] = qe;
             __syncwarp();
-            if (needs_image(Cl, true, qe)) walk(std::true_type{}, hv.start + hv.ulo, hv.len - hv.ulo, 0ull, hv.row, sq[w]);
-            else walk(std::false_type{}, hv.start + hv.ulo, hv.len - hv.ulo, 0ull, hv.row, sq[w]);
+            if (needs_image(Cl, true, qe))
+                walk(std::true_type{}, std::true_type{}, hv.start + hv.ulo, hv.len - hv.ulo, 0ull, hv.row, sq[w]);
+            else
+                walk(std::false_type{}, std::true_type{}, hv.start + hv.ulo, hv.len - hv.ulo, 0ull, hv.row, sq[w]);
         } else {
-            // every group's stream range, edge-array base and row positions, loaded together
+            // the item's stream range (its groups' ranges are consecutive), first light edge
+            // and row positions, loaded together; one walk over the whole range
             const int ngr = (cnt + 31) >> 5;
-            unsigned long long gu = 0, fb = 0;
-            if (lane <= ngr) gu = LP.gup[g + lane];
-            if (lane < ngr) fb = LP.ptr[r0 + 32 * lane];
+            unsigned long long eb = 0, ee = 0, fb = 0;
+            if (lane == 0) {
+                eb = LP.gup[g];
+                ee = LP.gup[g + ngr];
+                fb = LP.ptr[r0];
+            }
+            eb = __shfl_sync(FULL, eb, 0);
+            ee = __shfl_sync(FULL, ee, 0);
+            fb = __shfl_sync(FULL, fb, 0);
+            bool inner = true;   // every row of the item lies in the periodic box's interior
 #pragma unroll
             for (int j = 0; j < ITEM_GROUPS; ++j)
-                if (32 * j + lane < cnt) sq[w][32 * j + lane] = Qc[r0 + 32 * j + lane];
+                if (32 * j + lane < cnt) {
+                    const float4 q = Qc[r0 + 32 * j + lane];
+                    sq[w][32 * j + lane] = q;
+                    inner = inner && interior(Cl, q);
+                }
             __syncwarp();
-            for (int j = 0; j < ngr; ++j) {
-                const unsigned long long eb = __shfl_sync(FULL, gu, j);
-                const uint32_t vt = (uint32_t)(__shfl_sync(FULL, gu, j + 1) - eb);
-                const unsigned long long fbj = __shfl_sync(FULL, fb, j);
-                const bool have = 32 * j + lane < cnt;
-                const float4 qe = have ? sq[w][32 * j + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-                if (needs_image(Cl, have, qe)) walk(std::true_type{}, eb, vt, fbj, r0 + 32 * j, sq[w] + 32 * j);
-                else walk(std::false_type{}, eb, vt, fbj, r0 + 32 * j, sq[w] + 32 * j);
-            }
+            const bool pp = Cl.periodic != 0 && !__all_sync(FULL, Cl.interior_ok != 0 && inner);
+            if (pp) walk(std::true_type{}, std::false_type{}, eb, (uint32_t)(ee - eb), fb, r0, sq[w]);
+            else walk(std::false_type{}, std::false_type{}, eb, (uint32_t)(ee - eb), fb, r0, sq[w]);
         }
         __syncwarp();
     }
@@ -916,7 +968,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <bool MULTI, bool MT>
 __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
     int64_t ne, const float4 *__restrict__ PE, PgdBufs Bf, HeavyPlan H, LightPlan LP,
-    const uint32_t *__restrict__ hmap, const uint32_t *__restrict__ rb, uint32_t *__restrict__ ubits,
+    const uint32_t *__restrict__ hmap, float4 *__restrict__ HG, const uint32_t *__restrict__ rb,
+    uint32_t *__restrict__ ubits,
     uint8_t *__restrict__ uflag, const PgdConsts *__restrict__ CB, int nb, PgdBlk *blk, PgdGlobal *gs,
     const WorkTab wt, double *__restrict__ hist_loss, unsigned long long *__restrict__ hist_viol) {
     __shared__ int s_stop, s_t, s_reset, s_nact;
@@ -955,6 +1008,7 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
     // the ring holds 32 (or nothing is left to claim), 32 of them are processed as a chunk
     // (kind 2: each lane one row).  The flags are cleared as read.
     const int64_t n_light_items = MULTI ? (int64_t)s_items : (ne + ITEM_ROWS - 1) / ITEM_ROWS;
+    int qslice = (int)((blockIdx.x * WARPS + w) % NQ), qtried = 0;
     bool heavy_done = false, light_done = false;
     int nc = 0, ch = 0;          // candidates in the ring and its head (warp-uniform)
     unsigned hmask = 0u;         // lanes whose heavy row (hrow) has an uncertain pair, not yet taken
@@ -1026,7 +1080,7 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
                 nc += __popc(sm);
                 continue;
             }
-            if (lane == 0) k = atomicAdd(&gs->work2, 1ull);
+            if (lane == 0) k = (unsigned long long)claim_item(gs->q2, n_light_items, qslice, qtried);
             k = __shfl_sync(FULL, k, 0);
             if ((int64_t)k >= n_light_items) {
                 light_done = true;
@@ -1070,8 +1124,9 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
             lnum = (icnt + 31) >> 5;
         }
         if (kind == 0) break;
-        const uint32_t e = ce & ~CAND_UNC;
+        const uint32_t e = ce & ~(CAND_UNC | CAND_HG);
         const bool unc = have && (ce & CAND_UNC);
+        const bool hg = have && (ce & CAND_HG);
         const int b = MULTI ? (have ? (int)rb[e] : 0) : 0;
         const int tb = MULTI ? blk[b].t : s_t;
         const int pa = tb & 1;
@@ -1080,10 +1135,19 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
         bool rv = false;                   // the lane's row has a violated pair
         uint8_t av = 0;
         if (have) av = Bf.act[e];
-        // the rows' Adam state travels to shared memory while the uncertain pairs are evaluated
-        const bool due = have && !is_last(C, tb);
+        if (hg) {   // a heavy row's gradient, summed by the warp that read its pairs
+            const uint32_t hk = hmap[e];
+            const float4 gh = HG[2 * hk], gl = HG[2 * hk + 1];
+            g[0] = df_make(gh.x, gl.x);
+            g[1] = df_make(gh.y, gl.y);
+            g[2] = df_make(gh.z, gl.z);
+            rv = gh.w != 0.f;
+        }
+        // the rows' Adam state travels to shared memory while the uncertain pairs are evaluated;
+        // a heavy row read by the whole warp (kind 1) takes its Adam step later, in a chunk
+        const bool due = have && kind == 2 && !is_last(C, tb);
         const bool was = (av & ACT_ON) != 0;
-        if (due && (was || unc)) {
+        if (due && (was || unc || hg)) {
             cp_async16(&T.st[0][lane], Bf.dh(pa) + e);
             cp_async16(&T.st[1][lane], Bf.dl(pa) + e);
             cp_async16(&T.st[2][lane], PE + e);
@@ -1262,6 +1326,17 @@ __global__ void __launch_bounds__(PGD_THREADS, PGD_BLOCKS_PER_SM) k_pgd_update(
             }
         }
         while (qn > 0) batch();
+        if (kind == 1) {
+            // the heavy row's gradient goes to the table; the row joins the ring for Adam
+            if (lane == 0) {
+                const uint32_t hk = hmap[e];
+                HG[2 * hk] = make_float4(g[0].hi, g[1].hi, g[2].hi, rv ? 1.f : 0.f);
+                HG[2 * hk + 1] = make_float4(g[0].lo, g[1].lo, g[2].lo, 0.f);
+                T.cb[(ch + nc) & 63] = e | CAND_HG;
+            }
+            __syncwarp();
+            ++nc;
+        }
 
         // Adam on every candidate row that is due (its block is not at its last check)
         cp_async_wait_all();
@@ -1384,12 +1459,14 @@ __global__ void k_cols(const unsigned long long *__restrict__ keys, int64_t m, i
 template <uint32_t PMASK>
 __global__ void k_groups(int64_t ne, const uint32_t *__restrict__ rb, const int64_t *__restrict__ roff,
                          const uint32_t *__restrict__ gbase, const unsigned long long *__restrict__ lptr,
-                         const uint32_t *__restrict__ col, uint2 *__restrict__ grp,
+                         const uint32_t *__restrict__ col, uint4 *__restrict__ grp,
                          unsigned long long *__restrict__ nup) {
     GRID_STRIDE(e, ne) {
         const int64_t r0 = roff ? roff[rb[e]] : 0, r1 = roff ? roff[rb[e] + 1] : ne;
         const int64_t g = (roff ? (int64_t)gbase[rb[e]] : 0) + (e - r0) / 32;
-        if (((e - r0) & 31) == 0) grp[g] = make_uint2((uint32_t)e, (uint32_t)min((int64_t)32, r1 - e));
+        if (((e - r0) & 31) == 0)   // first row, rows, first row of the group's work item
+            grp[g] = make_uint4((uint32_t)e, (uint32_t)min((int64_t)32, r1 - e),
+                                (uint32_t)(r0 + (e - r0) / ITEM_ROWS * ITEM_ROWS), 0u);
         unsigned long long lo = lptr[e], hi = lptr[e + 1];
         const unsigned long long end = hi;
         while (lo < hi) {   // first partner after row e
@@ -1406,17 +1483,18 @@ __global__ void k_groups(int64_t ne, const uint32_t *__restrict__ rb, const int6
 // most 32 x HEAVY light edges, so a place fits 13 bits).
 constexpr int GSORT_CAP = 32 * HEAVY;
 template <uint32_t PMASK>
-__global__ void __launch_bounds__(256) k_group_sort(const uint2 *__restrict__ grp, const unsigned long long *__restrict__ lptr,
+__global__ void __launch_bounds__(256) k_group_sort(const uint4 *__restrict__ grp, const unsigned long long *__restrict__ lptr,
                                                     const uint32_t *__restrict__ col, const uint8_t *__restrict__ slot,
                                                     const unsigned long long *__restrict__ gup,
-                                                    uint32_t *__restrict__ scol, uint32_t *__restrict__ saux) {
+                                                    uint2 *__restrict__ sst) {
     extern __shared__ unsigned long long sk[];
     __shared__ int s_n;
     const int64_t g = blockIdx.x;
     const unsigned long long u0 = gup[g], nu = gup[g + 1] - u0;
     if (nu == 0) return;
-    const uint2 gr = grp[g];
+    const uint4 gr = grp[g];
     const unsigned long long a = lptr[gr.x], len = lptr[gr.x + gr.y] - a;
+    const uint32_t off0 = (uint32_t)(a - lptr[gr.z]), row0 = gr.x - gr.z;   // within the work item
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < (int)len; i += blockDim.x) {
@@ -1446,8 +1524,7 @@ __global__ void __launch_bounds__(256) k_group_sort(const uint2 *__restrict__ gr
         }
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const uint32_t i = (uint32_t)(sk[j] & 8191ull);
-        scol[u0 + j] = col[a + i];
-        saux[u0 + j] = (i << 5) | slot[a + i];
+        sst[u0 + j] = make_uint2(col[a + i], ((off0 + i) << 7) | (row0 + slot[a + i]));
     }
 }
 
@@ -1613,9 +1690,11 @@ struct PgdSolver::Impl {
     DBuf<PgdBlk> blk;
     DBuf<PgdGlobal> gs;
     DBuf<uint32_t> rb, ecol, hmap;
+    DBuf<float4> hgrad;   // per heavy row: gradient hi (w: has a violated pair), lo
     DBuf<unsigned long long> lptr;
     DBuf<HeavyItem> hitem;
-    DBuf<uint32_t> scol, saux, ubits;
+    DBuf<uint32_t> ubits;
+    DBuf<uint2> sst;
     DBuf<unsigned long long> gup, erev;
     DBuf<uint8_t> uflag;
     LightPlan LP{};
@@ -1646,21 +1725,21 @@ struct PgdSolver::Impl {
             k_pgd_screen<false, true><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, ubits.p,
                                                                  uflag.p);
             PC_CHECK_LAUNCH();
-            k_pgd_update<false, true><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, rb.p, ubits.p,
+            k_pgd_update<false, true><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, hgrad.p, rb.p, ubits.p,
                                                                    uflag.p, CB.p, nb, blk.p, gs.p, wt, hist_loss,
                                                                    hist_viol);
         } else if (nb == 1) {
             k_pgd_screen<false, false><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, ubits.p,
                                                                   uflag.p);
             PC_CHECK_LAUNCH();
-            k_pgd_update<false, false><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, rb.p, ubits.p,
+            k_pgd_update<false, false><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, hgrad.p, rb.p, ubits.p,
                                                                     uflag.p, CB.p, nb, blk.p, gs.p, wt, hist_loss,
                                                                     hist_viol);
         } else {
             k_pgd_screen<true, false><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, ubits.p,
                                                                  uflag.p);
             PC_CHECK_LAUNCH();
-            k_pgd_update<true, false><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, rb.p, ubits.p,
+            k_pgd_update<true, false><<<nblk, PGD_THREADS, 0, s>>>(ne, PE.p, Bf, HP, LP, hmap.p, hgrad.p, rb.p, ubits.p,
                                                                    uflag.p, CB.p, nb, blk.p, gs.p, wt, nullptr,
                                                                    nullptr);
         }
@@ -1734,6 +1813,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     const int64_t ne = *(uint32_t *)read_back(hs, tot.p, sizeof(uint32_t), s);
     I.ne = ne;
     if (I.mt && ne >= ((int64_t)1 << 29)) fail(PC_EINVAL, "several linking lengths: at most 2^29 editable particles");
+    if (ne >= ((int64_t)1 << 30)) fail(PC_EINVAL, "at most 2^30 editable particles");   // candidate entries carry 2 flag bits
     const int tb = I.mt ? 2 : 0;   // threshold-index bits of the directed keys
     ThrB2 tb2;
     for (int k = 0; k < MAX_THR; ++k) tb2.b2[k] = I.mt && k < (int)thr->c.size() ? thr->c[k].b2 : 0.f;
@@ -1838,7 +1918,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     const int64_t ng = hgb[nb];
     DBuf<uint32_t> gbase(nb + 1, s);
     PC_CUDA(cudaMemcpyAsync(gbase.p, hgb.data(), (nb + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
-    DBuf<uint2> grp(std::max<int64_t>(1, ng), s);
+    DBuf<uint4> grp(std::max<int64_t>(1, ng), s);
     DBuf<unsigned long long> nup(std::max<int64_t>(1, ng), s);
     I.gup.alloc(ng + 1, s);
     PC_CUDA(cudaMemsetAsync(nup.p, 0, std::max<int64_t>(1, ng) * sizeof(unsigned long long), s));
@@ -1851,18 +1931,17 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     PC_CHECK_LAUNCH();
     scan_exclusive_u64((const uint64_t *)nup.p, (uint64_t *)I.gup.p, ng, (uint64_t *)(I.gup.p + ng), s);
     const unsigned long long n_up = *(const unsigned long long *)read_back(hs, I.gup.p + ng, 8, s);
-    I.scol.alloc(std::max<unsigned long long>(1, n_up), s);
-    I.saux.alloc(std::max<unsigned long long>(1, n_up), s);
+    I.sst.alloc(std::max<unsigned long long>(1, n_up), s);
     if (n_up > 0) {
         const int smem = (int)(GSORT_CAP * sizeof(unsigned long long));
         if (I.mt) {
             PC_CUDA(cudaFuncSetAttribute(k_group_sort<0x1fffffffu>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             k_group_sort<0x1fffffffu><<<(unsigned)ng, 256, smem, s>>>(grp.p, I.lptr.p, I.ecol.p, eslot.p, I.gup.p,
-                                                                      I.scol.p, I.saux.p);
+                                                                      I.sst.p);
         } else {
             PC_CUDA(cudaFuncSetAttribute(k_group_sort<0x7fffffffu>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
             k_group_sort<0x7fffffffu><<<(unsigned)ng, 256, smem, s>>>(grp.p, I.lptr.p, I.ecol.p, eslot.p, I.gup.p,
-                                                                      I.scol.p, I.saux.p);
+                                                                      I.sst.p);
         }
         PC_CHECK_LAUNCH();
     }
@@ -1877,6 +1956,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     PC_CUDA(cudaMemsetAsync(h_per_blk.p, 0, nb * sizeof(uint32_t), s));
     I.hitem.alloc(std::max<int64_t>(1, I.n_heavy), s);
     I.hmap.alloc(ne, s);
+    I.hgrad.alloc(2 * std::max<int64_t>(1, I.n_heavy), s);
     if (I.n_heavy > 0) {
         DBuf<unsigned long long> hkey(I.n_heavy, s);
         DBuf<uint32_t> hrow(I.n_heavy, s);
@@ -1893,7 +1973,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
         PC_CHECK_LAUNCH();
     }
     scan_exclusive_u32(h_per_blk.p, h_off.p, nb, h_off.p + nb, s);
-    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.gup.p, I.scol.p, I.saux.p, I.erev.p};
+    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.gup.p, I.sst.p, I.erev.p};
     if (nb > 1) {
         // work table of the blocks still iterating (all of them before the first launch)
         I.bw.alloc(nb, s);
