@@ -92,12 +92,14 @@ typedef struct {
                               searched by one warp per 32 of their particles, the others by
                               one thread per particle (0 = no such cells).  Only speed
                               depends on it.                                              */
-    int32_t reserved_;     /* 0 */
+    int32_t screen_chunk;  /* tuning: the PGD screen of a single problem walks its light work
+                              items in chunks of at most this many pairs (0 = 1024).  Only
+                              speed depends on it.                                        */
 } pc_params;
 
 /* Fills defaults: m=16, t_max=10000, alpha_rel=0.2, beta=(0.9,0.999), eps_rel=2e-6,
  * loss_tol=0, replay_iters=-1, cell_cap_log2=0, stall_patience=0 (Algorithm 1 as printed), cell_factor=0,
- * dense_cell=0,
+ * dense_cell=0, screen_chunk=0,
  * unit box, non-periodic, mode VP. */
 void pc_params_default(pc_params *p);
 

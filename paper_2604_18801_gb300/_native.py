@@ -29,7 +29,7 @@ class Params(C.Structure):
                 ("alpha_rel", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps_rel", C.c_double),
                 ("loss_tol", C.c_double), ("replay_iters", C.c_int32), ("cell_cap_log2", C.c_int32),
                 ("stall_patience", C.c_int32), ("cell_factor", C.c_int32), ("dense_cell", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("screen_chunk", C.c_int32)]
 
 
 class SelectStats(C.Structure):

@@ -60,7 +60,8 @@ void check_params(const pc_params *p, int64_t n, bool need_pgd) {
         if (p->m_bits < 2 || p->m_bits > 32) fail(PC_EINVAL, "m_bits must be in [2, 32]");
         if (p->t_max < 0) fail(PC_EINVAL, "t_max must be >= 0");
         if (!(p->alpha_rel > 0.0) || !(p->beta1 >= 0.0 && p->beta1 < 1.0) || !(p->beta2 >= 0.0 && p->beta2 < 1.0) ||
-            !(p->eps_rel > 0.0) || !(p->loss_tol >= 0.0) || p->stall_patience < 0 || p->dense_cell < 0)
+            !(p->eps_rel > 0.0) || !(p->loss_tol >= 0.0) || p->stall_patience < 0 || p->dense_cell < 0 ||
+            p->screen_chunk < 0)
             fail(PC_EINVAL, "bad Adam parameters");
     }
 }
@@ -499,7 +500,7 @@ void pc_params_default(pc_params *p) {
     p->stall_patience = 0;   // Algorithm 1 as printed: no stall rule
     p->cell_factor = 0;
     p->dense_cell = 0;
-    p->reserved_ = 0;
+    p->screen_chunk = 0;
 }
 
 const char *pc_last_error(void) { return g_err.c_str(); }

@@ -662,6 +662,20 @@ struct LightPlan {
     // per edge to a later partner (by position in the edge array): the position of the
     // reverse edge in the partner's row
     const unsigned long long *erev;
+    // A single problem's screen takes its light items in chunks of at most screen_chunk
+    // stream entries (n_chunks of them, items in order; an item with no entries has none),
+    // so that items in dense regions, whose streams are many times a warp's mean share,
+    // do not leave a tail of one long walk.  Problem sets take whole items (chunk null).
+    const struct ScreenChunk *chunk;
+    int64_t n_chunks;
+};
+
+// One chunk of a light item's screen stream: entries [eb, eb + len) of the item `item`
+// (rows [ITEM_ROWS * item, ...)); the entries keep their places relative to the item.
+constexpr uint32_t SCREEN_CHUNK = 1024;   // default chunk length (pc_params.screen_chunk = 0)
+struct ScreenChunk {
+    unsigned long long eb;
+    uint32_t len, item;
 };
 
 struct PgdBufs {
@@ -813,7 +827,7 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     constexpr uint32_t PMASK = MT ? 0x1fffffffu : 0x7fffffffu;   // partner bits of a CSR entry
-    const int64_t n_items = MULTI ? (int64_t)s_items : (ne + ITEM_ROWS - 1) / ITEM_ROWS + H.n_heavy;
+    const int64_t n_items = MULTI ? (int64_t)s_items : H.n_heavy + LP.n_chunks;
     int qslice = (int)((blockIdx.x * WARPS + w) % NQ), qtried = 0;
     long long nitm = 0;
     if (lane == 0) nitm = claim_item(gs->q1, n_items, qslice, qtried);
@@ -824,7 +838,22 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
         int b, cnt;
         int64_t r0, hk, g;
         bool heavy_warp;
-        map_item<MULTI>(item, ne, H, wt, s_nact, b, heavy_warp, r0, cnt, hk, g);
+        ScreenChunk chk{0ull, 0u, 0u};   // a single problem's light chunk
+        if (MULTI) {
+            map_item<MULTI>(item, ne, H, wt, s_nact, b, heavy_warp, r0, cnt, hk, g);
+        } else {
+            b = 0;
+            g = 0;
+            heavy_warp = item < H.n_heavy;
+            hk = item;
+            r0 = 0;
+            cnt = 0;
+            if (!heavy_warp) {
+                chk = LP.chunk[item - H.n_heavy];
+                r0 = (int64_t)ITEM_ROWS * chk.item;
+                cnt = (int)min((int64_t)ITEM_ROWS, ne - r0);
+            }
+        }
         const int tb = MULTI ? blk[b].t : s_t;
         const int pa = tb & 1;
         const PgdConsts &Cl = CB[b];
@@ -911,8 +940,13 @@ __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_scree
             const int ngr = (cnt + 31) >> 5;
             unsigned long long eb = 0, ee = 0, fb = 0;
             if (lane == 0) {
-                eb = LP.gup[g];
-                ee = LP.gup[g + ngr];
+                if (MULTI) {
+                    eb = LP.gup[g];
+                    ee = LP.gup[g + ngr];
+                } else {
+                    eb = chk.eb;
+                    ee = chk.eb + chk.len;
+                }
                 fb = LP.ptr[r0];
             }
             eb = __shfl_sync(FULL, eb, 0);
@@ -1563,6 +1597,33 @@ __global__ void k_heavy_items(const uint32_t *__restrict__ hrow, int64_t nh, con
     }
 }
 
+// The screen's light chunks of a single problem: item j covers groups [ITEM_GROUPS j,
+// min(ng, ITEM_GROUPS (j + 1))) and so the stream range between their offsets.
+__global__ void k_chunk_count(const unsigned long long *__restrict__ gup, int64_t ng, int64_t nli, uint32_t clen,
+                              uint32_t *__restrict__ cnt) {
+    GRID_STRIDE(j, nli) {
+        const int64_t g = ITEM_GROUPS * j, g1 = min(ng, g + ITEM_GROUPS);
+        const unsigned long long vt = gup[g1] - gup[g];
+        cnt[j] = (uint32_t)((vt + clen - 1) / clen);
+    }
+}
+
+__global__ void k_chunk_fill(const unsigned long long *__restrict__ gup, int64_t ng, int64_t nli, uint32_t clen,
+                             const uint32_t *__restrict__ coff, ScreenChunk *__restrict__ ch) {
+    GRID_STRIDE(j, nli) {
+        const int64_t g = ITEM_GROUPS * j, g1 = min(ng, g + ITEM_GROUPS);
+        const unsigned long long e1 = gup[g1];
+        uint32_t c = coff[j];
+        for (unsigned long long e = gup[g]; e < e1; e += clen, ++c) {
+            ScreenChunk x;
+            x.eb = e;
+            x.len = (uint32_t)min((unsigned long long)clen, e1 - e);
+            x.item = (uint32_t)j;
+            ch[c] = x;
+        }
+    }
+}
+
 __global__ void k_copy_recon(const float *__restrict__ recon, float *__restrict__ out, int64_t m) {
     GRID_STRIDE(i, m) out[i] = recon[i];
 }
@@ -1696,6 +1757,8 @@ struct PgdSolver::Impl {
     DBuf<uint32_t> ubits;
     DBuf<uint2> sst;
     DBuf<unsigned long long> gup, erev;
+    DBuf<ScreenChunk> chunk;
+    int64_t n_chunks = 0;
     DBuf<uint8_t> uflag;
     LightPlan LP{};
     DBuf<float4> PE, Dh0, Dl0, Dh1, Dl1, Mh, Ml, Vh, Vl, Q0, Q1;
@@ -1946,6 +2009,19 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
         PC_CHECK_LAUNCH();
     }
     eslot.release();
+    if (nb == 1) {
+        // a single problem's screen chunks (screen_chunk entries at most)
+        const uint32_t clen = S.prm[0].screen_chunk > 0 ? (uint32_t)S.prm[0].screen_chunk : SCREEN_CHUNK;
+        const int64_t nli = cdiv(ne, ITEM_ROWS);
+        DBuf<uint32_t> ccnt(std::max<int64_t>(1, nli), s), coff(nli + 1, s);
+        k_chunk_count<<<grid_for(nli), 256, 0, s>>>(I.gup.p, ng, nli, clen, ccnt.p);
+        PC_CHECK_LAUNCH();
+        scan_exclusive_u32(ccnt.p, coff.p, nli, coff.p + nli, s);
+        I.n_chunks = *(const uint32_t *)read_back(hs, coff.p + nli, sizeof(uint32_t), s);
+        I.chunk.alloc(std::max<int64_t>(1, I.n_chunks), s);
+        k_chunk_fill<<<grid_for(nli), 256, 0, s>>>(I.gup.p, ng, nli, clen, coff.p, I.chunk.p);
+        PC_CHECK_LAUNCH();
+    }
     // the screen's bit mask over the edge array and the rows' flags (both cleared as read)
     I.ubits.alloc(std::max<int64_t>(1, cdiv(m, 32)), s);
     PC_CUDA(cudaMemsetAsync(I.ubits.p, 0, std::max<int64_t>(1, cdiv(m, 32)) * sizeof(uint32_t), s));
@@ -1973,7 +2049,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
         PC_CHECK_LAUNCH();
     }
     scan_exclusive_u32(h_per_blk.p, h_off.p, nb, h_off.p + nb, s);
-    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.gup.p, I.sst.p, I.erev.p};
+    I.LP = LightPlan{I.lptr.p, I.ecol.p, I.gup.p, I.sst.p, I.erev.p, nb == 1 ? I.chunk.p : nullptr, I.n_chunks};
     if (nb > 1) {
         // work table of the blocks still iterating (all of them before the first launch)
         I.bw.alloc(nb, s);
@@ -1988,7 +2064,7 @@ PgdSolver::PgdSolver(const Binned &B, const BlockSet &S, const std::vector<Const
     PC_CUDA(cudaStreamSynchronize(s));   // roff and the plan temporaries are released on return
     I.HP.n_heavy = I.n_heavy;
     I.HP.item = I.hitem.p;
-    I.n_items = cdiv(ne, ITEM_ROWS) + nb + I.n_heavy;
+    I.n_items = nb == 1 ? I.n_chunks + I.n_heavy : cdiv(ne, ITEM_ROWS) + nb + I.n_heavy;
     I.nblk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(ne, 32 * WARPS), (int64_t)num_sms() * PGD_BLOCKS_PER_SM));
 }
 

@@ -99,6 +99,8 @@ def test_tuning_knobs_change_speed_only(cuda, mode):
     # The pair search's knobs (cell factor, dense-cell threshold) change the binning, but the
     # correction numbers its editable particles in a canonical order, so the corrected
     # coordinates are the same bits for every setting; pc_autotune returns a valid setting.
+    # The PGD screen's chunk length changes only how its walk is split among warps (its
+    # outputs are set unions), so it too leaves every bit and counter unchanged.
     import torch
     import paper_2604_18801_gb300 as pc
     w = synth.hacc_box(eps_over_b=0.1, mode="VP", seed=62, n=120000)
@@ -107,10 +109,11 @@ def test_tuning_knobs_change_speed_only(cuda, mode):
     assert cf in (2, 4, 8, 16, 32) and dc in (0, 32, 128, 512)
     assert all(v > 0 for t in times.values() for v in t.values())
     ref = None
-    for f, d in ((2, 0), (8, 32), (32, 12), (cf, dc)):
-        c, st, code = pc.correct(o, r, w.params(mode=mode, cell_factor=f, dense_cell=d))
+    for f, d, k in ((2, 0, 0), (8, 32, 0), (32, 12, 0), (cf, dc, 0), (8, 0, 100), (8, 0, 1 << 30)):
+        c, st, code = pc.correct(o, r, w.params(mode=mode, cell_factor=f, dense_cell=d, screen_chunk=k))
         assert code == 0
         if ref is None:
-            ref = (c, st["iters"])
+            ref = (c, st["iters"], st["pair_evals"], st["row_updates"])
         else:
-            assert st["iters"] == ref[1] and torch.equal(c, ref[0]), (f, d)
+            assert (st["iters"], st["pair_evals"], st["row_updates"]) == ref[1:], (f, d, k)
+            assert torch.equal(c, ref[0]), (f, d, k)

@@ -47,7 +47,8 @@ def workload(name):
 @pytest.mark.parametrize("name,mode", [("hacc256_eps0.5", "VP"), ("hacc256_eps0.5", "HF"),
                                        ("hacc256_eps1.0", "HF"), ("md4m_eps0.3", "HF"),
                                        ("fluid8m_eps0.1", "SC"), ("fluid8m_eps0.5", "VP")])
-def test_configuration_membership_exact(cuda, name, mode):
+def test_configuration_membership_exact(cuda, name, mode, record_property):
+    import json
     import torch
     import paper_2604_18801_gb300 as pc
     w, lab0, n0 = workload(name)
@@ -58,6 +59,9 @@ def test_configuration_membership_exact(cuda, name, mode):
     ai, aj, al = [x.cpu().numpy() for x in cons.pairs()]
     corr, st, code = pc.correct(o, r, kw, constraints=cons)
     cons.close()
+    # the columns of the paper's Table 2 for this run (one call, not a benchmark timing)
+    record_property("stats", json.dumps({k: st[k] for k in (
+        "iters", "n_vulnerable", "n_active", "n_editable", "viol0", "resets", "ms_setup", "ms_pgd") if k in st}))
     assert code == 0 and st["converged"] == 1 and st["viol_final"] == 0
     assert len(ai) == st["n_active"]
     dec = pc.apply_edits(r, pc.encode_edits(r, corr, kw))
