@@ -703,10 +703,10 @@ struct PgdBufs {
 // Candidate entry: row | CAND_UNC when the row has an uncertain pair | CAND_HG when it is
 // a heavy row whose gradient a warp has already summed (kept in the heavy-gradient table).
 constexpr uint32_t CAND_UNC = 0x80000000u, CAND_HG = 0x40000000u;
-constexpr int SCREEN_BLOCKS_PER_SM = 4;
+constexpr int SCREEN_BLOCKS_PER_SM = 6;
 constexpr int KERNELS_PER_ITER = 2;   // screen, update
 constexpr int QCAP = 128;   // uncertain pairs waiting for evaluation (a ring per warp; < 32 + 2 x 32)
-constexpr int EPL = 4;      // edges per lane per trip of the screen's walk
+constexpr int EPL = 2;      // edges per lane per trip of the screen's walk
 
 // Edge range of one row: light rows own [ptr[e], ptr[e + 1]) of the light part, heavy rows
 // the range of their heavy item.
@@ -801,13 +801,16 @@ __device__ __forceinline__ void map_item(int64_t item, int64_t ne, const HeavyPl
 }
 
 // The screen.  Work items are heavy rows (more than HEAVY partners; longest first, so the
-// longest walks start early) and groups of 32 consecutive light rows, handed out from a
-// counter (the next item is claimed one item ahead).  Every pair is screened once, from
-// the row that comes first: a warp walks its item's stream of edges to later partners
-// 128 at a time (4 per lane, strided by 32 so that loads stay coalesced; the next trip's
-// entries load while this trip's partner positions are gathered).  A pair the float32
-// screen cannot certify sets the bits of both its directed edges in the bit mask of the
-// edge array and the flags of both rows; the list kernel and the update read them.
+// longest walks start early) and light items of ITEM_ROWS consecutive rows (for a single
+// problem, chunks of at most screen_chunk pairs of them), handed out from counters (the
+// next item is claimed one item ahead).  Every pair is screened once, from the row that
+// comes first: a warp walks its item's stream of edges to later partners 32 * EPL at a
+// time (EPL per lane, strided by 32 so that loads stay coalesced; the next trip's entries
+// load while this trip's partner positions are gathered).  The walk is bound by the
+// latency of the partner gathers, so the kernel runs small trips at high occupancy
+// (SCREEN_BLOCKS_PER_SM CTAs per SM) rather than long trips at low occupancy.  A pair the
+// float32 screen cannot certify sets the bits of both its directed edges in the bit mask
+// of the edge array and the flags of both rows; the update reads them.
 template <bool MULTI, bool MT>
 __global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_screen(
     int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP, const PgdConsts *__restrict__ CB,
