@@ -703,7 +703,8 @@ struct PgdBufs {
 // Candidate entry: row | CAND_UNC when the row has an uncertain pair | CAND_HG when it is
 // a heavy row whose gradient a warp has already summed (kept in the heavy-gradient table).
 constexpr uint32_t CAND_UNC = 0x80000000u, CAND_HG = 0x40000000u;
-constexpr int SCREEN_BLOCKS_PER_SM = 6;
+constexpr int SCREEN_BLOCKS_PER_SM = 6;        // a single problem
+constexpr int SCREEN_BLOCKS_PER_SM_MULTI = 4;  // a problem set (its item map needs more registers)
 constexpr int KERNELS_PER_ITER = 2;   // screen, update
 constexpr int QCAP = 128;   // uncertain pairs waiting for evaluation (a ring per warp; < 32 + 2 x 32)
 constexpr int EPL = 2;      // edges per lane per trip of the screen's walk
@@ -812,7 +813,7 @@ __device__ __forceinline__ void map_item(int64_t item, int64_t ne, const HeavyPl
 // float32 screen cannot certify sets the bits of both its directed edges in the bit mask
 // of the edge array and the flags of both rows; the update reads them.
 template <bool MULTI, bool MT>
-__global__ void __launch_bounds__(PGD_THREADS, SCREEN_BLOCKS_PER_SM) k_pgd_screen(
+__global__ void __launch_bounds__(PGD_THREADS, MULTI ? SCREEN_BLOCKS_PER_SM_MULTI : SCREEN_BLOCKS_PER_SM) k_pgd_screen(
     int64_t ne, PgdBufs Bf, HeavyPlan H, LightPlan LP, const PgdConsts *__restrict__ CB,
     const PgdBlk *__restrict__ blk, PgdGlobal *gs, const WorkTab wt, uint32_t *__restrict__ ubits,
     uint8_t *__restrict__ uflag) {
@@ -1785,8 +1786,9 @@ struct PgdSolver::Impl {
     bool mt = false;                         // several linking lengths (single block)
 
     void launch_iter() {
-        const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, WARPS),
-                                                                  (int64_t)num_sms() * SCREEN_BLOCKS_PER_SM));
+        const int g1 = (int)std::max<int64_t>(
+            1, std::min<int64_t>(cdiv(n_items, WARPS),
+                                 (int64_t)num_sms() * (nb > 1 ? SCREEN_BLOCKS_PER_SM_MULTI : SCREEN_BLOCKS_PER_SM)));
         if (mt) {
             k_pgd_screen<false, true><<<g1, PGD_THREADS, 0, s>>>(ne, Bf, HP, LP, CB.p, blk.p, gs.p, wt, ubits.p,
                                                                  uflag.p);
