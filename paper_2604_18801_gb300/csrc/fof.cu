@@ -255,13 +255,32 @@ __global__ void k_permute(const float *__restrict__ orig, const uint32_t *__rest
     }
 }
 
-// cell_start[c] = first sorted position with key >= c, for c in [0, ncells].
+// cell_start[c] = first sorted position with key >= c, for c in [0, ncells].  A warp takes
+// the 32 sorted positions k0 .. k0 + 31 (position n stands for key ncells) and writes the
+// cells (key[k0 - 1], key[k0 + 31]] 32 consecutive cells at a time: cell c gets k0 plus
+// the number of the warp's keys below c (a search over the lanes' keys), so the stores
+// stay coalesced however unevenly the particles fill the cells.
 __global__ void k_cell_bounds(const uint32_t *__restrict__ keys, int64_t n, int64_t ncells,
                               uint32_t *__restrict__ cell_start) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t prev = k == 0 ? -1 : (int64_t)keys[k - 1];
-        const int64_t cur = k == n ? ncells : (int64_t)keys[k];
-        for (int64_t c = prev + 1; c <= cur; ++c) cell_start[c] = (uint32_t)k;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (n + 1 + 31) / 32;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wk < nwarps; wk += wstride) {
+        const int64_t k0 = wk * 32, k = k0 + lane;
+        const int64_t cur = k < n ? (int64_t)keys[k] : ncells;   // non-decreasing over the lanes
+        const int64_t prev = k0 == 0 ? -1 : (int64_t)keys[k0 - 1];
+        const int64_t last = __shfl_sync(FULL, cur, 31);
+        for (int64_t c0 = prev + 1; c0 <= last; c0 += 32) {
+            const int64_t c = c0 + lane;
+            int below = 0;   // lanes whose key is below c (at most 31: the key of lane 31 is >= c)
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int64_t v = __shfl_sync(FULL, cur, below + step - 1);
+                if (v < c) below += step;
+            }
+            if (c <= last) cell_start[c] = (uint32_t)(k0 + below);
+        }
     }
 }
 
