@@ -192,6 +192,16 @@ def sub_cube(w, side: float):
     return sub
 
 
+L2_BYTES = 129 * 2 ** 20   # GB300 L2
+
+
+def l2_note(n: int) -> str:
+    """How the timed steps relate to L2: no flush between steps, so say whether the inputs
+    alone exceed it."""
+    mb = n * 12 / 2 ** 20
+    return "no L2 flush; inputs 2 x %.0f MB %s than the 129 MB L2" % (mb, "larger" if 2 * n * 12 > L2_BYTES else "smaller")
+
+
 def cpu_model() -> str:
     """The host CPU's model name (Linux /proc/cpuinfo), or the platform's processor string."""
     try:
@@ -777,7 +787,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload, "n_particles": w.n, "b": w.b, "xi": w.xi, "modes": modes, "base": a.base,
                    "cell_factor": cell_factor, "dense_cell": dense_cell,
-                   "parallelism": f"replicas{world}", "l2": "inputs (2 x 201 MB) and PGD state larger than L2"},
+                   "parallelism": f"replicas{world}", "l2": l2_note(w.n)},
         "membership_exact": exact,
         "per_mode": {m: {k: last[m][k] for k in PER_MODE_KEYS} for m in modes},
         "roofline": roofline,
